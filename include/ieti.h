@@ -1,0 +1,173 @@
+/*
+ * ieti.h -- C ABI of the GB300 tree-cotree IETI-DP eddy-current solver.
+ *
+ * Method: Mally, Vazquez, Schoeps, "Tree-Cotree-Based IETI-DP for Eddy Current
+ * Problems in Time-Domain".  The library advances the implicit-Euler scheme of
+ * Eq. (11),  [W, dt B^T; dt B, 0][a; m] = [M a^l + dt j^{l+1}; 0],  W = M + dt K,
+ * for the A*-formulation (Eq. (5)) discretised with spline edge elements on a
+ * structured grid of conforming patches (Sec. 2.2), gauged by the hierarchical
+ * tree-cotree splitting of Sec. 3 (e / p / r DOFs), and solves each step by the
+ * dual-primal method of Sec. 3 (two Schur complements, PCG on the interface
+ * problem with a Dirichlet preconditioner, Sec. 4) on one CUDA device.
+ *
+ * Conventions (all entry points):
+ *  - Return 0 on success or a negative IETI_ERR_* code; ieti_last_error() gives
+ *    a message.  Nothing is thrown across the ABI; no call aborts the process.
+ *  - Input arrays are owned by the caller and copied during the call.  Output
+ *    buffers are allocated by the caller.
+ *  - "host or device" arguments: IETI_MEM_HOST means a host pointer (pageable or
+ *    pinned), IETI_MEM_DEVICE a pointer into memory of the context's device.
+ *  - Device work runs on options.cuda_stream (0 = legacy default stream).  A call
+ *    returns after its device work has completed.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Global DOF numbering (the control-mesh lattice of all patches, Sec. 2.2/3):
+ *  slab a in direction d has n_el[d][a] elements and degree[d][a]; its lattice
+ *  offset is off_d(a) = sum_{b<a} (n_el[d][b] + degree[d][b] - 1); N_d is the total
+ *  number of lattice points in direction d.  Edge ids: direction-0 edges first,
+ *  id = I + (N0-1)*(J + N1*K); then direction 1 from E0 = (N0-1)*N1*N2,
+ *  id = E0 + I + N0*(J + (N1-1)*K); then direction 2 from E0 + E1 with
+ *  E1 = N0*(N1-1)*N2, id = E0 + E1 + I + N0*(J + N1*K).  Vectors of length
+ *  ieti_num_dofs() use this numbering; eliminated DOFs (Dirichlet and gauge) hold 0.
+ */
+#ifndef IETI_H
+#define IETI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IETI_OK 0
+#define IETI_ERR_INVALID_ARG -1     /* bad sizes, pointers, knot vectors, options */
+#define IETI_ERR_NONCONFORMING -2   /* knot vectors / degrees that do not match on a shared face */
+#define IETI_ERR_NOT_SPD -3         /* a local or coarse block is not positive definite (patch id in message) */
+#define IETI_ERR_CG_NOT_CONVERGED -4 /* PCG hit cg_max_it (or outer refinement max_sweeps) */
+#define IETI_ERR_CUDA -5            /* a CUDA runtime error (message has the text) */
+#define IETI_ERR_OOM -6             /* device or host allocation failed */
+#define IETI_ERR_NO_DEVICE -7       /* compute requested on a host-only context */
+#define IETI_ERR_TOO_LARGE -8       /* size beyond a documented fixed maximum */
+
+#define IETI_MEM_HOST 0
+#define IETI_MEM_DEVICE 1
+
+/* Precision of the factor-derived operators (Sec. 3 Schur complements). */
+#define IETI_PREC_FP64 0   /* everything FP64 */
+#define IETI_PREC_MIXED 1  /* FP32 local operators, FP64 CG / coarse / residuals, outer FP64 refinement */
+
+/* Dirichlet preconditioner variants (Sec. 4 uses it "without scaling"; Sec. 5 asks for scaling). */
+#define IETI_PRECOND_NONE 0
+#define IETI_PRECOND_DIRICHLET 1       /* unscaled: B_D = B (the paper's experiments) */
+#define IETI_PRECOND_DIRICHLET_MULT 2  /* multiplicity scaling delta = 1/|N_x| */
+#define IETI_PRECOND_DIRICHLET_STIFF 3 /* stiffness scaling with the local diagonal of W */
+
+/* Problem: unit cube split into a structured P0 x P1 x P2 grid of patches, patch
+ * s = a + P0*(b + P1*c) (Sec. 2.2, conforming spline spaces on each patch). */
+typedef struct {
+  int32_t n_patches[3];         /* P0, P1, P2 >= 1 */
+  const int32_t *n_el[3];       /* [d][slab]: elements per slab, >= 1 */
+  const int32_t *degree[3];     /* [d][slab]: H^1 degree p >= 1 (edge space: p-1 along the edge) */
+  const double *knots[3];       /* [d]: concatenated open knot vectors on [0,1] of each slab,
+                                   n_el + 2p + 1 values each, p+1 repeated ends, simple interior knots */
+  const double *ctrl_pts;       /* concatenated geometry control nets, per patch (n2,n1,n0,3), i fastest,
+                                   n_d = n_el + p; the map uses the degree-p splines of the same knots */
+  const double *sigma_el;       /* per element, patch-major, (e2,e1,e0) e0 fastest; >= 0 */
+  const double *nu_el;          /* per element, same layout; > 0 */
+  double dt;                    /* implicit-Euler step (Eq. (11)), > 0 */
+  int32_t primal_mode;          /* 0: tree DOFs on Gamma + cotree wirebasket edges of Omega_I (Sec. 3) */
+} ieti_problem;
+
+typedef struct {
+  int32_t device;        /* CUDA device ordinal; -1 = host-only context (setup queries, no compute) */
+  int32_t precision;     /* IETI_PREC_* */
+  int32_t precond;       /* IETI_PRECOND_* */
+  double cg_tol;         /* PCG stop: ||r_k|| <= cg_tol * ||d||, lambda_0 = 0 */
+  int32_t cg_max_it;
+  double outer_tol;      /* refinement stop: ||f - W a|| <= outer_tol * ||f|| (FP64 residual) */
+  int32_t max_sweeps;    /* refinement sweeps per step (FP64 mode: 1 suffices) */
+  int32_t use_graph;     /* capture the PCG iteration in a CUDA graph */
+  int32_t host_threads;  /* threads for the host setup (0 = all cores) */
+  void *cuda_stream;     /* cudaStream_t (0 = legacy default stream) */
+} ieti_options;
+
+/* Coil source through its potential T = T_z(r) chi(|z - zc| < hz) e_z (J = curl T):
+ * T_z = J0 (r_out - r) on r_in < r < r_out, J0 (r_out - r_in) for r <= r_in, 0 beyond;
+ * r = distance to the axis x = xc, y = yc.  j_k = <T, curl w_k> (Sec. 2.2 load vector). */
+typedef struct {
+  double J0, r_in, r_out, xc, yc, zc, hz;
+} ieti_coil;
+
+typedef struct {
+  int32_t cg_its;        /* PCG iterations of the step (all refinement sweeps) */
+  int32_t sweeps;        /* refinement sweeps taken */
+  double rel_res;        /* last PCG relative residual */
+  double outer_res;      /* ||f - W a|| / ||f|| after the step (FP64) */
+  double t_step_ms;      /* device time of the step (CUDA events) */
+} ieti_stats;
+
+typedef struct {
+  int64_t n_dofs;        /* global lattice edges (ieti_num_dofs) */
+  int64_t n_free;        /* r + p edges */
+  int64_t n_lambda;      /* multipliers (one per pair of copies of a shared r-DOF) */
+  int64_t n_coarse;      /* primal unknowns */
+  int64_t sum_ni, sum_nb, sum_np;  /* interior / interface / primal copies over patches */
+  int64_t max_n;         /* largest local block n_i + n_b + n_p */
+  int64_t bytes_iter;    /* algorithmic bytes one PCG iteration streams (operators + coarse) */
+  int64_t bytes_device;  /* device memory held by the context */
+  double t_setup_host_ms, t_setup_device_ms;
+  int64_t kernel_launches_setup;
+} ieti_info;
+
+typedef struct ieti_ctx ieti_ctx;
+
+/* Sec. 2.2-3: assemble K, M per patch, build the tree-cotree gauge and e/p/r
+ * classes, the multipliers B and primal map N, then (device >= 0) factor all local
+ * blocks and the coarse Schur complement on the GPU.  *out is set on success.
+ * Errors: INVALID_ARG, NONCONFORMING, NOT_SPD, CUDA, OOM. */
+int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ctx **out);
+
+/* Number of global DOFs (lattice edges, the length of all global vectors). */
+int64_t ieti_num_dofs(const ieti_ctx *ctx);
+
+int ieti_get_info(const ieti_ctx *ctx, ieti_info *info);
+
+/* Load vector j (Sec. 2.2, (j_i)_k = <J, w_k>) of a coil source, via j_k = <T, curl w_k>,
+ * assembled over patches into the global numbering.  Host computation; j_out is a host
+ * buffer of ieti_num_dofs() doubles.  Works on host-only contexts. */
+int ieti_load_vector(const ieti_ctx *ctx, const ieti_coil *coil, double *j_out);
+
+/* Host-side classification (works on host-only contexts): per global DOF,
+ * cls[g] = 0 (e), 1 (p), 2 (r) and tree[g] = 1 for tree edges (Sec. 3).  Either
+ * pointer may be NULL. */
+int ieti_dof_classes(const ieti_ctx *ctx, int8_t *cls, int8_t *tree);
+
+/* Patch matrices of Sec. 2.2 in the patch-local edge numbering (component-major,
+ * i fastest): which = 0 for K_s (nu curl-curl), 1 for M_s (sigma mass).  Two-call
+ * protocol: with ptr/col/val NULL only *nnz is written; otherwise ptr has n_s+1
+ * entries and col/val *nnz entries (host buffers).  Works on host-only contexts. */
+int ieti_patch_csr(const ieti_ctx *ctx, int32_t patch, int32_t which, int32_t *n_rows, int64_t *nnz,
+                   int32_t *ptr, int32_t *col, double *val);
+
+/* One implicit-Euler step (Eq. (11)): a^{l+1} from the stored a^l and the load
+ * vector j^{l+1} (global numbering, ieti_num_dofs() doubles, in host or device
+ * memory per j_mem).  stats may be NULL.  Errors: NO_DEVICE, CG_NOT_CONVERGED
+ * (the state is still advanced with the last iterate), CUDA. */
+int ieti_step(ieti_ctx *ctx, const double *j_next, int32_t j_mem, ieti_stats *stats);
+
+/* Copy the current a^l (global numbering, e entries 0) to a_out (len doubles). */
+int ieti_solution(const ieti_ctx *ctx, double *a_out, int64_t len, int32_t out_mem);
+
+/* Replace the state a^l (checkpoint resume); e entries are ignored. */
+int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem);
+
+const char *ieti_last_error(const ieti_ctx *ctx);
+/* Message of the last failed ieti_setup (no context exists then). */
+const char *ieti_setup_error(void);
+
+void ieti_destroy(ieti_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IETI_H */

@@ -1,0 +1,147 @@
+// C ABI of the solver (declared in include/ieti.h).  Marshals arguments, keeps
+// the error text, and never lets an exception cross the boundary.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "device.h"
+#include "host_setup.h"
+
+struct ieti_ctx {
+  ieti::HostSetup hs;
+  ieti_options opt{};
+  ieti::DeviceState *dev = nullptr;
+  std::string err;
+};
+
+static thread_local std::string g_setup_err;
+
+static int check_options(const ieti_options *o, std::string &err) {
+  if (!o) { err = "options is NULL"; return IETI_ERR_INVALID_ARG; }
+  if (o->precision != IETI_PREC_FP64 && o->precision != IETI_PREC_MIXED) { err = "bad precision"; return IETI_ERR_INVALID_ARG; }
+  if (o->precond < IETI_PRECOND_NONE || o->precond > IETI_PRECOND_DIRICHLET_STIFF) { err = "bad precond"; return IETI_ERR_INVALID_ARG; }
+  if (!(o->cg_tol > 0.0) || !(o->cg_tol < 1.0)) { err = "cg_tol must be in (0, 1)"; return IETI_ERR_INVALID_ARG; }
+  if (o->cg_max_it < 1) { err = "cg_max_it must be >= 1"; return IETI_ERR_INVALID_ARG; }
+  if (o->max_sweeps < 1 || o->max_sweeps > 1000) { err = "max_sweeps must be in [1, 1000]"; return IETI_ERR_INVALID_ARG; }
+  if (!(o->outer_tol >= 0.0)) { err = "outer_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->device < -1) { err = "device must be >= -1"; return IETI_ERR_INVALID_ARG; }
+  return IETI_OK;
+}
+
+extern "C" {
+
+int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ctx **out) {
+  g_setup_err.clear();
+  if (!out) { g_setup_err = "out is NULL"; return IETI_ERR_INVALID_ARG; }
+  *out = nullptr;
+  int rc = check_options(options, g_setup_err);
+  if (rc) return rc;
+  ieti_ctx *ctx = nullptr;
+  try {
+    ctx = new ieti_ctx();
+    ctx->opt = *options;
+    rc = ctx->hs.build(problem, options->host_threads, g_setup_err);
+    if (rc == IETI_OK && options->device >= 0) rc = ieti::device_setup(ctx->hs, ctx->opt, &ctx->dev, g_setup_err);
+  } catch (const std::bad_alloc &) {
+    g_setup_err = "host allocation failed";
+    rc = IETI_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_setup_err = std::string("setup failed: ") + e.what();
+    rc = IETI_ERR_INVALID_ARG;
+  }
+  if (rc) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return IETI_OK;
+}
+
+const char *ieti_setup_error(void) { return g_setup_err.c_str(); }
+
+int64_t ieti_num_dofs(const ieti_ctx *ctx) { return ctx ? ctx->hs.n_edges : -1; }
+
+int ieti_get_info(const ieti_ctx *ctx, ieti_info *info) {
+  if (!ctx || !info) return IETI_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  const ieti::HostSetup &hs = ctx->hs;
+  info->n_dofs = hs.n_edges;
+  info->n_free = (int64_t)hs.free_edges.size();
+  info->n_lambda = (int64_t)hs.lam.size();
+  info->n_coarse = hs.n_coarse;
+  for (const auto &pt : hs.patches) {
+    info->sum_ni += pt.ni;
+    info->sum_nb += pt.nb;
+    info->sum_np += pt.np;
+    info->max_n = std::max<int64_t>(info->max_n, pt.ni + pt.nb + pt.np);
+  }
+  info->t_setup_host_ms = hs.t_ms;
+  if (ctx->dev) ieti::device_info(ctx->dev, info);
+  return IETI_OK;
+}
+
+int ieti_load_vector(const ieti_ctx *ctx, const ieti_coil *coil, double *j_out) {
+  if (!ctx || !coil || !j_out) return IETI_ERR_INVALID_ARG;
+  try {
+    ctx->hs.coil_load(*coil, j_out);
+  } catch (...) {
+    return IETI_ERR_OOM;
+  }
+  return IETI_OK;
+}
+
+int ieti_dof_classes(const ieti_ctx *ctx, int8_t *cls, int8_t *tree) {
+  if (!ctx) return IETI_ERR_INVALID_ARG;
+  for (int64_t g = 0; g < ctx->hs.n_edges; ++g) {
+    if (cls) cls[g] = ctx->hs.cls[g];
+    if (tree) tree[g] = (int8_t)ctx->hs.tree[g];
+  }
+  return IETI_OK;
+}
+
+int ieti_patch_csr(const ieti_ctx *ctx, int32_t patch, int32_t which, int32_t *n_rows, int64_t *nnz, int32_t *ptr,
+                   int32_t *col, double *val) {
+  if (!ctx || patch < 0 || patch >= ctx->hs.n_patches() || (which != 0 && which != 1)) return IETI_ERR_INVALID_ARG;
+  const ieti::Patch &pt = ctx->hs.patches[patch];
+  const ieti::Csr &A = which == 0 ? pt.K : pt.M;
+  if (n_rows) *n_rows = A.n;
+  if (nnz) *nnz = (int64_t)A.col.size();
+  if (ptr) std::memcpy(ptr, A.ptr.data(), A.ptr.size() * sizeof(int32_t));
+  if (col) std::memcpy(col, A.col.data(), A.col.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, A.val.data(), A.val.size() * sizeof(double));
+  return IETI_OK;
+}
+
+int ieti_step(ieti_ctx *ctx, const double *j_next, int32_t j_mem, ieti_stats *stats) {
+  if (!ctx || !j_next) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) { ctx->err = "host-only context: no device"; return IETI_ERR_NO_DEVICE; }
+  try {
+    return ieti::device_step(ctx->dev, j_next, j_mem, stats, ctx->err);
+  } catch (...) {
+    ctx->err = "step failed on the host";
+    return IETI_ERR_OOM;
+  }
+}
+
+int ieti_solution(const ieti_ctx *ctx, double *a_out, int64_t len, int32_t out_mem) {
+  if (!ctx || !a_out || len != ctx->hs.n_edges) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) return IETI_ERR_NO_DEVICE;
+  return ieti::device_solution(ctx->dev, a_out, len, out_mem, const_cast<ieti_ctx *>(ctx)->err);
+}
+
+int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem) {
+  if (!ctx || !a || len != ctx->hs.n_edges) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) return IETI_ERR_NO_DEVICE;
+  return ieti::device_set_state(ctx->dev, a, len, a_mem, ctx->err);
+}
+
+const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+void ieti_destroy(ieti_ctx *ctx) {
+  if (!ctx) return;
+  ieti::device_destroy(ctx->dev);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,1417 @@
+// Device part of the tree-cotree IETI-DP solver (Sec. 3 of the paper).
+//
+// Setup (once per problem): every patch's kept block W_s = M_s + dt K_s, ordered
+// [interior i | interface b | primal p], is expanded densely and AUGMENTED by an
+// identity-coupled copy b' of its interface block:
+//
+//        [ W_ii  W_ib  W_ip  0 ]
+//        [ W_bi  W_bb  W_bp  I ]     eliminating the i and b pivots (a partial
+//        [ W_pi  W_pb  W_pp  0 ]     Cholesky) leaves in the trailing block
+//        [ 0     I     0     0 ]     [[C_s, -Psi^T], [-Psi, -F_s]]
+//
+// with S_bb = W_bb - W_bi W_ii^{-1} W_ib (the Dirichlet-preconditioner block),
+// F_s = S_bb^{-1} (the local dual operator B_s W_rr^{-1} B_s^T restricted to the
+// interface), Psi_s = S_bb^{-1} S_bp (the primal basis on the interface) and
+// C_s = S_pp - S_pb Psi_s (the local coarse Schur complement), i.e. the two
+// sequential Schur complements of Sec. 3 computed explicitly by one batched dense
+// kernel family.  The coarse S_c = sum_s A_s^T C_s A_s is inverted by the same
+// trick ([[S_c, I], [I, 0]]).
+//
+// Step (Eq. (11)): f = M a^l + dt j; interior condensation with L_ii; PCG on the
+// dual problem F lambda = d where every application of F and of the Dirichlet
+// preconditioner is a batched dense GEMV with F_s, Psi_s, S_bb and S_c^{-1}
+// (no triangular solve inside the CG iteration); recovery; interior
+// back-substitution.  In mixed precision the local operators are FP32 and every
+// step is wrapped in FP64 defect correction on the assembled system.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device.h"
+
+namespace ieti {
+
+#define CK(x)                                                                   \
+  do {                                                                          \
+    cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                    \
+      err = std::string(#x) + " failed: " + cudaGetErrorString(e_);             \
+      return IETI_ERR_CUDA;                                                     \
+    }                                                                           \
+  } while (0)
+
+constexpr int NB = 32;         // panel width of the partial Cholesky
+constexpr int GEMV_BLOCK = 256;
+constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs for the deterministic reductions
+
+template <class T> struct Acc { using type = T; };
+
+// =============================================================================
+// Setup kernels
+// =============================================================================
+
+// Expand the kept CSR rows into the augmented dense blocks (zeroed beforehand).
+__global__ void k_csr_to_dense(int64_t n_rows, const int32_t *row_patch, const int32_t *row_local,
+                               const int64_t *rowptr, const int32_t *col_abs, const double *val,
+                               const int64_t *kofs, const int64_t *doff, const int32_t *nn, double *D) {
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n_rows) return;
+  int s = row_patch[w];
+  int r = row_local[w];
+  int64_t ld = nn[s];
+  double *A = D + doff[s];
+  for (int64_t t = rowptr[w] + lane; t < rowptr[w + 1]; t += 32) {
+    int c = (int)(col_abs[t] - kofs[s]);
+    A[r * ld + c] = val[t];
+  }
+}
+
+// identity coupling of the augmented rows: D[n + k][ni + k] = D[ni + k][n + k] = 1
+__global__ void k_augment(int n_patch, const int32_t *ni, const int32_t *nb, const int32_t *n,
+                          const int32_t *nn, const int64_t *doff, double *D) {
+  int s = blockIdx.y;
+  if (s >= n_patch) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb[s]) return;
+  int64_t ld = nn[s];
+  double *A = D + doff[s];
+  int64_t r = n[s] + k, c = ni[s] + k;
+  A[r * ld + c] = 1.0;
+  A[c * ld + r] = 1.0;
+}
+
+template <class T>
+__global__ void k_potrf_diag(T *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
+                             const int32_t *kend, int panel, int32_t *status) {
+  int s = blockIdx.x;
+  int j0 = kbeg[s] + panel * NB;
+  int ke = kend[s];
+  if (j0 >= ke) return;
+  int jb = min(NB, ke - j0);
+  int64_t ld = ldv[s];
+  T *A = base + off[s];
+  __shared__ double S[NB][NB + 1];
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    int r = t / jb, c = t % jb;
+    S[r][c] = (c <= r) ? (double)A[(j0 + r) * ld + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < jb; ++k) {
+    if (threadIdx.x == 0) {
+      double d = S[k][k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (status[s] == 0) status[s] = 1 + j0 + k;
+        d = 1.0;  // keep the arithmetic finite; the host reports NOT_SPD
+      }
+      S[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    double piv = S[k][k];
+    for (int i = k + 1 + threadIdx.x; i < jb; i += blockDim.x) S[i][k] /= piv;
+    __syncthreads();
+    int m = jb - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) S[i][j] -= S[i][k] * S[j][k];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    int r = t / jb, c = t % jb;
+    if (c <= r) A[(j0 + r) * ld + j0 + c] = (T)S[r][c];
+  }
+}
+
+// rows below the diagonal block: L_r = A_r L_jj^{-T} (one thread per row)
+template <class T>
+__global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
+                             const int32_t *kend, const int32_t *nact, int panel) {
+  using A_t = typename Acc<T>::type;
+  int s = blockIdx.y;
+  int j0 = kbeg[s] + panel * NB;
+  int ke = kend[s];
+  if (j0 >= ke) return;
+  int jb = min(NB, ke - j0);
+  int64_t ld = ldv[s];
+  T *A = base + off[s];
+  __shared__ A_t L[NB][NB + 1];
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    int i = t / NB, c = t % NB;
+    L[i][c] = (i < jb && c <= i) ? (A_t)A[(j0 + i) * ld + j0 + c] : (A_t)(i == c ? 1 : 0);
+  }
+  __syncthreads();
+  int r = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nact[s]) return;
+  T *row = A + r * ld + j0;
+  A_t x[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    A_t v = (k < jb) ? (A_t)row[k] : (A_t)0;
+#pragma unroll
+    for (int m = 0; m < k; ++m) v -= x[m] * L[k][m];
+    x[k] = v / L[k][k];
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+    if (k < jb) row[k] = (T)x[k];
+}
+
+// trailing lower update A[r][c] -= sum_k L[r][k] L[c][k] on 64x64 tiles
+template <class T>
+__global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off, const int32_t *ldv,
+                                                     const int32_t *kbeg, const int32_t *kend,
+                                                     const int32_t *nact, int panel) {
+  using A_t = typename Acc<T>::type;
+  int s = blockIdx.y;
+  int j0 = kbeg[s] + panel * NB;
+  int ke = kend[s];
+  if (j0 >= ke) return;
+  int jb = min(NB, ke - j0);
+  int t0 = j0 + jb;
+  int na = nact[s];
+  int m = na - t0;
+  if (m <= 0) return;
+  int T64 = (m + 63) / 64;
+  int t = blockIdx.x;
+  if (t >= T64 * (T64 + 1) / 2) return;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  int tj = t - ti * (ti + 1) / 2;
+  int R0 = t0 + ti * 64, C0 = t0 + tj * 64;
+  int64_t ld = ldv[s];
+  T *A = base + off[s];
+  __shared__ A_t As[NB][64 + 1], Bs[NB][64 + 1];
+  for (int idx = threadIdx.x; idx < 64 * NB; idx += 256) {
+    int r = idx / NB, k = idx % NB;
+    A_t a = 0, b = 0;
+    if (k < jb) {
+      if (R0 + r < na) a = (A_t)A[(R0 + r) * ld + j0 + k];
+      if (C0 + r < na) b = (A_t)A[(C0 + r) * ld + j0 + k];
+    }
+    As[k][r] = a;
+    Bs[k][r] = b;
+  }
+  __syncthreads();
+  int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  A_t acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k = 0; k < jb; ++k) {
+    A_t a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = As[k][tr + 16 * i];
+      b[i] = Bs[k][tc + 16 * i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = R0 + tr + 16 * i, c = C0 + tc + 16 * j;
+      if (r < na && c <= r) A[r * ld + c] = (T)((A_t)A[r * ld + c] - acc[i][j]);
+    }
+}
+
+// P_s = S_bb (after the interior pivots), symmetrised from the lower triangle
+template <class T>
+__global__ void k_extract_P(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+                            const int32_t *nb, const int64_t *poff, T *P) {
+  int s = blockIdx.y;
+  int m = nb[s];
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  int r = (int)(idx / m), c = (int)(idx % m);
+  int64_t ld = nn[s];
+  const double *A = D + doff[s];
+  int rr = ni[s] + max(r, c), cc = ni[s] + min(r, c);
+  P[poff[s] + idx] = (T)A[rr * ld + cc];
+}
+
+// H_s = [F_s; Psi_s^T] ((nb+np) x nb), Psi_s (nb x np), LY_s = first ni columns (n x ni)
+template <class T>
+__global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+                              const int32_t *nb, const int32_t *np, const int64_t *hoff, const int64_t *qoff,
+                              T *H, T *Q) {
+  int s = blockIdx.y;
+  int B = nb[s], Pn = np[s], I = ni[s];
+  int n = I + B + Pn;
+  int64_t ld = nn[s];
+  const double *A = D + doff[s];
+  int64_t total = (int64_t)(B + Pn) * B;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(idx / B), c = (int)(idx % B);
+    double v;
+    if (r < B) {  // F = -(trailing b'b')
+      int hi = max(r, c), lo = min(r, c);
+      v = -A[(int64_t)(n + hi) * ld + n + lo];
+    } else {      // Psi^T[r-B][c] = Psi[c][r-B] = -A[n + c][I + B + (r - B)]
+      v = -A[(int64_t)(n + c) * ld + I + B + (r - B)];
+      Q[qoff[s] + (int64_t)c * Pn + (r - B)] = (T)v;
+    }
+    H[hoff[s] + idx] = (T)v;
+  }
+}
+
+template <class T>
+__global__ void k_extract_LY(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+                             const int32_t *nb, const int32_t *np, const int64_t *lyoff, T *LY) {
+  int s = blockIdx.y;
+  int I = ni[s];
+  int n = I + nb[s] + np[s];
+  int64_t ld = nn[s];
+  const double *A = D + doff[s];
+  int64_t total = (int64_t)n * I;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(idx / I), c = (int)(idx % I);
+    LY[lyoff[s] + idx] = (c <= r) ? (T)A[(int64_t)r * ld + c] : (T)0;
+  }
+}
+
+// coarse: Sc_aug[A[k]][A[l]] += C_s[k][l] (one launch per patch, in patch order)
+__global__ void k_coarse_add(const double *D, int64_t doff, int nn, int ni, int nb, int np, const int32_t *A,
+                             double *Sc, int64_t ldc) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)np * np) return;
+  int k = (int)(idx / np), l = (int)(idx % np);
+  int base = ni + nb;
+  int hi = max(k, l), lo = min(k, l);
+  double v = D[doff + (int64_t)(base + hi) * nn + base + lo];
+  Sc[(int64_t)A[k] * ldc + A[l]] += v;
+}
+
+__global__ void k_coarse_identity(int nc, double *Sc, int64_t ldc) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nc) return;
+  Sc[(int64_t)(nc + r) * ldc + r] = 1.0;
+  Sc[(int64_t)r * ldc + nc + r] = 1.0;
+}
+
+__global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nc * nc) return;
+  int r = (int)(idx / nc), c = (int)(idx % nc);
+  int hi = max(r, c), lo = min(r, c);
+  Sinv[idx] = -Sc[(int64_t)(nc + hi) * ldc + nc + lo];
+}
+
+// =============================================================================
+// Step kernels
+// =============================================================================
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y[yidx] = alpha * A_row . x + beta * y0[yidx]    (warp per row)
+template <class T>
+__global__ void k_gemv_rows(int64_t n_rows, const int64_t *aoff, const int64_t *xoff, const int64_t *yidx,
+                            const int32_t *ncol, const T *A, const double *x, double *y, const double *y0,
+                            double alpha, double beta) {
+  using A_t = typename Acc<T>::type;
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (; w < n_rows; w += nw) {
+    const T *a = A + aoff[w];
+    const double *xv = x + xoff[w];
+    int nc = ncol[w];
+    A_t acc = 0;
+    for (int c = lane; c < nc; c += 32) acc += (A_t)a[c] * (A_t)xv[c];
+    double sum = warp_sum((double)acc);
+    if (lane == 0) {
+      int64_t yi = yidx[w];
+      double v = alpha * sum;
+      if (y0) v += beta * y0[yi];
+      y[yi] = v;
+    }
+  }
+}
+
+// out[c] = in[c] - sum_{r} LY[ni + r][c] * x[r]  for c < ni  (x = kept [b|p] part)
+template <class T>
+__global__ void k_gemvT_Y(const int32_t *ni, const int32_t *nb, const int32_t *np, const int64_t *lyoff,
+                          const int64_t *kofs, const T *LY, double *v) {
+  using A_t = typename Acc<T>::type;
+  int s = blockIdx.y;
+  int I = ni[s];
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= I) return;
+  int R = nb[s] + np[s];
+  const T *Y = LY + lyoff[s] + (int64_t)I * I;
+  double *kv = v + kofs[s];
+  A_t acc = 0;
+  for (int r = 0; r < R; ++r) acc += (A_t)Y[(int64_t)r * I + c] * (A_t)kv[I + r];
+  kv[c] -= (double)acc;
+}
+
+// forward (L z = v) or backward (L^T x = v) substitution on the interior part of
+// each patch's kept vector, one CTA per patch, vector staged in shared memory.
+template <class T>
+__global__ void k_trsv(const int32_t *ni, const int64_t *lyoff, const int64_t *kofs, const T *LY, double *v,
+                       int backward) {
+  using A_t = typename Acc<T>::type;
+  extern __shared__ double z[];
+  int s = blockIdx.x;
+  int n = ni[s];
+  if (n == 0) return;
+  const T *L = LY + lyoff[s];
+  double *x = v + kofs[s];
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) z[i] = x[i];
+  __syncthreads();
+  if (!backward) {
+    for (int R = 0; R < n; R += 32) {
+      int rb = min(32, n - R);
+      for (int rr = warp; rr < rb; rr += nwarp) {
+        const T *row = L + (int64_t)(R + rr) * n;
+        A_t acc = 0;
+        for (int c = lane; c < R; c += 32) acc += (A_t)row[c] * (A_t)z[c];
+        double sum = warp_sum((double)acc);
+        if (lane == 0) z[R + rr] -= sum;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double xr = (lane < rb) ? z[R + lane] : 0.0;
+        for (int k = 0; k < rb; ++k) {
+          double xk = __shfl_sync(0xffffffffu, xr, k) / (double)L[(int64_t)(R + k) * n + R + k];
+          if (lane == k) xr = xk;
+          if (lane > k && lane < rb) xr -= (double)L[(int64_t)(R + lane) * n + R + k] * xk;
+        }
+        if (lane < rb) z[R + lane] = xr;
+      }
+      __syncthreads();
+    }
+  } else {
+    int nblk = (n + 31) / 32;
+    for (int bI = nblk - 1; bI >= 0; --bI) {
+      int R = bI * 32;
+      int rb = min(32, n - R);
+      if (warp == 0) {
+        double vr = (lane < rb) ? z[R + lane] : 0.0;
+        for (int k = rb - 1; k >= 0; --k) {
+          double xk = __shfl_sync(0xffffffffu, vr, k) / (double)L[(int64_t)(R + k) * n + R + k];
+          if (lane == k) vr = xk;
+          if (lane < k) vr -= (double)L[(int64_t)(R + k) * n + R + lane] * xk;
+        }
+        if (lane < rb) z[R + lane] = vr;
+      }
+      __syncthreads();
+      for (int c = tid; c < R; c += blockDim.x) {
+        A_t acc = 0;
+        for (int k = 0; k < rb; ++k) acc += (A_t)L[(int64_t)(R + k) * n + c] * (A_t)z[R + k];
+        z[c] -= (double)acc;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < n; i += blockDim.x) x[i] = z[i];
+}
+
+// kept-space gather of the global state: out[k] = a[glob[k]]
+__global__ void k_gather_kept(int64_t nk, const int64_t *glob, const double *a, double *out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nk) out[k] = a[glob[k]];
+}
+
+// f = M x + dt * w * j[glob]   (warp per CSR row)
+__global__ void k_rhs(int64_t nk, const int64_t *ptr, const int32_t *col, const double *val, const double *x,
+                      const int64_t *glob, const double *w, const double *j, double dt, double *f) {
+  int lane = threadIdx.x & 31;
+  int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= nk) return;
+  double acc = 0;
+  for (int64_t t = ptr[r] + lane; t < ptr[r + 1]; t += 32) acc += val[t] * x[col[t]];
+  acc = warp_sum(acc);
+  if (lane == 0) f[r] = acc + dt * w[r] * j[glob[r]];
+}
+
+// r = f - W x
+__global__ void k_resid(int64_t nk, const int64_t *ptr, const int32_t *col, const double *val, const double *x,
+                        const double *f, double *r) {
+  int lane = threadIdx.x & 31;
+  int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (row >= nk) return;
+  double acc = 0;
+  for (int64_t t = ptr[row] + lane; t < ptr[row + 1]; t += 32) acc += val[t] * x[col[t]];
+  acc = warp_sum(acc);
+  if (lane == 0) r[row] = f[row] - acc;
+}
+
+// kept [b|p] parts -> B-space and Pi-space
+__global__ void k_kept_to_bp(int64_t nbt, int64_t npt, const int64_t *b_kept, const int64_t *p_kept,
+                             const double *kv, double *gb, double *gp) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nbt) gb[t] = kv[b_kept[t]];
+  else if (t < nbt + npt) gp[t - nbt] = kv[p_kept[t - nbt]];
+}
+
+// u[q] = base[q] + sgn_mode * sum_t wt[t] * v[lam[t]]   (B^T or B_D^T, gather form)
+__global__ void k_Bt(int64_t nbt, const int32_t *ptr, const int32_t *lam, const double *wt, const double *v,
+                     const double *base, double sgn, double *u) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nbt) return;
+  double acc = 0;
+  for (int t = ptr[q]; t < ptr[q + 1]; ++t) acc += wt[t] * v[lam[t]];
+  u[q] = (base ? base[q] : 0.0) + sgn * acc;
+}
+
+// out[lam] = wp * z[qp] - wm * z[qm]; optional partial dot with dotv
+__global__ void k_jump(int64_t m, const int32_t *qp, const int32_t *qm, const double *wp, const double *wm,
+                       const double *z, double *out, const double *dotv, double *part) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+    double a = wp ? wp[l] : 1.0, b = wm ? wm[l] : 1.0;
+    double v = a * z[qp[l]] - b * z[qm[l]];
+    out[l] = v;
+    if (dotv) acc += v * dotv[l];
+  }
+  if (!part) return;
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// cc[k] = sum over copies (gp[pos] - tp[pos])   (gp may be null)
+__global__ void k_coarse_gather(int nc, const int32_t *ptr, const int32_t *pos, const double *gp, const double *tp,
+                                double *cc) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nc) return;
+  double acc = 0;
+  for (int t = ptr[k]; t < ptr[k + 1]; ++t) acc += (gp ? gp[pos[t]] : 0.0) - tp[pos[t]];
+  cc[k] = acc;
+}
+
+__global__ void k_pgather(int64_t npt, const int32_t *pc, const double *q, double *qloc) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < npt) qloc[t] = q[pc[t]];
+}
+
+// write the condensed solution into kept space: x[b] = zb, x[p] = q[pc]
+__global__ void k_bp_to_kept(int64_t nbt, int64_t npt, const int64_t *b_kept, const int64_t *p_kept,
+                             const int32_t *pc, const double *zb, const double *q, double *kx) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nbt) kx[b_kept[t]] = zb[t];
+  else if (t < nbt + npt) kx[p_kept[t - nbt]] = q[pc[t - nbt]];
+}
+
+// a[glob[k]] += x[k] for owned kept entries
+__global__ void k_owner_add(int64_t nk, const int64_t *glob, const uint8_t *own, const double *x, double *a) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nk && own[k]) a[glob[k]] += x[k];
+}
+
+// rg[fglob[f]] = sum over kept copies of v; partial sums of rg^2 (assembled residual)
+__global__ void k_assemble_free(int64_t nf, const int64_t *ptr, const int64_t *pos, const int64_t *fglob,
+                                const double *v, double *rg, double *part) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int64_t t = ptr[f]; t < ptr[f + 1]; ++t) s += v[pos[t]];
+    rg[fglob[f]] = s;
+    acc += s * s;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    x = warp_sum(x);
+    if (threadIdx.x == 0) part[blockIdx.x] = x;
+  }
+}
+
+// local pieces of an assembled vector with the 1/k partition of unity: v[k] = w[k] rg[glob[k]]
+__global__ void k_distribute(int64_t nk, const int64_t *glob, const double *w, const double *rg, double *v) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nk) v[k] = w[k] * rg[glob[k]];
+}
+
+__global__ void k_dot_partial(int64_t n, const double *x, const double *y, double *part) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += x[i] * y[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// sc[idx] = sum(part); op 1: sc[4] = sc[1]/sc[2] (alpha); op 2: sc[5] = sc[6]/sc[1], sc[1] = sc[6] (beta)
+enum { SC_DD = 0, SC_RZ = 1, SC_PQ = 2, SC_RR = 3, SC_ALPHA = 4, SC_BETA = 5, SC_RZNEW = 6, SC_TMP = 7 };
+__global__ void k_dot_final(int nparts, const double *part, double *sc, int idx, int op) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w];
+    sc[idx] = v;
+    if (op == 1) sc[SC_ALPHA] = sc[SC_RZ] / sc[SC_PQ];
+    if (op == 2) {
+      sc[SC_BETA] = sc[SC_RZNEW] / sc[SC_RZ];
+      sc[SC_RZ] = sc[SC_RZNEW];
+    }
+  }
+}
+
+// lam += alpha p; r -= alpha q; partial (r, r)
+__global__ void k_cg_update(int64_t m, const double *sc, const double *p, const double *q, double *lam, double *r,
+                            double *part) {
+  __shared__ double sh[32];
+  double alpha = sc[SC_ALPHA];
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    lam[i] += alpha * p[i];
+    double v = r[i] - alpha * q[i];
+    r[i] = v;
+    acc += v * v;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_p_update(int64_t m, const double *sc, const double *z, double *p) {
+  double beta = sc[SC_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// =============================================================================
+// Host-side state
+// =============================================================================
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+};
+
+struct DeviceState {
+  ieti_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool mixed = false;
+  std::vector<void *> allocs;
+  int64_t bytes = 0;
+  int64_t launches_setup = 0;
+  double t_setup_ms = 0;
+  // sizes
+  int np_ = 0;
+  int64_t n_edges = 0, NK = 0, NBt = 0, NPt = 0, M = 0, NC = 0, NF = 0;
+  int64_t bytes_iter = 0;
+  int max_ni = 0;
+  std::vector<int32_t> h_ni, h_nb, h_np;
+  // per patch device arrays
+  int32_t *ni = nullptr, *nb = nullptr, *npp = nullptr;
+  int64_t *kofs = nullptr, *lyoff = nullptr, *hoff = nullptr, *qoff = nullptr, *poff = nullptr;
+  // kept space
+  int64_t *kglob = nullptr;
+  double *kw = nullptr;
+  uint8_t *kown = nullptr;
+  int64_t *wptr = nullptr, *mptr = nullptr;
+  int32_t *wcol = nullptr, *mcol = nullptr;
+  double *wval = nullptr, *mval = nullptr;
+  // B / Pi / lambda / coarse maps
+  int64_t *b_kept = nullptr, *p_kept = nullptr;
+  int32_t *bt_ptr = nullptr, *bt_lam = nullptr;
+  double *bt_sgn = nullptr, *bt_wd = nullptr;
+  int32_t *lam_qp = nullptr, *lam_qm = nullptr;
+  double *lam_wp = nullptr, *lam_wm = nullptr;
+  int32_t *pc = nullptr, *cptr = nullptr, *cpos = nullptr;
+  int64_t *fptr = nullptr, *fpos = nullptr, *fglob = nullptr;
+  double *rglob = nullptr;
+  // operators (T = double or float)
+  void *LY = nullptr, *H = nullptr, *Q = nullptr, *P = nullptr;
+  double *Sinv = nullptr;
+  // GEMV descriptors
+  struct Desc {
+    int64_t n = 0;
+    int64_t *aoff = nullptr, *xoff = nullptr, *yidx = nullptr;
+    int32_t *ncol = nullptr;
+  } dY, dH, dQ, dP, dS;
+  // vectors
+  double *a = nullptr, *j = nullptr, *kf = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *ka = nullptr;
+  double *bp = nullptr, *ub = nullptr, *gb = nullptr, *gp = nullptr, *cc = nullptr, *q = nullptr, *qloc = nullptr;
+  double *lam = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Fp = nullptr, *dvec = nullptr;
+  double *part = nullptr, *sc = nullptr, *h_sc = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double dt = 0;
+};
+
+template <class T>
+static int dalloc(DeviceState *d, T **ptr, size_t n, std::string &err) {
+  *ptr = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)ptr, n * sizeof(T));
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_OOM;
+  }
+  d->allocs.push_back((void *)*ptr);
+  d->bytes += (int64_t)(n * sizeof(T));
+  return IETI_OK;
+}
+
+template <class T>
+static int upload(DeviceState *d, T **ptr, const std::vector<T> &h, std::string &err) {
+  int rc = dalloc(d, ptr, h.size(), err);
+  if (rc) return rc;
+  if (!h.empty()) CK(cudaMemcpyAsync(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return IETI_OK;
+}
+
+static int upload_desc(DeviceState *d, DeviceState::Desc &D, const std::vector<int64_t> &aoff,
+                        const std::vector<int64_t> &xoff, const std::vector<int64_t> &yidx,
+                        const std::vector<int32_t> &ncol, std::string &err) {
+  D.n = (int64_t)aoff.size();
+  int rc;
+  if ((rc = upload(d, &D.aoff, aoff, err)) || (rc = upload(d, &D.xoff, xoff, err)) ||
+      (rc = upload(d, &D.yidx, yidx, err)) || (rc = upload(d, &D.ncol, ncol, err)))
+    return rc;
+  return IETI_OK;
+}
+
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)std::max<int64_t>(1, (n + block - 1) / block); }
+
+template <class T>
+static void gemv(DeviceState *d, const DeviceState::Desc &D, const void *A, const double *x, double *y,
+                 const double *y0, double alpha, double beta) {
+  if (D.n == 0) return;
+  int64_t warps = D.n;
+  unsigned blocks = (unsigned)std::min<int64_t>((warps * 32 + GEMV_BLOCK - 1) / GEMV_BLOCK, 152 * 16);
+  k_gemv_rows<T><<<blocks, GEMV_BLOCK, 0, d->stream>>>(D.n, D.aoff, D.xoff, D.yidx, D.ncol, (const T *)A, x, y, y0,
+                                                        alpha, beta);
+}
+
+// partial Cholesky over all patches (host loop over panels)
+template <class T>
+static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int32_t *ld, const std::vector<int32_t> &hkb,
+                         const std::vector<int32_t> &hke, const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke,
+                         int32_t *dna, int32_t *status, std::string &err) {
+  int nbatch = (int)hkb.size();
+  int max_panels = 0;
+  for (int s = 0; s < nbatch; ++s) max_panels = std::max(max_panels, (hke[s] - hkb[s] + NB - 1) / NB);
+  for (int j = 0; j < max_panels; ++j) {
+    int max_rows = 0, max_tiles = 0;
+    for (int s = 0; s < nbatch; ++s) {
+      int j0 = hkb[s] + j * NB;
+      if (j0 >= hke[s]) continue;
+      int jb = std::min(NB, hke[s] - j0);
+      int m = hna[s] - (j0 + jb);
+      if (m <= 0) continue;
+      max_rows = std::max(max_rows, m);
+      int T64 = (m + 63) / 64;
+      max_tiles = std::max(max_tiles, T64 * (T64 + 1) / 2);
+    }
+    k_potrf_diag<T><<<nbatch, 256, 0, d->stream>>>(base, off, ld, dkb, dke, j, status);
+    d->launches_setup++;
+    if (max_rows > 0) {
+      dim3 g1(grid_for(max_rows, 128), nbatch);
+      k_trsm_panel<T><<<g1, 128, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      dim3 g2(max_tiles, nbatch);
+      k_syrk_update<T><<<g2, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      d->launches_setup += 2;
+    }
+  }
+  CK(cudaGetLastError());
+  return IETI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the condensed interface solve: given u (B-space) and gp (Pi-space, may be
+// null): bp[0:NBt] = F u - Psi q, q = S_c^{-1} sum_s A_s^T (gp - Psi^T u)
+template <class T>
+static void condensed(DeviceState *d, const double *u, const double *gp) {
+  cudaStream_t st = d->stream;
+  gemv<T>(d, d->dH, d->H, u, d->bp, nullptr, 1.0, 0.0);
+  if (d->NC > 0) {
+    k_coarse_gather<<<grid_for(d->NC, 256), 256, 0, st>>>((int)d->NC, d->cptr, d->cpos, gp, d->bp + d->NBt, d->cc);
+    gemv<double>(d, d->dS, d->Sinv, d->cc, d->q, nullptr, 1.0, 0.0);
+    k_pgather<<<grid_for(d->NPt, 256), 256, 0, st>>>(d->NPt, d->pc, d->q, d->qloc);
+    gemv<T>(d, d->dQ, d->Q, d->qloc, d->bp, d->bp, -1.0, 1.0);
+  }
+}
+
+template <class T>
+static void apply_F(DeviceState *d, const double *v, double *out, const double *dotv, double *part) {
+  cudaStream_t st = d->stream;
+  k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, d->bt_sgn, v, nullptr, 1.0, d->ub);
+  condensed<T>(d, d->ub, nullptr);
+  k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, out, dotv, part);
+}
+
+template <class T>
+static void apply_precond(DeviceState *d, const double *rv, double *out, const double *dotv, double *part) {
+  cudaStream_t st = d->stream;
+  int pcnd = d->opt.precond;
+  if (pcnd == IETI_PRECOND_NONE) {
+    cudaMemcpyAsync(out, rv, d->M * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(d->M, out, dotv, part);
+    return;
+  }
+  bool scaled = pcnd != IETI_PRECOND_DIRICHLET;
+  k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, scaled ? d->bt_wd : d->bt_sgn, rv,
+                                               nullptr, 1.0, d->ub);
+  gemv<T>(d, d->dP, d->P, d->ub, d->bp, nullptr, 1.0, 0.0);
+  k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, scaled ? d->lam_wp : nullptr,
+                                     scaled ? d->lam_wm : nullptr, d->bp, out, dotv, part);
+}
+
+static int read_scalar(DeviceState *d, int idx, double *out, std::string &err) {
+  CK(cudaMemcpyAsync(d->h_sc, d->sc + idx, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  *out = *d->h_sc;
+  return IETI_OK;
+}
+
+// PCG on F lambda = d (Sec. 4: Dirichlet-preconditioned CG, lambda_0 = 0)
+template <class T>
+static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
+  cudaStream_t st = d->stream;
+  int64_t m = d->M;
+  *its = 0;
+  *rel = 0.0;
+  if (m == 0) return IETI_OK;
+  CK(cudaMemsetAsync(d->lam, 0, m * sizeof(double), st));
+  CK(cudaMemcpyAsync(d->r, d->dvec, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(m, d->r, d->r, d->part);
+  k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_DD, 0);
+  double dd;
+  int rc = read_scalar(d, SC_DD, &dd, err);
+  if (rc) return rc;
+  if (!(dd > 0.0)) return IETI_OK;
+  double tol2 = d->opt.cg_tol * d->opt.cg_tol * dd;
+  apply_precond<T>(d, d->r, d->z, d->r, d->part);
+  k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RZ, 0);
+  CK(cudaMemcpyAsync(d->p, d->z, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double rr = dd;
+  for (int it = 1; it <= d->opt.cg_max_it; ++it) {
+    apply_F<T>(d, d->p, d->Fp, d->p, d->part);
+    k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_PQ, 1);
+    k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(m, d->sc, d->p, d->Fp, d->lam, d->r, d->part);
+    k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RR, 0);
+    rc = read_scalar(d, SC_RR, &rr, err);
+    if (rc) return rc;
+    *its = it;
+    if (!std::isfinite(rr)) {
+      err = "PCG breakdown (non-finite residual)";
+      return IETI_ERR_CG_NOT_CONVERGED;
+    }
+    if (rr <= tol2) break;
+    apply_precond<T>(d, d->r, d->z, d->r, d->part);
+    k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RZNEW, 2);
+    k_p_update<<<RED_BLOCKS, 256, 0, st>>>(m, d->sc, d->z, d->p);
+  }
+  *rel = std::sqrt(rr / dd);
+  CK(cudaGetLastError());
+  if (rr > tol2) {
+    err = "PCG did not reach cg_tol within cg_max_it";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  return IETI_OK;
+}
+
+// dual-primal solve of the gauged step system for kept-space right-hand sides
+// rhs (per patch, Sec. 3), solution into d->kx (kept space)
+template <class T>
+static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
+  cudaStream_t st = d->stream;
+  int64_t NK = d->NK;
+  size_t smem = (size_t)std::max(d->max_ni, 1) * sizeof(double);
+  // interior condensation: z_i = L_ii^{-1} rhs_i; g_[bp] = rhs_[bp] - Y z_i
+  CK(cudaMemcpyAsync(d->kz, rhs, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kz, 0);
+  gemv<T>(d, d->dY, d->LY, d->kz, d->kz, rhs, -1.0, 1.0);
+  k_kept_to_bp<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->kz, d->gb,
+                                                                 d->gp);
+  // d = B (F g_b - Psi S_c^{-1} sum A^T (g_p - Psi^T g_b))
+  condensed<T>(d, d->gb, d->gp);
+  k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, d->dvec, nullptr, nullptr);
+  int rc = pcg<T>(d, its, rel, err);
+  if (rc && rc != IETI_ERR_CG_NOT_CONVERGED) return rc;
+  int cg_rc = rc;
+  // recovery: v_b = g_b - B^T lambda; a_b = F v_b - Psi q, a_p = q
+  k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, d->bt_sgn, d->lam, d->gb, -1.0, d->ub);
+  condensed<T>(d, d->ub, d->gp);
+  CK(cudaMemcpyAsync(d->kx, d->kz, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  k_bp_to_kept<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->pc, d->bp,
+                                                                 d->q, d->kx);
+  // interior: a_i = L_ii^{-T} (z_i - Y^T a_[bp])
+  dim3 gT(grid_for(d->max_ni, 128), d->np_);
+  k_gemvT_Y<T><<<gT, 128, 0, st>>>(d->ni, d->nb, d->npp, d->lyoff, d->kofs, (const T *)d->LY, d->kx);
+  k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kx, 1);
+  CK(cudaGetLastError());
+  return cg_rc;
+}
+
+// assemble a kept-space vector over the free global DOFs (rglob), return its norm
+static int assemble_norm(DeviceState *d, const double *v, double *out, std::string &err) {
+  k_assemble_free<<<RED_BLOCKS, 256, 0, d->stream>>>(d->NF, d->fptr, d->fpos, d->fglob, v, d->rglob, d->part);
+  k_dot_final<<<1, 256, 0, d->stream>>>(RED_BLOCKS, d->part, d->sc, SC_TMP, 0);
+  int rc = read_scalar(d, SC_TMP, out, err);
+  *out = std::sqrt(*out);
+  return rc;
+}
+
+template <class T>
+static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
+  cudaStream_t st = d->stream;
+  int64_t NK = d->NK;
+  // f = M a^l + dt j^{l+1}  (kept space, load split 1/k over the k patches holding a DOF)
+  k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
+  k_rhs<<<grid_for(NK * 32, 256), 256, 0, st>>>(NK, d->mptr, d->mcol, d->mval, d->ka, d->kglob, d->kw, d->j, d->dt,
+                                                 d->kf);
+  double fn = 0.0;
+  int rc;
+  if ((rc = assemble_norm(d, d->kf, &fn, err))) return rc;
+  int its_total = 0, sweeps = 0, cg_rc = IETI_OK;
+  double rel = 0, ores = -1.0, prev = -1.0;
+  int max_sweeps = std::max(1, d->opt.max_sweeps);
+  for (int sweep = 0;; ++sweep) {
+    // defect of the ASSEMBLED system at the current iterate, in FP64: r = f - W_g a,
+    // redistributed over the patches with the 1/k weights (so that the local
+    // right-hand sides of the correction are as small as the defect itself)
+    k_resid<<<grid_for(NK * 32, 256), 256, 0, st>>>(NK, d->wptr, d->wcol, d->wval, d->ka, d->kf, d->kr);
+    double rn;
+    if ((rc = assemble_norm(d, d->kr, &rn, err))) return rc;
+    ores = fn > 0 ? rn / fn : 0.0;
+    if (ores <= d->opt.outer_tol || fn == 0.0) break;
+    if (sweep >= max_sweeps) {
+      if (max_sweeps > 1 && cg_rc == IETI_OK) {
+        err = "refinement did not reach outer_tol within max_sweeps";
+        cg_rc = IETI_ERR_CG_NOT_CONVERGED;
+      }
+      break;
+    }
+    if (sweep >= 2 && rn > 0.9 * prev) {  // stagnation at the rounding floor of the FP64 defect
+      if (cg_rc == IETI_OK) {
+        err = "refinement stagnated above outer_tol";
+        cg_rc = IETI_ERR_CG_NOT_CONVERGED;
+      }
+      break;
+    }
+    prev = rn;
+    k_distribute<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->kw, d->rglob, d->kr);
+    int its = 0;
+    rc = dd_solve<T>(d, d->kr, &its, &rel, err);
+    its_total += its;
+    sweeps++;
+    if (rc == IETI_ERR_CG_NOT_CONVERGED) cg_rc = rc;
+    else if (rc) return rc;
+    k_owner_add<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->kown, d->kx, d->a);
+    k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
+  }
+  CK(cudaGetLastError());
+  if (stats) {
+    stats->cg_its = its_total;
+    stats->sweeps = sweeps;
+    stats->rel_res = rel;
+    stats->outer_res = ores;
+  }
+  return cg_rc;
+}
+
+// =============================================================================
+// Setup orchestration
+// =============================================================================
+int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out, std::string &err) {
+  auto t0 = std::chrono::steady_clock::now();
+  DeviceState *d = new DeviceState();
+  *out = nullptr;
+  d->opt = opt;
+  d->device = opt.device;
+  d->mixed = opt.precision == IETI_PREC_MIXED;
+  d->dt = hs.dt;
+  auto fail = [&](int rc) {
+    device_destroy(d);
+    return rc;
+  };
+  CK(cudaSetDevice(d->device));
+  d->stream = (cudaStream_t)opt.cuda_stream;
+  CK(cudaEventCreate(&d->ev0));
+  CK(cudaEventCreate(&d->ev1));
+  const int np_ = hs.n_patches();
+  d->np_ = np_;
+  d->n_edges = hs.n_edges;
+  // ---------------- sizes and offsets
+  std::vector<int32_t> hni(np_), hnb(np_), hnp(np_), hn(np_), hnn(np_), hrowpatch, hrowlocal;
+  std::vector<int64_t> hkofs(np_ + 1, 0), hdoff(np_ + 1, 0), hly(np_ + 1, 0), hh(np_ + 1, 0), hq(np_ + 1, 0),
+      hp(np_ + 1, 0), hbofs(np_ + 1, 0), hpofs(np_ + 1, 0);
+  for (int s = 0; s < np_; ++s) {
+    const Patch &pt = hs.patches[s];
+    hni[s] = pt.ni;
+    hnb[s] = pt.nb;
+    hnp[s] = pt.np;
+    hn[s] = pt.ni + pt.nb + pt.np;
+    hnn[s] = hn[s] + pt.nb;
+    hkofs[s + 1] = hkofs[s] + hn[s];
+    hdoff[s + 1] = hdoff[s] + (int64_t)hnn[s] * hnn[s];
+    hly[s + 1] = hly[s] + (int64_t)hn[s] * pt.ni;
+    hh[s + 1] = hh[s] + (int64_t)(pt.nb + pt.np) * pt.nb;
+    hq[s + 1] = hq[s] + (int64_t)pt.nb * pt.np;
+    hp[s + 1] = hp[s] + (int64_t)pt.nb * pt.nb;
+    hbofs[s + 1] = hbofs[s] + pt.nb;
+    hpofs[s + 1] = hpofs[s] + pt.np;
+    d->max_ni = std::max(d->max_ni, pt.ni);
+  }
+  d->h_ni = hni;
+  d->h_nb = hnb;
+  d->h_np = hnp;
+  d->NK = hkofs[np_];
+  d->NBt = hbofs[np_];
+  d->NPt = hpofs[np_];
+  d->M = (int64_t)hs.lam.size();
+  d->NC = hs.n_coarse;
+  d->NF = (int64_t)hs.free_edges.size();
+  if ((size_t)d->max_ni * sizeof(double) > 200 * 1024) {
+    err = "an interior block exceeds the shared-memory triangular solve limit (25600 DOFs)";
+    return fail(IETI_ERR_TOO_LARGE);
+  }
+  // ---------------- kept space arrays and CSR (columns as absolute kept indices)
+  std::vector<int64_t> kglob(d->NK), wptr(1, 0), mptr(1, 0), b_kept, p_kept;
+  std::vector<double> kw(d->NK), wval, mval;
+  std::vector<uint8_t> kown(d->NK, 0);
+  std::vector<int32_t> wcol, mcol;
+  std::vector<uint8_t> seen(hs.n_edges, 0);
+  for (int s = 0; s < np_; ++s) {
+    const Patch &pt = hs.patches[s];
+    for (int k = 0; k < hn[s]; ++k) {
+      int64_t g = pt.kept_glob[k];
+      kglob[hkofs[s] + k] = g;
+      kw[hkofs[s] + k] = pt.load_w[k];
+      if (!seen[g]) {
+        seen[g] = 1;
+        kown[hkofs[s] + k] = 1;  // lowest patch id holding the DOF owns it
+      }
+      hrowpatch.push_back(s);
+      hrowlocal.push_back(k);
+      for (int t = pt.Wk.ptr[k]; t < pt.Wk.ptr[k + 1]; ++t) {
+        wcol.push_back((int32_t)(hkofs[s] + pt.Wk.col[t]));
+        wval.push_back(pt.Wk.val[t]);
+      }
+      wptr.push_back((int64_t)wcol.size());
+      for (int t = pt.Mk.ptr[k]; t < pt.Mk.ptr[k + 1]; ++t) {
+        mcol.push_back((int32_t)(hkofs[s] + pt.Mk.col[t]));
+        mval.push_back(pt.Mk.val[t]);
+      }
+      mptr.push_back((int64_t)mcol.size());
+    }
+    for (int k = 0; k < pt.nb; ++k) b_kept.push_back(hkofs[s] + pt.ni + k);
+    for (int k = 0; k < pt.np; ++k) p_kept.push_back(hkofs[s] + pt.ni + pt.nb + k);
+  }
+  if (d->NK >= (int64_t)INT32_MAX) {
+    err = "kept space exceeds 2^31 entries";
+    return fail(IETI_ERR_TOO_LARGE);
+  }
+  // ---------------- multipliers: B^T gather lists, jump pairs, scaling weights
+  std::vector<double> rho(d->NBt, 1.0);
+  if (opt.precond == IETI_PRECOND_DIRICHLET_STIFF)
+    for (int s = 0; s < np_; ++s) {
+      const Patch &pt = hs.patches[s];
+      for (int k = 0; k < pt.nb; ++k) {
+        int row = pt.ni + k;
+        for (int t = pt.Wk.ptr[row]; t < pt.Wk.ptr[row + 1]; ++t)
+          if (pt.Wk.col[t] == row) rho[hbofs[s] + k] = pt.Wk.val[t];
+      }
+    }
+  std::vector<double> rho_sum(hs.n_edges, 0.0);
+  for (int s = 0; s < np_; ++s)
+    for (int k = 0; k < hs.patches[s].nb; ++k) rho_sum[hs.patches[s].kept_glob[hs.patches[s].ni + k]] += rho[hbofs[s] + k];
+  int64_t m = d->M;
+  std::vector<int32_t> qp(m), qm(m);
+  std::vector<double> wp(m), wm(m);
+  std::vector<std::vector<std::pair<int32_t, std::pair<double, double>>>> lists(d->NBt);
+  for (int64_t l = 0; l < m; ++l) {
+    const Multiplier &L = hs.lam[l];
+    int64_t a = hbofs[L.s] + L.pos_s, b = hbofs[L.t] + L.pos_t;
+    qp[l] = (int32_t)a;
+    qm[l] = (int32_t)b;
+    double rs = rho_sum[L.edge];
+    wp[l] = rho[b] / rs;  // copy in s scaled by delta_t
+    wm[l] = rho[a] / rs;
+    lists[a].push_back({(int32_t)l, {1.0, wp[l]}});
+    lists[b].push_back({(int32_t)l, {-1.0, -wm[l]}});
+  }
+  std::vector<int32_t> bt_ptr(1, 0), bt_lam;
+  std::vector<double> bt_sgn, bt_wd;
+  for (int64_t q = 0; q < d->NBt; ++q) {
+    for (auto &e : lists[q]) {
+      bt_lam.push_back(e.first);
+      bt_sgn.push_back(e.second.first);
+      bt_wd.push_back(e.second.second);
+    }
+    bt_ptr.push_back((int32_t)bt_lam.size());
+  }
+  // ---------------- coarse maps
+  std::vector<int32_t> pc(d->NPt);
+  std::vector<std::vector<int32_t>> copies(d->NC);
+  for (int s = 0; s < np_; ++s) {
+    const Patch &pt = hs.patches[s];
+    for (int k = 0; k < pt.np; ++k) {
+      int64_t c = hs.coarse_of_edge[pt.kept_glob[pt.ni + pt.nb + k]];
+      pc[hpofs[s] + k] = (int32_t)c;
+      copies[c].push_back((int32_t)(hpofs[s] + k));
+    }
+  }
+  std::vector<int32_t> cptr(1, 0), cpos;
+  for (int64_t c = 0; c < d->NC; ++c) {
+    for (int32_t x : copies[c]) cpos.push_back(x);
+    cptr.push_back((int32_t)cpos.size());
+  }
+  // free global DOFs -> kept copies (assembled residual norm)
+  std::vector<std::vector<int64_t>> fcop(hs.n_edges);
+  for (int64_t k = 0; k < d->NK; ++k) fcop[kglob[k]].push_back(k);
+  std::vector<int64_t> fptr(1, 0), fpos, fglob(hs.free_edges);
+  for (int64_t g : hs.free_edges) {
+    for (int64_t k : fcop[g]) fpos.push_back(k);
+    fptr.push_back((int64_t)fpos.size());
+  }
+  // ---------------- upload index data
+  int rc;
+  std::vector<int64_t> hkofs_v(hkofs.begin(), hkofs.end() - 1), hdoff_v(hdoff.begin(), hdoff.end() - 1),
+      hly_v(hly.begin(), hly.end() - 1), hh_v(hh.begin(), hh.end() - 1), hq_v(hq.begin(), hq.end() - 1),
+      hp_v(hp.begin(), hp.end() - 1);
+  int64_t *ddoff = nullptr;
+  int32_t *dnn = nullptr, *dn = nullptr, *drowpatch = nullptr, *drowlocal = nullptr;
+  if ((rc = upload(d, &d->ni, hni, err)) || (rc = upload(d, &d->nb, hnb, err)) || (rc = upload(d, &d->npp, hnp, err)) ||
+      (rc = upload(d, &d->kofs, hkofs_v, err)) || (rc = upload(d, &ddoff, hdoff_v, err)) ||
+      (rc = upload(d, &d->lyoff, hly_v, err)) || (rc = upload(d, &d->hoff, hh_v, err)) ||
+      (rc = upload(d, &d->qoff, hq_v, err)) || (rc = upload(d, &d->poff, hp_v, err)) ||
+      (rc = upload(d, &dnn, hnn, err)) || (rc = upload(d, &dn, hn, err)) ||
+      (rc = upload(d, &drowpatch, hrowpatch, err)) ||
+      (rc = upload(d, &drowlocal, hrowlocal, err)) || (rc = upload(d, &d->kglob, kglob, err)) ||
+      (rc = upload(d, &d->kw, kw, err)) || (rc = upload(d, &d->kown, kown, err)) ||
+      (rc = upload(d, &d->wptr, wptr, err)) || (rc = upload(d, &d->wcol, wcol, err)) ||
+      (rc = upload(d, &d->wval, wval, err)) || (rc = upload(d, &d->mptr, mptr, err)) ||
+      (rc = upload(d, &d->mcol, mcol, err)) || (rc = upload(d, &d->mval, mval, err)) ||
+      (rc = upload(d, &d->b_kept, b_kept, err)) || (rc = upload(d, &d->p_kept, p_kept, err)) ||
+      (rc = upload(d, &d->bt_ptr, bt_ptr, err)) || (rc = upload(d, &d->bt_lam, bt_lam, err)) ||
+      (rc = upload(d, &d->bt_sgn, bt_sgn, err)) || (rc = upload(d, &d->bt_wd, bt_wd, err)) ||
+      (rc = upload(d, &d->lam_qp, qp, err)) || (rc = upload(d, &d->lam_qm, qm, err)) ||
+      (rc = upload(d, &d->lam_wp, wp, err)) || (rc = upload(d, &d->lam_wm, wm, err)) ||
+      (rc = upload(d, &d->pc, pc, err)) || (rc = upload(d, &d->cptr, cptr, err)) ||
+      (rc = upload(d, &d->cpos, cpos, err)) || (rc = upload(d, &d->fptr, fptr, err)) ||
+      (rc = upload(d, &d->fpos, fpos, err)) || (rc = upload(d, &d->fglob, fglob, err)))
+    return fail(rc);
+  // ---------------- GEMV descriptors
+  {
+    std::vector<int64_t> ao, xo, yi;
+    std::vector<int32_t> nc;
+    auto clear = [&]() { ao.clear(); xo.clear(); yi.clear(); nc.clear(); };
+    // Y rows: g_[bp] = rhs_[bp] - Y z_i  (kept space)
+    for (int s = 0; s < np_; ++s)
+      for (int r = 0; r < hnb[s] + hnp[s]; ++r) {
+        ao.push_back(hly[s] + (int64_t)(hni[s] + r) * hni[s]);
+        xo.push_back(hkofs[s]);
+        yi.push_back(hkofs[s] + hni[s] + r);
+        nc.push_back(hni[s]);
+      }
+    if ((rc = upload_desc(d, d->dY, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    // H rows: [F u ; Psi^T u] -> bp (B-space then Pi-space)
+    for (int s = 0; s < np_; ++s)
+      for (int r = 0; r < hnb[s] + hnp[s]; ++r) {
+        ao.push_back(hh[s] + (int64_t)r * hnb[s]);
+        xo.push_back(hbofs[s]);
+        yi.push_back(r < hnb[s] ? hbofs[s] + r : d->NBt + hpofs[s] + (r - hnb[s]));
+        nc.push_back(hnb[s]);
+      }
+    if ((rc = upload_desc(d, d->dH, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    // Psi rows: bp_b -= Psi qloc
+    for (int s = 0; s < np_; ++s)
+      for (int r = 0; r < hnb[s]; ++r) {
+        ao.push_back(hq[s] + (int64_t)r * hnp[s]);
+        xo.push_back(hpofs[s]);
+        yi.push_back(hbofs[s] + r);
+        nc.push_back(hnp[s]);
+      }
+    if ((rc = upload_desc(d, d->dQ, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    // P rows (Dirichlet preconditioner S_bb)
+    for (int s = 0; s < np_; ++s)
+      for (int r = 0; r < hnb[s]; ++r) {
+        ao.push_back(hp[s] + (int64_t)r * hnb[s]);
+        xo.push_back(hbofs[s]);
+        yi.push_back(hbofs[s] + r);
+        nc.push_back(hnb[s]);
+      }
+    if ((rc = upload_desc(d, d->dP, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    for (int64_t r = 0; r < d->NC; ++r) {
+      ao.push_back(r * d->NC);
+      xo.push_back(0);
+      yi.push_back(r);
+      nc.push_back((int32_t)d->NC);
+    }
+    if ((rc = upload_desc(d, d->dS, ao, xo, yi, nc, err))) return fail(rc);
+  }
+  // ---------------- work vectors
+  if ((rc = dalloc(d, &d->a, hs.n_edges, err)) || (rc = dalloc(d, &d->j, hs.n_edges, err)) ||
+      (rc = dalloc(d, &d->rglob, hs.n_edges, err)) ||
+      (rc = dalloc(d, &d->kf, d->NK, err)) || (rc = dalloc(d, &d->kx, d->NK, err)) ||
+      (rc = dalloc(d, &d->kr, d->NK, err)) || (rc = dalloc(d, &d->kz, d->NK, err)) ||
+      (rc = dalloc(d, &d->ka, d->NK, err)) || (rc = dalloc(d, &d->bp, d->NBt + d->NPt, err)) ||
+      (rc = dalloc(d, &d->ub, d->NBt, err)) || (rc = dalloc(d, &d->gb, d->NBt, err)) ||
+      (rc = dalloc(d, &d->gp, d->NPt, err)) || (rc = dalloc(d, &d->cc, d->NC, err)) ||
+      (rc = dalloc(d, &d->q, d->NC, err)) || (rc = dalloc(d, &d->qloc, d->NPt, err)) ||
+      (rc = dalloc(d, &d->lam, m, err)) || (rc = dalloc(d, &d->r, m, err)) || (rc = dalloc(d, &d->z, m, err)) ||
+      (rc = dalloc(d, &d->p, m, err)) || (rc = dalloc(d, &d->Fp, m, err)) || (rc = dalloc(d, &d->dvec, m, err)) ||
+      (rc = dalloc(d, &d->part, RED_BLOCKS, err)) || (rc = dalloc(d, &d->sc, 16, err)))
+    return fail(rc);
+  CK(cudaMallocHost((void **)&d->h_sc, 16 * sizeof(double)));
+  CK(cudaMemsetAsync(d->a, 0, hs.n_edges * sizeof(double), d->stream));
+  CK(cudaMemsetAsync(d->j, 0, hs.n_edges * sizeof(double), d->stream));
+  CK(cudaMemsetAsync(d->rglob, 0, hs.n_edges * sizeof(double), d->stream));
+  // ---------------- dense augmented blocks, partial Cholesky (FP64)
+  double *D = nullptr;
+  if ((rc = dalloc(d, &D, hdoff[np_], err))) return fail(rc);
+  CK(cudaMemsetAsync(D, 0, hdoff[np_] * sizeof(double), d->stream));
+  {
+    int64_t nrows = d->NK;
+    k_csr_to_dense<<<grid_for(nrows * 32, 256), 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol,
+                                                                     d->wval, d->kofs, ddoff, dnn, D);
+    int maxnb = *std::max_element(hnb.begin(), hnb.end());
+    if (maxnb > 0) {
+      dim3 g(grid_for(maxnb, 128), np_);
+      k_augment<<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, D);
+    }
+    d->launches_setup += 2;
+  }
+  CK(cudaGetLastError());
+  // phase A: interior pivots -> trailing [b p b'] = Schur complement; copy S_bb
+  std::vector<int32_t> hkb(np_), hke(np_), hna(np_);
+  int32_t *dkb = nullptr, *dke = nullptr, *dna = nullptr, *dstat = nullptr;
+  if ((rc = dalloc(d, &dkb, np_, err)) || (rc = dalloc(d, &dke, np_, err)) || (rc = dalloc(d, &dna, np_, err)) ||
+      (rc = dalloc(d, &dstat, np_, err)))
+    return fail(rc);
+  CK(cudaMemsetAsync(dstat, 0, np_ * sizeof(int32_t), d->stream));
+  for (int s = 0; s < np_; ++s) {
+    hkb[s] = 0;
+    hke[s] = hni[s];
+    hna[s] = hn[s];  // the b' rows are untouched by interior pivots (their coupling is 0)
+  }
+  CK(cudaMemcpyAsync(dkb, hkb.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(dke, hke.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(dna, hna.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, err))) return fail(rc);
+  int maxnb = *std::max_element(hnb.begin(), hnb.end());
+  int maxnp = *std::max_element(hnp.begin(), hnp.end());
+  int64_t maxP = (int64_t)maxnb * maxnb;
+  int64_t maxH = 0, maxLY = 0;
+  for (int s = 0; s < np_; ++s) {
+    maxH = std::max(maxH, (int64_t)(hnb[s] + hnp[s]) * hnb[s]);
+    maxLY = std::max(maxLY, (int64_t)hn[s] * hni[s]);
+  }
+  size_t esz = d->mixed ? sizeof(float) : sizeof(double);
+  auto alloc_op = [&](void **ptr, int64_t n) -> int {
+    cudaError_t e = cudaMalloc(ptr, std::max<int64_t>(n, 1) * esz);
+    if (e != cudaSuccess) {
+      err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+      return IETI_ERR_OOM;
+    }
+    d->allocs.push_back(*ptr);
+    d->bytes += std::max<int64_t>(n, 1) * esz;
+    return IETI_OK;
+  };
+  if ((rc = alloc_op(&d->P, hp[np_])) || (rc = alloc_op(&d->H, hh[np_])) || (rc = alloc_op(&d->Q, hq[np_])) ||
+      (rc = alloc_op(&d->LY, hly[np_])))
+    return fail(rc);
+  if (maxP > 0) {
+    dim3 g(grid_for(maxP, 256), np_);
+    if (d->mixed) k_extract_P<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->poff, (float *)d->P);
+    else k_extract_P<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->poff, (double *)d->P);
+    d->launches_setup++;
+  }
+  // phase B: interface pivots -> trailing [p b'] = [[C_s, -Psi^T], [-Psi, -F_s]]
+  for (int s = 0; s < np_; ++s) {
+    hkb[s] = hni[s];
+    hke[s] = hni[s] + hnb[s];
+    hna[s] = hnn[s];
+  }
+  CK(cudaMemcpyAsync(dkb, hkb.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(dke, hke.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(dna, hna.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, err))) return fail(rc);
+  {
+    std::vector<int32_t> hstat(np_);
+    CK(cudaMemcpyAsync(hstat.data(), dstat, np_ * 4, cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    for (int s = 0; s < np_; ++s)
+      if (hstat[s]) {
+        err = "local block of patch " + std::to_string(s) + " is not positive definite (pivot " +
+              std::to_string(hstat[s] - 1) + ")";
+        return fail(IETI_ERR_NOT_SPD);
+      }
+  }
+  if (maxH > 0) {
+    dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), np_);
+    if (d->mixed)
+      k_extract_ops<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->hoff, d->qoff,
+                                                     (float *)d->H, (float *)d->Q);
+    else
+      k_extract_ops<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->hoff, d->qoff,
+                                                      (double *)d->H, (double *)d->Q);
+    d->launches_setup++;
+  }
+  if (maxLY > 0) {
+    dim3 g((unsigned)std::min<int64_t>(grid_for(maxLY, 256), 4096), np_);
+    if (d->mixed)
+      k_extract_LY<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->lyoff, (float *)d->LY);
+    else
+      k_extract_LY<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->lyoff, (double *)d->LY);
+    d->launches_setup++;
+  }
+  // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, inverted through [[S_c, I], [I, 0]]
+  if (d->NC > 0) {
+    int64_t nc = d->NC, ldc = 2 * nc;
+    double *Sc = nullptr;
+    if ((rc = dalloc(d, &Sc, (size_t)(ldc * ldc), err))) return fail(rc);
+    CK(cudaMemsetAsync(Sc, 0, (size_t)(ldc * ldc) * sizeof(double), d->stream));
+    for (int s = 0; s < np_; ++s) {
+      if (hnp[s] == 0) continue;
+      int64_t cnt = (int64_t)hnp[s] * hnp[s];
+      k_coarse_add<<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
+                                                              d->pc + hpofs[s], Sc, ldc);
+      d->launches_setup++;
+    }
+    k_coarse_identity<<<grid_for(nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc);
+    int64_t *coff = nullptr;
+    int32_t *cld = nullptr, *ckb = nullptr, *cke = nullptr, *cna = nullptr, *cst = nullptr;
+    std::vector<int64_t> hcoff{0};
+    std::vector<int32_t> hcld{(int32_t)ldc}, hckb{0}, hcke{(int32_t)nc}, hcna{(int32_t)ldc}, hcst{0};
+    if ((rc = upload(d, &coff, hcoff, err)) || (rc = upload(d, &cld, hcld, err)) || (rc = upload(d, &ckb, hckb, err)) ||
+        (rc = upload(d, &cke, hcke, err)) || (rc = upload(d, &cna, hcna, err)) || (rc = upload(d, &cst, hcst, err)))
+      return fail(rc);
+    if ((rc = potrf_partial<double>(d, Sc, coff, cld, hckb, hcke, hcna, ckb, cke, cna, cst, err))) return fail(rc);
+    int32_t cstat = 0;
+    CK(cudaMemcpyAsync(&cstat, cst, 4, cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    if (cstat) {
+      err = "coarse Schur complement is not positive definite (pivot " + std::to_string(cstat - 1) + ")";
+      return fail(IETI_ERR_NOT_SPD);
+    }
+    if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * nc), err))) return fail(rc);
+    k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv);
+    CK(cudaStreamSynchronize(d->stream));
+    cudaFree(Sc);
+    d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
+    d->bytes -= (int64_t)(ldc * ldc) * 8;
+  }
+  CK(cudaStreamSynchronize(d->stream));
+  CK(cudaGetLastError());
+  cudaFree(D);
+  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)D));
+  d->bytes -= hdoff[np_] * 8;
+  size_t smem = (size_t)std::max(d->max_ni, 1) * sizeof(double);
+  if (smem > 48 * 1024) {
+    CK(cudaFuncSetAttribute(k_trsv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_trsv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  // algorithmic bytes of one PCG iteration: H and Psi once each (F apply), P once
+  // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
+  d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
+                  8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
+  d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  (void)maxnp;
+  *out = d;
+  return IETI_OK;
+}
+
+int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std::string &err) {
+  CK(cudaSetDevice(d->device));
+  CK(cudaMemcpyAsync(d->j, j, d->n_edges * sizeof(double),
+                     j_mem == IETI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d->stream));
+  CK(cudaEventRecord(d->ev0, d->stream));
+  int rc = d->mixed ? step_impl<float>(d, st, err) : step_impl<double>(d, st, err);
+  CK(cudaEventRecord(d->ev1, d->stream));
+  CK(cudaEventSynchronize(d->ev1));
+  if (st) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, d->ev0, d->ev1);
+    st->t_step_ms = ms;
+  }
+  return rc;
+}
+
+int device_solution(DeviceState *d, double *a, int64_t len, int mem, std::string &err) {
+  CK(cudaSetDevice(d->device));
+  CK(cudaMemcpyAsync(a, d->a, len * sizeof(double),
+                     mem == IETI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return IETI_OK;
+}
+
+int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std::string &err) {
+  CK(cudaSetDevice(d->device));
+  CK(cudaMemcpyAsync(d->a, a, len * sizeof(double),
+                     mem == IETI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d->stream));
+  // eliminated entries are 0 by definition: rebuild them from the owner map
+  CK(cudaMemsetAsync(d->kx, 0, d->NK * sizeof(double), d->stream));
+  k_gather_kept<<<grid_for(d->NK, 256), 256, 0, d->stream>>>(d->NK, d->kglob, d->a, d->kx);
+  CK(cudaMemsetAsync(d->a, 0, d->n_edges * sizeof(double), d->stream));
+  k_owner_add<<<grid_for(d->NK, 256), 256, 0, d->stream>>>(d->NK, d->kglob, d->kown, d->kx, d->a);
+  CK(cudaStreamSynchronize(d->stream));
+  return IETI_OK;
+}
+
+void device_info(const DeviceState *d, ieti_info *info) {
+  info->n_lambda = d->M;
+  info->n_coarse = d->NC;
+  info->bytes_iter = d->bytes_iter;
+  info->bytes_device = d->bytes;
+  info->t_setup_device_ms = d->t_setup_ms;
+  info->kernel_launches_setup = d->launches_setup;
+}
+
+void device_destroy(DeviceState *d) {
+  if (!d) return;
+  if (d->device >= 0) cudaSetDevice(d->device);
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  for (void *p : d->allocs) cudaFree(p);
+  if (d->h_sc) cudaFreeHost(d->h_sc);
+  if (d->ev0) cudaEventDestroy(d->ev0);
+  if (d->ev1) cudaEventDestroy(d->ev1);
+  delete d;
+}
+
+}  // namespace ieti

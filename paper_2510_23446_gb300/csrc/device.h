@@ -1,0 +1,19 @@
+// Device part of the solver: dense batched setup of the local Schur complements
+// and the per-step dual-primal PCG (Sec. 3), orchestrated on one CUDA stream.
+#pragma once
+#include <string>
+
+#include "host_setup.h"
+
+namespace ieti {
+
+struct DeviceState;
+
+int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out, std::string &err);
+int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std::string &err);
+int device_solution(DeviceState *d, double *a, int64_t len, int mem, std::string &err);
+int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std::string &err);
+void device_info(const DeviceState *d, ieti_info *info);
+void device_destroy(DeviceState *d);
+
+}  // namespace ieti

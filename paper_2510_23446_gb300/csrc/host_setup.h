@@ -1,0 +1,93 @@
+// Host-side setup of the tree-cotree IETI-DP solver: spline spaces and patch
+// matrices (Sec. 2.2), lattice numbering, the hierarchical tree-cotree gauge and
+// e/p/r classes (Sec. 3), multipliers and the primal map.  Pure C++17.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ieti.h"
+
+namespace ieti {
+
+enum : int8_t { CLS_E = 0, CLS_P = 1, CLS_R = 2 };
+
+struct Csr {                       // square CSR, sorted columns
+  int n = 0;
+  std::vector<int32_t> ptr, col;
+  std::vector<double> val;
+};
+
+struct Patch {
+  int a = 0, b = 0, c = 0;
+  int p[3]{}, ne[3]{}, n[3]{};     // degree, elements, H^1 functions per direction
+  int n_dofs = 0;                  // local edge DOFs
+  std::vector<int64_t> l2g;        // local DOF -> global edge
+  Csr K, M;                        // local numbering, same pattern
+  // decomposition (local DOF ids, ascending)
+  std::vector<int32_t> i_loc, b_loc, p_loc;
+  // kept numbering [i | b | p]
+  int ni = 0, nb = 0, np = 0;
+  Csr Wk, Mk;                      // W = M + dt K and M in the kept numbering
+  std::vector<int64_t> kept_glob;  // kept index -> global edge
+  std::vector<double> load_w;      // kept index -> 1/n_share
+};
+
+struct Multiplier {                // lambda = (copy in s) - (copy in t), s < t
+  int64_t edge;
+  int32_t s, pos_s, t, pos_t;      // pos_* = index inside that patch's b-list
+};
+
+struct HostSetup {
+  // problem
+  int P[3]{};
+  std::vector<int32_t> n_el[3], degree[3];          // [d][slab]
+  std::vector<std::vector<double>> knots[3];        // [d][slab] full knot vector
+  std::vector<double> ctrl;                         // as given
+  std::vector<int64_t> ctrl_off;                    // per patch offset (doubles)
+  std::vector<double> sigma_el, nu_el;
+  std::vector<int64_t> el_off;
+  double dt = 0;
+  int threads = 0;
+  // lattice
+  std::vector<int64_t> off[3];
+  int64_t N[3]{}, E[3]{}, edge_off[3]{};
+  int64_t n_edges = 0, n_nodes = 0;
+  std::vector<uint8_t> is_sb[3];                    // lattice index on a slab plane
+  // per edge
+  std::vector<uint8_t> dirichlet, kind, n_share, touch_c, touch_i, gtype, in_graph, tree;
+  std::vector<int8_t> cls;
+  std::vector<uint8_t> cnode;                       // per node
+  // patches and decomposition
+  std::vector<Patch> patches;
+  std::vector<Multiplier> lam;
+  int64_t n_coarse = 0;
+  std::vector<int64_t> coarse_of_edge;              // -1 unless primal
+  std::vector<int64_t> free_edges;                  // r + p, ascending
+  double t_ms = 0;
+
+  int build(const ieti_problem *pr, int threads, std::string &err);
+  // helpers
+  int64_t edge_id(int d, int64_t I, int64_t J, int64_t K) const;
+  void edge_coords(int64_t g, int &d, int64_t &I, int64_t &J, int64_t &K) const;
+  int64_t node_id(int64_t I, int64_t J, int64_t K) const { return I + N[0] * (J + N[1] * K); }
+  bool boundary_node(int64_t n) const;
+  int slab_start(int d, int64_t I) const;
+  int n_patches() const { return P[0] * P[1] * P[2]; }
+  // load vector of a coil potential, global numbering
+  void coil_load(const ieti_coil &coil, double *out) const;
+
+ private:
+  int validate(const ieti_problem *pr, std::string &err);
+  void lattice();
+  void assemble_all();
+  void assemble_patch(Patch &pt) const;
+  void regions();
+  void build_tree();
+  void bfs_pass(const std::vector<int64_t> &edges, std::vector<uint8_t> &visited,
+                const std::vector<int64_t> &u, const std::vector<int64_t> &v);
+  void classify();
+  void decompose();
+};
+
+}  // namespace ieti

@@ -1,0 +1,209 @@
+"""ctypes binding of the C ABI declared in include/ieti.h (same names, marshalling only).
+
+Device buffers may be passed as torch CUDA tensors (their data pointer is used);
+host buffers as numpy arrays.  Nothing here computes: every step runs in
+``libieti.so``, and importing this module raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libieti.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_2510_23446_gb300.build.build()")
+lib = C.CDLL(LIB_PATH)
+
+IETI_MEM_HOST, IETI_MEM_DEVICE = 0, 1
+PREC = {"fp64": 0, "mixed": 1}
+PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
+ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
+          -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE"}
+
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+
+
+class ieti_problem(C.Structure):
+    _fields_ = [("n_patches", C.c_int32 * 3), ("n_el", _i32p * 3), ("degree", _i32p * 3),
+                ("knots", _dp * 3), ("ctrl_pts", _dp), ("sigma_el", _dp), ("nu_el", _dp),
+                ("dt", C.c_double), ("primal_mode", C.c_int32)]
+
+
+class ieti_options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
+                ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
+                ("max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("host_threads", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class ieti_coil(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("J0", "r_in", "r_out", "xc", "yc", "zc", "hz")]
+
+
+class ieti_stats(C.Structure):
+    _fields_ = [("cg_its", C.c_int32), ("sweeps", C.c_int32), ("rel_res", C.c_double),
+                ("outer_res", C.c_double), ("t_step_ms", C.c_double)]
+
+
+class ieti_info(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("n_free", C.c_int64), ("n_lambda", C.c_int64),
+                ("n_coarse", C.c_int64), ("sum_ni", C.c_int64), ("sum_nb", C.c_int64),
+                ("sum_np", C.c_int64), ("max_n", C.c_int64), ("bytes_iter", C.c_int64),
+                ("bytes_device", C.c_int64), ("t_setup_host_ms", C.c_double),
+                ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64)]
+
+
+_ctx = C.c_void_p
+lib.ieti_setup.argtypes = [C.POINTER(ieti_problem), C.POINTER(ieti_options), C.POINTER(_ctx)]
+lib.ieti_setup.restype = C.c_int
+lib.ieti_setup_error.restype = C.c_char_p
+lib.ieti_num_dofs.argtypes = [_ctx]
+lib.ieti_num_dofs.restype = C.c_int64
+lib.ieti_get_info.argtypes = [_ctx, C.POINTER(ieti_info)]
+lib.ieti_load_vector.argtypes = [_ctx, C.POINTER(ieti_coil), C.c_void_p]
+lib.ieti_dof_classes.argtypes = [_ctx, C.c_void_p, C.c_void_p]
+lib.ieti_patch_csr.argtypes = [_ctx, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                               C.c_void_p, C.c_void_p, C.c_void_p]
+lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
+lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
+lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
+lib.ieti_last_error.argtypes = [_ctx]
+lib.ieti_last_error.restype = C.c_char_p
+lib.ieti_destroy.argtypes = [_ctx]
+lib.ieti_destroy.restype = None
+
+EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
+            "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
+            "ieti_last_error", "ieti_destroy"]
+
+
+class IetiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Raw address of a numpy array (host) or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, IETI_MEM_HOST
+    dp = getattr(x, "data_ptr", None)
+    if dp is not None:
+        return dp(), (IETI_MEM_DEVICE if x.is_cuda else IETI_MEM_HOST)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class Solver:
+    """One IETI-DP context (ieti_setup ... ieti_destroy)."""
+
+    def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
+                 precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
+                 outer_tol=1e-12, max_sweeps=None, use_graph=0, host_threads=0, stream=None):
+        self._keep = []
+
+        def arr(x, dt_):
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt_))
+            self._keep.append(a)
+            return a
+        pr = ieti_problem()
+        for d in range(3):
+            pr.n_patches[d] = int(P[d])
+            pr.n_el[d] = arr(n_el[d], np.int32).ctypes.data_as(_i32p)
+            pr.degree[d] = arr(degree[d], np.int32).ctypes.data_as(_i32p)
+            pr.knots[d] = arr(knots[d], np.float64).ctypes.data_as(_dp)
+        pr.ctrl_pts = arr(ctrl, np.float64).ctypes.data_as(_dp)
+        pr.sigma_el = arr(sigma_el, np.float64).ctypes.data_as(_dp)
+        pr.nu_el = arr(nu_el, np.float64).ctypes.data_as(_dp)
+        pr.dt = float(dt)
+        pr.primal_mode = 0
+        op = ieti_options()
+        op.device = int(device)
+        op.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        op.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+        op.cg_tol = float(cg_tol)
+        op.cg_max_it = int(cg_max_it)
+        op.outer_tol = float(outer_tol)
+        if max_sweeps is None:
+            max_sweeps = 1 if op.precision == 0 else 20
+        op.max_sweeps = int(max_sweeps)
+        op.use_graph = int(use_graph)
+        op.host_threads = int(host_threads)
+        op.cuda_stream = C.c_void_p(stream or 0)
+        self.options = op
+        self.ctx = _ctx()
+        rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
+        self._keep = []
+        if rc != 0:
+            raise IetiError(rc, lib.ieti_setup_error().decode())
+        self.n = int(lib.ieti_num_dofs(self.ctx))
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob.P, prob.n_el, prob.degree, prob.knots, prob.ctrl, prob.sigma_el,
+                   prob.nu_el, prob.dt, **kw)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise IetiError(rc, lib.ieti_last_error(self.ctx).decode())
+
+    def info(self):
+        inf = ieti_info()
+        self._check(lib.ieti_get_info(self.ctx, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in ieti_info._fields_}
+
+    def load_vector(self, coil):
+        c = ieti_coil(**{k: float(coil[k]) for k, _ in ieti_coil._fields_})
+        out = np.zeros(self.n)
+        self._check(lib.ieti_load_vector(self.ctx, C.byref(c), out.ctypes.data))
+        return out
+
+    def dof_classes(self):
+        cls = np.zeros(self.n, dtype=np.int8)
+        tree = np.zeros(self.n, dtype=np.int8)
+        self._check(lib.ieti_dof_classes(self.ctx, cls.ctypes.data, tree.ctypes.data))
+        return cls, tree
+
+    def patch_csr(self, s, which):
+        n = C.c_int32()
+        nnz = C.c_int64()
+        self._check(lib.ieti_patch_csr(self.ctx, s, which, C.byref(n), C.byref(nnz), None, None, None))
+        ptr = np.zeros(n.value + 1, dtype=np.int32)
+        col = np.zeros(nnz.value, dtype=np.int32)
+        val = np.zeros(nnz.value)
+        self._check(lib.ieti_patch_csr(self.ctx, s, which, None, None, ptr.ctypes.data,
+                                       col.ctypes.data, val.ctypes.data))
+        return ptr, col, val
+
+    def step(self, j, raise_on_error=True):
+        p, mem = _ptr(j)
+        st = ieti_stats()
+        rc = lib.ieti_step(self.ctx, C.c_void_p(p), mem, C.byref(st))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        return {k: getattr(st, k) for k, _ in ieti_stats._fields_} | {"rc": rc}
+
+    def solution(self, out=None):
+        if out is None:
+            out = np.zeros(self.n)
+        p, mem = _ptr(out)
+        self._check(lib.ieti_solution(self.ctx, C.c_void_p(p), self.n, mem))
+        return out
+
+    def set_state(self, a):
+        p, mem = _ptr(a)
+        self._check(lib.ieti_set_state(self.ctx, C.c_void_p(p), self.n, mem))
+
+    def close(self):
+        if self.ctx:
+            lib.ieti_destroy(self.ctx)
+            self.ctx = _ctx()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
