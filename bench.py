@@ -1,0 +1,299 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 tree-cotree IETI-DP solver: implicit-Euler time steps/s and
+PCG iterations/s on the 64-patch curved p=2 workload (4x4x4 patches of 8^3 elements,
+inner cube sigma = 1e2, coil J0 = 1e2, dt = 1e-3), mixed+batched vs FP64.
+
+One bench "step" = one implicit-Euler step of Eq. (11) through the C ABI: RHS,
+interior condensation, dual-primal PCG, recovery, FP64 defect correction of the
+assembled system (both paths stop on the same assembled FP64 residual, so they
+reach the same final accuracy).  Setup (assembly, gauge, batched factorizations)
+is timed separately.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s and CG its/s, mixed+batched vs FP64 on GB300 at rel. L2 err ≤1e-8"
+WORKLOAD = ("c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
+            "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3")
+OUTER_TOL = 1e-11
+OPTS = {
+    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20),
+    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, outer_tol=OUTER_TOL, max_sweeps=20),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (median SM clock under load, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (IndexError, ValueError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, budget_s, tol=1e-10):
+    """The oracle's dual-primal step (as it stands) on the same workload, on the host
+    cores: setup first (not part of the rate), then as many whole time steps as fit
+    in the budget (at least one)."""
+    from oracle.stepping import OracleProblem
+    from oracle.ietidp import PRECOND_STIFF, local_rhs, gather_global
+    import numpy as np
+    t0 = time.perf_counter()
+    op = OracleProblem(prob)
+    I = op.ietidp(PRECOND_STIFF)
+    t_setup = time.perf_counter() - t0
+    a = np.zeros(op.asm.lat.n_edges)
+    steps, its, t = 0, 0, 0.0
+    while steps == 0 or t < budget_s:
+        t1 = time.perf_counter()
+        a_loc, lam, it, res = I.solve(local_rhs(op.dec, a, op.asm.j_global), tol)
+        a = gather_global(op.dec, a_loc)
+        t += time.perf_counter() - t1
+        steps += 1
+        its += it
+        if steps >= 20:
+            break
+    return {"value": steps / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cg_its_per_s": its / t, "setup_s": t_setup,
+            "sample": f"{steps} whole time step(s) of the c2 workload (oracle IETI-DP, dense LAPACK local "
+                      f"solves, PCG tol {tol}, stiffness-scaled Dirichlet); oracle setup {t_setup:.1f} s excluded"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle is the reference arm (no reference code exists)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from workloads import make_problem
+    prob = make_problem("c2")
+    cb = cpu_baseline(prob, budget_s=args.cpu_seconds)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "oracle IETI-DP (CPU, FP64)"},
+            "cg_its_per_s": cb["cg_its_per_s"],
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
+    S = ieti.Solver.from_problem(prob, device=dev, stream=stream, profile=1, **OPTS[mode])
+    t_setup = S.info()
+    j = S.load_vector(prob.coil)
+    jd = torch.from_numpy(j).to(f"cuda:{dev}")
+    for _ in range(W):
+        S.step(jd)
+    S.kernel_stats(reset=True)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    its, launches, sweeps = 0, 0, 0
+    if clocks:
+        clocks.start()
+    for k in range(K):
+        flush_buf.zero_()                      # evict L2 between timed steps (256 MiB write)
+        ev[k][0].record()
+        st = S.step(jd)
+        ev[k][1].record()
+        its += st["cg_its"]
+        launches += st["kernel_launches"]
+        sweeps += st["sweeps"]
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    kst = S.kernel_stats(reset=True)
+    state = S.solution()
+    return S, dict(ms=ms, its=its, launches=launches, sweeps=sweeps, setup=t_setup, kstats=kst, clocks=clk,
+                   state=state, j=j, outer_res=st["outer_res"])
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    from workloads import make_problem
+    prob = make_problem("c2")
+    # the CPU oracle leg runs before the library touches the GPU
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(prob, budget_s=args.cpu_seconds)
+    from paper_2510_23446_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_2510_23446_gb300 import ieti
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    K, W = args.steps, max(3, args.warmup)
+    results = {}
+    for mode in ("fp64", "mixed"):
+        if world > 1:
+            dist.barrier()
+        clocks = Clocks(dev) if mode == "mixed" else None
+        S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks)
+        results[mode] = (S, r)
+    # end-to-end through the public API with host buffers (pinned), mixed path
+    S, r = results["mixed"]
+    jh = torch.from_numpy(r["j"]).pin_memory()
+    ah = torch.empty(S.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        S.step(jh)
+        S.solution(ah)
+    e2e_s = time.perf_counter() - t0
+    # timing over ranks: max
+    tot = {m: sum(results[m][1]["ms"]) / 1e3 for m in results}
+    if world > 1:
+        t = torch.tensor([tot["mixed"], tot["fp64"], e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot["mixed"], tot["fp64"], e2e_s = t.tolist()
+    rm, rf = results["mixed"][1], results["fp64"][1]
+    # the two paths ran the same number of steps from a^0 = 0: compare states
+    err = float(np.linalg.norm(rm["state"] - rf["state"]) / np.linalg.norm(rf["state"]))
+    # roofline of the dominant kernel class (largest share of event time in the mixed run)
+    pk, pk_src = peaks()
+    ks = rm["kstats"]
+    dom = max(ks, key=lambda k: ks[k]["total_ms"])
+    avg_ms = ks[dom]["total_ms"] / max(ks[dom]["launches"], 1)
+    bytes_per = ks[dom]["bytes"] / max(ks[dom]["launches"], 1)
+    achieved = bytes_per / (avg_ms * 1e-3) / 1e9
+    step_ms = tot["mixed"] * 1e3 / K
+    info = results["mixed"][0].info()
+    line = {
+        "metric": METRIC,
+        "value": world * K / tot["mixed"],
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": info["n_dofs"], "n_free": info["n_free"],
+                   "n_lambda": info["n_lambda"], "n_coarse": info["n_coarse"],
+                   "precond": "dirichlet_stiff", "inner_cg_tol": OPTS["mixed"]["cg_tol"],
+                   "outer_tol": OUTER_TOL, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "cg_its_per_s": world * rm["its"] / tot["mixed"],
+        "cg_its_per_step": rm["its"] / K,
+        "sweeps_per_step": rm["sweeps"] / K,
+        "rel_err_vs_fp64": err,
+        "fp64": {"value": world * K / tot["fp64"], "unit": "steps/s", "ms_per_step": tot["fp64"] * 1e3 / K,
+                 "cg_its_per_s": world * rf["its"] / tot["fp64"], "cg_its_per_step": rf["its"] / K,
+                 "sweeps_per_step": rf["sweeps"] / K},
+        "setup_ms": {"mixed_host": rm["setup"]["t_setup_host_ms"], "mixed_device": rm["setup"]["t_setup_device_ms"],
+                     "fp64_host": rf["setup"]["t_setup_host_ms"], "fp64_device": rf["setup"]["t_setup_device_ms"]},
+        "clocks": rm["clocks"],
+        "e2e": {"value": world * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 8 * S.n,
+                "d2h_bytes_per_step": 8 * S.n},
+        "gpu_launches": rm["launches"],
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms,
+                     "share_of_step": ks[dom]["total_ms"] / (tot["mixed"] * 1e3),
+                     "peak_source": f"{pk_src} hbm_gbs (copy)"},
+        "kernel_classes_ms_per_step": {k: v["total_ms"] / K for k, v in ks.items() if v["launches"]},
+    }
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for m in results:
+        results[m][0].close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

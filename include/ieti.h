@@ -89,6 +89,7 @@ typedef struct {
   int32_t use_graph;     /* capture the PCG iteration in a CUDA graph */
   int32_t host_threads;  /* threads for the host setup (0 = all cores) */
   void *cuda_stream;     /* cudaStream_t (0 = legacy default stream) */
+  int32_t profile;       /* 1: time every launch of the operator kernels with CUDA events (ieti_kernel_stats) */
 } ieti_options;
 
 /* Coil source through its potential T = T_z(r) chi(|z - zc| < hz) e_z (J = curl T):
@@ -104,6 +105,7 @@ typedef struct {
   double rel_res;        /* last PCG relative residual */
   double outer_res;      /* ||f - W a|| / ||f|| after the step (FP64) */
   double t_step_ms;      /* device time of the step (CUDA events) */
+  int64_t kernel_launches; /* kernels this library launched for the step */
 } ieti_stats;
 
 typedef struct {
@@ -118,6 +120,23 @@ typedef struct {
   double t_setup_host_ms, t_setup_device_ms;
   int64_t kernel_launches_setup;
 } ieti_info;
+
+/* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
+#define IETI_K_GEMV_H 0   /* [F_s; Psi_s^T] u: dual operator and primal right-hand side, one launch per F apply */
+#define IETI_K_GEMV_Q 1   /* Psi_s q: primal correction */
+#define IETI_K_GEMV_P 2   /* S_bb u: Dirichlet preconditioner */
+#define IETI_K_GEMV_S 3   /* S_c^{-1} c: coarse solve */
+#define IETI_K_GEMV_Y 4   /* interior condensation / recovery GEMVs */
+#define IETI_K_TRSV 5     /* batched triangular solves with L_ii */
+#define IETI_K_SPMV 6     /* FP64 sparse M a, W a */
+#define IETI_K_VEC 7      /* gathers, jumps, dots, axpys */
+#define IETI_K_NCLASS 8
+
+typedef struct {
+  int64_t launches;
+  double total_ms;       /* sum of CUDA-event durations */
+  double bytes;          /* algorithmic bytes moved by those launches (operator entries + vectors, once) */
+} ieti_kernel_stat;
 
 typedef struct ieti_ctx ieti_ctx;
 
@@ -160,6 +179,10 @@ int ieti_solution(const ieti_ctx *ctx, double *a_out, int64_t len, int32_t out_m
 
 /* Replace the state a^l (checkpoint resume); e entries are ignored. */
 int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem);
+
+/* Per-class kernel statistics accumulated since the last reset (options.profile = 1);
+ * out has IETI_K_NCLASS entries.  reset != 0 clears the counters after reading. */
+int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);
 
 const char *ieti_last_error(const ieti_ctx *ctx);
 /* Message of the last failed ieti_setup (no context exists then). */

@@ -136,6 +136,13 @@ int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem) {
   return ieti::device_set_state(ctx->dev, a, len, a_mem, ctx->err);
 }
 
+int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset) {
+  if (!ctx || !out) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) return IETI_ERR_NO_DEVICE;
+  ieti::device_kernel_stats(ctx->dev, out, reset != 0);
+  return IETI_OK;
+}
+
 const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 void ieti_destroy(ieti_ctx *ctx) {

@@ -674,7 +674,47 @@ struct DeviceState {
   double *part = nullptr, *sc = nullptr, *h_sc = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dt = 0;
+  // kernel-class profiler (options.profile)
+  ieti_kernel_stat kstat[IETI_K_NCLASS] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pend { int cls; int e0; double bytes; };
+  std::vector<Pend> pend;
+  int ev_used = 0;
+  double gemv_bytes[IETI_K_NCLASS] = {};  // algorithmic bytes of one launch per GEMV class
+  int64_t nlaunch = 0;                    // kernels launched by the current step
 };
+
+// event pair around one launch of a kernel class (no-op unless profiling)
+static void prof_begin(DeviceState *d, int cls, double bytes) {
+  if (!d->opt.profile) return;
+  if (d->ev_used + 2 > (int)d->ev_pool.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      d->ev_pool.push_back(e);
+    }
+  }
+  d->pend.push_back({cls, d->ev_used, bytes});
+  cudaEventRecord(d->ev_pool[d->ev_used], d->stream);
+  d->ev_used += 2;
+}
+static void prof_end(DeviceState *d) {
+  if (!d->opt.profile) return;
+  cudaEventRecord(d->ev_pool[d->pend.back().e0 + 1], d->stream);
+}
+static void prof_collect(DeviceState *d) {
+  if (!d->opt.profile || d->pend.empty()) return;
+  cudaStreamSynchronize(d->stream);
+  for (auto &p : d->pend) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, d->ev_pool[p.e0], d->ev_pool[p.e0 + 1]);
+    d->kstat[p.cls].launches++;
+    d->kstat[p.cls].total_ms += ms;
+    d->kstat[p.cls].bytes += p.bytes;
+  }
+  d->pend.clear();
+  d->ev_used = 0;
+}
 
 template <class T>
 static int dalloc(DeviceState *d, T **ptr, size_t n, std::string &err) {
@@ -714,12 +754,15 @@ static inline unsigned grid_for(int64_t n, int block) { return (unsigned)std::ma
 
 template <class T>
 static void gemv(DeviceState *d, const DeviceState::Desc &D, const void *A, const double *x, double *y,
-                 const double *y0, double alpha, double beta) {
+                 const double *y0, double alpha, double beta, int cls) {
   if (D.n == 0) return;
+  prof_begin(d, cls, d->gemv_bytes[cls]);
   int64_t warps = D.n;
   unsigned blocks = (unsigned)std::min<int64_t>((warps * 32 + GEMV_BLOCK - 1) / GEMV_BLOCK, 152 * 16);
   k_gemv_rows<T><<<blocks, GEMV_BLOCK, 0, d->stream>>>(D.n, D.aoff, D.xoff, D.yidx, D.ncol, (const T *)A, x, y, y0,
                                                         alpha, beta);
+  d->nlaunch++;
+  prof_end(d);
 }
 
 // partial Cholesky over all patches (host loop over panels)
@@ -743,12 +786,15 @@ static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int3
       max_tiles = std::max(max_tiles, T64 * (T64 + 1) / 2);
     }
     k_potrf_diag<T><<<nbatch, 256, 0, d->stream>>>(base, off, ld, dkb, dke, j, status);
+    d->nlaunch++;
     d->launches_setup++;
     if (max_rows > 0) {
       dim3 g1(grid_for(max_rows, 128), nbatch);
       k_trsm_panel<T><<<g1, 128, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      d->nlaunch++;
       dim3 g2(max_tiles, nbatch);
       k_syrk_update<T><<<g2, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      d->nlaunch++;
       d->launches_setup += 2;
     }
   }
@@ -762,12 +808,14 @@ static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int3
 template <class T>
 static void condensed(DeviceState *d, const double *u, const double *gp) {
   cudaStream_t st = d->stream;
-  gemv<T>(d, d->dH, d->H, u, d->bp, nullptr, 1.0, 0.0);
+  gemv<T>(d, d->dH, d->H, u, d->bp, nullptr, 1.0, 0.0, IETI_K_GEMV_H);
   if (d->NC > 0) {
     k_coarse_gather<<<grid_for(d->NC, 256), 256, 0, st>>>((int)d->NC, d->cptr, d->cpos, gp, d->bp + d->NBt, d->cc);
-    gemv<double>(d, d->dS, d->Sinv, d->cc, d->q, nullptr, 1.0, 0.0);
+    d->nlaunch++;
+    gemv<double>(d, d->dS, d->Sinv, d->cc, d->q, nullptr, 1.0, 0.0, IETI_K_GEMV_S);
     k_pgather<<<grid_for(d->NPt, 256), 256, 0, st>>>(d->NPt, d->pc, d->q, d->qloc);
-    gemv<T>(d, d->dQ, d->Q, d->qloc, d->bp, d->bp, -1.0, 1.0);
+    d->nlaunch++;
+    gemv<T>(d, d->dQ, d->Q, d->qloc, d->bp, d->bp, -1.0, 1.0, IETI_K_GEMV_Q);
   }
 }
 
@@ -775,8 +823,10 @@ template <class T>
 static void apply_F(DeviceState *d, const double *v, double *out, const double *dotv, double *part) {
   cudaStream_t st = d->stream;
   k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, d->bt_sgn, v, nullptr, 1.0, d->ub);
+  d->nlaunch++;
   condensed<T>(d, d->ub, nullptr);
   k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, out, dotv, part);
+  d->nlaunch++;
 }
 
 template <class T>
@@ -786,14 +836,17 @@ static void apply_precond(DeviceState *d, const double *rv, double *out, const d
   if (pcnd == IETI_PRECOND_NONE) {
     cudaMemcpyAsync(out, rv, d->M * sizeof(double), cudaMemcpyDeviceToDevice, st);
     k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(d->M, out, dotv, part);
+    d->nlaunch++;
     return;
   }
   bool scaled = pcnd != IETI_PRECOND_DIRICHLET;
   k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, scaled ? d->bt_wd : d->bt_sgn, rv,
                                                nullptr, 1.0, d->ub);
-  gemv<T>(d, d->dP, d->P, d->ub, d->bp, nullptr, 1.0, 0.0);
+  d->nlaunch++;
+  gemv<T>(d, d->dP, d->P, d->ub, d->bp, nullptr, 1.0, 0.0, IETI_K_GEMV_P);
   k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, scaled ? d->lam_wp : nullptr,
                                      scaled ? d->lam_wm : nullptr, d->bp, out, dotv, part);
+  d->nlaunch++;
 }
 
 static int read_scalar(DeviceState *d, int idx, double *out, std::string &err) {
@@ -814,7 +867,9 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
   CK(cudaMemsetAsync(d->lam, 0, m * sizeof(double), st));
   CK(cudaMemcpyAsync(d->r, d->dvec, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(m, d->r, d->r, d->part);
+  d->nlaunch++;
   k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_DD, 0);
+  d->nlaunch++;
   double dd;
   int rc = read_scalar(d, SC_DD, &dd, err);
   if (rc) return rc;
@@ -822,13 +877,17 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
   double tol2 = d->opt.cg_tol * d->opt.cg_tol * dd;
   apply_precond<T>(d, d->r, d->z, d->r, d->part);
   k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RZ, 0);
+  d->nlaunch++;
   CK(cudaMemcpyAsync(d->p, d->z, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   double rr = dd;
   for (int it = 1; it <= d->opt.cg_max_it; ++it) {
     apply_F<T>(d, d->p, d->Fp, d->p, d->part);
     k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_PQ, 1);
+    d->nlaunch++;
     k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(m, d->sc, d->p, d->Fp, d->lam, d->r, d->part);
+    d->nlaunch++;
     k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RR, 0);
+    d->nlaunch++;
     rc = read_scalar(d, SC_RR, &rr, err);
     if (rc) return rc;
     *its = it;
@@ -839,7 +898,9 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
     if (rr <= tol2) break;
     apply_precond<T>(d, d->r, d->z, d->r, d->part);
     k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_RZNEW, 2);
+    d->nlaunch++;
     k_p_update<<<RED_BLOCKS, 256, 0, st>>>(m, d->sc, d->z, d->p);
+    d->nlaunch++;
   }
   *rel = std::sqrt(rr / dd);
   CK(cudaGetLastError());
@@ -859,26 +920,39 @@ static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, st
   size_t smem = (size_t)std::max(d->max_ni, 1) * sizeof(double);
   // interior condensation: z_i = L_ii^{-1} rhs_i; g_[bp] = rhs_[bp] - Y z_i
   CK(cudaMemcpyAsync(d->kz, rhs, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  prof_begin(d, IETI_K_TRSV, d->gemv_bytes[IETI_K_TRSV]);
   k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kz, 0);
-  gemv<T>(d, d->dY, d->LY, d->kz, d->kz, rhs, -1.0, 1.0);
+  d->nlaunch++;
+  prof_end(d);
+  gemv<T>(d, d->dY, d->LY, d->kz, d->kz, rhs, -1.0, 1.0, IETI_K_GEMV_Y);
   k_kept_to_bp<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->kz, d->gb,
                                                                  d->gp);
+  d->nlaunch++;
   // d = B (F g_b - Psi S_c^{-1} sum A^T (g_p - Psi^T g_b))
   condensed<T>(d, d->gb, d->gp);
   k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, d->dvec, nullptr, nullptr);
+  d->nlaunch++;
   int rc = pcg<T>(d, its, rel, err);
   if (rc && rc != IETI_ERR_CG_NOT_CONVERGED) return rc;
   int cg_rc = rc;
   // recovery: v_b = g_b - B^T lambda; a_b = F v_b - Psi q, a_p = q
   k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, d->bt_sgn, d->lam, d->gb, -1.0, d->ub);
+  d->nlaunch++;
   condensed<T>(d, d->ub, d->gp);
   CK(cudaMemcpyAsync(d->kx, d->kz, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
   k_bp_to_kept<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->pc, d->bp,
                                                                  d->q, d->kx);
+  d->nlaunch++;
   // interior: a_i = L_ii^{-T} (z_i - Y^T a_[bp])
   dim3 gT(grid_for(d->max_ni, 128), d->np_);
+  prof_begin(d, IETI_K_GEMV_Y, d->gemv_bytes[IETI_K_GEMV_Y]);
   k_gemvT_Y<T><<<gT, 128, 0, st>>>(d->ni, d->nb, d->npp, d->lyoff, d->kofs, (const T *)d->LY, d->kx);
+  d->nlaunch++;
+  prof_end(d);
+  prof_begin(d, IETI_K_TRSV, d->gemv_bytes[IETI_K_TRSV]);
   k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kx, 1);
+  d->nlaunch++;
+  prof_end(d);
   CK(cudaGetLastError());
   return cg_rc;
 }
@@ -886,7 +960,9 @@ static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, st
 // assemble a kept-space vector over the free global DOFs (rglob), return its norm
 static int assemble_norm(DeviceState *d, const double *v, double *out, std::string &err) {
   k_assemble_free<<<RED_BLOCKS, 256, 0, d->stream>>>(d->NF, d->fptr, d->fpos, d->fglob, v, d->rglob, d->part);
+  d->nlaunch++;
   k_dot_final<<<1, 256, 0, d->stream>>>(RED_BLOCKS, d->part, d->sc, SC_TMP, 0);
+  d->nlaunch++;
   int rc = read_scalar(d, SC_TMP, out, err);
   *out = std::sqrt(*out);
   return rc;
@@ -898,8 +974,10 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   int64_t NK = d->NK;
   // f = M a^l + dt j^{l+1}  (kept space, load split 1/k over the k patches holding a DOF)
   k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
+  d->nlaunch++;
   k_rhs<<<grid_for(NK * 32, 256), 256, 0, st>>>(NK, d->mptr, d->mcol, d->mval, d->ka, d->kglob, d->kw, d->j, d->dt,
                                                  d->kf);
+  d->nlaunch++;
   double fn = 0.0;
   int rc;
   if ((rc = assemble_norm(d, d->kf, &fn, err))) return rc;
@@ -910,7 +988,10 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     // defect of the ASSEMBLED system at the current iterate, in FP64: r = f - W_g a,
     // redistributed over the patches with the 1/k weights (so that the local
     // right-hand sides of the correction are as small as the defect itself)
+    prof_begin(d, IETI_K_SPMV, d->gemv_bytes[IETI_K_SPMV]);
     k_resid<<<grid_for(NK * 32, 256), 256, 0, st>>>(NK, d->wptr, d->wcol, d->wval, d->ka, d->kf, d->kr);
+    d->nlaunch++;
+    prof_end(d);
     double rn;
     if ((rc = assemble_norm(d, d->kr, &rn, err))) return rc;
     ores = fn > 0 ? rn / fn : 0.0;
@@ -931,6 +1012,7 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     }
     prev = rn;
     k_distribute<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->kw, d->rglob, d->kr);
+    d->nlaunch++;
     int its = 0;
     rc = dd_solve<T>(d, d->kr, &its, &rel, err);
     its_total += its;
@@ -938,7 +1020,9 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     if (rc == IETI_ERR_CG_NOT_CONVERGED) cg_rc = rc;
     else if (rc) return rc;
     k_owner_add<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->kown, d->kx, d->a);
+    d->nlaunch++;
     k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
+    d->nlaunch++;
   }
   CK(cudaGetLastError());
   if (stats) {
@@ -1351,6 +1435,22 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
   d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
                   8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
+  {
+    // algorithmic bytes of one launch: every operator entry once, input vectors once per patch, outputs once
+    double e = (double)esz;
+    d->gemv_bytes[IETI_K_GEMV_H] = e * hh[np_] + 8.0 * (d->NBt + d->NBt + d->NPt);
+    d->gemv_bytes[IETI_K_GEMV_Q] = e * hq[np_] + 8.0 * (d->NPt + 2 * d->NBt);
+    d->gemv_bytes[IETI_K_GEMV_P] = e * hp[np_] + 8.0 * (2 * d->NBt);
+    d->gemv_bytes[IETI_K_GEMV_S] = 8.0 * (double)d->NC * d->NC + 16.0 * d->NC;
+    int64_t sy = 0, sl = 0;
+    for (int s = 0; s < np_; ++s) {
+      sy += (int64_t)(hnb[s] + hnp[s]) * hni[s];
+      sl += (int64_t)hni[s] * (hni[s] + 1) / 2;
+    }
+    d->gemv_bytes[IETI_K_GEMV_Y] = e * sy + 8.0 * (2 * (double)d->NK);
+    d->gemv_bytes[IETI_K_TRSV] = e * sl + 8.0 * 2 * (double)d->NK;
+    d->gemv_bytes[IETI_K_SPMV] = 12.0 * (double)wval.size() + 8.0 * 3 * (double)d->NK;
+  }
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   (void)maxnp;
   *out = d;
@@ -1362,13 +1462,16 @@ int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std:
   CK(cudaMemcpyAsync(d->j, j, d->n_edges * sizeof(double),
                      j_mem == IETI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d->stream));
   CK(cudaEventRecord(d->ev0, d->stream));
+  d->nlaunch = 0;
   int rc = d->mixed ? step_impl<float>(d, st, err) : step_impl<double>(d, st, err);
   CK(cudaEventRecord(d->ev1, d->stream));
   CK(cudaEventSynchronize(d->ev1));
+  prof_collect(d);
   if (st) {
     float ms = 0;
     cudaEventElapsedTime(&ms, d->ev0, d->ev1);
     st->t_step_ms = ms;
+    st->kernel_launches = d->nlaunch;
   }
   return rc;
 }
@@ -1403,8 +1506,16 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->kernel_launches_setup = d->launches_setup;
 }
 
+void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
+  prof_collect(d);
+  for (int c = 0; c < IETI_K_NCLASS; ++c) out[c] = d->kstat[c];
+  if (reset)
+    for (int c = 0; c < IETI_K_NCLASS; ++c) d->kstat[c] = ieti_kernel_stat{};
+}
+
 void device_destroy(DeviceState *d) {
   if (!d) return;
+  for (cudaEvent_t e : d->ev_pool) cudaEventDestroy(e);
   if (d->device >= 0) cudaSetDevice(d->device);
   if (d->stream) cudaStreamSynchronize(d->stream);
   for (void *p : d->allocs) cudaFree(p);

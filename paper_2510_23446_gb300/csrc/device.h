@@ -14,6 +14,7 @@ int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std:
 int device_solution(DeviceState *d, double *a, int64_t len, int mem, std::string &err);
 int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std::string &err);
 void device_info(const DeviceState *d, ieti_info *info);
+void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset);
 void device_destroy(DeviceState *d);
 
 }  // namespace ieti

@@ -37,7 +37,7 @@ class ieti_options(C.Structure):
     _fields_ = [("device", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("host_threads", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("profile", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -46,7 +46,14 @@ class ieti_coil(C.Structure):
 
 class ieti_stats(C.Structure):
     _fields_ = [("cg_its", C.c_int32), ("sweeps", C.c_int32), ("rel_res", C.c_double),
-                ("outer_res", C.c_double), ("t_step_ms", C.c_double)]
+                ("outer_res", C.c_double), ("t_step_ms", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+class ieti_kernel_stat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double)]
+
+
+KERNEL_CLASSES = ["gemv_H", "gemv_Q", "gemv_P", "gemv_S", "gemv_Y", "trsv", "spmv", "vec"]
 
 
 class ieti_info(C.Structure):
@@ -71,6 +78,7 @@ lib.ieti_patch_csr.argtypes = [_ctx, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
 lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
 lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
+lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
 lib.ieti_last_error.argtypes = [_ctx]
 lib.ieti_last_error.restype = C.c_char_p
 lib.ieti_destroy.argtypes = [_ctx]
@@ -78,7 +86,7 @@ lib.ieti_destroy.restype = None
 
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
-            "ieti_last_error", "ieti_destroy"]
+            "ieti_last_error", "ieti_destroy", "ieti_kernel_stats"]
 
 
 class IetiError(RuntimeError):
@@ -102,7 +110,7 @@ class Solver:
 
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
-                 outer_tol=1e-12, max_sweeps=None, use_graph=0, host_threads=0, stream=None):
+                 outer_tol=1e-12, max_sweeps=None, use_graph=0, host_threads=0, stream=None, profile=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -133,6 +141,7 @@ class Solver:
         op.use_graph = int(use_graph)
         op.host_threads = int(host_threads)
         op.cuda_stream = C.c_void_p(stream or 0)
+        op.profile = int(profile)
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
@@ -177,6 +186,12 @@ class Solver:
         self._check(lib.ieti_patch_csr(self.ctx, s, which, None, None, ptr.ctypes.data,
                                        col.ctypes.data, val.ctypes.data))
         return ptr, col, val
+
+    def kernel_stats(self, reset=False):
+        arr = (ieti_kernel_stat * len(KERNEL_CLASSES))()
+        self._check(lib.ieti_kernel_stats(self.ctx, C.cast(arr, C.c_void_p), int(reset)))
+        return {name: {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes}
+                for i, name in enumerate(KERNEL_CLASSES)}
 
     def step(self, j, raise_on_error=True):
         p, mem = _ptr(j)
