@@ -170,8 +170,10 @@ def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
     kst = S.kernel_stats(reset=True)
+    phases = S.pcg_phase_times(reset=True)
     state = S.solution()
     return S, dict(ms=ms, its=its, launches=launches, sweeps=sweeps, setup=t_setup, kstats=kst, clocks=clk,
+                   phases=phases,
                    state=state, j=j, outer_res=st["outer_res"])
 
 
@@ -275,6 +277,9 @@ def run_ours(args):
                      "share_of_step": ks[dom]["total_ms"] / (tot["mixed"] * 1e3),
                      "peak_source": f"{pk_src} hbm_gbs (copy)"},
         "kernel_classes_ms_per_step": {k: v["total_ms"] / K for k, v in ks.items() if v["launches"]},
+        "pcg_phase_us": {"phases": ["P1 B^T p, [F;Psi^T]", "P2 coarse rhs", "P3 S_c^-1", "P4 Psi q",
+                                    "P5 update+precond", "P6 jump+dot"],
+                         "work": rm["phases"]["work_us"], "barrier_wait": rm["phases"]["wait_us"]},
     }
     if cb is not None:
         line["cpu_baseline"] = cb

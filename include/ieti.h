@@ -86,7 +86,7 @@ typedef struct {
   int32_t cg_max_it;
   double outer_tol;      /* refinement stop: ||f - W a|| <= outer_tol * ||f|| (FP64 residual) */
   int32_t max_sweeps;    /* refinement sweeps per step (FP64 mode: 1 suffices) */
-  int32_t use_graph;     /* capture the PCG iteration in a CUDA graph */
+  int32_t pcg_mode;      /* 0: PCG as one persistent cooperative kernel (default); 1: one launch per phase */
   int32_t host_threads;  /* threads for the host setup (0 = all cores) */
   void *cuda_stream;     /* cudaStream_t (0 = legacy default stream) */
   int32_t profile;       /* 1: time every launch of the operator kernels with CUDA events (ieti_kernel_stats) */
@@ -127,10 +127,11 @@ typedef struct {
 #define IETI_K_GEMV_P 2   /* S_bb u: Dirichlet preconditioner */
 #define IETI_K_GEMV_S 3   /* S_c^{-1} c: coarse solve */
 #define IETI_K_GEMV_Y 4   /* interior condensation / recovery GEMVs */
-#define IETI_K_TRSV 5     /* batched triangular solves with L_ii */
+#define IETI_K_TRI 5      /* interior substitutions: batched triangular GEMVs with X = L_ii^{-1} and X^T */
 #define IETI_K_SPMV 6     /* FP64 sparse M a, W a */
-#define IETI_K_VEC 7      /* gathers, jumps, dots, axpys */
-#define IETI_K_NCLASS 8
+#define IETI_K_VEC 7      /* gathers, jumps, dots, axpys (not timed) */
+#define IETI_K_PCG 8      /* the persistent PCG kernel (bytes = iterations x algorithmic bytes per iteration) */
+#define IETI_K_NCLASS 9
 
 typedef struct {
   int64_t launches;
@@ -183,6 +184,12 @@ int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem);
 /* Per-class kernel statistics accumulated since the last reset (options.profile = 1);
  * out has IETI_K_NCLASS entries.  reset != 0 clears the counters after reading. */
 int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);
+
+/* Per-phase timing of the persistent PCG kernel (options.profile = 1): mean over the
+ * traced iterations of the work time of CTA 0 in each of its six phases and of its
+ * wait at the grid barrier that ends the phase, in microseconds (%globaltimer).
+ * work_us and wait_us have 6 entries each.  reset != 0 clears the accumulators. */
+int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_t reset);
 
 const char *ieti_last_error(const ieti_ctx *ctx);
 /* Message of the last failed ieti_setup (no context exists then). */

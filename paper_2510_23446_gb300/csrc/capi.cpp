@@ -26,6 +26,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->max_sweeps < 1 || o->max_sweeps > 1000) { err = "max_sweeps must be in [1, 1000]"; return IETI_ERR_INVALID_ARG; }
   if (!(o->outer_tol >= 0.0)) { err = "outer_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->device < -1) { err = "device must be >= -1"; return IETI_ERR_INVALID_ARG; }
+  if (o->pcg_mode != 0 && o->pcg_mode != 1) { err = "pcg_mode must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   return IETI_OK;
 }
 
@@ -140,6 +141,13 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset) {
   if (!ctx || !out) return IETI_ERR_INVALID_ARG;
   if (!ctx->dev) return IETI_ERR_NO_DEVICE;
   ieti::device_kernel_stats(ctx->dev, out, reset != 0);
+  return IETI_OK;
+}
+
+int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_t reset) {
+  if (!ctx || !work_us || !wait_us) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) return IETI_ERR_NO_DEVICE;
+  ieti::device_pcg_trace(ctx->dev, work_us, wait_us, reset != 0);
   return IETI_OK;
 }
 

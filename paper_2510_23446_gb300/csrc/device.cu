@@ -1,13 +1,14 @@
 // Device part of the tree-cotree IETI-DP solver (Sec. 3 of the paper).
 //
 // Setup (once per problem): every patch's kept block W_s = M_s + dt K_s, ordered
-// [interior i | interface b | primal p], is expanded densely and AUGMENTED by an
-// identity-coupled copy b' of its interface block:
+// [interior i | interface b | primal p], is expanded densely and AUGMENTED by
+// identity-coupled copies b' of its interface block and i' of its interior block:
 //
-//        [ W_ii  W_ib  W_ip  0 ]
-//        [ W_bi  W_bb  W_bp  I ]     eliminating the i and b pivots (a partial
-//        [ W_pi  W_pb  W_pp  0 ]     Cholesky) leaves in the trailing block
-//        [ 0     I     0     0 ]     [[C_s, -Psi^T], [-Psi, -F_s]]
+//        [ W_ii  W_ib  W_ip  0  I ]
+//        [ W_bi  W_bb  W_bp  I  0 ]   eliminating the i and b pivots (a partial
+//        [ W_pi  W_pb  W_pp  0  0 ]   Cholesky) leaves in the trailing block
+//        [ 0     I     0     0  0 ]   [[C_s, -Psi^T], [-Psi, -F_s]] and in the
+//        [ I     0     0     0  0 ]   factor rows i' the block L_ii^{-T}
 //
 // with S_bb = W_bb - W_bi W_ii^{-1} W_ib (the Dirichlet-preconditioner block),
 // F_s = S_bb^{-1} (the local dual operator B_s W_rr^{-1} B_s^T restricted to the
@@ -32,6 +33,7 @@
 #include <vector>
 
 #include "device.h"
+#include "pcg_kernel.cuh"
 
 namespace ieti {
 
@@ -71,18 +73,25 @@ __global__ void k_csr_to_dense(int64_t n_rows, const int32_t *row_patch, const i
   }
 }
 
-// identity coupling of the augmented rows: D[n + k][ni + k] = D[ni + k][n + k] = 1
+// identity couplings of the augmented rows: b' (rows n..n+nb) to b, i' (rows
+// n+nb..n+nb+ni) to i
 __global__ void k_augment(int n_patch, const int32_t *ni, const int32_t *nb, const int32_t *n,
                           const int32_t *nn, const int64_t *doff, double *D) {
   int s = blockIdx.y;
   if (s >= n_patch) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nb[s]) return;
   int64_t ld = nn[s];
   double *A = D + doff[s];
-  int64_t r = n[s] + k, c = ni[s] + k;
-  A[r * ld + c] = 1.0;
-  A[c * ld + r] = 1.0;
+  if (k < nb[s]) {
+    int64_t r = n[s] + k, c = ni[s] + k;
+    A[r * ld + c] = 1.0;
+    A[c * ld + r] = 1.0;
+  }
+  if (k < ni[s]) {
+    int64_t r = n[s] + nb[s] + k, c = k;
+    A[r * ld + c] = 1.0;
+    A[c * ld + r] = 1.0;
+  }
 }
 
 template <class T>
@@ -128,9 +137,15 @@ __global__ void k_potrf_diag(T *base, const int64_t *off, const int32_t *ldv, co
 }
 
 // rows below the diagonal block: L_r = A_r L_jj^{-T} (one thread per row)
+// Per-patch restrictions of a phase (AugLimits): rows in [sk_lo, sk_hi) hold zeros in
+// the pivot columns (no work); rows >= rlim only need columns < clim.
+struct AugLimits {
+  const int32_t *sk_lo, *sk_hi, *rlim, *clim;
+};
+
 template <class T>
 __global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
-                             const int32_t *kend, const int32_t *nact, int panel) {
+                             const int32_t *kend, const int32_t *nact, int panel, AugLimits lim) {
   using A_t = typename Acc<T>::type;
   int s = blockIdx.y;
   int j0 = kbeg[s] + panel * NB;
@@ -147,6 +162,7 @@ __global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, co
   __syncthreads();
   int r = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nact[s]) return;
+  if (r >= lim.sk_lo[s] && r < lim.sk_hi[s]) return;
   T *row = A + r * ld + j0;
   A_t x[NB];
 #pragma unroll
@@ -165,7 +181,7 @@ __global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, co
 template <class T>
 __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off, const int32_t *ldv,
                                                      const int32_t *kbeg, const int32_t *kend,
-                                                     const int32_t *nact, int panel) {
+                                                     const int32_t *nact, int panel, AugLimits lim) {
   using A_t = typename Acc<T>::type;
   int s = blockIdx.y;
   int j0 = kbeg[s] + panel * NB;
@@ -184,6 +200,10 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off
   while (ti * (ti + 1) / 2 > t) --ti;
   int tj = t - ti * (ti + 1) / 2;
   int R0 = t0 + ti * 64, C0 = t0 + tj * 64;
+  int sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
+  if (R0 >= sk_lo && min(R0 + 64, na) <= sk_hi) return;   // rows with zero panel entries
+  if (C0 >= sk_lo && min(C0 + 64, na) <= sk_hi) return;   // columns with zero panel entries
+  if (R0 >= rlim && C0 >= clim) return;                   // block nobody reads
   int64_t ld = ldv[s];
   T *A = base + off[s];
   __shared__ A_t As[NB][64 + 1], Bs[NB][64 + 1];
@@ -221,14 +241,15 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int r = R0 + tr + 16 * i, c = C0 + tc + 16 * j;
-      if (r < na && c <= r) A[r * ld + c] = (T)((A_t)A[r * ld + c] - acc[i][j]);
+      bool skip = (r >= sk_lo && r < sk_hi) || (r >= rlim && c >= clim);
+      if (r < na && c <= r && !skip) A[r * ld + c] = (T)((A_t)A[r * ld + c] - acc[i][j]);
     }
 }
 
 // P_s = S_bb (after the interior pivots), symmetrised from the lower triangle
 template <class T>
 __global__ void k_extract_P(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
-                            const int32_t *nb, const int64_t *poff, T *P) {
+                            const int32_t *nb, const int32_t *ldb, const int64_t *poff, T *P) {
   int s = blockIdx.y;
   int m = nb[s];
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -237,14 +258,14 @@ __global__ void k_extract_P(const double *D, const int64_t *doff, const int32_t 
   int64_t ld = nn[s];
   const double *A = D + doff[s];
   int rr = ni[s] + max(r, c), cc = ni[s] + min(r, c);
-  P[poff[s] + idx] = (T)A[rr * ld + cc];
+  P[poff[s] + (int64_t)r * ldb[s] + c] = (T)A[rr * ld + cc];
 }
 
 // H_s = [F_s; Psi_s^T] ((nb+np) x nb), Psi_s (nb x np), LY_s = first ni columns (n x ni)
 template <class T>
 __global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
-                              const int32_t *nb, const int32_t *np, const int64_t *hoff, const int64_t *qoff,
-                              T *H, T *Q) {
+                              const int32_t *nb, const int32_t *np, const int32_t *ldb, const int32_t *ldp,
+                              const int64_t *hoff, const int64_t *qoff, T *H, T *Q) {
   int s = blockIdx.y;
   int B = nb[s], Pn = np[s], I = ni[s];
   int n = I + B + Pn;
@@ -260,25 +281,35 @@ __global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_
       v = -A[(int64_t)(n + hi) * ld + n + lo];
     } else {      // Psi^T[r-B][c] = Psi[c][r-B] = -A[n + c][I + B + (r - B)]
       v = -A[(int64_t)(n + c) * ld + I + B + (r - B)];
-      Q[qoff[s] + (int64_t)c * Pn + (r - B)] = (T)v;
+      Q[qoff[s] + (int64_t)c * ldp[s] + (r - B)] = (T)v;
     }
-    H[hoff[s] + idx] = (T)v;
+    H[hoff[s] + (int64_t)r * ldb[s] + c] = (T)v;
   }
 }
 
+// LY_s (n x ni): rows < ni hold X = L_ii^{-1} in the lower triangle and X^T in the
+// strict upper triangle (XX[r][c] = X[max][min]); rows >= ni hold Y = L_[bp]i.
+// X[r][c] = (L_{i'i})[c][r] = D[n + nb + c][r] (c <= r).
 template <class T>
 __global__ void k_extract_LY(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
                              const int32_t *nb, const int32_t *np, const int64_t *lyoff, T *LY) {
   int s = blockIdx.y;
-  int I = ni[s];
-  int n = I + nb[s] + np[s];
+  int I = ni[s], B = nb[s];
+  int n = I + B + np[s];
   int64_t ld = nn[s];
   const double *A = D + doff[s];
   int64_t total = (int64_t)n * I;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(idx / I), c = (int)(idx % I);
-    LY[lyoff[s] + idx] = (c <= r) ? (T)A[(int64_t)r * ld + c] : (T)0;
+    double v;
+    if (r < I) {
+      int hi = max(r, c), lo = min(r, c);
+      v = A[(int64_t)(n + B + lo) * ld + hi];
+    } else {
+      v = A[(int64_t)r * ld + c];
+    }
+    LY[lyoff[s] + idx] = (T)v;
   }
 }
 
@@ -301,12 +332,12 @@ __global__ void k_coarse_identity(int nc, double *Sc, int64_t ldc) {
   Sc[(int64_t)r * ldc + nc + r] = 1.0;
 }
 
-__global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv) {
+__global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv, int ldo) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nc * nc) return;
   int r = (int)(idx / nc), c = (int)(idx % nc);
   int hi = max(r, c), lo = min(r, c);
-  Sinv[idx] = -Sc[(int64_t)(nc + hi) * ldc + nc + lo];
+  Sinv[(int64_t)r * ldo + c] = -Sc[(int64_t)(nc + hi) * ldc + nc + lo];
 }
 
 // =============================================================================
@@ -344,10 +375,10 @@ __global__ void k_gemv_rows(int64_t n_rows, const int64_t *aoff, const int64_t *
   }
 }
 
-// out[c] = in[c] - sum_{r} LY[ni + r][c] * x[r]  for c < ni  (x = kept [b|p] part)
+// t[c] = z[c] - sum_r Y[r][c] x[ni + r]  for c < ni  (x: kept [b|p] part)
 template <class T>
 __global__ void k_gemvT_Y(const int32_t *ni, const int32_t *nb, const int32_t *np, const int64_t *lyoff,
-                          const int64_t *kofs, const T *LY, double *v) {
+                          const int64_t *kofs, const T *LY, const double *z, const double *x, double *t) {
   using A_t = typename Acc<T>::type;
   int s = blockIdx.y;
   int I = ni[s];
@@ -355,73 +386,11 @@ __global__ void k_gemvT_Y(const int32_t *ni, const int32_t *nb, const int32_t *n
   if (c >= I) return;
   int R = nb[s] + np[s];
   const T *Y = LY + lyoff[s] + (int64_t)I * I;
-  double *kv = v + kofs[s];
+  const double *xv = x + kofs[s] + I;
   A_t acc = 0;
-  for (int r = 0; r < R; ++r) acc += (A_t)Y[(int64_t)r * I + c] * (A_t)kv[I + r];
-  kv[c] -= (double)acc;
-}
-
-// forward (L z = v) or backward (L^T x = v) substitution on the interior part of
-// each patch's kept vector, one CTA per patch, vector staged in shared memory.
-template <class T>
-__global__ void k_trsv(const int32_t *ni, const int64_t *lyoff, const int64_t *kofs, const T *LY, double *v,
-                       int backward) {
-  using A_t = typename Acc<T>::type;
-  extern __shared__ double z[];
-  int s = blockIdx.x;
-  int n = ni[s];
-  if (n == 0) return;
-  const T *L = LY + lyoff[s];
-  double *x = v + kofs[s];
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  for (int i = tid; i < n; i += blockDim.x) z[i] = x[i];
-  __syncthreads();
-  if (!backward) {
-    for (int R = 0; R < n; R += 32) {
-      int rb = min(32, n - R);
-      for (int rr = warp; rr < rb; rr += nwarp) {
-        const T *row = L + (int64_t)(R + rr) * n;
-        A_t acc = 0;
-        for (int c = lane; c < R; c += 32) acc += (A_t)row[c] * (A_t)z[c];
-        double sum = warp_sum((double)acc);
-        if (lane == 0) z[R + rr] -= sum;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        double xr = (lane < rb) ? z[R + lane] : 0.0;
-        for (int k = 0; k < rb; ++k) {
-          double xk = __shfl_sync(0xffffffffu, xr, k) / (double)L[(int64_t)(R + k) * n + R + k];
-          if (lane == k) xr = xk;
-          if (lane > k && lane < rb) xr -= (double)L[(int64_t)(R + lane) * n + R + k] * xk;
-        }
-        if (lane < rb) z[R + lane] = xr;
-      }
-      __syncthreads();
-    }
-  } else {
-    int nblk = (n + 31) / 32;
-    for (int bI = nblk - 1; bI >= 0; --bI) {
-      int R = bI * 32;
-      int rb = min(32, n - R);
-      if (warp == 0) {
-        double vr = (lane < rb) ? z[R + lane] : 0.0;
-        for (int k = rb - 1; k >= 0; --k) {
-          double xk = __shfl_sync(0xffffffffu, vr, k) / (double)L[(int64_t)(R + k) * n + R + k];
-          if (lane == k) vr = xk;
-          if (lane < k) vr -= (double)L[(int64_t)(R + k) * n + R + lane] * xk;
-        }
-        if (lane < rb) z[R + lane] = vr;
-      }
-      __syncthreads();
-      for (int c = tid; c < R; c += blockDim.x) {
-        A_t acc = 0;
-        for (int k = 0; k < rb; ++k) acc += (A_t)L[(int64_t)(R + k) * n + c] * (A_t)z[R + k];
-        z[c] -= (double)acc;
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = tid; i < n; i += blockDim.x) x[i] = z[i];
+#pragma unroll 4
+  for (int r = 0; r < R; ++r) acc += (A_t)Y[(int64_t)r * I + c] * (A_t)xv[r];
+  t[kofs[s] + c] = z[kofs[s] + c] - (double)acc;
 }
 
 // kept-space gather of the global state: out[k] = a[glob[k]]
@@ -666,12 +635,33 @@ struct DeviceState {
     int64_t n = 0;
     int64_t *aoff = nullptr, *xoff = nullptr, *yidx = nullptr;
     int32_t *ncol = nullptr;
-  } dY, dH, dQ, dP, dS;
+  } dY, dH, dQ, dP, dS, dXf, dXb;
   // vectors
-  double *a = nullptr, *j = nullptr, *kf = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *ka = nullptr;
+  double *a = nullptr, *j = nullptr, *kf = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *ka = nullptr,
+         *kt = nullptr;
   double *bp = nullptr, *ub = nullptr, *gb = nullptr, *gp = nullptr, *cc = nullptr, *q = nullptr, *qloc = nullptr;
   double *lam = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Fp = nullptr, *dvec = nullptr;
   double *part = nullptr, *sc = nullptr, *h_sc = nullptr;
+  // persistent PCG
+  int G = 0, ldc = 0;
+  size_t pcg_smem = 0;
+  int32_t *ldb = nullptr, *ldp = nullptr, *bpatch = nullptr;
+  int64_t *bofs_d = nullptr, *pofs_d = nullptr;
+  int32_t *hseg_ptr = nullptr, *hseg_s = nullptr, *hseg_r0 = nullptr, *hseg_r1 = nullptr;
+  int32_t *bseg_ptr = nullptr, *bseg_s = nullptr, *bseg_r0 = nullptr, *bseg_r1 = nullptr;
+  int32_t *ell_lam = nullptr, *cp_pos = nullptr;
+  double *ell_sgn = nullptr, *ell_wd = nullptr;
+  double *p1 = nullptr, *r1 = nullptr, *zb = nullptr, *zf = nullptr, *ubp = nullptr, *tpi = nullptr, *zp = nullptr,
+         *ccg = nullptr, *ppart = nullptr;
+  unsigned *bar = nullptr;
+  int *pcg_its = nullptr;
+  unsigned long long *trace = nullptr;
+  double trace_acc[8] = {};   // summed per-phase time (us) over traced iterations: work P1..P6, waits
+  double trace_wait[8] = {};
+  int64_t trace_n = 0;
+  double *pcg_rr = nullptr, *pcg_dd = nullptr;
+  double bytes_iter_alg = 0;
+  unsigned xs_bytes = 0, stage_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dt = 0;
   // kernel-class profiler (options.profile)
@@ -701,6 +691,9 @@ static void prof_begin(DeviceState *d, int cls, double bytes) {
 static void prof_end(DeviceState *d) {
   if (!d->opt.profile) return;
   cudaEventRecord(d->ev_pool[d->pend.back().e0 + 1], d->stream);
+}
+static void prof_set_bytes(DeviceState *d, double bytes) {
+  if (d->opt.profile && !d->pend.empty()) d->pend.back().bytes = bytes;
 }
 static void prof_collect(DeviceState *d) {
   if (!d->opt.profile || d->pend.empty()) return;
@@ -769,7 +762,7 @@ static void gemv(DeviceState *d, const DeviceState::Desc &D, const void *A, cons
 template <class T>
 static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int32_t *ld, const std::vector<int32_t> &hkb,
                          const std::vector<int32_t> &hke, const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke,
-                         int32_t *dna, int32_t *status, std::string &err) {
+                         int32_t *dna, int32_t *status, AugLimits lim, std::string &err) {
   int nbatch = (int)hkb.size();
   int max_panels = 0;
   for (int s = 0; s < nbatch; ++s) max_panels = std::max(max_panels, (hke[s] - hkb[s] + NB - 1) / NB);
@@ -790,10 +783,10 @@ static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int3
     d->launches_setup++;
     if (max_rows > 0) {
       dim3 g1(grid_for(max_rows, 128), nbatch);
-      k_trsm_panel<T><<<g1, 128, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      k_trsm_panel<T><<<g1, 128, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j, lim);
       d->nlaunch++;
       dim3 g2(max_tiles, nbatch);
-      k_syrk_update<T><<<g2, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j);
+      k_syrk_update<T><<<g2, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j, lim);
       d->nlaunch++;
       d->launches_setup += 2;
     }
@@ -911,19 +904,127 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
   return IETI_OK;
 }
 
+// PCG as one persistent cooperative launch (pcg_kernel.cuh)
+template <class T>
+static int pcg_persistent(DeviceState *d, int *its, double *rel, std::string &err) {
+  cudaStream_t st = d->stream;
+  *its = 0;
+  *rel = 0.0;
+  if (d->M == 0) return IETI_OK;
+  CK(cudaMemsetAsync(d->bar, 0, 3 * sizeof(unsigned), st));
+  PcgArgs<T> a;
+  a.m = d->M;
+  a.nc = (int)d->NC;
+  a.ldc = d->ldc;
+  a.precond_none = d->opt.precond == IETI_PRECOND_NONE;
+  a.scaled = d->opt.precond == IETI_PRECOND_DIRICHLET_MULT || d->opt.precond == IETI_PRECOND_DIRICHLET_STIFF;
+  a.max_it = d->opt.cg_max_it;
+  a.tol2 = d->opt.cg_tol * d->opt.cg_tol;
+  a.bt_lam = d->ell_lam; a.bt_sgn = d->ell_sgn; a.bt_wd = d->ell_wd;
+  a.lam_qp = d->lam_qp; a.lam_qm = d->lam_qm;
+  a.lam_wp = a.scaled ? d->lam_wp : nullptr;
+  a.lam_wm = a.scaled ? d->lam_wm : nullptr;
+  a.bofs = d->bofs_d; a.pofs = d->pofs_d; a.hoff = d->hoff; a.qoff = d->qoff; a.poff = d->poff;
+  a.nb = d->nb; a.np = d->npp; a.ldb = d->ldb; a.ldp = d->ldp;
+  a.pc = d->pc; a.cp_pos = d->cp_pos;
+  a.H = (const T *)d->H; a.Q = (const T *)d->Q; a.P = (const T *)d->P; a.Sinv = d->Sinv;
+  a.hseg_ptr = d->hseg_ptr; a.hseg_s = d->hseg_s; a.hseg_r0 = d->hseg_r0; a.hseg_r1 = d->hseg_r1;
+  a.bseg_ptr = d->bseg_ptr; a.bseg_s = d->bseg_s; a.bseg_r0 = d->bseg_r0; a.bseg_r1 = d->bseg_r1;
+  a.d = d->dvec; a.lam = d->lam; a.p0 = d->p; a.p1 = d->p1; a.r0 = d->r; a.r1 = d->r1; a.z = d->z;
+  a.ub = d->ubp; a.zb = d->zb; a.zf = d->zf; a.tpi = d->tpi; a.cc = d->ccg; a.q = d->q; a.zp = d->zp;
+  a.part = d->ppart;
+  a.bar = d->bar; a.out_its = d->pcg_its; a.out_rr = d->pcg_rr; a.out_dd = d->pcg_dd;
+  a.trace = d->opt.profile ? d->trace : nullptr;
+  a.stage_bytes = d->stage_bytes;
+  a.xs_bytes = d->xs_bytes;
+  if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * 16 * sizeof(unsigned long long), st));
+  void *args[] = {&a};
+  prof_begin(d, IETI_K_PCG, 0.0);
+  CK(cudaLaunchCooperativeKernel((void *)k_pcg<T>, d->G, PCG_THREADS, args, d->pcg_smem, st));
+  d->nlaunch++;
+  prof_end(d);
+  struct {
+    int its;
+    unsigned bar[3];
+    double rr, dd;
+  } h;
+  CK(cudaMemcpyAsync(&h.its, d->pcg_its, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h.bar, d->bar, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h.rr, d->pcg_rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h.dd, d->pcg_dd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h.bar[1]) {
+    err = "persistent PCG: a grid barrier timed out";
+    return IETI_ERR_CUDA;
+  }
+  *its = h.its;
+  prof_set_bytes(d, d->bytes_iter_alg * h.its);
+  if (a.trace) {
+    unsigned long long tr[TRACE_IT * 16];
+    CK(cudaMemcpy(tr, d->trace, sizeof(tr), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < std::min(h.its - 1, TRACE_IT); ++i) {
+      unsigned long long *t = tr + i * 16;
+      if (!t[14] || !t[11]) continue;
+      unsigned long long prev = t[14];
+      for (int ph = 0; ph < 6; ++ph) {
+        d->trace_acc[ph] += (t[2 * ph] - prev) * 1e-3;
+        d->trace_wait[ph] += (t[2 * ph + 1] - t[2 * ph]) * 1e-3;
+        prev = t[2 * ph + 1];
+      }
+      d->trace_n++;
+    }
+  }
+  if (!(h.dd > 0.0)) return IETI_OK;
+  *rel = std::sqrt(h.rr / h.dd);
+  if (!std::isfinite(h.rr)) {
+    err = "PCG breakdown (non-finite residual)";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  if (h.rr > a.tol2 * h.dd) {
+    err = "PCG did not reach cg_tol within cg_max_it";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  return IETI_OK;
+}
+
+// contiguous byte-balanced row ranges per CTA, split into per-patch segments
+static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std::vector<int32_t> &ld, int G,
+                           std::vector<int32_t> &sptr, std::vector<int32_t> &ss, std::vector<int32_t> &r0,
+                           std::vector<int32_t> &r1) {
+  int np_ = (int)rows_per_patch.size();
+  double W = 0;
+  for (int s = 0; s < np_; ++s) W += (double)rows_per_patch[s] * (ld[s] + 16);
+  sptr.assign(1, 0);
+  ss.clear(); r0.clear(); r1.clear();
+  int s = 0, r = 0;
+  double acc = 0;
+  for (int c = 0; c < G; ++c) {
+    double target = W * (c + 1) / G;
+    while (s < np_ && (acc < target || c == G - 1)) {
+      if (r >= rows_per_patch[s]) { ++s; r = 0; continue; }
+      // take rows of patch s until the target is reached
+      int take = rows_per_patch[s] - r;
+      double per = ld[s] + 16;
+      if (c < G - 1) {
+        int need = (int)std::ceil((target - acc) / per);
+        take = std::max(1, std::min(take, need));
+      }
+      ss.push_back(s); r0.push_back(r); r1.push_back(r + take);
+      acc += take * per;
+      r += take;
+      if (r >= rows_per_patch[s]) { ++s; r = 0; }
+    }
+    sptr.push_back((int32_t)ss.size());
+  }
+}
+
 // dual-primal solve of the gauged step system for kept-space right-hand sides
 // rhs (per patch, Sec. 3), solution into d->kx (kept space)
 template <class T>
 static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
   cudaStream_t st = d->stream;
-  int64_t NK = d->NK;
-  size_t smem = (size_t)std::max(d->max_ni, 1) * sizeof(double);
-  // interior condensation: z_i = L_ii^{-1} rhs_i; g_[bp] = rhs_[bp] - Y z_i
-  CK(cudaMemcpyAsync(d->kz, rhs, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  prof_begin(d, IETI_K_TRSV, d->gemv_bytes[IETI_K_TRSV]);
-  k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kz, 0);
-  d->nlaunch++;
-  prof_end(d);
+  // interior condensation with the explicit X = L_ii^{-1}: z_i = X rhs_i; g_[bp] = rhs_[bp] - Y z_i
+  gemv<T>(d, d->dXf, d->LY, rhs, d->kz, nullptr, 1.0, 0.0, IETI_K_TRI);
   gemv<T>(d, d->dY, d->LY, d->kz, d->kz, rhs, -1.0, 1.0, IETI_K_GEMV_Y);
   k_kept_to_bp<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->kz, d->gb,
                                                                  d->gp);
@@ -932,27 +1033,23 @@ static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, st
   condensed<T>(d, d->gb, d->gp);
   k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, d->dvec, nullptr, nullptr);
   d->nlaunch++;
-  int rc = pcg<T>(d, its, rel, err);
+  int rc = d->opt.pcg_mode == 1 ? pcg<T>(d, its, rel, err) : pcg_persistent<T>(d, its, rel, err);
   if (rc && rc != IETI_ERR_CG_NOT_CONVERGED) return rc;
   int cg_rc = rc;
   // recovery: v_b = g_b - B^T lambda; a_b = F v_b - Psi q, a_p = q
   k_Bt<<<grid_for(d->NBt, 256), 256, 0, st>>>(d->NBt, d->bt_ptr, d->bt_lam, d->bt_sgn, d->lam, d->gb, -1.0, d->ub);
   d->nlaunch++;
   condensed<T>(d, d->ub, d->gp);
-  CK(cudaMemcpyAsync(d->kx, d->kz, NK * sizeof(double), cudaMemcpyDeviceToDevice, st));
   k_bp_to_kept<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->pc, d->bp,
                                                                  d->q, d->kx);
   d->nlaunch++;
-  // interior: a_i = L_ii^{-T} (z_i - Y^T a_[bp])
+  // interior: a_i = X^T (z_i - Y^T a_[bp])
   dim3 gT(grid_for(d->max_ni, 128), d->np_);
-  prof_begin(d, IETI_K_GEMV_Y, d->gemv_bytes[IETI_K_GEMV_Y]);
-  k_gemvT_Y<T><<<gT, 128, 0, st>>>(d->ni, d->nb, d->npp, d->lyoff, d->kofs, (const T *)d->LY, d->kx);
+  prof_begin(d, IETI_K_GEMV_Y, 0.0);
+  k_gemvT_Y<T><<<gT, 128, 0, st>>>(d->ni, d->nb, d->npp, d->lyoff, d->kofs, (const T *)d->LY, d->kz, d->kx, d->kt);
   d->nlaunch++;
   prof_end(d);
-  prof_begin(d, IETI_K_TRSV, d->gemv_bytes[IETI_K_TRSV]);
-  k_trsv<T><<<d->np_, 256, smem, st>>>(d->ni, d->lyoff, d->kofs, (const T *)d->LY, d->kx, 1);
-  d->nlaunch++;
-  prof_end(d);
+  gemv<T>(d, d->dXb, d->LY, d->kt, d->kx, nullptr, 1.0, 0.0, IETI_K_TRI);
   CK(cudaGetLastError());
   return cg_rc;
 }
@@ -1057,7 +1154,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->np_ = np_;
   d->n_edges = hs.n_edges;
   // ---------------- sizes and offsets
-  std::vector<int32_t> hni(np_), hnb(np_), hnp(np_), hn(np_), hnn(np_), hrowpatch, hrowlocal;
+  std::vector<int32_t> hni(np_), hnb(np_), hnp(np_), hn(np_), hnn(np_), hrowpatch, hrowlocal, hldb(np_), hldp(np_);
   std::vector<int64_t> hkofs(np_ + 1, 0), hdoff(np_ + 1, 0), hly(np_ + 1, 0), hh(np_ + 1, 0), hq(np_ + 1, 0),
       hp(np_ + 1, 0), hbofs(np_ + 1, 0), hpofs(np_ + 1, 0);
   for (int s = 0; s < np_; ++s) {
@@ -1066,13 +1163,16 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     hnb[s] = pt.nb;
     hnp[s] = pt.np;
     hn[s] = pt.ni + pt.nb + pt.np;
-    hnn[s] = hn[s] + pt.nb;
+    hnn[s] = hn[s] + pt.nb + pt.ni;  // augmented: [i b p | b' | i']
     hkofs[s + 1] = hkofs[s] + hn[s];
     hdoff[s + 1] = hdoff[s] + (int64_t)hnn[s] * hnn[s];
     hly[s + 1] = hly[s] + (int64_t)hn[s] * pt.ni;
-    hh[s + 1] = hh[s] + (int64_t)(pt.nb + pt.np) * pt.nb;
-    hq[s + 1] = hq[s] + (int64_t)pt.nb * pt.np;
-    hp[s + 1] = hp[s] + (int64_t)pt.nb * pt.nb;
+    int ldb_s = (pt.nb + 3) / 4 * 4, ldp_s = (pt.np + 3) / 4 * 4;  // 16-byte aligned rows
+    hldb[s] = ldb_s;
+    hldp[s] = ldp_s;
+    hh[s + 1] = hh[s] + (int64_t)(pt.nb + pt.np) * ldb_s;
+    hq[s + 1] = hq[s] + (int64_t)pt.nb * ldp_s;
+    hp[s + 1] = hp[s] + (int64_t)pt.nb * ldb_s;
     hbofs[s + 1] = hbofs[s] + pt.nb;
     hpofs[s + 1] = hpofs[s] + pt.np;
     d->max_ni = std::max(d->max_ni, pt.ni);
@@ -1086,10 +1186,6 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->M = (int64_t)hs.lam.size();
   d->NC = hs.n_coarse;
   d->NF = (int64_t)hs.free_edges.size();
-  if ((size_t)d->max_ni * sizeof(double) > 200 * 1024) {
-    err = "an interior block exceeds the shared-memory triangular solve limit (25600 DOFs)";
-    return fail(IETI_ERR_TOO_LARGE);
-  }
   // ---------------- kept space arrays and CSR (columns as absolute kept indices)
   std::vector<int64_t> kglob(d->NK), wptr(1, 0), mptr(1, 0), b_kept, p_kept;
   std::vector<double> kw(d->NK), wval, mval;
@@ -1216,6 +1312,16 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       (rc = upload(d, &d->cpos, cpos, err)) || (rc = upload(d, &d->fptr, fptr, err)) ||
       (rc = upload(d, &d->fpos, fpos, err)) || (rc = upload(d, &d->fglob, fglob, err)))
     return fail(rc);
+  {
+    std::vector<int64_t> hb(hbofs.begin(), hbofs.end() - 1), hpo(hpofs.begin(), hpofs.end() - 1);
+    std::vector<int32_t> bp_(d->NBt);
+    for (int s = 0; s < np_; ++s)
+      for (int64_t k = hbofs[s]; k < hbofs[s + 1]; ++k) bp_[k] = s;
+    if ((rc = upload(d, &d->ldb, hldb, err)) || (rc = upload(d, &d->ldp, hldp, err)) ||
+        (rc = upload(d, &d->bofs_d, hb, err)) || (rc = upload(d, &d->pofs_d, hpo, err)) ||
+        (rc = upload(d, &d->bpatch, bp_, err)))
+      return fail(rc);
+  }
   // ---------------- GEMV descriptors
   {
     std::vector<int64_t> ao, xo, yi;
@@ -1231,10 +1337,31 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       }
     if ((rc = upload_desc(d, d->dY, ao, xo, yi, nc, err))) return fail(rc);
     clear();
+    // X rows (forward): z_i[r] = sum_{c<=r} X[r][c] rhs_i[c]
+    for (int s = 0; s < np_; ++s)
+      for (int r = 0; r < hni[s]; ++r) {
+        ao.push_back(hly[s] + (int64_t)r * hni[s]);
+        xo.push_back(hkofs[s]);
+        yi.push_back(hkofs[s] + r);
+        nc.push_back(r + 1);
+      }
+    if ((rc = upload_desc(d, d->dXf, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    // X^T rows (backward, strict upper part + diagonal of the same array):
+    // x_i[c] = sum_{r>=c} X[r][c] t[r]
+    for (int s = 0; s < np_; ++s)
+      for (int c = 0; c < hni[s]; ++c) {
+        ao.push_back(hly[s] + (int64_t)c * hni[s] + c);
+        xo.push_back(hkofs[s] + c);
+        yi.push_back(hkofs[s] + c);
+        nc.push_back(hni[s] - c);
+      }
+    if ((rc = upload_desc(d, d->dXb, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
     // H rows: [F u ; Psi^T u] -> bp (B-space then Pi-space)
     for (int s = 0; s < np_; ++s)
       for (int r = 0; r < hnb[s] + hnp[s]; ++r) {
-        ao.push_back(hh[s] + (int64_t)r * hnb[s]);
+        ao.push_back(hh[s] + (int64_t)r * hldb[s]);
         xo.push_back(hbofs[s]);
         yi.push_back(r < hnb[s] ? hbofs[s] + r : d->NBt + hpofs[s] + (r - hnb[s]));
         nc.push_back(hnb[s]);
@@ -1244,7 +1371,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     // Psi rows: bp_b -= Psi qloc
     for (int s = 0; s < np_; ++s)
       for (int r = 0; r < hnb[s]; ++r) {
-        ao.push_back(hq[s] + (int64_t)r * hnp[s]);
+        ao.push_back(hq[s] + (int64_t)r * hldp[s]);
         xo.push_back(hpofs[s]);
         yi.push_back(hbofs[s] + r);
         nc.push_back(hnp[s]);
@@ -1254,15 +1381,16 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     // P rows (Dirichlet preconditioner S_bb)
     for (int s = 0; s < np_; ++s)
       for (int r = 0; r < hnb[s]; ++r) {
-        ao.push_back(hp[s] + (int64_t)r * hnb[s]);
+        ao.push_back(hp[s] + (int64_t)r * hldb[s]);
         xo.push_back(hbofs[s]);
         yi.push_back(hbofs[s] + r);
         nc.push_back(hnb[s]);
       }
     if ((rc = upload_desc(d, d->dP, ao, xo, yi, nc, err))) return fail(rc);
     clear();
+    d->ldc = (int)((d->NC + 3) / 4 * 4);
     for (int64_t r = 0; r < d->NC; ++r) {
-      ao.push_back(r * d->NC);
+      ao.push_back(r * d->ldc);
       xo.push_back(0);
       yi.push_back(r);
       nc.push_back((int32_t)d->NC);
@@ -1274,7 +1402,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       (rc = dalloc(d, &d->rglob, hs.n_edges, err)) ||
       (rc = dalloc(d, &d->kf, d->NK, err)) || (rc = dalloc(d, &d->kx, d->NK, err)) ||
       (rc = dalloc(d, &d->kr, d->NK, err)) || (rc = dalloc(d, &d->kz, d->NK, err)) ||
-      (rc = dalloc(d, &d->ka, d->NK, err)) || (rc = dalloc(d, &d->bp, d->NBt + d->NPt, err)) ||
+      (rc = dalloc(d, &d->ka, d->NK, err)) || (rc = dalloc(d, &d->kt, d->NK, err)) ||
+      (rc = dalloc(d, &d->bp, d->NBt + d->NPt, err)) ||
       (rc = dalloc(d, &d->ub, d->NBt, err)) || (rc = dalloc(d, &d->gb, d->NBt, err)) ||
       (rc = dalloc(d, &d->gp, d->NPt, err)) || (rc = dalloc(d, &d->cc, d->NC, err)) ||
       (rc = dalloc(d, &d->q, d->NC, err)) || (rc = dalloc(d, &d->qloc, d->NPt, err)) ||
@@ -1294,9 +1423,9 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     int64_t nrows = d->NK;
     k_csr_to_dense<<<grid_for(nrows * 32, 256), 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol,
                                                                      d->wval, d->kofs, ddoff, dnn, D);
-    int maxnb = *std::max_element(hnb.begin(), hnb.end());
-    if (maxnb > 0) {
-      dim3 g(grid_for(maxnb, 128), np_);
+    int maxaug = std::max(*std::max_element(hnb.begin(), hnb.end()), d->max_ni);
+    if (maxaug > 0) {
+      dim3 g(grid_for(maxaug, 128), np_);
       k_augment<<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, D);
     }
     d->launches_setup += 2;
@@ -1305,19 +1434,32 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   // phase A: interior pivots -> trailing [b p b'] = Schur complement; copy S_bb
   std::vector<int32_t> hkb(np_), hke(np_), hna(np_);
   int32_t *dkb = nullptr, *dke = nullptr, *dna = nullptr, *dstat = nullptr;
+  int32_t *dsklo = nullptr, *dskhi = nullptr, *drlim = nullptr, *dclim = nullptr;
   if ((rc = dalloc(d, &dkb, np_, err)) || (rc = dalloc(d, &dke, np_, err)) || (rc = dalloc(d, &dna, np_, err)) ||
-      (rc = dalloc(d, &dstat, np_, err)))
+      (rc = dalloc(d, &dstat, np_, err)) || (rc = dalloc(d, &dsklo, np_, err)) || (rc = dalloc(d, &dskhi, np_, err)) ||
+      (rc = dalloc(d, &drlim, np_, err)) || (rc = dalloc(d, &dclim, np_, err)))
     return fail(rc);
   CK(cudaMemsetAsync(dstat, 0, np_ * sizeof(int32_t), d->stream));
+  std::vector<int32_t> hsklo(np_), hskhi(np_), hrlim(np_), hclim(np_);
+  auto put = [&](int32_t *dst, const std::vector<int32_t> &h) -> int {
+    CK(cudaMemcpyAsync(dst, h.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return IETI_OK;
+  };
+  AugLimits lim{dsklo, dskhi, drlim, dclim};
   for (int s = 0; s < np_; ++s) {
     hkb[s] = 0;
     hke[s] = hni[s];
-    hna[s] = hn[s];  // the b' rows are untouched by interior pivots (their coupling is 0)
+    hna[s] = hnn[s];
+    hsklo[s] = hn[s];              // b' rows: zero in the interior columns
+    hskhi[s] = hn[s] + hnb[s];
+    hrlim[s] = hn[s] + hnb[s];     // i' rows: only their interior columns are read
+    hclim[s] = hni[s];
   }
-  CK(cudaMemcpyAsync(dkb, hkb.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  CK(cudaMemcpyAsync(dke, hke.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  CK(cudaMemcpyAsync(dna, hna.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, err))) return fail(rc);
+  if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
+      (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
+    return fail(rc);
+  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, lim, err))) return fail(rc);
   int maxnb = *std::max_element(hnb.begin(), hnb.end());
   int maxnp = *std::max_element(hnp.begin(), hnp.end());
   int64_t maxP = (int64_t)maxnb * maxnb;
@@ -1340,22 +1482,30 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   if ((rc = alloc_op(&d->P, hp[np_])) || (rc = alloc_op(&d->H, hh[np_])) || (rc = alloc_op(&d->Q, hq[np_])) ||
       (rc = alloc_op(&d->LY, hly[np_])))
     return fail(rc);
+  CK(cudaMemsetAsync(d->P, 0, std::max<int64_t>(hp[np_], 1) * esz, d->stream));
+  CK(cudaMemsetAsync(d->H, 0, std::max<int64_t>(hh[np_], 1) * esz, d->stream));
+  CK(cudaMemsetAsync(d->Q, 0, std::max<int64_t>(hq[np_], 1) * esz, d->stream));
   if (maxP > 0) {
     dim3 g(grid_for(maxP, 256), np_);
-    if (d->mixed) k_extract_P<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->poff, (float *)d->P);
-    else k_extract_P<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->poff, (double *)d->P);
+    if (d->mixed)
+      k_extract_P<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff, (float *)d->P);
+    else
+      k_extract_P<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff, (double *)d->P);
     d->launches_setup++;
   }
   // phase B: interface pivots -> trailing [p b'] = [[C_s, -Psi^T], [-Psi, -F_s]]
   for (int s = 0; s < np_; ++s) {
     hkb[s] = hni[s];
     hke[s] = hni[s] + hnb[s];
-    hna[s] = hnn[s];
+    hna[s] = hn[s] + hnb[s];       // the i' rows are done
+    hsklo[s] = hskhi[s] = 0;
+    hrlim[s] = INT32_MAX;
+    hclim[s] = 0;
   }
-  CK(cudaMemcpyAsync(dkb, hkb.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  CK(cudaMemcpyAsync(dke, hke.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  CK(cudaMemcpyAsync(dna, hna.data(), np_ * 4, cudaMemcpyHostToDevice, d->stream));
-  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, err))) return fail(rc);
+  if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
+      (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
+    return fail(rc);
+  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, lim, err))) return fail(rc);
   {
     std::vector<int32_t> hstat(np_);
     CK(cudaMemcpyAsync(hstat.data(), dstat, np_ * 4, cudaMemcpyDeviceToHost, d->stream));
@@ -1370,11 +1520,11 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   if (maxH > 0) {
     dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), np_);
     if (d->mixed)
-      k_extract_ops<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->hoff, d->qoff,
-                                                     (float *)d->H, (float *)d->Q);
+      k_extract_ops<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp, d->hoff,
+                                                     d->qoff, (float *)d->H, (float *)d->Q);
     else
-      k_extract_ops<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->hoff, d->qoff,
-                                                      (double *)d->H, (double *)d->Q);
+      k_extract_ops<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp, d->hoff,
+                                                      d->qoff, (double *)d->H, (double *)d->Q);
     d->launches_setup++;
   }
   if (maxLY > 0) {
@@ -1403,10 +1553,15 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     int32_t *cld = nullptr, *ckb = nullptr, *cke = nullptr, *cna = nullptr, *cst = nullptr;
     std::vector<int64_t> hcoff{0};
     std::vector<int32_t> hcld{(int32_t)ldc}, hckb{0}, hcke{(int32_t)nc}, hcna{(int32_t)ldc}, hcst{0};
+    std::vector<int32_t> hz{0}, hbig{INT32_MAX};
+    int32_t *cz = nullptr, *cbig = nullptr;
     if ((rc = upload(d, &coff, hcoff, err)) || (rc = upload(d, &cld, hcld, err)) || (rc = upload(d, &ckb, hckb, err)) ||
-        (rc = upload(d, &cke, hcke, err)) || (rc = upload(d, &cna, hcna, err)) || (rc = upload(d, &cst, hcst, err)))
+        (rc = upload(d, &cke, hcke, err)) || (rc = upload(d, &cna, hcna, err)) || (rc = upload(d, &cst, hcst, err)) ||
+        (rc = upload(d, &cz, hz, err)) || (rc = upload(d, &cbig, hbig, err)))
       return fail(rc);
-    if ((rc = potrf_partial<double>(d, Sc, coff, cld, hckb, hcke, hcna, ckb, cke, cna, cst, err))) return fail(rc);
+    AugLimits clim_{cz, cz, cbig, cz};
+    if ((rc = potrf_partial<double>(d, Sc, coff, cld, hckb, hcke, hcna, ckb, cke, cna, cst, clim_, err)))
+      return fail(rc);
     int32_t cstat = 0;
     CK(cudaMemcpyAsync(&cstat, cst, 4, cudaMemcpyDeviceToHost, d->stream));
     CK(cudaStreamSynchronize(d->stream));
@@ -1414,8 +1569,9 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       err = "coarse Schur complement is not positive definite (pivot " + std::to_string(cstat - 1) + ")";
       return fail(IETI_ERR_NOT_SPD);
     }
-    if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * nc), err))) return fail(rc);
-    k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv);
+    if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * d->ldc), err))) return fail(rc);
+    CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
+    k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
     CK(cudaStreamSynchronize(d->stream));
     cudaFree(Sc);
     d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
@@ -1426,15 +1582,94 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   cudaFree(D);
   d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)D));
   d->bytes -= hdoff[np_] * 8;
-  size_t smem = (size_t)std::max(d->max_ni, 1) * sizeof(double);
-  if (smem > 48 * 1024) {
-    CK(cudaFuncSetAttribute(k_trsv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CK(cudaFuncSetAttribute(k_trsv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
   // algorithmic bytes of one PCG iteration: H and Psi once each (F apply), P once
   // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
   d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
                   8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
+  {
+    // ---- persistent PCG plan: grid from occupancy, byte-balanced partitions
+    int ldmax = 4, ldbmax = 4, ldpmax = 4;
+    for (int s = 0; s < np_; ++s) {
+      ldbmax = std::max(ldbmax, hldb[s]);
+      ldpmax = std::max(ldpmax, hldp[s]);
+    }
+    ldmax = std::max(ldbmax, ldpmax);
+    // shared memory: staged x vector, then NS TMA stages (whole rows per stage)
+    size_t xs_bytes = (std::max((size_t)ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
+    size_t budget = 220 * 1024;
+    size_t stage = std::min<size_t>(64 * 1024, (budget - std::min(budget - 3 * 4096, xs_bytes)) / NS) / 128 * 128;
+    d->xs_bytes = (unsigned)xs_bytes;
+    d->stage_bytes = (unsigned)stage;
+    if ((size_t)ldmax * esz > stage) {
+      err = "an interface block is too wide for the TMA stage of the PCG kernel";
+      return fail(IETI_ERR_TOO_LARGE);
+    }
+    d->pcg_smem = xs_bytes + NS * stage;
+    const void *fn = d->mixed ? (const void *)k_pcg<float> : (const void *)k_pcg<double>;
+    if (d->pcg_smem > 48 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->pcg_smem));
+    int per_sm = 0, n_sm = 0, coop = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, d->pcg_smem));
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, d->device));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, d->device));
+    if (!coop || per_sm < 1) {
+      err = "device cannot run the cooperative PCG kernel";
+      return fail(IETI_ERR_CUDA);
+    }
+    d->G = std::min(per_sm, 2) * n_sm;
+    std::vector<int32_t> hrows(np_);
+    for (int s = 0; s < np_; ++s) hrows[s] = hnb[s] + hnp[s];
+    std::vector<int32_t> sp, ss, r0v, r1v;
+    partition_rows(hrows, hldb, d->G, sp, ss, r0v, r1v);
+    if ((rc = upload(d, &d->hseg_ptr, sp, err)) || (rc = upload(d, &d->hseg_s, ss, err)) ||
+        (rc = upload(d, &d->hseg_r0, r0v, err)) || (rc = upload(d, &d->hseg_r1, r1v, err)))
+      return fail(rc);
+    partition_rows(hnb, hldb, d->G, sp, ss, r0v, r1v);
+    if ((rc = upload(d, &d->bseg_ptr, sp, err)) || (rc = upload(d, &d->bseg_s, ss, err)) ||
+        (rc = upload(d, &d->bseg_r0, r0v, err)) || (rc = upload(d, &d->bseg_r1, r1v, err)))
+      return fail(rc);
+    // fixed-width gather lists (an edge DOF is shared by at most 4 patches)
+    std::vector<int32_t> ell_l(d->NBt * BT_W, -1), cpp(d->NC * CP_W, -1);
+    std::vector<double> ell_s(d->NBt * BT_W, 0.0), ell_w(d->NBt * BT_W, 0.0);
+    for (int64_t q = 0; q < d->NBt; ++q) {
+      if (bt_ptr[q + 1] - bt_ptr[q] > BT_W) {
+        err = "an interface copy has more than 3 multipliers";
+        return fail(IETI_ERR_INVALID_ARG);
+      }
+      for (int t = bt_ptr[q]; t < bt_ptr[q + 1]; ++t) {
+        ell_l[q * BT_W + (t - bt_ptr[q])] = bt_lam[t];
+        ell_s[q * BT_W + (t - bt_ptr[q])] = bt_sgn[t];
+        ell_w[q * BT_W + (t - bt_ptr[q])] = bt_wd[t];
+      }
+    }
+    for (int64_t c = 0; c < d->NC; ++c) {
+      if (cptr[c + 1] - cptr[c] > CP_W) {
+        err = "a primal DOF has more than 4 copies";
+        return fail(IETI_ERR_INVALID_ARG);
+      }
+      for (int t = cptr[c]; t < cptr[c + 1]; ++t) cpp[c * CP_W + (t - cptr[c])] = cpos[t];
+    }
+    if ((rc = upload(d, &d->ell_lam, ell_l, err)) || (rc = upload(d, &d->ell_sgn, ell_s, err)) ||
+        (rc = upload(d, &d->ell_wd, ell_w, err)) || (rc = upload(d, &d->cp_pos, cpp, err)))
+      return fail(rc);
+    if ((rc = dalloc(d, &d->p1, m, err)) || (rc = dalloc(d, &d->r1, m, err)) || (rc = dalloc(d, &d->zb, d->NBt, err)) ||
+        (rc = dalloc(d, &d->zf, d->NBt, err)) || (rc = dalloc(d, &d->ubp, d->NBt, err)) ||
+        (rc = dalloc(d, &d->tpi, d->NPt, err)) || (rc = dalloc(d, &d->zp, d->NBt, err)) ||
+        (rc = dalloc(d, &d->ccg, d->NC, err)) || (rc = dalloc(d, &d->ppart, 4 * (size_t)d->G, err)) ||
+        (rc = dalloc(d, &d->bar, 4, err)) || (rc = dalloc(d, &d->pcg_its, 1, err)) ||
+        (rc = dalloc(d, &d->pcg_rr, 1, err)) || (rc = dalloc(d, &d->pcg_dd, 1, err)) ||
+        (rc = dalloc(d, &d->trace, TRACE_IT * 16, err)))
+      return fail(rc);
+    CK(cudaMemsetAsync(d->p, 0, m * sizeof(double), d->stream));
+    CK(cudaMemsetAsync(d->p1, 0, m * sizeof(double), d->stream));
+    int64_t sH = 0, sQ = 0, sP = 0;
+    for (int s = 0; s < np_; ++s) {
+      sH += (int64_t)(hnb[s] + hnp[s]) * hnb[s];
+      sQ += (int64_t)hnb[s] * hnp[s];
+      sP += (int64_t)hnb[s] * hnb[s];
+    }
+    d->bytes_iter_alg = (double)esz * (sH + sQ + sP) + 8.0 * (double)d->NC * d->NC +
+                        8.0 * (14.0 * d->M + 8.0 * d->NBt + 2.0 * d->NPt + 2.0 * d->NC);
+  }
   {
     // algorithmic bytes of one launch: every operator entry once, input vectors once per patch, outputs once
     double e = (double)esz;
@@ -1448,7 +1683,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       sl += (int64_t)hni[s] * (hni[s] + 1) / 2;
     }
     d->gemv_bytes[IETI_K_GEMV_Y] = e * sy + 8.0 * (2 * (double)d->NK);
-    d->gemv_bytes[IETI_K_TRSV] = e * sl + 8.0 * 2 * (double)d->NK;
+    d->gemv_bytes[IETI_K_TRI] = e * sl + 8.0 * 2 * (double)d->NK;
     d->gemv_bytes[IETI_K_SPMV] = 12.0 * (double)wval.size() + 8.0 * 3 * (double)d->NK;
   }
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1500,7 +1735,7 @@ int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std:
 void device_info(const DeviceState *d, ieti_info *info) {
   info->n_lambda = d->M;
   info->n_coarse = d->NC;
-  info->bytes_iter = d->bytes_iter;
+  info->bytes_iter = (int64_t)d->bytes_iter_alg;
   info->bytes_device = d->bytes;
   info->t_setup_device_ms = d->t_setup_ms;
   info->kernel_launches_setup = d->launches_setup;
@@ -1511,6 +1746,17 @@ void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
   for (int c = 0; c < IETI_K_NCLASS; ++c) out[c] = d->kstat[c];
   if (reset)
     for (int c = 0; c < IETI_K_NCLASS; ++c) d->kstat[c] = ieti_kernel_stat{};
+}
+
+void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, bool reset) {
+  for (int ph = 0; ph < 6; ++ph) {
+    work_us[ph] = d->trace_n ? d->trace_acc[ph] / d->trace_n : 0.0;
+    wait_us[ph] = d->trace_n ? d->trace_wait[ph] / d->trace_n : 0.0;
+  }
+  if (reset) {
+    for (int ph = 0; ph < 8; ++ph) d->trace_acc[ph] = d->trace_wait[ph] = 0;
+    d->trace_n = 0;
+  }
 }
 
 void device_destroy(DeviceState *d) {

@@ -36,7 +36,7 @@ class ieti_problem(C.Structure):
 class ieti_options(C.Structure):
     _fields_ = [("device", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
-                ("max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("host_threads", C.c_int32),
+                ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32)]
 
 
@@ -53,7 +53,7 @@ class ieti_kernel_stat(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double)]
 
 
-KERNEL_CLASSES = ["gemv_H", "gemv_Q", "gemv_P", "gemv_S", "gemv_Y", "trsv", "spmv", "vec"]
+KERNEL_CLASSES = ["gemv_H", "gemv_Q", "gemv_P", "gemv_S", "gemv_Y", "tri", "spmv", "vec", "pcg"]
 
 
 class ieti_info(C.Structure):
@@ -79,6 +79,7 @@ lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
 lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
+lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_last_error.argtypes = [_ctx]
 lib.ieti_last_error.restype = C.c_char_p
 lib.ieti_destroy.argtypes = [_ctx]
@@ -86,7 +87,7 @@ lib.ieti_destroy.restype = None
 
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
-            "ieti_last_error", "ieti_destroy", "ieti_kernel_stats"]
+            "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times"]
 
 
 class IetiError(RuntimeError):
@@ -110,7 +111,7 @@ class Solver:
 
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
-                 outer_tol=1e-12, max_sweeps=None, use_graph=0, host_threads=0, stream=None, profile=0):
+                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -138,7 +139,7 @@ class Solver:
         if max_sweeps is None:
             max_sweeps = 1 if op.precision == 0 else 20
         op.max_sweeps = int(max_sweeps)
-        op.use_graph = int(use_graph)
+        op.pcg_mode = int(pcg_mode)
         op.host_threads = int(host_threads)
         op.cuda_stream = C.c_void_p(stream or 0)
         op.profile = int(profile)
@@ -192,6 +193,12 @@ class Solver:
         self._check(lib.ieti_kernel_stats(self.ctx, C.cast(arr, C.c_void_p), int(reset)))
         return {name: {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes}
                 for i, name in enumerate(KERNEL_CLASSES)}
+
+    def pcg_phase_times(self, reset=False):
+        work = np.zeros(6)
+        wait = np.zeros(6)
+        self._check(lib.ieti_pcg_phase_times(self.ctx, work.ctypes.data, wait.ctypes.data, int(reset)))
+        return {"work_us": work.tolist(), "wait_us": wait.tolist()}
 
     def step(self, j, raise_on_error=True):
         p, mem = _ptr(j)

@@ -177,3 +177,15 @@ def test_c2_full_size_residual(ieti, c2_oracle, mode):
                          outer_tol=1e-13, max_sweeps=5)
         for a, b in zip(ref, got):
             assert np.linalg.norm(a - b) <= TOL["mixed"] * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_pcg_modes_agree(ieti, mode):
+    """The persistent cooperative PCG kernel and the launch-per-phase loop run the
+    same algorithm: same iteration count, same solution within the mode tolerance."""
+    prob, op, ref = oracle_run("ragged_p23", 2)
+    a, sa = gpu_run(ieti, prob, 2, precond="dirichlet_stiff", pcg_mode=0, **OPTS[mode])
+    b, sb = gpu_run(ieti, prob, 2, precond="dirichlet_stiff", pcg_mode=1, **OPTS[mode])
+    for x, y, s1, s2 in zip(a, b, sa, sb):
+        assert abs(s1["cg_its"] - s2["cg_its"]) <= 1
+        assert np.linalg.norm(x - y) <= TOL[mode] * np.linalg.norm(x)
