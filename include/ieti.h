@@ -191,8 +191,24 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);
  * work_us and wait_us have 6 entries each.  reset != 0 clears the accumulators. */
 int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_t reset);
 
+/* Batched dense partial Cholesky, the kernel family behind both Schur complements
+ * of Sec. 3 (local W_rr eliminations and the coarse block), exposed for callers and
+ * kernel-level tests.  Matrix b is row-major n[b] x n[b] at base_dev + offsets[b]
+ * (device memory of the current device, offsets in doubles, caller-owned; only the
+ * lower triangle is read and written).  The first n_pivots[b] pivots are eliminated
+ * in place: those columns hold the factor L (A = L L^T on the leading block,
+ * L21 = A21 L11^{-T}) and the trailing lower triangle holds the Schur complement
+ * A22 - L21 L21^T.  status_out[b] (host) is 0, or 1 + the index of the first
+ * non-positive pivot (the factorization then continues with a unit pivot).
+ * offsets, n, n_pivots, status_out are host arrays of length batch; stream is a
+ * cudaStream_t (0 = legacy default).  Allocates and frees its device scratch (the
+ * descriptor copies and the status words) on every call.  Returns 0, INVALID_ARG
+ * (batch < 1, n < 1, n_pivots outside [0, n], NULL pointers), CUDA or OOM. */
+int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
+                       const int32_t *n_pivots, int32_t *status_out, void *stream);
+
 const char *ieti_last_error(const ieti_ctx *ctx);
-/* Message of the last failed ieti_setup (no context exists then). */
+/* Message of the last failed ieti_setup or ieti_potrf_batched (no context exists then). */
 const char *ieti_setup_error(void);
 
 void ieti_destroy(ieti_ctx *ctx);

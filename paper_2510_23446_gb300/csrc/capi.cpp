@@ -151,6 +151,27 @@ int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_
   return IETI_OK;
 }
 
+int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
+                       const int32_t *n_pivots, int32_t *status_out, void *stream) {
+  g_setup_err.clear();
+  if (batch < 1 || !base_dev || !offsets || !n || !n_pivots || !status_out) {
+    g_setup_err = "ieti_potrf_batched: invalid arguments";
+    return IETI_ERR_INVALID_ARG;
+  }
+  for (int32_t b = 0; b < batch; ++b)
+    if (n[b] < 1 || n_pivots[b] < 0 || n_pivots[b] > n[b] || offsets[b] < 0) {
+      g_setup_err = "ieti_potrf_batched: bad size, pivot count or offset of matrix " + std::to_string(b);
+      return IETI_ERR_INVALID_ARG;
+    }
+  try {
+    return ieti::device_potrf_batched(batch, base_dev, offsets, n, n_pivots, status_out, (cudaStream_t)stream,
+                                      g_setup_err);
+  } catch (...) {
+    g_setup_err = "ieti_potrf_batched: host allocation failed";
+    return IETI_ERR_OOM;
+  }
+}
+
 const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 void ieti_destroy(ieti_ctx *ctx) {

@@ -1772,3 +1772,59 @@ void device_destroy(DeviceState *d) {
 }
 
 }  // namespace ieti
+
+namespace ieti {
+
+// standalone batched partial Cholesky on caller memory (descriptor scratch allocated here)
+int device_potrf_batched(int batch, double *base, const int64_t *off, const int32_t *n, const int32_t *npiv,
+                         int32_t *status, cudaStream_t st, std::string &err) {
+  std::vector<int32_t> hkb(batch, 0), hke(npiv, npiv + batch), hna(n, n + batch), hz(batch, 0),
+      hbig(batch, INT32_MAX);
+  std::vector<int64_t> hoff(off, off + batch);
+  std::vector<int32_t> hn(n, n + batch);
+  // one device block holds every descriptor array and the status words
+  size_t bytes = (size_t)batch * (sizeof(int64_t) + 8 * sizeof(int32_t));
+  unsigned char *blk = nullptr;
+  cudaError_t e = cudaMalloc((void **)&blk, bytes);
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_OOM;
+  }
+  int64_t *doff = (int64_t *)blk;
+  int32_t *dn = (int32_t *)(doff + batch), *dkb = dn + batch, *dke = dkb + batch, *dna = dke + batch,
+          *dst = dna + batch, *dz = dst + batch, *dbig = dz + batch, *dz2 = dbig + batch;
+  int rc = IETI_OK;
+  auto cp = [&](void *dst_, const void *src, size_t nbytes) {
+    if (rc == IETI_OK && cudaMemcpyAsync(dst_, src, nbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      err = "cudaMemcpyAsync failed";
+      rc = IETI_ERR_CUDA;
+    }
+  };
+  cp(doff, hoff.data(), batch * 8);
+  cp(dn, hn.data(), batch * 4);
+  cp(dkb, hkb.data(), batch * 4);
+  cp(dke, hke.data(), batch * 4);
+  cp(dna, hna.data(), batch * 4);
+  cp(dz, hz.data(), batch * 4);
+  cp(dbig, hbig.data(), batch * 4);
+  cp(dz2, hz.data(), batch * 4);
+  if (rc == IETI_OK && cudaMemsetAsync(dst, 0, batch * 4, st) != cudaSuccess) rc = IETI_ERR_CUDA;
+  if (rc == IETI_OK) {
+    DeviceState tmp;
+    tmp.stream = st;
+    AugLimits lim{dz, dz2, dbig, dz};
+    rc = potrf_partial<double>(&tmp, base, doff, dn, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+  }
+  if (rc == IETI_OK) {
+    if (cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      err = std::string("batched partial Cholesky failed: ") + cudaGetErrorString(cudaGetLastError());
+      rc = IETI_ERR_CUDA;
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(blk);
+  return rc;
+}
+
+}  // namespace ieti

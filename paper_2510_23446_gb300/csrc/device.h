@@ -3,6 +3,8 @@
 #pragma once
 #include <string>
 
+#include <cuda_runtime.h>
+
 #include "host_setup.h"
 
 namespace ieti {
@@ -17,5 +19,7 @@ void device_info(const DeviceState *d, ieti_info *info);
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset);
 void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, bool reset);
 void device_destroy(DeviceState *d);
+int device_potrf_batched(int batch, double *base, const int64_t *off, const int32_t *n, const int32_t *npiv,
+                         int32_t *status, cudaStream_t st, std::string &err);
 
 }  // namespace ieti

@@ -80,6 +80,8 @@ lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
+lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]
 lib.ieti_last_error.argtypes = [_ctx]
 lib.ieti_last_error.restype = C.c_char_p
 lib.ieti_destroy.argtypes = [_ctx]
@@ -87,7 +89,8 @@ lib.ieti_destroy.restype = None
 
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
-            "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times"]
+            "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
+            "ieti_potrf_batched"]
 
 
 class IetiError(RuntimeError):
@@ -229,3 +232,21 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def potrf_batched(base, offsets, n, n_pivots, stream=0):
+    """ieti_potrf_batched on a device buffer `base` (torch CUDA float64 tensor).
+
+    Returns the per-matrix status array (0 = all pivots positive)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nn = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    kp = np.ascontiguousarray(np.asarray(n_pivots, dtype=np.int32))
+    st = np.zeros(len(nn), dtype=np.int32)
+    p, mem = _ptr(base)
+    if mem != IETI_MEM_DEVICE:
+        raise TypeError("base must be a CUDA tensor")
+    rc = lib.ieti_potrf_batched(len(nn), C.c_void_p(p), off.ctypes.data, nn.ctypes.data, kp.ctypes.data,
+                                st.ctypes.data, C.c_void_p(stream or 0))
+    if rc != 0:
+        raise IetiError(rc, lib.ieti_setup_error().decode())
+    return st
