@@ -207,8 +207,27 @@ int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_
 int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
                        const int32_t *n_pivots, int32_t *status_out, void *stream);
 
+/* ieti_potrf_batched for callers that must not allocate device memory: code that
+ * runs under a fixed memory budget (an application that reserved all device memory
+ * for its own pool), inside a host callback or library hook where cudaMalloc is not
+ * allowed, or that must avoid the implicit device synchronisation cudaFree causes.
+ * The paper has no counterpart; this is a library convenience.
+ *
+ * Same arguments, results and errors as ieti_potrf_batched.  Its scratch (the
+ * descriptor copies and status words, 40 bytes per matrix) lives in one static
+ * device array of IETI_NOALLOC_MAX_BATCH entries, which every device that loads the
+ * library holds until the process exits; batch > IETI_NOALLOC_MAX_BATCH returns
+ * IETI_ERR_TOO_LARGE.  It calls no cudaMalloc or cudaFree.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array (the status words are cleared at each call), so calls
+ * whose GPU work overlaps, on different streams or threads, race. */
+#define IETI_NOALLOC_MAX_BATCH 4096
+int ieti_potrf_batched_noalloc(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
+                               const int32_t *n_pivots, int32_t *status_out, void *stream);
+
 const char *ieti_last_error(const ieti_ctx *ctx);
-/* Message of the last failed ieti_setup or ieti_potrf_batched (no context exists then). */
+/* Message of the last failed ieti_setup or ieti_potrf_batched[_noalloc] (no context exists then). */
 const char *ieti_setup_error(void);
 
 void ieti_destroy(ieti_ctx *ctx);

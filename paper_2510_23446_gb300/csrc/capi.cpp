@@ -172,6 +172,23 @@ int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, 
   }
 }
 
+// Variant of ieti_potrf_batched that allocates no device memory (static scratch).
+int ieti_potrf_batched_noalloc(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
+                               const int32_t *n_pivots, int32_t *status_out, void *stream) {
+  g_setup_err.clear();
+  if (batch < 1 || !base_dev || !offsets || !n || !n_pivots || !status_out) {
+    g_setup_err = "ieti_potrf_batched_noalloc: invalid arguments";
+    return IETI_ERR_INVALID_ARG;
+  }
+  for (int32_t b = 0; b < batch && b <= IETI_NOALLOC_MAX_BATCH; ++b)
+    if (n[b] < 1 || n_pivots[b] < 0 || n_pivots[b] > n[b] || offsets[b] < 0) {
+      g_setup_err = "ieti_potrf_batched_noalloc: bad size, pivot count or offset of matrix " + std::to_string(b);
+      return IETI_ERR_INVALID_ARG;
+    }
+  return ieti::device_potrf_batched_noalloc(batch, base_dev, offsets, n, n_pivots, status_out,
+                                            (cudaStream_t)stream, g_setup_err);
+}
+
 const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 void ieti_destroy(ieti_ctx *ctx) {

@@ -30,6 +30,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "device.h"
@@ -1825,6 +1826,99 @@ int device_potrf_batched(int batch, double *base, const int64_t *off, const int3
   cudaStreamSynchronize(st);
   cudaFree(blk);
   return rc;
+}
+
+}  // namespace ieti
+
+namespace ieti {
+
+// Scratch of ieti_potrf_batched_noalloc: per matrix one int64 offset and eight int32
+// words (size, first pivot, pivot end, active rows, status, two zero words, one
+// "no limit" word).  Held by every device that loads the library.
+constexpr int NOALLOC_MAX = IETI_NOALLOC_MAX_BATCH;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * (8 + 8 * 4)];
+
+// device address of the scratch array, looked up once per device (with it current)
+static void *noalloc_scratch_address(int dev, std::string &err) {
+  static std::mutex mu;
+  static void *addr[256] = {};
+  if (dev < 0 || dev >= 256) {
+    err = "device ordinal out of range";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      err = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+int device_potrf_batched_noalloc(int batch, double *base, const int64_t *off, const int32_t *n,
+                                 const int32_t *npiv, int32_t *status, cudaStream_t st, std::string &err) {
+  if (batch > NOALLOC_MAX) {
+    err = "ieti_potrf_batched_noalloc: batch " + std::to_string(batch) + " exceeds IETI_NOALLOC_MAX_BATCH (" +
+          std::to_string(NOALLOC_MAX) + ")";
+    return IETI_ERR_TOO_LARGE;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    err = "cudaGetDevice failed";
+    return IETI_ERR_CUDA;
+  }
+  unsigned char *blk = (unsigned char *)noalloc_scratch_address(dev, err);
+  if (!blk) return IETI_ERR_CUDA;
+  int64_t *doff = (int64_t *)blk;
+  int32_t *dn = (int32_t *)(blk + 8 * NOALLOC_MAX);
+  int32_t *dkb = dn + NOALLOC_MAX, *dke = dkb + NOALLOC_MAX, *dna = dke + NOALLOC_MAX, *dst = dna + NOALLOC_MAX,
+          *dz = dst + NOALLOC_MAX, *dz2 = dz + NOALLOC_MAX, *dbig = dz2 + NOALLOC_MAX;
+  // the previous call's contents remain: set every word this call reads
+  if (cudaMemcpyAsync(doff, off, batch * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dn, n, batch * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dke, npiv, batch * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dna, n, batch * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(dkb, 0, batch * 4, st) != cudaSuccess || cudaMemsetAsync(dst, 0, batch * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(dz, 0, batch * 4, st) != cudaSuccess || cudaMemsetAsync(dz2, 0, batch * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(dbig, 0x7f, batch * 4, st) != cudaSuccess) {  // 0x7f7f7f7f: no row limit
+    err = std::string("scratch upload failed: ") + cudaGetErrorString(cudaGetLastError());
+    return IETI_ERR_CUDA;
+  }
+  AugLimits lim{dz, dz2, dbig, dz};
+  int max_panels = 0;
+  for (int b = 0; b < batch; ++b) max_panels = std::max(max_panels, (npiv[b] + NB - 1) / NB);
+  for (int j = 0; j < max_panels; ++j) {
+    int max_rows = 0, max_tiles = 0;
+    for (int b = 0; b < batch; ++b) {
+      int j0 = j * NB;
+      if (j0 >= npiv[b]) continue;
+      int jb = std::min(NB, npiv[b] - j0);
+      int m = n[b] - (j0 + jb);
+      if (m <= 0) continue;
+      max_rows = std::max(max_rows, m);
+      int T64 = (m + 63) / 64;
+      max_tiles = std::max(max_tiles, T64 * (T64 + 1) / 2);
+    }
+    k_potrf_diag<double><<<batch, 256, 0, st>>>(base, doff, dn, dkb, dke, j, dst);
+    if (max_rows > 0) {
+      dim3 g1(grid_for(max_rows, 128), batch);
+      k_trsm_panel<double><<<g1, 128, 0, st>>>(base, doff, dn, dkb, dke, dna, j, lim);
+      dim3 g2(max_tiles, batch);
+      k_syrk_update<double><<<g2, 256, 0, st>>>(base, doff, dn, dkb, dke, dna, j, lim);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    err = std::string("batched partial Cholesky failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_CUDA;
+  }
+  return IETI_OK;
 }
 
 }  // namespace ieti

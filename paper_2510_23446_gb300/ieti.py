@@ -82,6 +82,7 @@ lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
+lib.ieti_potrf_batched_noalloc.argtypes = lib.ieti_potrf_batched.argtypes
 lib.ieti_last_error.argtypes = [_ctx]
 lib.ieti_last_error.restype = C.c_char_p
 lib.ieti_destroy.argtypes = [_ctx]
@@ -90,7 +91,7 @@ lib.ieti_destroy.restype = None
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
-            "ieti_potrf_batched"]
+            "ieti_potrf_batched", "ieti_potrf_batched_noalloc"]
 
 
 class IetiError(RuntimeError):
@@ -234,8 +235,9 @@ class Solver:
             pass
 
 
-def potrf_batched(base, offsets, n, n_pivots, stream=0):
-    """ieti_potrf_batched on a device buffer `base` (torch CUDA float64 tensor).
+def potrf_batched(base, offsets, n, n_pivots, stream=0, noalloc=False):
+    """ieti_potrf_batched (or, with noalloc=True, ieti_potrf_batched_noalloc, which
+    allocates no device memory) on a device buffer `base` (torch CUDA float64 tensor).
 
     Returns the per-matrix status array (0 = all pivots positive)."""
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -245,8 +247,9 @@ def potrf_batched(base, offsets, n, n_pivots, stream=0):
     p, mem = _ptr(base)
     if mem != IETI_MEM_DEVICE:
         raise TypeError("base must be a CUDA tensor")
-    rc = lib.ieti_potrf_batched(len(nn), C.c_void_p(p), off.ctypes.data, nn.ctypes.data, kp.ctypes.data,
-                                st.ctypes.data, C.c_void_p(stream or 0))
+    fn = lib.ieti_potrf_batched_noalloc if noalloc else lib.ieti_potrf_batched
+    rc = fn(len(nn), C.c_void_p(p), off.ctypes.data, nn.ctypes.data, kp.ctypes.data, st.ctypes.data,
+            C.c_void_p(stream or 0))
     if rc != 0:
         raise IetiError(rc, lib.ieti_setup_error().decode())
     return st
