@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
     return ap.parse_args()
 
 
@@ -293,8 +295,28 @@ def run_ours(args):
     return 0
 
 
+def run_profile_step(args):
+    """Set up the mixed path on the bench workload and run a few steps (for ncu)."""
+    import torch
+    from workloads import make_problem
+    from paper_2510_23446_gb300.build import build
+    build()
+    from paper_2510_23446_gb300 import ieti
+    prob = make_problem("c2")
+    S = ieti.Solver.from_problem(prob, device=0, **OPTS["mixed"])
+    jd = torch.from_numpy(S.load_vector(prob.coil)).cuda()
+    for _ in range(max(1, args.warmup) + 2):
+        st = S.step(jd)
+    torch.cuda.synchronize()
+    print("profile-step done:", st, flush=True)
+    S.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_step:
+        return run_profile_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

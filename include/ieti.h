@@ -90,6 +90,8 @@ typedef struct {
   int32_t host_threads;  /* threads for the host setup (0 = all cores) */
   void *cuda_stream;     /* cudaStream_t (0 = legacy default stream) */
   int32_t profile;       /* 1: time every launch of the operator kernels with CUDA events (ieti_kernel_stats) */
+  int32_t l2_persist;    /* 1: keep the per-iteration operators in a persisting L2 carve-out during a step
+                            (reset to normal at the end of every step); 0: plain streaming */
 } ieti_options;
 
 /* Coil source through its potential T = T_z(r) chi(|z - zc| < hz) e_z (J = curl T):
@@ -119,6 +121,9 @@ typedef struct {
   int64_t bytes_device;  /* device memory held by the context */
   double t_setup_host_ms, t_setup_device_ms;
   int64_t kernel_launches_setup;
+  int64_t l2_window_bytes;   /* per-iteration operators covered by the persisting L2 window (0: off) */
+  double l2_hit_ratio;       /* fraction of that window marked persisting */
+  int64_t iter_operator_bytes; /* size of the per-iteration operator arena */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -288,29 +288,33 @@ __global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_
   }
 }
 
-// LY_s (n x ni): rows < ni hold X = L_ii^{-1} in the lower triangle and X^T in the
-// strict upper triangle (XX[r][c] = X[max][min]); rows >= ni hold Y = L_[bp]i.
-// X[r][c] = (L_{i'i})[c][r] = D[n + nb + c][r] (c <= r).
+// IG_s (n x ldi): rows < ni hold W_ii^{-1} (= -trailing i'i'), rows >= ni hold
+// G = W_[bp]i W_ii^{-1}; GT_s (ni x ldg) holds G^T.  After the interior pivots the
+// trailing block of the augmented matrix has (i', i') = -W_ii^{-1} and
+// (i', [b p]) = -W_ii^{-1} W_i[bp] = -G^T.
 template <class T>
-__global__ void k_extract_LY(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
-                             const int32_t *nb, const int32_t *np, const int64_t *lyoff, T *LY) {
+__global__ void k_extract_IG(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+                             const int32_t *nb, const int32_t *np, const int32_t *ldi, const int32_t *ldg,
+                             const int64_t *igoff, const int64_t *gtoff, T *IG, T *GT) {
   int s = blockIdx.y;
   int I = ni[s], B = nb[s];
   int n = I + B + np[s];
   int64_t ld = nn[s];
   const double *A = D + doff[s];
   int64_t total = (int64_t)n * I;
+  int64_t ip = n + B;  // first i' row
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(idx / I), c = (int)(idx % I);
     double v;
     if (r < I) {
       int hi = max(r, c), lo = min(r, c);
-      v = A[(int64_t)(n + B + lo) * ld + hi];
+      v = -A[(ip + hi) * ld + ip + lo];
     } else {
-      v = A[(int64_t)r * ld + c];
+      v = -A[(ip + c) * ld + r];
+      GT[gtoff[s] + (int64_t)c * ldg[s] + (r - I)] = (T)v;
     }
-    LY[lyoff[s] + idx] = (T)v;
+    IG[igoff[s] + (int64_t)r * ldi[s] + c] = (T)v;
   }
 }
 
@@ -331,6 +335,15 @@ __global__ void k_coarse_identity(int nc, double *Sc, int64_t ldc) {
   if (r >= nc) return;
   Sc[(int64_t)(nc + r) * ldc + r] = 1.0;
   Sc[(int64_t)r * ldc + nc + r] = 1.0;
+}
+
+// (hi, lo) FP32 pairs of FP64 values: hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_split_pairs(int64_t n, const double *x, float2 *out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = x[i];
+  float hi = (float)v;
+  out[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
 __global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv, int ldo) {
@@ -374,24 +387,6 @@ __global__ void k_gemv_rows(int64_t n_rows, const int64_t *aoff, const int64_t *
       y[yi] = v;
     }
   }
-}
-
-// t[c] = z[c] - sum_r Y[r][c] x[ni + r]  for c < ni  (x: kept [b|p] part)
-template <class T>
-__global__ void k_gemvT_Y(const int32_t *ni, const int32_t *nb, const int32_t *np, const int64_t *lyoff,
-                          const int64_t *kofs, const T *LY, const double *z, const double *x, double *t) {
-  using A_t = typename Acc<T>::type;
-  int s = blockIdx.y;
-  int I = ni[s];
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= I) return;
-  int R = nb[s] + np[s];
-  const T *Y = LY + lyoff[s] + (int64_t)I * I;
-  const double *xv = x + kofs[s] + I;
-  A_t acc = 0;
-#pragma unroll 4
-  for (int r = 0; r < R; ++r) acc += (A_t)Y[(int64_t)r * I + c] * (A_t)xv[r];
-  t[kofs[s] + c] = z[kofs[s] + c] - (double)acc;
 }
 
 // kept-space gather of the global state: out[k] = a[glob[k]]
@@ -611,7 +606,7 @@ struct DeviceState {
   std::vector<int32_t> h_ni, h_nb, h_np;
   // per patch device arrays
   int32_t *ni = nullptr, *nb = nullptr, *npp = nullptr;
-  int64_t *kofs = nullptr, *lyoff = nullptr, *hoff = nullptr, *qoff = nullptr, *poff = nullptr;
+  int64_t *kofs = nullptr, *igoff = nullptr, *gtoff = nullptr, *hoff = nullptr, *qoff = nullptr, *poff = nullptr;
   // kept space
   int64_t *kglob = nullptr;
   double *kw = nullptr;
@@ -629,14 +624,14 @@ struct DeviceState {
   int64_t *fptr = nullptr, *fpos = nullptr, *fglob = nullptr;
   double *rglob = nullptr;
   // operators (T = double or float)
-  void *LY = nullptr, *H = nullptr, *Q = nullptr, *P = nullptr;
+  void *IG = nullptr, *GT = nullptr, *H = nullptr, *Q = nullptr, *P = nullptr;
   double *Sinv = nullptr;
   // GEMV descriptors
   struct Desc {
     int64_t n = 0;
     int64_t *aoff = nullptr, *xoff = nullptr, *yidx = nullptr;
     int32_t *ncol = nullptr;
-  } dY, dH, dQ, dP, dS, dXf, dXb;
+  } dH, dQ, dP, dS, dIGi, dIGg, dGT;
   // vectors
   double *a = nullptr, *j = nullptr, *kf = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *ka = nullptr,
          *kt = nullptr;
@@ -646,10 +641,22 @@ struct DeviceState {
   // persistent PCG
   int G = 0, ldc = 0;
   size_t pcg_smem = 0;
-  int32_t *ldb = nullptr, *ldp = nullptr, *bpatch = nullptr;
+  int32_t *ldb = nullptr, *ldp = nullptr, *ldi = nullptr, *ldg = nullptr, *bpatch = nullptr;
   int64_t *bofs_d = nullptr, *pofs_d = nullptr;
   int32_t *hseg_ptr = nullptr, *hseg_s = nullptr, *hseg_r0 = nullptr, *hseg_r1 = nullptr;
   int32_t *bseg_ptr = nullptr, *bseg_s = nullptr, *bseg_r0 = nullptr, *bseg_r1 = nullptr;
+  int32_t *iseg_ptr = nullptr, *iseg_s = nullptr, *iseg_r0 = nullptr, *iseg_r1 = nullptr;
+  int32_t *tseg_ptr = nullptr, *tseg_s = nullptr, *tseg_r0 = nullptr, *tseg_r1 = nullptr;
+  double *kg = nullptr, *ub1 = nullptr, *uz = nullptr;
+  double *Sdf = nullptr;  // mixed path: S_c^{-1} as (hi, lo) FP32 pairs, viewed as doubles
+  // per-iteration operators (H, Q, P, coarse) share one arena, the L2 access-policy window
+  unsigned char *iter_arena = nullptr;
+  double *Scoarse_slot = nullptr;  // coarse operator used by the PCG kernel (inside iter_arena)
+  size_t iter_bytes = 0, l2_window = 0;
+  float l2_hit_ratio = 0.f;
+  bool l2_set = false;
+  size_t l2_prev_limit = 0;
+  int n_stages = 3;
   int32_t *ell_lam = nullptr, *cp_pos = nullptr;
   double *ell_sgn = nullptr, *ell_wd = nullptr;
   double *p1 = nullptr, *r1 = nullptr, *zb = nullptr, *zf = nullptr, *ubp = nullptr, *tpi = nullptr, *zp = nullptr,
@@ -661,7 +668,7 @@ struct DeviceState {
   double trace_wait[8] = {};
   int64_t trace_n = 0;
   double *pcg_rr = nullptr, *pcg_dd = nullptr;
-  double bytes_iter_alg = 0;
+  double bytes_iter_alg = 0, bytes_sweep_alg = 0;
   unsigned xs_bytes = 0, stage_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dt = 0;
@@ -905,13 +912,13 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
   return IETI_OK;
 }
 
-// PCG as one persistent cooperative launch (pcg_kernel.cuh)
+// the whole dual-primal solve of a sweep as one persistent cooperative launch
+// (pcg_kernel.cuh): condensation, d, PCG, recovery
 template <class T>
-static int pcg_persistent(DeviceState *d, int *its, double *rel, std::string &err) {
+static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
   cudaStream_t st = d->stream;
   *its = 0;
   *rel = 0.0;
-  if (d->M == 0) return IETI_OK;
   CK(cudaMemsetAsync(d->bar, 0, 3 * sizeof(unsigned), st));
   PcgArgs<T> a;
   a.m = d->M;
@@ -925,23 +932,52 @@ static int pcg_persistent(DeviceState *d, int *its, double *rel, std::string &er
   a.lam_qp = d->lam_qp; a.lam_qm = d->lam_qm;
   a.lam_wp = a.scaled ? d->lam_wp : nullptr;
   a.lam_wm = a.scaled ? d->lam_wm : nullptr;
-  a.bofs = d->bofs_d; a.pofs = d->pofs_d; a.hoff = d->hoff; a.qoff = d->qoff; a.poff = d->poff;
-  a.nb = d->nb; a.np = d->npp; a.ldb = d->ldb; a.ldp = d->ldp;
-  a.pc = d->pc; a.cp_pos = d->cp_pos;
+  a.kofs = d->kofs; a.bofs = d->bofs_d; a.pofs = d->pofs_d; a.hoff = d->hoff; a.qoff = d->qoff; a.poff = d->poff;
+  a.igoff = d->igoff; a.gtoff = d->gtoff;
+  a.ni = d->ni; a.nb = d->nb; a.np = d->npp; a.ldb = d->ldb; a.ldp = d->ldp; a.ldi = d->ldi; a.ldg = d->ldg;
+  a.pc = d->pc; a.cp_pos = d->cp_pos; a.p_kept = d->p_kept; a.b_kept = d->b_kept;
+  a.IG = (const T *)d->IG; a.GT = (const T *)d->GT;
   a.H = (const T *)d->H; a.Q = (const T *)d->Q; a.P = (const T *)d->P; a.Sinv = d->Sinv;
   a.hseg_ptr = d->hseg_ptr; a.hseg_s = d->hseg_s; a.hseg_r0 = d->hseg_r0; a.hseg_r1 = d->hseg_r1;
   a.bseg_ptr = d->bseg_ptr; a.bseg_s = d->bseg_s; a.bseg_r0 = d->bseg_r0; a.bseg_r1 = d->bseg_r1;
-  a.d = d->dvec; a.lam = d->lam; a.p0 = d->p; a.p1 = d->p1; a.r0 = d->r; a.r1 = d->r1; a.z = d->z;
+  a.iseg_ptr = d->iseg_ptr; a.iseg_s = d->iseg_s; a.iseg_r0 = d->iseg_r0; a.iseg_r1 = d->iseg_r1;
+  a.tseg_ptr = d->tseg_ptr; a.tseg_s = d->tseg_s; a.tseg_r0 = d->tseg_r0; a.tseg_r1 = d->tseg_r1;
+  a.rhs = rhs; a.kg = d->kg; a.kx = d->kx; a.ub1 = d->ub1; a.uz = d->uz; a.nbt = d->NBt;
+  a.Sinv = d->Scoarse_slot;
+  a.lam = d->lam; a.p0 = d->p; a.p1 = d->p1; a.r0 = d->r; a.r1 = d->r1; a.z = d->z;
   a.ub = d->ubp; a.zb = d->zb; a.zf = d->zf; a.tpi = d->tpi; a.cc = d->ccg; a.q = d->q; a.zp = d->zp;
   a.part = d->ppart;
   a.bar = d->bar; a.out_its = d->pcg_its; a.out_rr = d->pcg_rr; a.out_dd = d->pcg_dd;
   a.trace = d->opt.profile ? d->trace : nullptr;
   a.stage_bytes = d->stage_bytes;
   a.xs_bytes = d->xs_bytes;
+  a.n_stages = d->n_stages;
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * 16 * sizeof(unsigned long long), st));
   void *args[] = {&a};
   prof_begin(d, IETI_K_PCG, 0.0);
-  CK(cudaLaunchCooperativeKernel((void *)k_pcg<T>, d->G, PCG_THREADS, args, d->pcg_smem, st));
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(d->G);
+    cfg.blockDim = dim3(PCG_THREADS);
+    cfg.dynamicSmemBytes = d->pcg_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    int nattr = 1;
+    if (d->l2_window > 0) {
+      attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+      attr[1].val.accessPolicyWindow.base_ptr = d->iter_arena;
+      attr[1].val.accessPolicyWindow.num_bytes = d->l2_window;
+      attr[1].val.accessPolicyWindow.hitRatio = d->l2_hit_ratio;
+      attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+      nattr = 2;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = nattr;
+    CK(cudaLaunchKernelExC(&cfg, (const void *)k_ddsolve<T>, args));
+  }
   d->nlaunch++;
   prof_end(d);
   struct {
@@ -959,7 +995,7 @@ static int pcg_persistent(DeviceState *d, int *its, double *rel, std::string &er
     return IETI_ERR_CUDA;
   }
   *its = h.its;
-  prof_set_bytes(d, d->bytes_iter_alg * h.its);
+  prof_set_bytes(d, d->bytes_iter_alg * (h.its + 2) + d->bytes_sweep_alg);
   if (a.trace) {
     unsigned long long tr[TRACE_IT * 16];
     CK(cudaMemcpy(tr, d->trace, sizeof(tr), cudaMemcpyDeviceToHost));
@@ -1022,19 +1058,25 @@ static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std
 // dual-primal solve of the gauged step system for kept-space right-hand sides
 // rhs (per patch, Sec. 3), solution into d->kx (kept space)
 template <class T>
+static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err);
+
+// dual-primal solve of the gauged step system for kept-space right-hand sides rhs
+// (per patch, Sec. 3), solution into d->kx (kept space)
+template <class T>
 static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
+  if (d->opt.pcg_mode == 0) return pcg_persistent<T>(d, rhs, its, rel, err);
   cudaStream_t st = d->stream;
-  // interior condensation with the explicit X = L_ii^{-1}: z_i = X rhs_i; g_[bp] = rhs_[bp] - Y z_i
-  gemv<T>(d, d->dXf, d->LY, rhs, d->kz, nullptr, 1.0, 0.0, IETI_K_TRI);
-  gemv<T>(d, d->dY, d->LY, d->kz, d->kz, rhs, -1.0, 1.0, IETI_K_GEMV_Y);
-  k_kept_to_bp<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->kz, d->gb,
+  // interior condensation: z_i = W_ii^{-1} f_i, g_[bp] = f_[bp] - G f_i  (kg)
+  gemv<T>(d, d->dIGi, d->IG, rhs, d->kg, nullptr, 1.0, 0.0, IETI_K_TRI);
+  gemv<T>(d, d->dIGg, d->IG, rhs, d->kg, rhs, -1.0, 1.0, IETI_K_GEMV_Y);
+  k_kept_to_bp<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->kg, d->gb,
                                                                  d->gp);
   d->nlaunch++;
   // d = B (F g_b - Psi S_c^{-1} sum A^T (g_p - Psi^T g_b))
   condensed<T>(d, d->gb, d->gp);
   k_jump<<<RED_BLOCKS, 256, 0, st>>>(d->M, d->lam_qp, d->lam_qm, nullptr, nullptr, d->bp, d->dvec, nullptr, nullptr);
   d->nlaunch++;
-  int rc = d->opt.pcg_mode == 1 ? pcg<T>(d, its, rel, err) : pcg_persistent<T>(d, its, rel, err);
+  int rc = pcg<T>(d, its, rel, err);
   if (rc && rc != IETI_ERR_CG_NOT_CONVERGED) return rc;
   int cg_rc = rc;
   // recovery: v_b = g_b - B^T lambda; a_b = F v_b - Psi q, a_p = q
@@ -1044,13 +1086,8 @@ static int dd_solve(DeviceState *d, const double *rhs, int *its, double *rel, st
   k_bp_to_kept<<<grid_for(d->NBt + d->NPt, 256), 256, 0, st>>>(d->NBt, d->NPt, d->b_kept, d->p_kept, d->pc, d->bp,
                                                                  d->q, d->kx);
   d->nlaunch++;
-  // interior: a_i = X^T (z_i - Y^T a_[bp])
-  dim3 gT(grid_for(d->max_ni, 128), d->np_);
-  prof_begin(d, IETI_K_GEMV_Y, 0.0);
-  k_gemvT_Y<T><<<gT, 128, 0, st>>>(d->ni, d->nb, d->npp, d->lyoff, d->kofs, (const T *)d->LY, d->kz, d->kx, d->kt);
-  d->nlaunch++;
-  prof_end(d);
-  gemv<T>(d, d->dXb, d->LY, d->kt, d->kx, nullptr, 1.0, 0.0, IETI_K_TRI);
+  // interior: a_i = z_i - G^T a_[bp]
+  gemv<T>(d, d->dGT, d->GT, d->kx, d->kx, d->kg, -1.0, 1.0, IETI_K_GEMV_Y);
   CK(cudaGetLastError());
   return cg_rc;
 }
@@ -1156,8 +1193,9 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->n_edges = hs.n_edges;
   // ---------------- sizes and offsets
   std::vector<int32_t> hni(np_), hnb(np_), hnp(np_), hn(np_), hnn(np_), hrowpatch, hrowlocal, hldb(np_), hldp(np_);
-  std::vector<int64_t> hkofs(np_ + 1, 0), hdoff(np_ + 1, 0), hly(np_ + 1, 0), hh(np_ + 1, 0), hq(np_ + 1, 0),
-      hp(np_ + 1, 0), hbofs(np_ + 1, 0), hpofs(np_ + 1, 0);
+  std::vector<int64_t> hkofs(np_ + 1, 0), hdoff(np_ + 1, 0), hig(np_ + 1, 0), hgt(np_ + 1, 0), hh(np_ + 1, 0),
+      hq(np_ + 1, 0), hp(np_ + 1, 0), hbofs(np_ + 1, 0), hpofs(np_ + 1, 0);
+  std::vector<int32_t> hldi(np_), hldg(np_);
   for (int s = 0; s < np_; ++s) {
     const Patch &pt = hs.patches[s];
     hni[s] = pt.ni;
@@ -1167,7 +1205,10 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     hnn[s] = hn[s] + pt.nb + pt.ni;  // augmented: [i b p | b' | i']
     hkofs[s + 1] = hkofs[s] + hn[s];
     hdoff[s + 1] = hdoff[s] + (int64_t)hnn[s] * hnn[s];
-    hly[s + 1] = hly[s] + (int64_t)hn[s] * pt.ni;
+    hldi[s] = (pt.ni + 3) / 4 * 4;
+    hldg[s] = (pt.nb + pt.np + 3) / 4 * 4;
+    hig[s + 1] = hig[s] + (int64_t)hn[s] * hldi[s];
+    hgt[s + 1] = hgt[s] + (int64_t)pt.ni * hldg[s];
     int ldb_s = (pt.nb + 3) / 4 * 4, ldp_s = (pt.np + 3) / 4 * 4;  // 16-byte aligned rows
     hldb[s] = ldb_s;
     hldp[s] = ldp_s;
@@ -1289,13 +1330,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   // ---------------- upload index data
   int rc;
   std::vector<int64_t> hkofs_v(hkofs.begin(), hkofs.end() - 1), hdoff_v(hdoff.begin(), hdoff.end() - 1),
-      hly_v(hly.begin(), hly.end() - 1), hh_v(hh.begin(), hh.end() - 1), hq_v(hq.begin(), hq.end() - 1),
-      hp_v(hp.begin(), hp.end() - 1);
+      hig_v(hig.begin(), hig.end() - 1), hgt_v(hgt.begin(), hgt.end() - 1), hh_v(hh.begin(), hh.end() - 1),
+      hq_v(hq.begin(), hq.end() - 1), hp_v(hp.begin(), hp.end() - 1);
   int64_t *ddoff = nullptr;
   int32_t *dnn = nullptr, *dn = nullptr, *drowpatch = nullptr, *drowlocal = nullptr;
   if ((rc = upload(d, &d->ni, hni, err)) || (rc = upload(d, &d->nb, hnb, err)) || (rc = upload(d, &d->npp, hnp, err)) ||
       (rc = upload(d, &d->kofs, hkofs_v, err)) || (rc = upload(d, &ddoff, hdoff_v, err)) ||
-      (rc = upload(d, &d->lyoff, hly_v, err)) || (rc = upload(d, &d->hoff, hh_v, err)) ||
+      (rc = upload(d, &d->igoff, hig_v, err)) || (rc = upload(d, &d->gtoff, hgt_v, err)) ||
+      (rc = upload(d, &d->hoff, hh_v, err)) ||
       (rc = upload(d, &d->qoff, hq_v, err)) || (rc = upload(d, &d->poff, hp_v, err)) ||
       (rc = upload(d, &dnn, hnn, err)) || (rc = upload(d, &dn, hn, err)) ||
       (rc = upload(d, &drowpatch, hrowpatch, err)) ||
@@ -1319,6 +1361,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     for (int s = 0; s < np_; ++s)
       for (int64_t k = hbofs[s]; k < hbofs[s + 1]; ++k) bp_[k] = s;
     if ((rc = upload(d, &d->ldb, hldb, err)) || (rc = upload(d, &d->ldp, hldp, err)) ||
+        (rc = upload(d, &d->ldi, hldi, err)) || (rc = upload(d, &d->ldg, hldg, err)) ||
         (rc = upload(d, &d->bofs_d, hb, err)) || (rc = upload(d, &d->pofs_d, hpo, err)) ||
         (rc = upload(d, &d->bpatch, bp_, err)))
       return fail(rc);
@@ -1328,36 +1371,35 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     std::vector<int64_t> ao, xo, yi;
     std::vector<int32_t> nc;
     auto clear = [&]() { ao.clear(); xo.clear(); yi.clear(); nc.clear(); };
-    // Y rows: g_[bp] = rhs_[bp] - Y z_i  (kept space)
-    for (int s = 0; s < np_; ++s)
-      for (int r = 0; r < hnb[s] + hnp[s]; ++r) {
-        ao.push_back(hly[s] + (int64_t)(hni[s] + r) * hni[s]);
-        xo.push_back(hkofs[s]);
-        yi.push_back(hkofs[s] + hni[s] + r);
-        nc.push_back(hni[s]);
-      }
-    if ((rc = upload_desc(d, d->dY, ao, xo, yi, nc, err))) return fail(rc);
-    clear();
-    // X rows (forward): z_i[r] = sum_{c<=r} X[r][c] rhs_i[c]
+    // W_ii^{-1} rows: z_i = W_ii^{-1} f_i  (kept space)
     for (int s = 0; s < np_; ++s)
       for (int r = 0; r < hni[s]; ++r) {
-        ao.push_back(hly[s] + (int64_t)r * hni[s]);
+        ao.push_back(hig[s] + (int64_t)r * hldi[s]);
         xo.push_back(hkofs[s]);
         yi.push_back(hkofs[s] + r);
-        nc.push_back(r + 1);
+        nc.push_back(hni[s]);
       }
-    if ((rc = upload_desc(d, d->dXf, ao, xo, yi, nc, err))) return fail(rc);
+    if ((rc = upload_desc(d, d->dIGi, ao, xo, yi, nc, err))) return fail(rc);
     clear();
-    // X^T rows (backward, strict upper part + diagonal of the same array):
-    // x_i[c] = sum_{r>=c} X[r][c] t[r]
+    // G rows: g_[bp] = f_[bp] - G f_i
     for (int s = 0; s < np_; ++s)
-      for (int c = 0; c < hni[s]; ++c) {
-        ao.push_back(hly[s] + (int64_t)c * hni[s] + c);
-        xo.push_back(hkofs[s] + c);
-        yi.push_back(hkofs[s] + c);
-        nc.push_back(hni[s] - c);
+      for (int r = hni[s]; r < hn[s]; ++r) {
+        ao.push_back(hig[s] + (int64_t)r * hldi[s]);
+        xo.push_back(hkofs[s]);
+        yi.push_back(hkofs[s] + r);
+        nc.push_back(hni[s]);
       }
-    if ((rc = upload_desc(d, d->dXb, ao, xo, yi, nc, err))) return fail(rc);
+    if ((rc = upload_desc(d, d->dIGg, ao, xo, yi, nc, err))) return fail(rc);
+    clear();
+    // G^T rows: a_i = z_i - G^T a_[bp]
+    for (int s = 0; s < np_; ++s)
+      for (int t = 0; t < hni[s]; ++t) {
+        ao.push_back(hgt[s] + (int64_t)t * hldg[s]);
+        xo.push_back(hkofs[s] + hni[s]);
+        yi.push_back(hkofs[s] + t);
+        nc.push_back(hnb[s] + hnp[s]);
+      }
+    if ((rc = upload_desc(d, d->dGT, ao, xo, yi, nc, err))) return fail(rc);
     clear();
     // H rows: [F u ; Psi^T u] -> bp (B-space then Pi-space)
     for (int s = 0; s < np_; ++s)
@@ -1404,6 +1446,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       (rc = dalloc(d, &d->kf, d->NK, err)) || (rc = dalloc(d, &d->kx, d->NK, err)) ||
       (rc = dalloc(d, &d->kr, d->NK, err)) || (rc = dalloc(d, &d->kz, d->NK, err)) ||
       (rc = dalloc(d, &d->ka, d->NK, err)) || (rc = dalloc(d, &d->kt, d->NK, err)) ||
+      (rc = dalloc(d, &d->kg, d->NK, err)) ||
       (rc = dalloc(d, &d->bp, d->NBt + d->NPt, err)) ||
       (rc = dalloc(d, &d->ub, d->NBt, err)) || (rc = dalloc(d, &d->gb, d->NBt, err)) ||
       (rc = dalloc(d, &d->gp, d->NPt, err)) || (rc = dalloc(d, &d->cc, d->NC, err)) ||
@@ -1454,8 +1497,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     hna[s] = hnn[s];
     hsklo[s] = hn[s];              // b' rows: zero in the interior columns
     hskhi[s] = hn[s] + hnb[s];
-    hrlim[s] = hn[s] + hnb[s];     // i' rows: only their interior columns are read
-    hclim[s] = hni[s];
+    hrlim[s] = INT32_MAX;          // i' rows: full updates (W_ii^{-1} and G^T come out of them)
+    hclim[s] = 0;
   }
   if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
       (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
@@ -1464,10 +1507,10 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   int maxnb = *std::max_element(hnb.begin(), hnb.end());
   int maxnp = *std::max_element(hnp.begin(), hnp.end());
   int64_t maxP = (int64_t)maxnb * maxnb;
-  int64_t maxH = 0, maxLY = 0;
+  int64_t maxH = 0, maxIG = 0;
   for (int s = 0; s < np_; ++s) {
     maxH = std::max(maxH, (int64_t)(hnb[s] + hnp[s]) * hnb[s]);
-    maxLY = std::max(maxLY, (int64_t)hn[s] * hni[s]);
+    maxIG = std::max(maxIG, (int64_t)hn[s] * hni[s]);
   }
   size_t esz = d->mixed ? sizeof(float) : sizeof(double);
   auto alloc_op = [&](void **ptr, int64_t n) -> int {
@@ -1480,9 +1523,27 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     d->bytes += std::max<int64_t>(n, 1) * esz;
     return IETI_OK;
   };
-  if ((rc = alloc_op(&d->P, hp[np_])) || (rc = alloc_op(&d->H, hh[np_])) || (rc = alloc_op(&d->Q, hq[np_])) ||
-      (rc = alloc_op(&d->LY, hly[np_])))
-    return fail(rc);
+  {
+    // H, Q, P and the coarse inverse are re-read every PCG iteration: one arena
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t bH = al(std::max<int64_t>(hh[np_], 1) * esz), bQ = al(std::max<int64_t>(hq[np_], 1) * esz),
+           bP = al(std::max<int64_t>(hp[np_], 1) * esz), bS = al(std::max<int64_t>(d->NC * d->ldc, 1) * 8);
+    d->iter_bytes = bH + bQ + bP + bS;
+    cudaError_t e = cudaMalloc((void **)&d->iter_arena, d->iter_bytes);
+    if (e != cudaSuccess) {
+      err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+      return fail(IETI_ERR_OOM);
+    }
+    d->allocs.push_back(d->iter_arena);
+    d->bytes += d->iter_bytes;
+    d->H = d->iter_arena;
+    d->Q = d->iter_arena + bH;
+    d->P = d->iter_arena + bH + bQ;
+    d->Scoarse_slot = (double *)(d->iter_arena + bH + bQ + bP);
+  }
+  if ((rc = alloc_op(&d->IG, hig[np_])) || (rc = alloc_op(&d->GT, hgt[np_]))) return fail(rc);
+  CK(cudaMemsetAsync(d->IG, 0, std::max<int64_t>(hig[np_], 1) * esz, d->stream));
+  CK(cudaMemsetAsync(d->GT, 0, std::max<int64_t>(hgt[np_], 1) * esz, d->stream));
   CK(cudaMemsetAsync(d->P, 0, std::max<int64_t>(hp[np_], 1) * esz, d->stream));
   CK(cudaMemsetAsync(d->H, 0, std::max<int64_t>(hh[np_], 1) * esz, d->stream));
   CK(cudaMemsetAsync(d->Q, 0, std::max<int64_t>(hq[np_], 1) * esz, d->stream));
@@ -1528,12 +1589,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
                                                       d->qoff, (double *)d->H, (double *)d->Q);
     d->launches_setup++;
   }
-  if (maxLY > 0) {
-    dim3 g((unsigned)std::min<int64_t>(grid_for(maxLY, 256), 4096), np_);
+  if (maxIG > 0) {
+    dim3 g((unsigned)std::min<int64_t>(grid_for(maxIG, 256), 4096), np_);
     if (d->mixed)
-      k_extract_LY<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->lyoff, (float *)d->LY);
+      k_extract_IG<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg, d->igoff,
+                                                     d->gtoff, (float *)d->IG, (float *)d->GT);
     else
-      k_extract_LY<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->lyoff, (double *)d->LY);
+      k_extract_IG<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
+                                                      d->igoff, d->gtoff, (double *)d->IG, (double *)d->GT);
     d->launches_setup++;
   }
   // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, inverted through [[S_c, I], [I, 0]]
@@ -1573,6 +1636,13 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * d->ldc), err))) return fail(rc);
     CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
     k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
+    if (d->mixed) {
+      d->Sdf = d->Scoarse_slot;
+      k_split_pairs<<<grid_for(nc * d->ldc, 256), 256, 0, d->stream>>>(nc * d->ldc, d->Sinv, (float2 *)d->Sdf);
+    } else {
+      CK(cudaMemcpyAsync(d->Scoarse_slot, d->Sinv, (size_t)(nc * d->ldc) * sizeof(double), cudaMemcpyDeviceToDevice,
+                         d->stream));
+    }
     CK(cudaStreamSynchronize(d->stream));
     cudaFree(Sc);
     d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
@@ -1589,24 +1659,22 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
                   8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
   {
     // ---- persistent PCG plan: grid from occupancy, byte-balanced partitions
-    int ldmax = 4, ldbmax = 4, ldpmax = 4;
-    for (int s = 0; s < np_; ++s) {
-      ldbmax = std::max(ldbmax, hldb[s]);
-      ldpmax = std::max(ldpmax, hldp[s]);
-    }
-    ldmax = std::max(ldbmax, ldpmax);
-    // shared memory: staged x vector, then NS TMA stages (whole rows per stage)
+    int ldmax = 4;
+    for (int s = 0; s < np_; ++s) ldmax = std::max({ldmax, hldb[s], hldp[s], hldi[s], hldg[s]});
+    // shared memory: staged x vector, then n_stages TMA stages (whole rows per stage)
     size_t xs_bytes = (std::max((size_t)ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
-    size_t budget = 220 * 1024;
-    size_t stage = std::min<size_t>(64 * 1024, (budget - std::min(budget - 3 * 4096, xs_bytes)) / NS) / 128 * 128;
-    d->xs_bytes = (unsigned)xs_bytes;
-    d->stage_bytes = (unsigned)stage;
-    if ((size_t)ldmax * esz > stage) {
-      err = "an interface block is too wide for the TMA stage of the PCG kernel";
+    size_t budget = 220 * 1024, row_max = std::max((size_t)ldmax * esz, (size_t)d->ldc * sizeof(double));
+    if (xs_bytes + 2 * row_max > budget) {
+      err = "a patch block is too wide for the shared-memory staging of the dual-primal kernel";
       return fail(IETI_ERR_TOO_LARGE);
     }
-    d->pcg_smem = xs_bytes + NS * stage;
-    const void *fn = d->mixed ? (const void *)k_pcg<float> : (const void *)k_pcg<double>;
+    d->n_stages = (xs_bytes + 3 * row_max <= budget) ? 3 : 2;
+    size_t stage = std::min<size_t>(64 * 1024, (budget - xs_bytes) / d->n_stages) / 128 * 128;
+    stage = std::max(stage, (row_max + 127) / 128 * 128);
+    d->xs_bytes = (unsigned)xs_bytes;
+    d->stage_bytes = (unsigned)stage;
+    d->pcg_smem = xs_bytes + d->n_stages * stage;
+    const void *fn = d->mixed ? (const void *)k_ddsolve<float> : (const void *)k_ddsolve<double>;
     if (d->pcg_smem > 48 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->pcg_smem));
     int per_sm = 0, n_sm = 0, coop = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, d->pcg_smem));
@@ -1627,6 +1695,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     partition_rows(hnb, hldb, d->G, sp, ss, r0v, r1v);
     if ((rc = upload(d, &d->bseg_ptr, sp, err)) || (rc = upload(d, &d->bseg_s, ss, err)) ||
         (rc = upload(d, &d->bseg_r0, r0v, err)) || (rc = upload(d, &d->bseg_r1, r1v, err)))
+      return fail(rc);
+    partition_rows(hn, hldi, d->G, sp, ss, r0v, r1v);
+    if ((rc = upload(d, &d->iseg_ptr, sp, err)) || (rc = upload(d, &d->iseg_s, ss, err)) ||
+        (rc = upload(d, &d->iseg_r0, r0v, err)) || (rc = upload(d, &d->iseg_r1, r1v, err)))
+      return fail(rc);
+    partition_rows(hni, hldg, d->G, sp, ss, r0v, r1v);
+    if ((rc = upload(d, &d->tseg_ptr, sp, err)) || (rc = upload(d, &d->tseg_s, ss, err)) ||
+        (rc = upload(d, &d->tseg_r0, r0v, err)) || (rc = upload(d, &d->tseg_r1, r1v, err)))
       return fail(rc);
     // fixed-width gather lists (an edge DOF is shared by at most 4 patches)
     std::vector<int32_t> ell_l(d->NBt * BT_W, -1), cpp(d->NC * CP_W, -1);
@@ -1654,6 +1730,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       return fail(rc);
     if ((rc = dalloc(d, &d->p1, m, err)) || (rc = dalloc(d, &d->r1, m, err)) || (rc = dalloc(d, &d->zb, d->NBt, err)) ||
         (rc = dalloc(d, &d->zf, d->NBt, err)) || (rc = dalloc(d, &d->ubp, d->NBt, err)) ||
+        (rc = dalloc(d, &d->ub1, d->NBt, err)) || (rc = dalloc(d, &d->uz, d->NBt, err)) ||
         (rc = dalloc(d, &d->tpi, d->NPt, err)) || (rc = dalloc(d, &d->zp, d->NBt, err)) ||
         (rc = dalloc(d, &d->ccg, d->NC, err)) || (rc = dalloc(d, &d->ppart, 4 * (size_t)d->G, err)) ||
         (rc = dalloc(d, &d->bar, 4, err)) || (rc = dalloc(d, &d->pcg_its, 1, err)) ||
@@ -1662,6 +1739,19 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       return fail(rc);
     CK(cudaMemsetAsync(d->p, 0, m * sizeof(double), d->stream));
     CK(cudaMemsetAsync(d->p1, 0, m * sizeof(double), d->stream));
+    if (opt.l2_persist) {
+      int max_persist = 0, max_window = 0;
+      CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, d->device));
+      CK(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, d->device));
+      if (max_persist > 0 && max_window > 0) {
+        CK(cudaDeviceGetLimit(&d->l2_prev_limit, cudaLimitPersistingL2CacheSize));
+        size_t want = std::min((size_t)max_persist, d->iter_bytes);
+        CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::max(want, d->l2_prev_limit)));
+        d->l2_set = true;
+        d->l2_window = std::min((size_t)max_window, d->iter_bytes);
+        d->l2_hit_ratio = (float)std::min(1.0, (double)want / (double)d->l2_window);
+      }
+    }
     int64_t sH = 0, sQ = 0, sP = 0;
     for (int s = 0; s < np_; ++s) {
       sH += (int64_t)(hnb[s] + hnp[s]) * hnb[s];
@@ -1681,10 +1771,11 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     int64_t sy = 0, sl = 0;
     for (int s = 0; s < np_; ++s) {
       sy += (int64_t)(hnb[s] + hnp[s]) * hni[s];
-      sl += (int64_t)hni[s] * (hni[s] + 1) / 2;
+      sl += (int64_t)hni[s] * hni[s];
     }
     d->gemv_bytes[IETI_K_GEMV_Y] = e * sy + 8.0 * (2 * (double)d->NK);
     d->gemv_bytes[IETI_K_TRI] = e * sl + 8.0 * 2 * (double)d->NK;
+    d->bytes_sweep_alg = e * (2.0 * sy + sl) + 8.0 * 6 * (double)d->NK;
     d->gemv_bytes[IETI_K_SPMV] = 12.0 * (double)wval.size() + 8.0 * 3 * (double)d->NK;
   }
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1702,6 +1793,9 @@ int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std:
   int rc = d->mixed ? step_impl<float>(d, st, err) : step_impl<double>(d, st, err);
   CK(cudaEventRecord(d->ev1, d->stream));
   CK(cudaEventSynchronize(d->ev1));
+  // the carve-out only serves the iterations inside a step: return its lines to
+  // normal so that whatever runs between steps can evict them
+  if (d->l2_window > 0) CK(cudaCtxResetPersistingL2Cache());
   prof_collect(d);
   if (st) {
     float ms = 0;
@@ -1740,6 +1834,9 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->bytes_device = d->bytes;
   info->t_setup_device_ms = d->t_setup_ms;
   info->kernel_launches_setup = d->launches_setup;
+  info->l2_window_bytes = (int64_t)d->l2_window;
+  info->l2_hit_ratio = d->l2_hit_ratio;
+  info->iter_operator_bytes = (int64_t)d->iter_bytes;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
@@ -1762,6 +1859,11 @@ void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, bool res
 
 void device_destroy(DeviceState *d) {
   if (!d) return;
+  if (d->l2_set) {
+    if (d->device >= 0) cudaSetDevice(d->device);
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, d->l2_prev_limit);
+  }
   for (cudaEvent_t e : d->ev_pool) cudaEventDestroy(e);
   if (d->device >= 0) cudaSetDevice(d->device);
   if (d->stream) cudaStreamSynchronize(d->stream);

@@ -1,20 +1,27 @@
-// Persistent cooperative PCG on the dual interface problem F lambda = d (Sec. 3-4:
-// Dirichlet-preconditioned CG, lambda_0 = 0, stop on ||r|| <= tol ||d||).
+// Persistent cooperative dual-primal solve of one defect-correction sweep (Sec. 3-4):
+// interior condensation, right-hand side d of the dual problem, PCG on
+// F lambda = d (Dirichlet preconditioner, lambda_0 = 0, stop on ||r|| <= tol ||d||)
+// and recovery of the patch unknowns, all in one launch.
 //
-// One launch runs every iteration.  Per iteration six phases separated by grid
-// barriers (monotonic arrival counter; a wait that does not complete within ~2 s
-// sets an error flag and every CTA returns):
-//   P1  beta from the (r,z) partials; p_new = z + beta p_old (owners store it, the
-//       gathers recompute it); u = B^T p_new per patch (kept in ub);
-//       [F_s; Psi_s^T] u_s  -> zb, tpi
-//   P2  coarse right-hand side c = -sum_s A_s^T tpi  (chunk per CTA)
-//   P3  q = S_c^{-1} c (c staged whole in shared memory, rows per CTA)
-//   P4  zf = zb - Psi_s q per interface row; partials of (p, F p) = (u, zf)
-//   P5  alpha; owners: F p = B zf, lambda += alpha p, r_new = r - alpha F p;
-//       Dirichlet preconditioner S_bb (B_D^T r_new) per patch -> zp (r_new
-//       recomputed in the gather)
-//   P6  convergence test on ||r_new||; z = B_D zp; partials of (r_new, z)
-// Every vector written by another CTA inside the launch is read with ld.global.cg.
+// Per-patch operators (rows padded to 16-byte multiples, streamed HBM -> shared
+// memory by 1-D TMA bulk copies through an NS-stage mbarrier ring):
+//   IG_s = [W_ii^{-1}; G_s]  (G_s = W_[bp]i W_ii^{-1})  condensation
+//   H_s  = [F_s; Psi_s^T]                              dual operator / primal rhs
+//   Q_s  = Psi_s                                       primal correction
+//   P_s  = S_bb                                        Dirichlet preconditioner
+//   GT_s = G_s^T                                       interior recovery
+// and the dense FP64 S_c^{-1} (coarse problem).
+//
+// Phases are separated by grid barriers (monotonic arrival counter; a wait that does
+// not complete within ~1-3 s sets an error flag and every CTA returns).  Every
+// vector written by another CTA inside the launch is read with ld.global.cg.
+//   C   z_i = W_ii^{-1} f_i, g_[bp] = f_[bp] - G f_i                      (kg)
+//   D1-D4  d = B (F g_b - Psi S_c^{-1} sum A^T (g_p - Psi^T g_b))         (zf)
+//   per iteration: P1 beta, p_new, u = B^T p_new, [F; Psi^T] u; P2 coarse rhs;
+//     P3 q = S_c^{-1} c; P4 zf = zb - Psi q, (p, F p) = (u, zf); P5 alpha, owner
+//     updates, S_bb (B_D^T r_new); P6 convergence, z = B_D zp, (r, z)
+//   R1-R4  v_b = g_b - B^T lambda: a_b = F v_b - Psi q, a_p = q               (kx)
+//   R5  a_i = z_i - G^T a_[bp]                                             (kx)
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -40,26 +47,30 @@ struct PcgArgs {
   const int32_t *lam_qp, *lam_qm;
   const double *lam_wp, *lam_wm;
   // per patch
-  const int64_t *bofs, *pofs, *hoff, *qoff, *poff;
-  const int32_t *nb, *np, *ldb, *ldp;
+  const int64_t *kofs, *bofs, *pofs, *hoff, *qoff, *poff, *igoff, *gtoff;
+  const int32_t *ni, *nb, *np, *ldb, *ldp, *ldi, *ldg;
   const int32_t *pc;
+  const int64_t *p_kept, *b_kept;   // Pi / B position -> kept-space index
   const int32_t *cp_pos;            // [nc][CP_W], -1 = none
-  const T *H, *Q, *P;
-  const double *Sinv;
-  // work partitions (per CTA)
+  const T *IG, *H, *Q, *P, *GT;
+  const double *Sinv;               // FP64 path: S_c^{-1}; mixed path: (hi, lo) FP32 pairs of it
+  int64_t nbt;
+  // work partitions (per CTA): patch segments of operator rows
+  const int32_t *iseg_ptr, *iseg_s, *iseg_r0, *iseg_r1;   // IG rows
   const int32_t *hseg_ptr, *hseg_s, *hseg_r0, *hseg_r1;   // H rows
   const int32_t *bseg_ptr, *bseg_s, *bseg_r0, *bseg_r1;   // interface rows (Psi and P)
+  const int32_t *tseg_ptr, *tseg_s, *tseg_r0, *tseg_r1;   // GT rows
   // vectors
-  const double *d;
-  double *lam, *p0, *p1, *r0, *r1, *z, *ub, *zb, *zf, *tpi, *cc, *q, *zp;
+  const double *rhs;                // kept space
+  double *kg, *kx;                  // kept space: condensed rhs, solution
+  double *lam, *p0, *p1, *r0, *r1, *z, *ub, *ub1, *uz, *zb, *zf, *tpi, *cc, *q, *zp;
   double *part;        // [4][G]
   unsigned *bar;       // arrival counter, error flag
   int *out_its;
   double *out_rr, *out_dd;
-  unsigned long long *trace;  // optional: CTA 0 phase timestamps, [TRACE_IT][2 * 8]
-  // TMA streaming: stage size and per-operator switch (rows longer than a stage are
-  // read directly from global memory)
+  unsigned long long *trace;  // optional: CTA 0 phase timestamps, [TRACE_IT][16]
   unsigned stage_bytes, xs_bytes;
+  int n_stages;
 };
 
 constexpr int TRACE_IT = 16;
@@ -116,6 +127,13 @@ __device__ __forceinline__ double warp_red(double v) {
   return v;
 }
 
+template <class T>
+__device__ __forceinline__ T warp_red_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // block sum of v, result broadcast to every thread
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   v = warp_red(v);
@@ -143,18 +161,10 @@ template <> struct V16<double> { using t = double2; static constexpr int n = 2; 
 __device__ __forceinline__ float dot16(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 __device__ __forceinline__ double dot16(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
 
-template <class T>
-__device__ __forceinline__ T warp_red_t(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // R padded (16-byte aligned, zero-padded) rows against the staged x, by one warp.
 // Every lane issues its loads of a 32*U-vector chunk of all R rows before using
-// them (R*U independent 16-byte loads in flight per lane).  Partial sums and the
-// warp reduction stay in the operator precision T (the FP64 pipe of this GPU is
-// ~1/64 of its FP32 rate).  On return every lane holds all R row sums.
+// them.  Partial sums and the warp reduction stay in the operator precision T (the
+// FP64 pipe of this GPU is ~1/64 of its FP32 rate).  Every lane gets all R sums.
 template <class T, int R, bool GLOBAL = true>
 __device__ __forceinline__ void rows_dot(const T *A, int64_t ld, int r, int nvalid, const T *xs, T (&out)[R]) {
   using V = typename V16<T>::t;
@@ -190,105 +200,231 @@ __device__ __forceinline__ void rows_dot(const T *A, int64_t ld, int r, int nval
   for (int i = 0; i < R; ++i) out[i] = warp_red_t(out[i]);
 }
 
-// rows [r0, r1) of a patch operator against xs, RW rows per warp; out(r, value) is
-// called by lane i of the warp for its i-th row (epilogues run in parallel)
-template <int RW, bool GLOBAL = true, class T, class Out>
-__device__ __forceinline__ void rows_gemv(const T *A, int ld, int r0, int r1, const T *xs, Out out) {
+// dot products of one row of double-FP32 pairs (hi, lo) with staged pairs, by one
+// warp: exact products (TwoProd by FMA) accumulated with TwoSum in FP32, so the
+// result carries ~2^-46 relative accuracy without the FP64 pipe; the final
+// cross-lane sum is done in FP64 (one row per warp, cheap)
+__device__ __forceinline__ double row_dot_df(const float2 *row, const float2 *xs, int n) {
+  int lane = threadIdx.x & 31;
+  float sh = 0.f, sl = 0.f;
+  for (int k = lane; k < n; k += 32) {
+    float2 av = row[k], xv = xs[k];
+    float p = av.x * xv.x;
+    float e = fmaf(av.x, xv.x, -p);
+    float t = fmaf(av.x, xv.y, fmaf(av.y, xv.x, e));
+    float sum = sh + p;
+    float bb = sum - sh;
+    float err = (sh - (sum - bb)) + (p - bb);
+    sh = sum;
+    sl += err + t;
+  }
+  return warp_red((double)sh + (double)sl);
+}
+
+struct NoPre {
+  __device__ double2 operator()(int) const { return make_double2(0.0, 0.0); }
+  __device__ double2 operator()(int, int) const { return make_double2(0.0, 0.0); }
+};
+
+// rows [r0, r1) of an operator against xs, RW rows per warp; lane i of the warp
+// handles the epilogue of the group's i-th row: pre(r) is loaded before the dot
+// products (so its latency overlaps them) and out(r, value, pre) runs after
+template <int RW, bool GLOBAL = true, class T, class Out, class Pre = NoPre>
+__device__ __forceinline__ void rows_gemv(const T *A, int ld, int r0, int r1, const T *xs, Out out,
+                                          Pre pre = Pre()) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r = r0 + RW * warp; r < r1; r += RW * nw) {
     int nvalid = min(RW, r1 - r);
+    double2 pv = make_double2(0.0, 0.0);
+    if (lane < nvalid) pv = pre(r + lane);
     T v[RW];
     rows_dot<T, RW, GLOBAL>(A, ld, r, nvalid, xs, v);
     T mine = 0;
 #pragma unroll
     for (int i = 0; i < RW; ++i)
       if (lane == i) mine = v[i];
-    if (lane < nvalid) out(r + lane, (double)mine);
+    if (lane < nvalid) out(r + lane, (double)mine, pv);
   }
 }
 
 // ---------------------------------------------------------------------------
-// TMA ring: rows of a contiguous row-major block streamed HBM -> shared memory in
-// chunks of whole rows (NS stages in flight), dot products computed from shared.
-constexpr int NS = 3;
+// TMA ring.  The operator rows a CTA multiplies in a phase are fixed by the static
+// partition, independent of the iteration's vectors, so they are streamed HBM ->
+// shared memory in chunks of whole rows through an ns-stage mbarrier ring, and the
+// first chunks of the NEXT phase are issued before the grid barrier that ends the
+// current one (they arrive while the CTA waits).
+constexpr int NS_MAX = 3;
 struct Ring {
-  unsigned char *stage;   // NS * bytes
-  uint64_t *bar;          // NS mbarriers
+  unsigned char *stage;   // ns * bytes
+  uint64_t *bar;          // ns mbarriers
   unsigned bytes;
+  int ns;
   unsigned long long issued, consumed;
 };
 
-// returns false (after setting the error flag and draining its copies) when a
-// wait timed out
-template <int RW, class T, class Out>
-__device__ bool stream_rows(Ring &ring, const T *A, int ld, int r0, int r1, const T *xs, unsigned *errflag,
-                            Out out) {
-  int nrows = r1 - r0;
-  if (nrows <= 0) return true;
-  if (ld == 0) {
-    for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) out(r, 0.0);
-    return true;
+// the rows of one operator a CTA processes in one phase: segments (patch s, rows
+// [r0, r1)) of row-major blocks at base + off[s] with leading dimension ld[s];
+// single-segment form (s = 0, rows [r0s, r1s), off 0, ld lds) when seg_s is null
+template <class E>
+struct OpRows {
+  const E *base;
+  const int64_t *off;
+  const int32_t *ld;
+  const int32_t *seg_s, *seg_r0, *seg_r1;
+  int sb, se;
+  int r0s, r1s, lds;
+  __device__ int nseg() const { return seg_s ? se - sb : (r1s > r0s ? 1 : 0); }
+  __device__ void seg(int k, int &s, int &r0, int &r1, int &l, const E *&A) const {
+    if (seg_s) {
+      s = seg_s[sb + k]; r0 = seg_r0[sb + k]; r1 = seg_r1[sb + k]; l = ld[s]; A = base + off[s];
+    } else {
+      s = 0; r0 = r0s; r1 = r1s; l = lds; A = base;
+    }
   }
-  unsigned row_bytes = (unsigned)ld * sizeof(T);
-  int rpc = max(1, (int)(ring.bytes / row_bytes));
-  int nchunks = (nrows + rpc - 1) / rpc;
-  auto issue = [&](int c) {
-    int st = (int)(ring.issued % NS);
+};
+
+// producer cursor over the chunks of an OpRows (uniform across the CTA)
+struct Cursor {
+  int seg = 0, chunk = 0, issued = 0;
+};
+
+template <class E>
+__device__ __forceinline__ int rows_per_chunk(const Ring &ring, int ld) {
+  unsigned rb = (unsigned)ld * sizeof(E);
+  return rb == 0 ? 1 << 30 : max(1, (int)(ring.bytes / rb));
+}
+
+// issue the next chunk of `op` (if any) into the next ring stage; returns false at the end
+template <class E>
+__device__ bool issue_next(Ring &ring, const OpRows<E> &op, Cursor &cur) {
+  int nseg = op.nseg();
+  while (cur.seg < nseg) {
+    int s, r0, r1, ld;
+    const E *A;
+    op.seg(cur.seg, s, r0, r1, ld, A);
+    int rpc = rows_per_chunk<E>(ring, ld);
+    int c0 = cur.chunk * rpc;
+    if (ld == 0 || r0 + c0 >= r1) {
+      cur.seg++;
+      cur.chunk = 0;
+      continue;
+    }
+    int st = (int)(ring.issued % ring.ns);
     if (threadIdx.x == 0) {
-      int c0 = c * rpc;
-      unsigned bytes = (unsigned)min(rpc, nrows - c0) * row_bytes;
+      unsigned bytes = (unsigned)min(rpc, r1 - r0 - c0) * (unsigned)ld * sizeof(E);
       fence_proxy_async();
       mbar_arrive_expect_tx(ring.bar + st, bytes);
       tma_load_1d(ring.stage + (size_t)st * ring.bytes, A + (int64_t)(r0 + c0) * ld, bytes, ring.bar + st);
     }
     ring.issued++;
-  };
-  int pre = min(NS, nchunks);
-  for (int c = 0; c < pre; ++c) issue(c);
-  for (int c = 0; c < nchunks; ++c) {
-    int st = (int)(ring.consumed % NS);
-    unsigned parity = (unsigned)((ring.consumed / NS) & 1ull);
-    bool ok = mbar_wait(ring.bar + st, parity);
-    if (__syncthreads_or(!ok)) {  // the same decision in every thread of the CTA
-      atomicExch(errflag, 1u);
-      // drain the copies still in flight before leaving (bounded)
-      for (unsigned long long g = ring.consumed + 1; g < ring.issued; ++g)
-        mbar_wait(ring.bar + (g % NS), (unsigned)((g / NS) & 1ull));
-      return false;
+    cur.chunk++;
+    cur.issued++;
+    return true;
+  }
+  return false;
+}
+
+// issue up to ns chunks of the next phase's operator rows (the ring is empty here)
+template <class E>
+__device__ __forceinline__ Cursor prefetch(Ring &ring, const OpRows<E> &op) {
+  Cursor cur;
+  for (int k = 0; k < ring.ns; ++k)
+    if (!issue_next(ring, op, cur)) break;
+  return cur;
+}
+
+// stream every row of `op` through the ring (continuing cursor `cur`, whose first
+// chunks may have been prefetched): before the first chunk of each segment,
+// stage(s, r0, r1) runs with every thread of the CTA; out(s, r, value, pre) per row.
+// Returns false (after setting the error flag and draining) when a wait timed out.
+template <int RW, class E, class Stage, class Out, class Pre = NoPre>
+__device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, unsigned *errflag,
+                             Stage stage, Out out, Pre pre = Pre()) {
+  while (cur.issued - 0 < ring.ns && issue_next(ring, op, cur)) {
+  }
+  int nseg = op.nseg();
+  for (int k = 0; k < nseg; ++k) {
+    int s, r0, r1, ld;
+    const E *A;
+    op.seg(k, s, r0, r1, ld, A);
+    __syncthreads();
+    stage(s, r0, r1);
+    __syncthreads();
+    if (ld == 0) {
+      for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) out(s, r, 0.0, pre(s, r));
+      continue;
     }
-    ring.consumed++;
-    const T *buf = reinterpret_cast<const T *>(ring.stage + (size_t)st * ring.bytes);
-    int c0 = c * rpc, cn = min(rpc, nrows - c0);
-    rows_gemv<RW, false>(buf, ld, 0, cn, xs, [&](int r, double v) { out(r0 + c0 + r, v); });
-    __syncthreads();  // every warp is done with this stage
-    if (c + NS < nchunks) issue(c + NS);
+    int rpc = rows_per_chunk<E>(ring, ld);
+    for (int c0 = 0; r0 + c0 < r1; c0 += rpc) {
+      int st = (int)(ring.consumed % ring.ns);
+      unsigned parity = (unsigned)((ring.consumed / ring.ns) & 1ull);
+      bool ok = mbar_wait(ring.bar + st, parity);
+      if (__syncthreads_or(!ok)) {  // the same decision in every thread of the CTA
+        atomicExch(errflag, 1u);
+        for (unsigned long long g = ring.consumed + 1; g < ring.issued; ++g)
+          mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
+        ring.consumed = ring.issued;
+        return false;
+      }
+      ring.consumed++;
+      const E *buf = reinterpret_cast<const E *>(ring.stage + (size_t)st * ring.bytes);
+      int cn = min(rpc, r1 - r0 - c0);
+      int base_r = r0 + c0;
+      rows_gemv<RW, false>(buf, ld, 0, cn, xs,
+                           [&](int r, double v, double2 pv) { out(s, base_r + r, v, pv); },
+                           [&](int r) { return pre(s, base_r + r); });
+      __syncthreads();  // every warp is done with this stage
+      issue_next(ring, op, cur);
+    }
   }
   return true;
 }
 
-// operator rows of one phase: TMA-streamed (patch operators) or direct (S_c^{-1},
-// whose FP64 rows are bound by the FP64 pipe, not by the memory system)
-template <int RW, bool TMA, class T, class Out>
-__device__ __forceinline__ bool phase_rows(Ring &ring, const T *A, int ld, int r0, int r1, const T *xs,
-                                           unsigned *errflag, Out out) {
-  if constexpr (TMA) {
-    return stream_rows<RW>(ring, A, ld, r0, r1, xs, errflag, out);
-  } else {
-    rows_gemv<RW, true>(A, ld, r0, r1, xs, out);
-    return true;
+// stream the rows of a single-segment OpRows<double> and hand each chunk to consume
+// (buffer, ld, first row, rows); stage() runs once before the first chunk
+template <class Stage, class Consume>
+__device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &cur, unsigned *errflag, Stage stage,
+                                 Consume consume) {
+  while (cur.issued < ring.ns && issue_next(ring, op, cur)) {
   }
+  if (op.nseg() == 0) return true;
+  int s, r0, r1, ld;
+  const double *A;
+  op.seg(0, s, r0, r1, ld, A);
+  __syncthreads();
+  stage();
+  __syncthreads();
+  int rpc = rows_per_chunk<double>(ring, ld);
+  for (int c0 = 0; r0 + c0 < r1; c0 += rpc) {
+    int st = (int)(ring.consumed % ring.ns);
+    unsigned parity = (unsigned)((ring.consumed / ring.ns) & 1ull);
+    bool ok = mbar_wait(ring.bar + st, parity);
+    if (__syncthreads_or(!ok)) {
+      atomicExch(errflag, 1u);
+      for (unsigned long long g = ring.consumed + 1; g < ring.issued; ++g)
+        mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
+      ring.consumed = ring.issued;
+      return false;
+    }
+    ring.consumed++;
+    consume(reinterpret_cast<const double *>(ring.stage + (size_t)st * ring.bytes), ld, r0 + c0,
+            min(rpc, r1 - r0 - c0));
+    __syncthreads();
+    issue_next(ring, op, cur);
+  }
+  return true;
 }
 
 template <class T>
-__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ PcgArgs<T> a) {
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constant__ PcgArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sh[32];
-  __shared__ __align__(8) uint64_t ring_bar[NS];
+  __shared__ __align__(8) uint64_t ring_bar[NS_MAX];
   T *xs = reinterpret_cast<T *>(smem_raw);
   double *ccs = reinterpret_cast<double *>(smem_raw);
-  Ring ring{smem_raw + a.xs_bytes, ring_bar, a.stage_bytes, 0ull, 0ull};
+  Ring ring{smem_raw + a.xs_bytes, ring_bar, a.stage_bytes, a.n_stages, 0ull, 0ull};
   if (threadIdx.x == 0) {
-    for (int k = 0; k < NS; ++k) mbar_init(ring_bar + k, 1);
+    for (int k = 0; k < a.n_stages; ++k) mbar_init(ring_bar + k, 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -301,175 +437,340 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(const __grid_constant__ 
   const double *wd = a.scaled ? a.bt_wd : a.bt_sgn;
   double *part_dd = a.part, *part_rz = a.part + G, *part_pq = a.part + 2 * G, *part_rr = a.part + 3 * G;
 
-  // stage B^T-type gathers of patch s into xs (and into ub for this CTA's rows)
+  // the operator rows of each phase (static per CTA)
+  const OpRows<T> opIG{a.IG, a.igoff, a.ldi, a.iseg_s, a.iseg_r0, a.iseg_r1, a.iseg_ptr[cta], a.iseg_ptr[cta + 1], 0, 0, 0};
+  const OpRows<T> opH{a.H, a.hoff, a.ldb, a.hseg_s, a.hseg_r0, a.hseg_r1, a.hseg_ptr[cta], a.hseg_ptr[cta + 1], 0, 0, 0};
+  const OpRows<T> opQ{a.Q, a.qoff, a.ldp, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1], 0, 0, 0};
+  const OpRows<T> opP{a.P, a.poff, a.ldb, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1], 0, 0, 0};
+  const OpRows<T> opGT{a.GT, a.gtoff, a.ldg, a.tseg_s, a.tseg_r0, a.tseg_r1, a.tseg_ptr[cta], a.tseg_ptr[cta + 1], 0, 0, 0};
+  const OpRows<double> opS{a.Sinv, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, (int)cb, (int)ce, a.ldc};
+
+  // stage x_s[k] = f(k) (k < n), zero-padded to ld
+  auto stage = [&](int n, int ld, auto f) {
+    for (int k = threadIdx.x; k < ld; k += nthr) xs[k] = (T)(k < n ? f(k) : 0.0);
+  };
+  // stage u_s = B^T-type gather of patch s (ELL lists); keep it in ub for rows [r0, r1)
   auto gather = [&](int s, const double *w, int r0, int r1, bool store_ub, auto val) {
     int nbs = a.nb[s], ld = a.ldb[s];
     int64_t b0 = a.bofs[s];
-    for (int k = threadIdx.x; k < ld; k += nthr) {
-      double acc = 0;
-      if (k < nbs) {
-        const int32_t *L = a.bt_lam + (b0 + k) * BT_W;
-        const double *W = w + (b0 + k) * BT_W;
+    constexpr int KP = 4;  // entries per thread per round, loads issued together
+    for (int kb = threadIdx.x; kb < ld; kb += KP * nthr) {
+      int lidx[KP][BT_W];
 #pragma unroll
-        for (int t = 0; t < BT_W; ++t) {
-          int l = L[t];
-          if (l >= 0) acc += W[t] * val(l);
-        }
-        if (store_ub && k >= r0 && k < r1) a.ub[b0 + k] = acc;
+      for (int u = 0; u < KP; ++u) {
+        int k = kb + u * nthr;
+#pragma unroll
+        for (int t = 0; t < BT_W; ++t) lidx[u][t] = (k < nbs) ? a.bt_lam[(b0 + k) * BT_W + t] : -1;
       }
-      xs[k] = (T)acc;
+      double vals[KP][BT_W];
+#pragma unroll
+      for (int u = 0; u < KP; ++u)
+#pragma unroll
+        for (int t = 0; t < BT_W; ++t) vals[u][t] = lidx[u][t] >= 0 ? val(lidx[u][t]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < KP; ++u) {
+        int k = kb + u * nthr;
+        if (k >= ld) continue;
+        double acc = 0;
+        if (k < nbs) {
+#pragma unroll
+          for (int t = 0; t < BT_W; ++t)
+            if (lidx[u][t] >= 0) acc += w[(b0 + k) * BT_W + t] * vals[u][t];
+          if (store_ub && k >= r0 && k < r1) a.ub[b0 + k] = acc;
+        }
+        xs[k] = (T)acc;
+      }
     }
   };
   auto jumpD = [&](const double *v, int64_t l) {
     double wp = a.lam_wp ? a.lam_wp[l] : 1.0, wm = a.lam_wm ? a.lam_wm[l] : 1.0;
     return wp * ldcg(v + a.lam_qp[l]) - wm * ldcg(v + a.lam_qm[l]);
   };
-  auto precond_rows = [&](auto val) -> bool {
-    for (int sg = a.bseg_ptr[cta]; sg < a.bseg_ptr[cta + 1]; ++sg) {
-      int s = a.bseg_s[sg];
-      __syncthreads();
-      gather(s, wd, 0, 0, false, val);
-      __syncthreads();
-      int64_t bo = a.bofs[s];
-      if (!phase_rows<4, true>(ring, a.P + a.poff[s], a.ldb[s], a.bseg_r0[sg], a.bseg_r1[sg], xs, errflag,
-                         [&](int r, double v) { a.zp[bo + r] = v; }))
-        return false;
+  auto jump = [&](const double *v, int64_t l) { return ldcg(v + a.lam_qp[l]) - ldcg(v + a.lam_qm[l]); };
+  Cursor cur;  // producer cursor of the phase about to run (possibly prefetched)
+  double *ub_old = a.ub1, *ub_new = a.ub;  // B^T p of the previous / current iteration
+  // H phase: [F; Psi^T] u_s -> zb, tpi, with a staging functor for u_s
+  auto h_phase = [&](auto stage_u) -> bool {
+    return stream_phase<4>(ring, opH, cur, xs, errflag, [&](int s, int r0, int r1) { stage_u(s, r0, r1); },
+                           [&](int s, int r, double v, double2) {
+                             int nbs = a.nb[s];
+                             if (r < nbs) a.zb[a.bofs[s] + r] = v;
+                             else a.tpi[a.pofs[s] + (r - nbs)] = v;
+                           });
+  };
+  // coarse right-hand side c = sum_copies (g_p - tpi), chunk per CTA
+  auto coarse_rhs = [&](bool with_g) {
+    for (int64_t k = cb + threadIdx.x; k < ce; k += nthr) {
+      double c = 0;
+#pragma unroll
+      for (int t = 0; t < CP_W; ++t) {
+        int pos = a.cp_pos[k * CP_W + t];
+        if (pos >= 0) c += (with_g ? ldcg(a.kg + a.p_kept[pos]) : 0.0) - ldcg(a.tpi + pos);
+      }
+      a.cc[k] = c;
     }
-    return true;
+  };
+  auto coarse_solve = [&]() -> bool {
+    if constexpr (sizeof(T) == 8) {
+      return stream_phase<1>(ring, opS, cur, ccs, errflag,
+                             [&](int, int, int) {
+                               for (int k = threadIdx.x; k < a.ldc; k += nthr)
+                                 ccs[k] = k < a.nc ? ldcg(a.cc + k) : 0.0;
+                             },
+                             [&](int, int r, double v, double2) { a.q[r] = v; });
+    } else {
+      // rows of (hi, lo) pairs, streamed as doubles (8 bytes per entry), computed in
+      // double-FP32 arithmetic by warp-per-row dots
+      float2 *xp = reinterpret_cast<float2 *>(smem_raw);
+      int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      return stream_phase_raw(ring, opS, cur, errflag,
+                              [&]() {
+                                for (int k = threadIdx.x; k < a.ldc; k += nthr) {
+                                  double c = k < a.nc ? ldcg(a.cc + k) : 0.0;
+                                  float hi = (float)c;
+                                  xp[k] = make_float2(hi, (float)(c - (double)hi));
+                                }
+                              },
+                              [&](const double *buf, int ld, int row0, int nrows) {
+                                const float2 *rows = reinterpret_cast<const float2 *>(buf);
+                                for (int r = warp; r < nrows; r += nw) {
+                                  double v = row_dot_df(rows + (int64_t)r * ld, xp, a.nc);
+                                  if (lane == 0) a.q[row0 + r] = v;
+                                }
+                              });
+    }
+  };
+  // zf = zb - Psi q on the interface rows; out(global B index, zf, ub)
+  auto psi_phase = [&](auto out) -> bool {
+    return stream_phase<4>(
+        ring, opQ, cur, xs, errflag,
+        [&](int s, int, int) {
+          const int32_t *pcs = a.pc + a.pofs[s];
+          stage(a.np[s], a.ldp[s], [&](int k) { return ldcg(a.q + pcs[k]); });
+        },
+        [&](int s, int r, double v, double2 pv) { out(a.bofs[s] + r, pv.x - v, pv.y); },
+        [&](int s, int r) {
+          int64_t q = a.bofs[s] + r;
+          return make_double2(ldcg(a.zb + q), ldcg(ub_new + q));
+        });
+  };
+  auto precond_rows = [&](auto val) -> bool {
+    return stream_phase<4>(ring, opP, cur, xs, errflag, [&](int s, int, int) { gather(s, wd, 0, 0, false, val); },
+                           [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; });
+  };
+  auto sync = [&](unsigned long long *tr) { return grid_sync(a.bar, G, target, tr); };
+  // z on the multipliers from the preconditioned interface values (or r itself)
+  auto zval = [&](double rv, int l) { return a.precond_none ? rv : jumpD(a.zp, l); };
+  // uz = B^T z on this CTA's chunk of interface copies (z recomputed on the fly)
+  const int64_t qb = a.nbt * cta / G, qe = a.nbt * (cta + 1) / G;
+  auto uz_chunk = [&](auto zf_of) {
+    for (int64_t q = qb + threadIdx.x; q < qe; q += nthr) {
+      double u = 0.0;
+#pragma unroll
+      for (int t = 0; t < BT_W; ++t) {
+        int l = a.bt_lam[q * BT_W + t];
+        if (l >= 0) u += a.bt_sgn[q * BT_W + t] * zf_of(l);
+      }
+      a.uz[q] = u;
+    }
   };
 
-  // ---------------- initial residual r = d, z = M^{-1} d
+
+  // ================= C: interior condensation  kg = [W_ii^{-1} f_i ; f_[bp] - G f_i]
+  cur = prefetch(ring, opIG);
+  if (!stream_phase<4>(ring, opIG, cur, xs, errflag,
+                       [&](int s, int, int) {
+                         int64_t ko = a.kofs[s];
+                         stage(a.ni[s], a.ldi[s], [&](int k) { return a.rhs[ko + k]; });
+                       },
+                       [&](int s, int r, double v, double2) {
+                         int64_t ko = a.kofs[s];
+                         a.kg[ko + r] = r < a.ni[s] ? v : a.rhs[ko + r] - v;
+                       }))
+    return;
+  cur = prefetch(ring, opH);
+  if (!sync(nullptr)) return;
+  // ================= D: d = B zf with u = g_b, g_p
+  if (!h_phase([&](int s, int, int) {
+        int64_t kb = a.kofs[s] + a.ni[s];
+        stage(a.nb[s], a.ldb[s], [&](int k) { return ldcg(a.kg + kb + k); });
+      }))
+    return;
+  Cursor curS = prefetch(ring, opS);
+  if (!sync(nullptr)) return;
+  coarse_rhs(true);
+  if (!sync(nullptr)) return;
+  cur = curS;
+  if (!coarse_solve()) return;
+  cur = prefetch(ring, opQ);
+  if (!sync(nullptr)) return;
+  if (!psi_phase([&](int64_t q, double v, double) { a.zf[q] = v; })) return;
+  if (!a.precond_none) cur = prefetch(ring, opP);
+  if (!sync(nullptr)) return;
+
+  // ================= PCG: r = d, z = M^{-1} d
   double acc = 0;
   for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
-    double dv = a.d[l];
+    double dv = jump(a.zf, l);
     a.lam[l] = 0.0;
     a.r0[l] = dv;
     acc += dv * dv;
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part_dd[cta] = acc;
-  if (!a.precond_none && !precond_rows([&](int l) { return ldcg(a.d + l); })) return;
-  if (!grid_sync(a.bar, G, target)) return;
+  if (!a.precond_none && !precond_rows([&](int l) { return jump(a.zf, l); })) return;
+  cur = prefetch(ring, opH);
+  if (!sync(nullptr)) return;
   const double dd = reduce_slot(part_dd, G, sh);
   if (cta == 0 && threadIdx.x == 0) *a.out_dd = dd;
-  if (!(dd > 0.0)) {
-    if (cta == 0 && threadIdx.x == 0) { *a.out_its = 0; *a.out_rr = 0.0; }
-    return;
-  }
-  acc = 0;
-  for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
-    double zv = a.precond_none ? a.d[l] : jumpD(a.zp, l);
-    a.z[l] = zv;
-    acc += a.d[l] * zv;
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) part_rz[cta] = acc;
-  if (!grid_sync(a.bar, G, target)) return;
-  double rz_old = reduce_slot(part_rz, G, sh);
   double rr = dd;
-  double *rcur = a.r0, *rnxt = a.r1, *pcur = a.p0, *pnxt = a.p1;
   int it = 0;
-  for (it = 1; it <= a.max_it; ++it) {
-    unsigned long long *tr =
-        (a.trace && cta == 0 && it <= TRACE_IT) ? a.trace + (size_t)(it - 1) * 16 : nullptr;
-    if (tr && threadIdx.x == 0) tr[14] = gtimer();
-    // ---------------- P1: p_new, u = B^T p_new, [F; Psi^T] u
-    double beta = 0.0;
-    if (it > 1) {
-      double rz_new = reduce_slot(part_rz, G, sh);
-      beta = rz_new / rz_old;
-      rz_old = rz_new;
-    }
-    for (int64_t l = lb + threadIdx.x; l < le; l += nthr) pnxt[l] = ldcg(a.z + l) + beta * ldcg(pcur + l);
-    for (int sg = a.hseg_ptr[cta]; sg < a.hseg_ptr[cta + 1]; ++sg) {
-      int s = a.hseg_s[sg], r0 = a.hseg_r0[sg], r1 = a.hseg_r1[sg];
-      __syncthreads();
-      gather(s, a.bt_sgn, r0, r1, true, [&](int l) { return ldcg(a.z + l) + beta * ldcg(pcur + l); });
-      __syncthreads();
-      int nbs = a.nb[s];
-      int64_t bo = a.bofs[s], po = a.pofs[s];
-      if (!phase_rows<4, true>(ring, a.H + a.hoff[s], a.ldb[s], r0, r1, xs, errflag, [&](int r, double v) {
-            if (r < nbs) a.zb[bo + r] = v;
-            else a.tpi[po + (r - nbs)] = v;
-          }))
-        return;
-    }
-    if (!grid_sync(a.bar, G, target, tr ? tr + 0 : nullptr)) return;
-    // ---------------- P2: coarse right-hand side, chunk per CTA
-    for (int64_t k = cb + threadIdx.x; k < ce; k += nthr) {
-      double c = 0;
-#pragma unroll
-      for (int t = 0; t < CP_W; ++t) {
-        int pos = a.cp_pos[k * CP_W + t];
-        if (pos >= 0) c -= ldcg(a.tpi + pos);
-      }
-      a.cc[k] = c;
-    }
-    if (!grid_sync(a.bar, G, target, tr ? tr + 2 : nullptr)) return;
-    // ---------------- P3: q = S_c^{-1} c
-    if (ce > cb) {
-      for (int k = threadIdx.x; k < a.ldc; k += nthr) ccs[k] = k < a.nc ? ldcg(a.cc + k) : 0.0;
-      __syncthreads();
-      if (!phase_rows<1, false>(ring, a.Sinv, a.ldc, (int)cb, (int)ce, ccs, errflag,
-                         [&](int r, double v) { a.q[r] = v; }))
-        return;
-    }
-    if (!grid_sync(a.bar, G, target, tr ? tr + 4 : nullptr)) return;
-    // ---------------- P4: zf = zb - Psi q on the interface rows; (p, F p) = (u, zf)
-    acc = 0;
-    for (int sg = a.bseg_ptr[cta]; sg < a.bseg_ptr[cta + 1]; ++sg) {
-      int s = a.bseg_s[sg];
-      int nps = a.np[s], ldq = a.ldp[s];
-      __syncthreads();
-      const int32_t *pcs = a.pc + a.pofs[s];
-      for (int k = threadIdx.x; k < ldq; k += nthr) xs[k] = (T)(k < nps ? ldcg(a.q + pcs[k]) : 0.0);
-      __syncthreads();
-      int64_t bo = a.bofs[s];
-      if (!phase_rows<4, true>(ring, a.Q + a.qoff[s], ldq, a.bseg_r0[sg], a.bseg_r1[sg], xs, errflag,
-                         [&](int r, double v) {
-                           double zv = ldcg(a.zb + bo + r) - v;
-                           a.zf[bo + r] = zv;
-                           acc += zv * ldcg(a.ub + bo + r);
-                         }))
-        return;
-    }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) part_pq[cta] = acc;
-    if (!grid_sync(a.bar, G, target, tr ? tr + 6 : nullptr)) return;
-    // ---------------- P5: alpha, owner updates, preconditioner
-    double pq = reduce_slot(part_pq, G, sh);
-    double alpha = rz_old / pq;
+  if (dd > 0.0) {
     acc = 0;
     for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
-      double fp = ldcg(a.zf + a.lam_qp[l]) - ldcg(a.zf + a.lam_qm[l]);
-      a.lam[l] += alpha * ldcg(pnxt + l);
-      double rv = ldcg(rcur + l) - alpha * fp;
-      rnxt[l] = rv;
-      acc += rv * rv;
-    }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) part_rr[cta] = acc;
-    if (!a.precond_none && !precond_rows([&](int l) {
-          return ldcg(rcur + l) - alpha * (ldcg(a.zf + a.lam_qp[l]) - ldcg(a.zf + a.lam_qm[l]));
-        }))
-      return;
-    if (!grid_sync(a.bar, G, target, tr ? tr + 8 : nullptr)) return;
-    // ---------------- P6: convergence, z = B_D zp, (r, z)
-    rr = reduce_slot(part_rr, G, sh);
-    if (!(rr > a.tol2 * dd) || !isfinite(rr)) break;
-    acc = 0;
-    for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
-      double rv = ldcg(rnxt + l);
+      double rv = ldcg(a.r0 + l);
       double zv = a.precond_none ? rv : jumpD(a.zp, l);
       a.z[l] = zv;
       acc += rv * zv;
     }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) part_rz[cta] = acc;
-    if (!grid_sync(a.bar, G, target, tr ? tr + 10 : nullptr)) return;
-    double *t = rcur; rcur = rnxt; rnxt = t;
-    t = pcur; pcur = pnxt; pnxt = t;
+    uz_chunk([&](int l) { return zval(ldcg(a.r0 + l), l); });
+    if (!sync(nullptr)) return;
+    double rz_old = reduce_slot(part_rz, G, sh);
+    double *rcur = a.r0, *rnxt = a.r1, *pcur = a.p0, *pnxt = a.p1;
+    for (it = 1; it <= a.max_it; ++it) {
+      unsigned long long *tr =
+          (a.trace && cta == 0 && it <= TRACE_IT) ? a.trace + (size_t)(it - 1) * 16 : nullptr;
+      if (tr && threadIdx.x == 0) tr[14] = gtimer();
+      // ---------------- P1: p_new, u = B^T p_new, [F; Psi^T] u
+      double beta = 0.0;
+      if (it > 1) {
+        double rz_new = reduce_slot(part_rz, G, sh);
+        beta = rz_new / rz_old;
+        rz_old = rz_new;
+      }
+      for (int64_t l = lb + threadIdx.x; l < le; l += nthr) pnxt[l] = ldcg(a.z + l) + beta * ldcg(pcur + l);
+      // u = B^T p_new = B^T z + beta B^T p_old  (uz from the previous phase, ub_old from the
+      // previous iteration); this CTA stores u for its own rows into ub_new
+      if (!h_phase([&](int s, int r0, int r1) {
+            int64_t b0 = a.bofs[s];
+            int nbs = a.nb[s];
+            for (int k = threadIdx.x; k < a.ldb[s]; k += nthr) {
+              double u = 0.0;
+              if (k < nbs) {
+                u = ldcg(a.uz + b0 + k) + (it > 1 ? beta * ldcg(ub_old + b0 + k) : 0.0);
+                if (k >= r0 && k < r1) ub_new[b0 + k] = u;
+              }
+              xs[k] = (T)u;
+            }
+          }))
+        return;
+      curS = prefetch(ring, opS);
+      if (!sync(tr ? tr + 0 : nullptr)) return;
+      // ---------------- P2, P3: coarse
+      coarse_rhs(false);
+      if (!sync(tr ? tr + 2 : nullptr)) return;
+      cur = curS;
+      if (!coarse_solve()) return;
+      cur = prefetch(ring, opQ);
+      if (!sync(tr ? tr + 4 : nullptr)) return;
+      // ---------------- P4: zf = zb - Psi q; (p, F p) = (u, zf)
+      acc = 0;
+      if (!psi_phase([&](int64_t q, double v, double ubv) {  // ubv = B^T p_new (ub_new)
+            a.zf[q] = v;
+            acc += v * ubv;
+          }))
+        return;
+      acc = block_sum(acc, sh);
+      if (threadIdx.x == 0) part_pq[cta] = acc;
+      if (!a.precond_none) cur = prefetch(ring, opP);
+      if (!sync(tr ? tr + 6 : nullptr)) return;
+      // ---------------- P5: alpha, owner updates, preconditioner
+      double pq = reduce_slot(part_pq, G, sh);
+      double alpha = rz_old / pq;
+      acc = 0;
+      for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
+        double fp = jump(a.zf, l);
+        a.lam[l] += alpha * ldcg(pnxt + l);
+        double rv = ldcg(rcur + l) - alpha * fp;
+        rnxt[l] = rv;
+        acc += rv * rv;
+      }
+      acc = block_sum(acc, sh);
+      if (threadIdx.x == 0) part_rr[cta] = acc;
+      if (!a.precond_none &&
+          !precond_rows([&](int l) { return ldcg(rcur + l) - alpha * jump(a.zf, l); }))
+        return;
+      cur = prefetch(ring, opH);
+      if (!sync(tr ? tr + 8 : nullptr)) return;
+      // ---------------- P6: convergence, z = B_D zp, (r, z)
+      rr = reduce_slot(part_rr, G, sh);
+      if (!(rr > a.tol2 * dd) || !isfinite(rr)) break;
+      acc = 0;
+      for (int64_t l = lb + threadIdx.x; l < le; l += nthr) {
+        double rv = ldcg(rnxt + l);
+        double zv = a.precond_none ? rv : jumpD(a.zp, l);
+        a.z[l] = zv;
+        acc += rv * zv;
+      }
+      acc = block_sum(acc, sh);
+      if (threadIdx.x == 0) part_rz[cta] = acc;
+      uz_chunk([&](int l) { return zval(ldcg(rnxt + l), l); });
+      if (!sync(tr ? tr + 10 : nullptr)) return;
+      double *t = rcur; rcur = rnxt; rnxt = t;
+      t = pcur; pcur = pnxt; pnxt = t;
+      t = ub_old; ub_old = ub_new; ub_new = t;
+    }
   }
+  // ================= R: recovery with v_b = g_b - B^T lambda  (H rows prefetched)
+  if (!h_phase([&](int s, int, int) {
+        int64_t kb = a.kofs[s] + a.ni[s];
+        int64_t b0 = a.bofs[s];
+        int nbs = a.nb[s];
+        for (int k = threadIdx.x; k < a.ldb[s]; k += nthr) {
+          double v = 0;
+          if (k < nbs) {
+            const int32_t *L = a.bt_lam + (b0 + k) * BT_W;
+            const double *W = a.bt_sgn + (b0 + k) * BT_W;
+            v = ldcg(a.kg + kb + k);
+#pragma unroll
+            for (int t = 0; t < BT_W; ++t)
+              if (L[t] >= 0) v -= W[t] * ldcg(a.lam + L[t]);
+          }
+          xs[k] = (T)v;
+        }
+      }))
+    return;
+  curS = prefetch(ring, opS);
+  if (!sync(nullptr)) return;
+  coarse_rhs(true);
+  if (!sync(nullptr)) return;
+  cur = curS;
+  if (!coarse_solve()) return;
+  cur = prefetch(ring, opQ);
+  if (!sync(nullptr)) return;
+  if (!psi_phase([&](int64_t q, double v, double) { a.kx[a.b_kept[q]] = v; })) return;
+  for (int64_t k = cb + threadIdx.x; k < ce; k += nthr) {  // a_p = q, every copy
+#pragma unroll
+    for (int t = 0; t < CP_W; ++t) {
+      int pos = a.cp_pos[k * CP_W + t];
+      if (pos >= 0) a.kx[a.p_kept[pos]] = ldcg(a.q + k);
+    }
+  }
+  cur = prefetch(ring, opGT);
+  if (!sync(nullptr)) return;
+  // R5: a_i = z_i - G^T a_[bp]
+  if (!stream_phase<4>(ring, opGT, cur, xs, errflag,
+                       [&](int s, int, int) {
+                         int64_t ko = a.kofs[s] + a.ni[s];
+                         stage(a.nb[s] + a.np[s], a.ldg[s], [&](int k) { return ldcg(a.kx + ko + k); });
+                       },
+                       [&](int s, int r, double v, double2) {
+                         int64_t ko = a.kofs[s];
+                         a.kx[ko + r] = ldcg(a.kg + ko + r) - v;
+                       }))
+    return;
   if (cta == 0 && threadIdx.x == 0) {
     *a.out_its = it > a.max_it ? a.max_it : it;
     *a.out_rr = rr;

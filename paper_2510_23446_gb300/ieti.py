@@ -37,7 +37,7 @@ class ieti_options(C.Structure):
     _fields_ = [("device", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("profile", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -61,7 +61,8 @@ class ieti_info(C.Structure):
                 ("n_coarse", C.c_int64), ("sum_ni", C.c_int64), ("sum_nb", C.c_int64),
                 ("sum_np", C.c_int64), ("max_n", C.c_int64), ("bytes_iter", C.c_int64),
                 ("bytes_device", C.c_int64), ("t_setup_host_ms", C.c_double),
-                ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64)]
+                ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64),
+                ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64)]
 
 
 _ctx = C.c_void_p
@@ -115,7 +116,7 @@ class Solver:
 
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
-                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0):
+                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1):
         self._keep = []
 
         def arr(x, dt_):
@@ -147,6 +148,7 @@ class Solver:
         op.host_threads = int(host_threads)
         op.cuda_stream = C.c_void_p(stream or 0)
         op.profile = int(profile)
+        op.l2_persist = int(l2_persist)
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
