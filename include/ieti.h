@@ -56,6 +56,16 @@ extern "C" {
 #define IETI_PREC_FP64 0   /* everything FP64 */
 #define IETI_PREC_MIXED 1  /* FP32 local operators, FP64 CG / coarse / residuals, outer FP64 refinement */
 
+/* Arithmetic of the setup factorizations of the patch blocks (the partial Cholesky
+ * behind both Schur complements of Sec. 3) in the MIXED precision mode; the FP64
+ * mode always factors in FP64.  The coarse block is always factored in FP64.  The
+ * outer FP64 refinement of every step recovers the accuracy of the reduced factors. */
+#define IETI_FACTOR_FP64 0    /* FP64 on the FP64 pipe, operators rounded to FP32 afterwards */
+#define IETI_FACTOR_FP32 1    /* FP32 on the SIMT pipe */
+#define IETI_FACTOR_TF32X3 2  /* FP32 panels, trailing updates on the tensor cores as three TF32 products
+                                 (hi*hi + hi*lo + lo*hi, FP32 accumulation): FP32-class accuracy */
+#define IETI_FACTOR_TF32 3    /* as TF32X3 with one TF32 product (ablation: 11-bit operands) */
+
 /* Dirichlet preconditioner variants (Sec. 4 uses it "without scaling"; Sec. 5 asks for scaling). */
 #define IETI_PRECOND_NONE 0
 #define IETI_PRECOND_DIRICHLET 1       /* unscaled: B_D = B (the paper's experiments) */
@@ -92,6 +102,7 @@ typedef struct {
   int32_t profile;       /* 1: time every launch of the operator kernels with CUDA events (ieti_kernel_stats) */
   int32_t l2_persist;    /* 1: keep the per-iteration operators in a persisting L2 carve-out during a step
                             (reset to normal at the end of every step); 0: plain streaming */
+  int32_t factor;        /* IETI_FACTOR_* (MIXED precision only; must be IETI_FACTOR_FP64 with FP64) */
 } ieti_options;
 
 /* Coil source through its potential T = T_z(r) chi(|z - zc| < hz) e_z (J = curl T):
@@ -124,6 +135,11 @@ typedef struct {
   int64_t l2_window_bytes;   /* per-iteration operators covered by the persisting L2 window (0: off) */
   double l2_hit_ratio;       /* fraction of that window marked persisting */
   int64_t iter_operator_bytes; /* size of the per-iteration operator arena */
+  double t_factor_ms;        /* device time of the patch-block partial Cholesky (both phases, CUDA events) */
+  double tc_ms;              /* of which in the tensor-core trailing updates (IETI_FACTOR_TF32X3 / TF32) */
+  double tc_flops;           /* tensor-core flops those updates issued (3 products per update for TF32X3) */
+  double tc_useful_flops;    /* the multiply-adds of the updated entries, x 2 */
+  int64_t tc_launches;       /* tensor-core update launches */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
@@ -211,6 +227,18 @@ int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_
  * (batch < 1, n < 1, n_pivots outside [0, n], NULL pointers), CUDA or OOM. */
 int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
                        const int32_t *n_pivots, int32_t *status_out, void *stream);
+
+/* The FP32 variant of ieti_potrf_batched in the arithmetic `factor` (IETI_FACTOR_FP32,
+ * IETI_FACTOR_TF32X3 or IETI_FACTOR_TF32).  Matrix b is row-major n[b] x n[b] with
+ * leading dimension ld[b] >= n[b] at base_dev + offsets[b] (floats).  The tensor-core
+ * variants need 16-byte rows and bases: ld[b] and offsets[b] multiples of 4.  Same
+ * results, status and ownership rules as ieti_potrf_batched; the error is that of
+ * the FP32 (or TF32) arithmetic.  Allocates its scratch (tile list, the panel buffer
+ * of 2 x sum(n) x 256 floats) per call.  Returns 0, INVALID_ARG (also for a bad
+ * factor or misaligned ld / offsets), CUDA or OOM. */
+int ieti_potrf_batched_f32(int32_t batch, float *base_dev, const int64_t *offsets, const int32_t *n,
+                           const int32_t *ld, const int32_t *n_pivots, int32_t factor, int32_t *status_out,
+                           void *stream);
 
 /* ieti_potrf_batched for callers that must not allocate device memory: code that
  * runs under a fixed memory budget (an application that reserved all device memory

@@ -28,6 +28,11 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->device < -1) { err = "device must be >= -1"; return IETI_ERR_INVALID_ARG; }
   if (o->pcg_mode != 0 && o->pcg_mode != 1) { err = "pcg_mode must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->l2_persist != 0 && o->l2_persist != 1) { err = "l2_persist must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
+  if (o->factor < IETI_FACTOR_FP64 || o->factor > IETI_FACTOR_TF32) { err = "bad factor"; return IETI_ERR_INVALID_ARG; }
+  if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
+    err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
+    return IETI_ERR_INVALID_ARG;
+  }
   return IETI_OK;
 }
 
@@ -169,6 +174,32 @@ int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, 
                                       g_setup_err);
   } catch (...) {
     g_setup_err = "ieti_potrf_batched: host allocation failed";
+    return IETI_ERR_OOM;
+  }
+}
+
+int ieti_potrf_batched_f32(int32_t batch, float *base_dev, const int64_t *offsets, const int32_t *n,
+                           const int32_t *ld, const int32_t *n_pivots, int32_t factor, int32_t *status_out,
+                           void *stream) {
+  g_setup_err.clear();
+  if (batch < 1 || !base_dev || !offsets || !n || !ld || !n_pivots || !status_out ||
+      factor < IETI_FACTOR_FP32 || factor > IETI_FACTOR_TF32) {
+    g_setup_err = "ieti_potrf_batched_f32: invalid arguments";
+    return IETI_ERR_INVALID_ARG;
+  }
+  const bool tc = factor != IETI_FACTOR_FP32;
+  for (int32_t b = 0; b < batch; ++b)
+    if (n[b] < 1 || ld[b] < n[b] || n_pivots[b] < 0 || n_pivots[b] > n[b] || offsets[b] < 0 ||
+        (tc && (ld[b] % 4 != 0 || offsets[b] % 4 != 0))) {
+      g_setup_err = "ieti_potrf_batched_f32: bad size, leading dimension, pivot count or offset of matrix " +
+                    std::to_string(b);
+      return IETI_ERR_INVALID_ARG;
+    }
+  try {
+    return ieti::device_potrf_batched_f32(batch, base_dev, offsets, n, ld, n_pivots, factor, status_out,
+                                          (cudaStream_t)stream, g_setup_err);
+  } catch (...) {
+    g_setup_err = "ieti_potrf_batched_f32: host allocation failed";
     return IETI_ERR_OOM;
   }
 }

@@ -1,0 +1,278 @@
+// Tensor-core trailing update of the batched partial Cholesky (FP32 data).
+//
+// The right-looking blocked factorization of every augmented patch block (the
+// two Schur complements of Sec. 3) spends its flops in the trailing update
+// A22 -= L21 L21^T.  Here that update runs on the tcgen05 tensor cores in TF32
+// with FP32 accumulation in tensor memory, once per outer panel of TC_KP = 256
+// columns (the inner 32-column steps stay on the SIMT kernels):
+//
+//   1. k_panel_split writes the finished panel rows L21 of every patch into a
+//      stacked panel buffer (rows ro[s] + r, TC_KP columns, zero padded) as two
+//      planes, hi = rna_tf32(L21) and lo = L21 - hi.
+//   2. k_syrk_tc: one persistent CTA per SM walks a host-built list of
+//      128 x 256 output tiles (patch-major, lower triangle only).  Warp 0 feeds
+//      the 128-byte-swizzled K-major operand tiles by TMA through a shared-memory
+//      ring, warp 1 issues the MMAs (hi*hi + hi*lo + lo*hi for the three-term
+//      split, which carries FP32 accuracy; hi*hi alone for the one-term
+//      ablation) into one of two TMEM accumulators, and warps 2-5 read the
+//      accumulator, subtract it from A22 in global memory (lower triangle, the
+//      patch's active rows, the AugLimits restrictions) while the next tile is
+//      multiplied.
+//
+// Every wait is bounded; a timeout sets *err_flag, stops the work loops, drains
+// the copies and MMAs in flight and frees the tensor memory before returning.
+#pragma once
+#include <cuda.h>  // CUtensorMap
+
+#include <climits>
+#include <cstdint>
+
+#include "tc.cuh"
+
+namespace ieti {
+
+// Per-patch restrictions of a partial-Cholesky phase: rows in [sk_lo, sk_hi) hold
+// zeros in the pivot columns (no work); rows >= rlim only need columns < clim.
+struct AugLimits {
+  const int32_t *sk_lo, *sk_hi, *rlim, *clim;
+};
+
+constexpr int TC_KP = 256;  // outer panel width = K of one trailing update
+constexpr int TC_BM = 128;  // tile rows (MMA M)
+constexpr int TC_BN = 256;  // tile columns (MMA N)
+constexpr int TC_THREADS = 192;
+
+struct TcItem {
+  int32_t s, R0, C0, t0, nk, pad;  // patch, tile origin, first trailing column, 32-wide K chunks
+};
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Panel P of every patch: rows [t0, nact) x columns [J, J + jb) -> planes hi (and lo)
+// of the stacked panel buffer PB (plane stride R_total * TC_KP floats), zero padded
+// to TC_KP columns.  One warp per row.
+template <int X3>
+__global__ void k_panel_split(const float *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
+                              const int32_t *kend, const int32_t *nact, int P, const int64_t *ro, int64_t R_total,
+                              float *PB) {
+  int s = blockIdx.y;
+  int J = kbeg[s] + P * TC_KP;
+  int ke = kend[s];
+  if (J >= ke) return;
+  int jb = min(TC_KP, ke - J);
+  int t0 = J + jb;
+  int m = nact[s] - t0;
+  int lane = threadIdx.x & 31;
+  int wpb = blockDim.x >> 5;
+  int64_t ld = ldv[s];
+  const float *A = base + off[s];
+  for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < m; rr += gridDim.x * wpb) {
+    int r = t0 + rr;
+    const float *src = A + (int64_t)r * ld + J;
+    float *hi = PB + (ro[s] + r) * (int64_t)TC_KP;
+    float *lo = hi + R_total * (int64_t)TC_KP;
+    for (int k = lane; k < TC_KP; k += 32) {
+      float v = k < jb ? src[k] : 0.f;
+      float h = tf32_rna(v);
+      hi[k] = h;
+      if (X3) lo[k] = v - h;
+    }
+  }
+}
+
+template <int X3>
+struct TcCfg {
+  static constexpr int NPLANE = X3 ? 2 : 1;
+  static constexpr int NS = X3 ? 2 : 4;  // ring stages
+  static constexpr uint32_t A_BYTES = TC_BM * 128;  // one plane, 32 FP32 of K per row
+  static constexpr uint32_t B_BYTES = TC_BN * 128;
+  static constexpr uint32_t STAGE = NPLANE * (A_BYTES + B_BYTES);
+  static constexpr uint32_t SMEM = NS * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+};
+
+template <int X3>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_syrk_tc(const __grid_constant__ CUtensorMap tmap, const TcItem *items, int n_items, float *base,
+              const int64_t *off, const int32_t *ldv, const int64_t *ro, const int32_t *nact, AugLimits lim,
+              int32_t *err_flag) {
+  using C = TcCfg<X3>;
+  constexpr uint32_t IDESC = tc_idesc(2u /* TF32 */, TC_BM, TC_BN);
+  extern __shared__ unsigned char smraw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(sm + C::NS * C::STAGE);
+  uint64_t *empty = full + C::NS;
+  uint64_t *tfull = empty + C::NS;  // [2] accumulator ready
+  uint64_t *tempty = tfull + 2;     // [2] accumulator drained by the epilogue
+  uint64_t *drain = tempty + 2;
+  uint32_t *tbase = (uint32_t *)(drain + 1);
+  volatile int *abort_ = (volatile int *)(tbase + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NS; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull + i, 1);
+      mbar_init(tempty + i, 4);
+    }
+    mbar_init(drain, 1);
+    *abort_ = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tbase, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase;
+  auto give_up = [&](int code) {
+    *abort_ = 1;
+    atomicCAS(err_flag, 0, code);
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tmap);
+      int it = 0;
+      for (int w = blockIdx.x; w < n_items && !*abort_; w += gridDim.x) {
+        const TcItem t = items[w];
+        const int ya = (int)(ro[t.s] + t.R0), yb = (int)(ro[t.s] + t.C0);
+        for (int kc = 0; kc < t.nk; ++kc, ++it) {
+          const int st = it % C::NS;
+          const unsigned ph = (unsigned)(it / C::NS) & 1u;
+          if (!mbar_wait(empty + st, ph ^ 1u)) {
+            give_up(1);
+            break;
+          }
+          unsigned char *sb = sm + st * C::STAGE;
+          mbar_arrive_expect_tx(full + st, C::STAGE);
+#pragma unroll
+          for (int pl = 0; pl < C::NPLANE; ++pl) {
+            unsigned char *a = sb + pl * C::A_BYTES;
+            unsigned char *b = sb + C::NPLANE * C::A_BYTES + pl * C::B_BYTES;
+            tma_load_3d(a, &tmap, kc * 32, ya, pl, full + st);
+            tma_load_3d(b, &tmap, kc * 32, yb, pl, full + st);
+            tma_load_3d(b + C::A_BYTES, &tmap, kc * 32, yb + TC_BM, pl, full + st);
+          }
+        }
+      }
+      // the last fill of every stage has landed before the CTA may exit
+      for (int i = (it > C::NS ? it - C::NS : 0); i < it; ++i)
+        if (!mbar_wait(full + i % C::NS, (unsigned)(i / C::NS) & 1u)) give_up(2);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int it = 0, tile = 0;
+      for (int w = blockIdx.x; w < n_items && !*abort_; w += gridDim.x, ++tile) {
+        const TcItem t = items[w];
+        const int ab = tile & 1;
+        const unsigned tph = (unsigned)(tile >> 1) & 1u;
+        if (!mbar_wait(tempty + ab, tph ^ 1u)) {
+          give_up(3);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(ab * TC_BN);
+        bool ok = true;
+        for (int kc = 0; kc < t.nk; ++kc, ++it) {
+          const int st = it % C::NS;
+          const unsigned ph = (unsigned)(it / C::NS) & 1u;
+          if (!mbar_wait(full + st, ph)) {
+            give_up(4);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sm + st * C::STAGE);
+          const uint32_t sb = sa + C::NPLANE * C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x K=8 inside the 128-byte row
+            const uint64_t ah = tc_desc_sw128(sa + kk * 32), bh = tc_desc_sw128(sb + kk * 32);
+            tc_mma<0>(dt, ah, bh, IDESC, (kc | kk) != 0);
+            if constexpr (X3) {
+              const uint64_t al = tc_desc_sw128(sa + C::A_BYTES + kk * 32);
+              const uint64_t bl = tc_desc_sw128(sb + C::B_BYTES + kk * 32);
+              tc_mma<0>(dt, ah, bl, IDESC, 1u);
+              tc_mma<0>(dt, al, bh, IDESC, 1u);
+            }
+          }
+          tc_commit(empty + st);  // the stage is free once these MMAs have read it
+        }
+        if (!ok) break;
+        tc_commit(tfull + ab);
+      }
+      tc_commit(drain);
+      if (!mbar_wait(drain, 0)) give_up(5);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2-5)
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    int tile = 0;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x, ++tile) {
+      const TcItem t = items[w];
+      const int ab = tile & 1;
+      const unsigned tph = (unsigned)(tile >> 1) & 1u;
+      const bool ok = mbar_wait(tfull + ab, tph);
+      if (__any_sync(0xffffffffu, !ok || *abort_)) {
+        if (lane == 0) give_up(6);
+        break;
+      }
+      tc_fence_after();
+      const int s = t.s;
+      const int na = nact[s], sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
+      const int64_t ld = ldv[s];
+      const int rw0 = t.R0 + q * 32;  // first row of this warp
+      const int r = rw0 + lane;
+      const bool row_ok = r < na && !(r >= sk_lo && r < sk_hi);
+      const int cmax = min(r, (r >= rlim) ? clim - 1 : INT_MAX);  // last column this row updates
+      float *Arow = base + off[s] + (int64_t)r * ld;
+#pragma unroll 1
+      for (int c32 = 0; c32 < TC_BN / 32; ++c32) {
+        const int cb = t.C0 + c32 * 32;
+        if (cb > rw0 + 31 || cb >= na) break;  // warp-uniform: beyond every row of this warp
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * TC_BN + c32 * 32), v);
+        if (row_ok) {
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const int c = cb + 4 * g;
+            if (c + 3 < t.t0 || c > cmax) continue;  // no updated column in this group
+            float4 *p = reinterpret_cast<float4 *>(Arow + c);
+            float4 x = *p;
+            if (c + 0 >= t.t0 && c + 0 <= cmax) x.x -= v[4 * g + 0];
+            if (c + 1 >= t.t0 && c + 1 <= cmax) x.y -= v[4 * g + 1];
+            if (c + 2 >= t.t0 && c + 2 <= cmax) x.z -= v[4 * g + 2];
+            if (c + 3 >= t.t0 && c + 3 <= cmax) x.w -= v[4 * g + 3];
+            *p = x;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + ab);
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace ieti

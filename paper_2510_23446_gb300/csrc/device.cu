@@ -27,12 +27,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "chol_tc.cuh"
 #include "device.h"
 #include "pcg_kernel.cuh"
 
@@ -58,31 +60,33 @@ template <class T> struct Acc { using type = T; };
 // =============================================================================
 
 // Expand the kept CSR rows into the augmented dense blocks (zeroed beforehand).
+template <class TD>
 __global__ void k_csr_to_dense(int64_t n_rows, const int32_t *row_patch, const int32_t *row_local,
                                const int64_t *rowptr, const int32_t *col_abs, const double *val,
-                               const int64_t *kofs, const int64_t *doff, const int32_t *nn, double *D) {
+                               const int64_t *kofs, const int64_t *doff, const int32_t *nn, TD *D) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n_rows) return;
   int s = row_patch[w];
   int r = row_local[w];
   int64_t ld = nn[s];
-  double *A = D + doff[s];
+  TD *A = D + doff[s];
   for (int64_t t = rowptr[w] + lane; t < rowptr[w + 1]; t += 32) {
     int c = (int)(col_abs[t] - kofs[s]);
-    A[r * ld + c] = val[t];
+    A[r * ld + c] = (TD)val[t];
   }
 }
 
 // identity couplings of the augmented rows: b' (rows n..n+nb) to b, i' (rows
 // n+nb..n+nb+ni) to i
+template <class TD>
 __global__ void k_augment(int n_patch, const int32_t *ni, const int32_t *nb, const int32_t *n,
-                          const int32_t *nn, const int64_t *doff, double *D) {
+                          const int32_t *nn, const int64_t *doff, TD *D) {
   int s = blockIdx.y;
   if (s >= n_patch) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   int64_t ld = nn[s];
-  double *A = D + doff[s];
+  TD *A = D + doff[s];
   if (k < nb[s]) {
     int64_t r = n[s] + k, c = ni[s] + k;
     A[r * ld + c] = 1.0;
@@ -138,11 +142,6 @@ __global__ void k_potrf_diag(T *base, const int64_t *off, const int32_t *ldv, co
 }
 
 // rows below the diagonal block: L_r = A_r L_jj^{-T} (one thread per row)
-// Per-patch restrictions of a phase (AugLimits): rows in [sk_lo, sk_hi) hold zeros in
-// the pivot columns (no work); rows >= rlim only need columns < clim.
-struct AugLimits {
-  const int32_t *sk_lo, *sk_hi, *rlim, *clim;
-};
 
 template <class T>
 __global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
@@ -178,11 +177,14 @@ __global__ void k_trsm_panel(T *base, const int64_t *off, const int32_t *ldv, co
     if (k < jb) row[k] = (T)x[k];
 }
 
-// trailing lower update A[r][c] -= sum_k L[r][k] L[c][k] on 64x64 tiles
+// trailing lower update A[r][c] -= sum_k L[r][k] L[c][k] on 64x64 tiles.  With
+// cend_panel >= 0 only the columns below kbeg + cend_panel * NB (and kend) are
+// updated: the inner steps of a panel whose trailing part is updated separately.
 template <class T>
 __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off, const int32_t *ldv,
                                                      const int32_t *kbeg, const int32_t *kend,
-                                                     const int32_t *nact, int panel, AugLimits lim) {
+                                                     const int32_t *nact, int panel, AugLimits lim,
+                                                     int cend_panel = -1) {
   using A_t = typename Acc<T>::type;
   int s = blockIdx.y;
   int j0 = kbeg[s] + panel * NB;
@@ -195,11 +197,21 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off
   if (m <= 0) return;
   int T64 = (m + 63) / 64;
   int t = blockIdx.x;
-  if (t >= T64 * (T64 + 1) / 2) return;
-  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-  while (ti * (ti + 1) / 2 > t) --ti;
-  int tj = t - ti * (ti + 1) / 2;
+  int ti, tj, cend = INT_MAX;
+  if (cend_panel >= 0) {
+    cend = min(kbeg[s] + cend_panel * NB, ke);
+    int nc = (cend - t0 + 63) / 64;
+    if (cend <= t0 || t >= T64 * nc) return;
+    ti = t / nc;
+    tj = t % nc;
+    if (tj > ti) return;
+  } else {
+    if (t >= T64 * (T64 + 1) / 2) return;
+    ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    tj = t - ti * (ti + 1) / 2;
+  }
   int R0 = t0 + ti * 64, C0 = t0 + tj * 64;
   int sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
   if (R0 >= sk_lo && min(R0 + 64, na) <= sk_hi) return;   // rows with zero panel entries
@@ -242,14 +254,14 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *base, const int64_t *off
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int r = R0 + tr + 16 * i, c = C0 + tc + 16 * j;
-      bool skip = (r >= sk_lo && r < sk_hi) || (r >= rlim && c >= clim);
+      bool skip = (r >= sk_lo && r < sk_hi) || (r >= rlim && c >= clim) || c >= cend;
       if (r < na && c <= r && !skip) A[r * ld + c] = (T)((A_t)A[r * ld + c] - acc[i][j]);
     }
 }
 
 // P_s = S_bb (after the interior pivots), symmetrised from the lower triangle
-template <class T>
-__global__ void k_extract_P(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+template <class TD, class T>
+__global__ void k_extract_P(const TD *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
                             const int32_t *nb, const int32_t *ldb, const int64_t *poff, T *P) {
   int s = blockIdx.y;
   int m = nb[s];
@@ -257,21 +269,21 @@ __global__ void k_extract_P(const double *D, const int64_t *doff, const int32_t 
   if (idx >= (int64_t)m * m) return;
   int r = (int)(idx / m), c = (int)(idx % m);
   int64_t ld = nn[s];
-  const double *A = D + doff[s];
+  const TD *A = D + doff[s];
   int rr = ni[s] + max(r, c), cc = ni[s] + min(r, c);
   P[poff[s] + (int64_t)r * ldb[s] + c] = (T)A[rr * ld + cc];
 }
 
 // H_s = [F_s; Psi_s^T] ((nb+np) x nb), Psi_s (nb x np), LY_s = first ni columns (n x ni)
-template <class T>
-__global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+template <class TD, class T>
+__global__ void k_extract_ops(const TD *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
                               const int32_t *nb, const int32_t *np, const int32_t *ldb, const int32_t *ldp,
                               const int64_t *hoff, const int64_t *qoff, T *H, T *Q) {
   int s = blockIdx.y;
   int B = nb[s], Pn = np[s], I = ni[s];
   int n = I + B + Pn;
   int64_t ld = nn[s];
-  const double *A = D + doff[s];
+  const TD *A = D + doff[s];
   int64_t total = (int64_t)(B + Pn) * B;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -292,15 +304,15 @@ __global__ void k_extract_ops(const double *D, const int64_t *doff, const int32_
 // G = W_[bp]i W_ii^{-1}; GT_s (ni x ldg) holds G^T.  After the interior pivots the
 // trailing block of the augmented matrix has (i', i') = -W_ii^{-1} and
 // (i', [b p]) = -W_ii^{-1} W_i[bp] = -G^T.
-template <class T>
-__global__ void k_extract_IG(const double *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
+template <class TD, class T>
+__global__ void k_extract_IG(const TD *D, const int64_t *doff, const int32_t *nn, const int32_t *ni,
                              const int32_t *nb, const int32_t *np, const int32_t *ldi, const int32_t *ldg,
                              const int64_t *igoff, const int64_t *gtoff, T *IG, T *GT) {
   int s = blockIdx.y;
   int I = ni[s], B = nb[s];
   int n = I + B + np[s];
   int64_t ld = nn[s];
-  const double *A = D + doff[s];
+  const TD *A = D + doff[s];
   int64_t total = (int64_t)n * I;
   int64_t ip = n + B;  // first i' row
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -319,14 +331,15 @@ __global__ void k_extract_IG(const double *D, const int64_t *doff, const int32_t
 }
 
 // coarse: Sc_aug[A[k]][A[l]] += C_s[k][l] (one launch per patch, in patch order)
-__global__ void k_coarse_add(const double *D, int64_t doff, int nn, int ni, int nb, int np, const int32_t *A,
+template <class TD>
+__global__ void k_coarse_add(const TD *D, int64_t doff, int nn, int ni, int nb, int np, const int32_t *A,
                              double *Sc, int64_t ldc) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)np * np) return;
   int k = (int)(idx / np), l = (int)(idx % np);
   int base = ni + nb;
   int hi = max(k, l), lo = min(k, l);
-  double v = D[doff + (int64_t)(base + hi) * nn + base + lo];
+  double v = (double)D[doff + (int64_t)(base + hi) * nn + base + lo];
   Sc[(int64_t)A[k] * ldc + A[l]] += v;
 }
 
@@ -680,6 +693,11 @@ struct DeviceState {
   int ev_used = 0;
   double gemv_bytes[IETI_K_NCLASS] = {};  // algorithmic bytes of one launch per GEMV class
   int64_t nlaunch = 0;                    // kernels launched by the current step
+  // setup factorization
+  int factor = IETI_FACTOR_FP64;
+  double t_factor_ms = 0;                 // both partial-Cholesky phases of the patch blocks
+  double tc_ms = 0, tc_flops = 0, tc_useful_flops = 0;  // tensor-core trailing updates
+  int64_t tc_launches = 0;
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -800,6 +818,237 @@ static int potrf_partial(DeviceState *d, T *base, const int64_t *off, const int3
     }
   }
   CK(cudaGetLastError());
+  return IETI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Partial Cholesky of FP32 blocks with tensor-core trailing updates.
+//
+// Outer panels of TC_KP columns.  Each is factored by the SIMT kernels in NB-wide
+// steps that update only the panel's own columns, then its rows below the panel
+// are split into TF32 hi/lo planes (k_panel_split) and the whole trailing lower
+// triangle is updated once on the tensor cores (k_syrk_tc).
+
+// cuTensorMapEncodeTiled, resolved from the driver at run time (the library links
+// only the CUDA runtime, so it loads on machines without a driver)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled(std::string &err) {
+  static std::mutex mu;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      err = "cuTensorMapEncodeTiled is not available from the driver";
+      return nullptr;
+    }
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// host copies of the per-patch limits, for building the tile list
+struct TcHost {
+  std::vector<int64_t> off;
+  std::vector<int32_t> ld, sk_lo, sk_hi, rlim, clim;
+};
+
+// The output tiles of every outer panel (patch-major, lower triangle, restricted by
+// the limits), their useful flops, and each panel's slice of the list.
+static void tc_plan(const TcHost &th, const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
+                    const std::vector<int32_t> &hna, std::vector<TcItem> &items, std::vector<int64_t> &pofs,
+                    double &flops) {
+  const int nb = (int)hkb.size();
+  int max_outer = 0;
+  for (int s = 0; s < nb; ++s) max_outer = std::max(max_outer, (hke[s] - hkb[s] + TC_KP - 1) / TC_KP);
+  items.clear();
+  pofs.assign(1, 0);
+  flops = 0;
+  for (int P = 0; P < max_outer; ++P) {
+    for (int s = 0; s < nb; ++s) {
+      const int J = hkb[s] + P * TC_KP;
+      if (J >= hke[s]) continue;
+      const int Je = std::min(J + TC_KP, hke[s]), t0 = Je, na = hna[s];
+      if (t0 >= na) continue;
+      const int t0a = t0 & ~3, nk = (Je - J + 31) / 32;
+      const int sklo = th.sk_lo[s], skhi = th.sk_hi[s], rlim = th.rlim[s], clim = th.clim[s];
+      for (int R0 = t0; R0 < na; R0 += TC_BM) {
+        const int Rend = std::min(R0 + TC_BM, na);
+        if (R0 >= sklo && Rend <= skhi) continue;
+        for (int C0 = t0a; C0 < Rend; C0 += TC_BN) {
+          const int cf = std::max(C0, t0), cl = std::min(C0 + TC_BN, Rend) - 1;
+          if (cf > cl) continue;
+          if (cf >= sklo && cl < skhi) continue;
+          if (R0 >= rlim && cf >= clim) continue;
+          items.push_back({s, R0, C0, t0, nk, 0});
+        }
+      }
+      // useful multiply-adds: every updated (r, c) with K = Je - J
+      for (int r = t0; r < na; ++r) {
+        if (r >= sklo && r < skhi) continue;
+        int cmax = (r >= rlim) ? std::min(r, clim - 1) : r;
+        if (cmax >= t0) flops += 2.0 * (double)(cmax - t0 + 1) * (Je - J);
+      }
+    }
+    pofs.push_back((int64_t)items.size());
+  }
+}
+
+template <int X3>
+static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, const int32_t *ld, const TcHost &th,
+                            const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
+                            const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke, int32_t *dna,
+                            int32_t *status, AugLimits lim, std::string &err) {
+  const int nbatch = (int)hkb.size();
+  constexpr int IN = TC_KP / NB;  // inner steps per outer panel
+  std::vector<TcItem> items;
+  std::vector<int64_t> pofs;
+  double flops = 0;
+  tc_plan(th, hkb, hke, hna, items, pofs, flops);
+  const int max_outer = (int)pofs.size() - 1;
+  if (max_outer <= 0) return IETI_OK;
+  // stacked panel buffer: patch s owns rows [ro[s], ro[s] + nact[s])
+  std::vector<int64_t> hro(nbatch);
+  int64_t R = 0;
+  for (int s = 0; s < nbatch; ++s) {
+    hro[s] = R;
+    R += std::max(hna[s], 1);
+  }
+  if (R + 2 * TC_BN >= (int64_t)INT32_MAX) {
+    err = "the stacked panel buffer exceeds 2^31 rows";
+    return IETI_ERR_TOO_LARGE;
+  }
+  EncodeTiledFn enc = encode_tiled(err);
+  if (!enc) return IETI_ERR_CUDA;
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaFuncSetAttribute(k_syrk_tc<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<X3>::SMEM));
+  // scratch: tile list, panel planes, row offsets, error word (freed before returning)
+  float *PB = nullptr;
+  TcItem *ditems = nullptr;
+  int64_t *dro = nullptr;
+  int32_t *derr = nullptr;
+  auto release = [&]() {
+    cudaStreamSynchronize(d->stream);
+    cudaFree(PB);
+    cudaFree(ditems);
+    cudaFree(dro);
+    cudaFree(derr);
+  };
+  size_t pb_bytes = (size_t)2 * R * TC_KP * sizeof(float);
+  if (cudaMalloc((void **)&PB, pb_bytes) != cudaSuccess ||
+      cudaMalloc((void **)&ditems, std::max<size_t>(items.size(), 1) * sizeof(TcItem)) != cudaSuccess ||
+      cudaMalloc((void **)&dro, nbatch * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc((void **)&derr, sizeof(int32_t)) != cudaSuccess) {
+    release();
+    err = "cudaMalloc failed for the tensor-core factorization scratch";
+    return IETI_ERR_OOM;
+  }
+  if (cudaMemsetAsync(PB, 0, pb_bytes, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(derr, 0, sizeof(int32_t), d->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, d->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dro, hro.data(), nbatch * sizeof(int64_t), cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+      cudaStreamSynchronize(d->stream) != cudaSuccess) {
+    release();
+    err = "upload of the tensor-core factorization plan failed";
+    return IETI_ERR_CUDA;
+  }
+  CUtensorMap tm;
+  {
+    cuuint64_t gdim[3] = {(cuuint64_t)TC_KP, (cuuint64_t)R, 2};
+    cuuint64_t gstr[2] = {(cuuint64_t)TC_KP * 4, (cuuint64_t)R * TC_KP * 4};
+    cuuint32_t box[3] = {32, (cuuint32_t)TC_BM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, PB, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      release();
+      err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+      return IETI_ERR_CUDA;
+    }
+  }
+  std::vector<cudaEvent_t> evs;
+  for (int P = 0; P < max_outer; ++P) {
+    for (int q = 0; q < IN; ++q) {
+      const int j = P * IN + q;
+      bool any = false;
+      int max_rows = 0, max_tiles = 0;
+      for (int s = 0; s < nbatch; ++s) {
+        const int j0 = hkb[s] + j * NB;
+        const int Je = std::min(hkb[s] + (P + 1) * TC_KP, hke[s]);
+        if (j0 >= Je) continue;
+        any = true;
+        const int jb = std::min(NB, hke[s] - j0);
+        const int m = hna[s] - (j0 + jb);
+        if (m <= 0) continue;
+        max_rows = std::max(max_rows, m);
+        const int nc = (Je - (j0 + jb) + 63) / 64;
+        if (nc > 0) max_tiles = std::max(max_tiles, ((m + 63) / 64) * nc);
+      }
+      if (!any) continue;
+      k_potrf_diag<float><<<nbatch, 256, 0, d->stream>>>(base, off, ld, dkb, dke, j, status);
+      d->launches_setup++;
+      if (max_rows > 0) {
+        dim3 g1(grid_for(max_rows, 128), nbatch);
+        k_trsm_panel<float><<<g1, 128, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j, lim);
+        d->launches_setup++;
+        if (max_tiles > 0) {
+          dim3 g2(max_tiles, nbatch);
+          k_syrk_update<float><<<g2, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, j, lim, (P + 1) * IN);
+          d->launches_setup++;
+        }
+      }
+    }
+    const int64_t n_it = pofs[P + 1] - pofs[P];
+    if (n_it == 0) continue;
+    int max_m = 0;
+    for (int s = 0; s < nbatch; ++s) {
+      const int J = hkb[s] + P * TC_KP;
+      if (J < hke[s]) max_m = std::max(max_m, hna[s] - std::min(J + TC_KP, hke[s]));
+    }
+    dim3 gs(std::min<unsigned>(grid_for(max_m, 8), 512), nbatch);
+    k_panel_split<X3><<<gs, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, P, dro, R, PB);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    evs.push_back(e0);
+    evs.push_back(e1);
+    cudaEventRecord(e0, d->stream);
+    const unsigned grid = (unsigned)std::min<int64_t>(n_it, nsm);
+    k_syrk_tc<X3><<<grid, TC_THREADS, TcCfg<X3>::SMEM, d->stream>>>(tm, ditems + pofs[P], (int)n_it, base, off, ld,
+                                                                   dro, dna, lim, derr);
+    cudaEventRecord(e1, d->stream);
+    d->launches_setup += 2;
+    d->tc_launches++;
+  }
+  cudaError_t e = cudaGetLastError();
+  int32_t herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int32_t), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  for (size_t k = 0; k + 1 < evs.size(); k += 2) {
+    float ms = 0;
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, evs[k], evs[k + 1]) == cudaSuccess) d->tc_ms += ms;
+    cudaEventDestroy(evs[k]);
+    cudaEventDestroy(evs[k + 1]);
+  }
+  d->tc_flops += flops * (X3 ? 3.0 : 1.0);
+  d->tc_useful_flops += flops;
+  release();
+  if (e != cudaSuccess) {
+    err = std::string("tensor-core partial Cholesky failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_CUDA;
+  }
+  if (herr) {
+    err = "tensor-core trailing update gave up waiting (stage " + std::to_string(herr) + ")";
+    return IETI_ERR_CUDA;
+  }
   return IETI_OK;
 }
 
@@ -1179,6 +1428,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->opt = opt;
   d->device = opt.device;
   d->mixed = opt.precision == IETI_PREC_MIXED;
+  d->factor = d->mixed ? opt.factor : IETI_FACTOR_FP64;
   d->dt = hs.dt;
   auto fail = [&](int rc) {
     device_destroy(d);
@@ -1202,7 +1452,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     hnb[s] = pt.nb;
     hnp[s] = pt.np;
     hn[s] = pt.ni + pt.nb + pt.np;
-    hnn[s] = hn[s] + pt.nb + pt.ni;  // augmented: [i b p | b' | i']
+    hnn[s] = (hn[s] + pt.nb + pt.ni + 3) / 4 * 4;  // augmented [i b p | b' | i'], 16-byte rows (zero padded)
     hkofs[s + 1] = hkofs[s] + hn[s];
     hdoff[s + 1] = hdoff[s] + (int64_t)hnn[s] * hnn[s];
     hldi[s] = (pt.ni + 3) / 4 * 4;
@@ -1459,18 +1709,35 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   CK(cudaMemsetAsync(d->a, 0, hs.n_edges * sizeof(double), d->stream));
   CK(cudaMemsetAsync(d->j, 0, hs.n_edges * sizeof(double), d->stream));
   CK(cudaMemsetAsync(d->rglob, 0, hs.n_edges * sizeof(double), d->stream));
-  // ---------------- dense augmented blocks, partial Cholesky (FP64)
-  double *D = nullptr;
-  if ((rc = dalloc(d, &D, hdoff[np_], err))) return fail(rc);
-  CK(cudaMemsetAsync(D, 0, hdoff[np_] * sizeof(double), d->stream));
+  // ---------------- dense augmented blocks, partial Cholesky (FP64, or FP32 with
+  // SIMT or tensor-core trailing updates)
+  const bool f32 = d->factor != IETI_FACTOR_FP64;
+  const size_t dsz = f32 ? sizeof(float) : sizeof(double);
+  double *D = nullptr;  // FP64 arena
+  float *Df = nullptr;  // FP32 arena
+  if (f32) {
+    if ((rc = dalloc(d, &Df, hdoff[np_], err))) return fail(rc);
+  } else if ((rc = dalloc(d, &D, hdoff[np_], err))) {
+    return fail(rc);
+  }
+  void *Dv = f32 ? (void *)Df : (void *)D;
+  CK(cudaMemsetAsync(Dv, 0, hdoff[np_] * dsz, d->stream));
   {
     int64_t nrows = d->NK;
-    k_csr_to_dense<<<grid_for(nrows * 32, 256), 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol,
-                                                                     d->wval, d->kofs, ddoff, dnn, D);
+    unsigned g0 = grid_for(nrows * 32, 256);
+    if (f32)
+      k_csr_to_dense<float><<<g0, 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol, d->wval,
+                                                       d->kofs, ddoff, dnn, Df);
+    else
+      k_csr_to_dense<double><<<g0, 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol, d->wval,
+                                                        d->kofs, ddoff, dnn, D);
     int maxaug = std::max(*std::max_element(hnb.begin(), hnb.end()), d->max_ni);
     if (maxaug > 0) {
       dim3 g(grid_for(maxaug, 128), np_);
-      k_augment<<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, D);
+      if (f32)
+        k_augment<float><<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, Df);
+      else
+        k_augment<double><<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, D);
     }
     d->launches_setup += 2;
   }
@@ -1491,6 +1758,23 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     return IETI_OK;
   };
   AugLimits lim{dsklo, dskhi, drlim, dclim};
+  TcHost th;
+  th.off = hdoff;
+  th.ld = hnn;
+  // one partial-Cholesky phase over all patches in the chosen factor precision
+  auto factor_phase = [&](const std::vector<int32_t> &kb, const std::vector<int32_t> &ke,
+                          const std::vector<int32_t> &na, AugLimits lm) -> int {
+    switch (d->factor) {
+      case IETI_FACTOR_FP64:
+        return potrf_partial<double>(d, D, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
+      case IETI_FACTOR_FP32:
+        return potrf_partial<float>(d, Df, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
+      case IETI_FACTOR_TF32X3:
+        return potrf_partial_tc<1>(d, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
+      default:
+        return potrf_partial_tc<0>(d, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
+    }
+  };
   for (int s = 0; s < np_; ++s) {
     hkb[s] = 0;
     hke[s] = hni[s];
@@ -1503,7 +1787,12 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
       (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
     return fail(rc);
-  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, lim, err))) return fail(rc);
+  th.sk_lo = hsklo;
+  th.sk_hi = hskhi;
+  th.rlim = hrlim;
+  th.clim = hclim;
+  CK(cudaEventRecord(d->ev0, d->stream));
+  if ((rc = factor_phase(hkb, hke, hna, lim))) return fail(rc);
   int maxnb = *std::max_element(hnb.begin(), hnb.end());
   int maxnp = *std::max_element(hnp.begin(), hnp.end());
   int64_t maxP = (int64_t)maxnb * maxnb;
@@ -1549,10 +1838,15 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   CK(cudaMemsetAsync(d->Q, 0, std::max<int64_t>(hq[np_], 1) * esz, d->stream));
   if (maxP > 0) {
     dim3 g(grid_for(maxP, 256), np_);
-    if (d->mixed)
-      k_extract_P<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff, (float *)d->P);
+    if (f32)
+      k_extract_P<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
+                                                          (float *)d->P);
+    else if (d->mixed)
+      k_extract_P<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
+                                                           (float *)d->P);
     else
-      k_extract_P<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff, (double *)d->P);
+      k_extract_P<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
+                                                            (double *)d->P);
     d->launches_setup++;
   }
   // phase B: interface pivots -> trailing [p b'] = [[C_s, -Psi^T], [-Psi, -F_s]]
@@ -1567,7 +1861,12 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
       (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
     return fail(rc);
-  if ((rc = potrf_partial<double>(d, D, ddoff, dnn, hkb, hke, hna, dkb, dke, dna, dstat, lim, err))) return fail(rc);
+  th.sk_lo = hsklo;
+  th.sk_hi = hskhi;
+  th.rlim = hrlim;
+  th.clim = hclim;
+  if ((rc = factor_phase(hkb, hke, hna, lim))) return fail(rc);
+  CK(cudaEventRecord(d->ev1, d->stream));
   {
     std::vector<int32_t> hstat(np_);
     CK(cudaMemcpyAsync(hstat.data(), dstat, np_ * 4, cudaMemcpyDeviceToHost, d->stream));
@@ -1581,22 +1880,28 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   }
   if (maxH > 0) {
     dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), np_);
-    if (d->mixed)
-      k_extract_ops<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp, d->hoff,
-                                                     d->qoff, (float *)d->H, (float *)d->Q);
+    if (f32)
+      k_extract_ops<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
+                                                            d->hoff, d->qoff, (float *)d->H, (float *)d->Q);
+    else if (d->mixed)
+      k_extract_ops<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
+                                                             d->hoff, d->qoff, (float *)d->H, (float *)d->Q);
     else
-      k_extract_ops<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp, d->hoff,
-                                                      d->qoff, (double *)d->H, (double *)d->Q);
+      k_extract_ops<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
+                                                              d->hoff, d->qoff, (double *)d->H, (double *)d->Q);
     d->launches_setup++;
   }
   if (maxIG > 0) {
     dim3 g((unsigned)std::min<int64_t>(grid_for(maxIG, 256), 4096), np_);
-    if (d->mixed)
-      k_extract_IG<float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg, d->igoff,
-                                                     d->gtoff, (float *)d->IG, (float *)d->GT);
+    if (f32)
+      k_extract_IG<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
+                                                           d->igoff, d->gtoff, (float *)d->IG, (float *)d->GT);
+    else if (d->mixed)
+      k_extract_IG<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
+                                                            d->igoff, d->gtoff, (float *)d->IG, (float *)d->GT);
     else
-      k_extract_IG<double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
-                                                      d->igoff, d->gtoff, (double *)d->IG, (double *)d->GT);
+      k_extract_IG<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
+                                                             d->igoff, d->gtoff, (double *)d->IG, (double *)d->GT);
     d->launches_setup++;
   }
   // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, inverted through [[S_c, I], [I, 0]]
@@ -1608,8 +1913,12 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     for (int s = 0; s < np_; ++s) {
       if (hnp[s] == 0) continue;
       int64_t cnt = (int64_t)hnp[s] * hnp[s];
-      k_coarse_add<<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
-                                                              d->pc + hpofs[s], Sc, ldc);
+      if (f32)
+        k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
+                                                                       d->pc + hpofs[s], Sc, ldc);
+      else
+        k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
+                                                                        hnp[s], d->pc + hpofs[s], Sc, ldc);
       d->launches_setup++;
     }
     k_coarse_identity<<<grid_for(nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc);
@@ -1650,9 +1959,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   }
   CK(cudaStreamSynchronize(d->stream));
   CK(cudaGetLastError());
-  cudaFree(D);
-  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)D));
-  d->bytes -= hdoff[np_] * 8;
+  {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, d->ev0, d->ev1));
+    d->t_factor_ms = ms;
+  }
+  cudaFree(Dv);
+  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), Dv));
+  d->bytes -= hdoff[np_] * (int64_t)dsz;
   // algorithmic bytes of one PCG iteration: H and Psi once each (F apply), P once
   // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
   d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
@@ -1837,6 +2151,11 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->l2_window_bytes = (int64_t)d->l2_window;
   info->l2_hit_ratio = d->l2_hit_ratio;
   info->iter_operator_bytes = (int64_t)d->iter_bytes;
+  info->t_factor_ms = d->t_factor_ms;
+  info->tc_ms = d->tc_ms;
+  info->tc_flops = d->tc_flops;
+  info->tc_useful_flops = d->tc_useful_flops;
+  info->tc_launches = d->tc_launches;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
@@ -1917,6 +2236,67 @@ int device_potrf_batched(int batch, double *base, const int64_t *off, const int3
     tmp.stream = st;
     AugLimits lim{dz, dz2, dbig, dz};
     rc = potrf_partial<double>(&tmp, base, doff, dn, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+  }
+  if (rc == IETI_OK) {
+    if (cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      err = std::string("batched partial Cholesky failed: ") + cudaGetErrorString(cudaGetLastError());
+      rc = IETI_ERR_CUDA;
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(blk);
+  return rc;
+}
+
+// standalone FP32 batched partial Cholesky (SIMT, or tensor-core trailing updates)
+int device_potrf_batched_f32(int batch, float *base, const int64_t *off, const int32_t *n, const int32_t *ld,
+                             const int32_t *npiv, int factor, int32_t *status, cudaStream_t st, std::string &err) {
+  std::vector<int32_t> hkb(batch, 0), hke(npiv, npiv + batch), hna(n, n + batch);
+  TcHost th;
+  th.off.assign(off, off + batch);
+  th.ld.assign(ld, ld + batch);
+  th.sk_lo.assign(batch, 0);
+  th.sk_hi.assign(batch, 0);
+  th.rlim.assign(batch, INT32_MAX);
+  th.clim.assign(batch, 0);
+  size_t bytes = (size_t)batch * (sizeof(int64_t) + 9 * sizeof(int32_t));
+  unsigned char *blk = nullptr;
+  cudaError_t e = cudaMalloc((void **)&blk, bytes);
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_OOM;
+  }
+  int64_t *doff = (int64_t *)blk;
+  int32_t *dld = (int32_t *)(doff + batch), *dkb = dld + batch, *dke = dkb + batch, *dna = dke + batch,
+          *dst = dna + batch, *dz = dst + batch, *dbig = dz + batch, *dz2 = dbig + batch;
+  int rc = IETI_OK;
+  auto cp = [&](void *dst_, const void *src, size_t nbytes) {
+    if (rc == IETI_OK && cudaMemcpyAsync(dst_, src, nbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      err = "cudaMemcpyAsync failed";
+      rc = IETI_ERR_CUDA;
+    }
+  };
+  cp(doff, th.off.data(), batch * 8);
+  cp(dld, th.ld.data(), batch * 4);
+  cp(dkb, hkb.data(), batch * 4);
+  cp(dke, hke.data(), batch * 4);
+  cp(dna, hna.data(), batch * 4);
+  cp(dz, th.sk_lo.data(), batch * 4);
+  cp(dbig, th.rlim.data(), batch * 4);
+  cp(dz2, th.sk_hi.data(), batch * 4);
+  if (rc == IETI_OK && cudaMemsetAsync(dst, 0, batch * 4, st) != cudaSuccess) rc = IETI_ERR_CUDA;
+  if (rc == IETI_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = IETI_ERR_CUDA;
+  if (rc == IETI_OK) {
+    DeviceState tmp;
+    tmp.stream = st;
+    AugLimits lim{dz, dz2, dbig, dz};
+    if (factor == IETI_FACTOR_FP32)
+      rc = potrf_partial<float>(&tmp, base, doff, dld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+    else if (factor == IETI_FACTOR_TF32X3)
+      rc = potrf_partial_tc<1>(&tmp, base, doff, dld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+    else
+      rc = potrf_partial_tc<0>(&tmp, base, doff, dld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
   }
   if (rc == IETI_OK) {
     if (cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

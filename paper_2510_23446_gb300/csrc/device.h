@@ -21,6 +21,8 @@ void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, bool res
 void device_destroy(DeviceState *d);
 int device_potrf_batched(int batch, double *base, const int64_t *off, const int32_t *n, const int32_t *npiv,
                          int32_t *status, cudaStream_t st, std::string &err);
+int device_potrf_batched_f32(int batch, float *base, const int64_t *off, const int32_t *n, const int32_t *ld,
+                             const int32_t *npiv, int factor, int32_t *status, cudaStream_t st, std::string &err);
 int device_potrf_batched_noalloc(int batch, double *base, const int64_t *off, const int32_t *n,
                                  const int32_t *npiv, int32_t *status, cudaStream_t st, std::string &err);
 

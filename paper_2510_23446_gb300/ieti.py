@@ -20,6 +20,7 @@ lib = C.CDLL(LIB_PATH)
 IETI_MEM_HOST, IETI_MEM_DEVICE = 0, 1
 PREC = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
+FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3}
 ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
           -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE"}
 
@@ -37,7 +38,8 @@ class ieti_options(C.Structure):
     _fields_ = [("device", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
+                ("factor", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -62,7 +64,9 @@ class ieti_info(C.Structure):
                 ("sum_np", C.c_int64), ("max_n", C.c_int64), ("bytes_iter", C.c_int64),
                 ("bytes_device", C.c_int64), ("t_setup_host_ms", C.c_double),
                 ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64),
-                ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64)]
+                ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64),
+                ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
+                ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64)]
 
 
 _ctx = C.c_void_p
@@ -84,6 +88,8 @@ lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
 lib.ieti_potrf_batched_noalloc.argtypes = lib.ieti_potrf_batched.argtypes
+lib.ieti_potrf_batched_f32.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int32, C.c_void_p, C.c_void_p]
 lib.ieti_last_error.argtypes = [_ctx]
 lib.ieti_last_error.restype = C.c_char_p
 lib.ieti_destroy.argtypes = [_ctx]
@@ -92,7 +98,7 @@ lib.ieti_destroy.restype = None
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
-            "ieti_potrf_batched", "ieti_potrf_batched_noalloc"]
+            "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32"]
 
 
 class IetiError(RuntimeError):
@@ -116,7 +122,8 @@ class Solver:
 
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
-                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1):
+                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1,
+                 factor="fp64"):
         self._keep = []
 
         def arr(x, dt_):
@@ -149,6 +156,7 @@ class Solver:
         op.cuda_stream = C.c_void_p(stream or 0)
         op.profile = int(profile)
         op.l2_persist = int(l2_persist)
+        op.factor = FACTOR[factor] if isinstance(factor, str) else int(factor)
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
@@ -252,6 +260,26 @@ def potrf_batched(base, offsets, n, n_pivots, stream=0, noalloc=False):
     fn = lib.ieti_potrf_batched_noalloc if noalloc else lib.ieti_potrf_batched
     rc = fn(len(nn), C.c_void_p(p), off.ctypes.data, nn.ctypes.data, kp.ctypes.data, st.ctypes.data,
             C.c_void_p(stream or 0))
+    if rc != 0:
+        raise IetiError(rc, lib.ieti_setup_error().decode())
+    return st
+
+
+def potrf_batched_f32(base, offsets, n, ld, n_pivots, factor="tf32x3", stream=0):
+    """ieti_potrf_batched_f32 on a device buffer `base` (torch CUDA float32 tensor):
+    the FP32 batched partial Cholesky with SIMT ("fp32") or tensor-core ("tf32x3",
+    "tf32") trailing updates.  Returns the per-matrix status array."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nn = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    ldv = np.ascontiguousarray(np.asarray(ld, dtype=np.int32))
+    kp = np.ascontiguousarray(np.asarray(n_pivots, dtype=np.int32))
+    st = np.zeros(len(nn), dtype=np.int32)
+    p, mem = _ptr(base)
+    if mem != IETI_MEM_DEVICE:
+        raise TypeError("base must be a CUDA tensor")
+    f = FACTOR[factor] if isinstance(factor, str) else int(factor)
+    rc = lib.ieti_potrf_batched_f32(len(nn), C.c_void_p(p), off.ctypes.data, nn.ctypes.data, ldv.ctypes.data,
+                                    kp.ctypes.data, f, st.ctypes.data, C.c_void_p(stream or 0))
     if rc != 0:
         raise IetiError(rc, lib.ieti_setup_error().decode())
     return st

@@ -82,6 +82,45 @@ def test_steps_match_oracle(ieti, name, mode):
         assert np.all(b[op.gauge.cls == 0] == 0.0)     # eliminated DOFs are exactly zero
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("factor", ["fp32", "tf32x3"])
+def test_mixed_reduced_factors_match_oracle(ieti, name, factor):
+    """Mixed path with the patch blocks factored in FP32 (SIMT, or tensor-core
+    trailing updates as three TF32 products): the FP64 defect correction brings
+    every step to the mixed tolerance against the oracle."""
+    steps = 3
+    prob, op, ref = oracle_run(name, steps)
+    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", factor=factor, **OPTS["mixed"])
+    for l, (a, b) in enumerate(zip(ref, got)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(a)
+        assert err <= TOL["mixed"], (name, factor, l, err, stats[l])
+        assert np.all(b[op.gauge.cls == 0] == 0.0)
+
+
+def test_tf32_ablation_factor_reaches_tolerance_or_reports(ieti):
+    """One-TF32-product factors (11-bit operands): the refinement either still reaches
+    the mixed tolerance (in more sweeps) or reports non-convergence; it never
+    returns a wrong state as converged."""
+    prob, op, ref = oracle_run("c1", 2)
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", factor="tf32", **OPTS["mixed"])
+    j = S.load_vector(prob.coil)
+    for l in range(2):
+        st = S.step(j, raise_on_error=False)
+        if st["rc"] == -4:
+            break
+        assert st["rc"] == 0
+        a = S.solution()
+        assert np.linalg.norm(a - ref[l]) <= TOL["mixed"] * np.linalg.norm(ref[l]), st
+    S.close()
+
+
+def test_factor_option_validation(ieti):
+    prob = CASES["c1"]()
+    with pytest.raises(ieti.IetiError) as e:
+        ieti.Solver.from_problem(prob, device=0, precision="fp64", factor="tf32x3")
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("precond", ["none", "dirichlet", "dirichlet_mult", "dirichlet_stiff"])
 def test_preconditioners_same_solution(ieti, precond):
     prob, op, ref = oracle_run("uneven_p123", 2)
@@ -158,21 +197,24 @@ def c2_oracle():
     return prob, op
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_tf32x3"])
 def test_c2_full_size_residual(ieti, c2_oracle, mode):
     """Bench configuration (64 curved p=2 patches of 8^3 elements), launched as the
     bench launches it: each GPU step solves the oracle's assembled gauged system
     W_g a = M_g a^l + dt j to a small FP64 residual (a property that holds at any
     size), and the FP64 and mixed paths agree to the mixed tolerance."""
     prob, op = c2_oracle
-    opts = dict(precision=mode, cg_tol=1e-10 if mode == "fp64" else 1e-6, outer_tol=1e-11, max_sweeps=20)
+    opts = dict(precision=mode.split("_")[0], cg_tol=1e-10 if mode == "fp64" else 1e-6, outer_tol=1e-11,
+                max_sweeps=20)
+    if mode == "mixed_tf32x3":
+        opts["factor"] = "tf32x3"
     got, stats = gpu_run(ieti, prob, 2, precond="dirichlet_stiff", **opts)
     prev = np.zeros(op.asm.lat.n_edges)
     for l, a in enumerate(got):
         res = op.mono.residual(a, prev, op.asm.j_global)
         assert res <= 2e-11, (mode, l, res, stats[l])
         prev = a
-    if mode == "mixed":
+    if mode != "fp64":
         ref, _ = gpu_run(ieti, prob, 2, precond="dirichlet_stiff", precision="fp64", cg_tol=1e-12,
                          outer_tol=1e-13, max_sweeps=5)
         for a, b in zip(ref, got):

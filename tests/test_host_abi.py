@@ -25,7 +25,7 @@ def ieti():
 
 def test_exports_every_declared_symbol(ieti):
     hdr = open(os.path.join(ROOT, "include", "ieti.h")).read()
-    declared = set(re.findall(r"\b(ieti_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(ieti_[a-z0-9_]+)\s*\(", hdr))
     lib = ctypes.CDLL(ieti.LIB_PATH)
     for name in declared:
         assert hasattr(lib, name), name
@@ -97,3 +97,30 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     with pytest.raises(ieti.IetiError) as e:
         ieti.Solver.from_problem(prob, device=-1)
     assert e.value.code == code
+
+
+@pytest.mark.parametrize("kw", [
+    dict(precision="fp64", factor="tf32x3"),   # the FP64 mode factors in FP64
+    dict(precision="mixed", factor=7),
+    dict(precision="mixed", pcg_mode=3),
+])
+def test_invalid_options_return_codes(ieti, kw):
+    prob = make_problem("c1")
+    with pytest.raises(ieti.IetiError) as e:
+        ieti.Solver.from_problem(prob, device=-1, **kw)
+    assert e.value.code == -1
+
+
+def test_potrf_f32_rejects_bad_arguments_without_a_device(ieti):
+    """Argument checks of ieti_potrf_batched_f32 run before any device work."""
+    import ctypes as C
+    z = np.zeros(1, dtype=np.int64)
+    n = np.array([30], dtype=np.int32)
+    ld = np.array([30], dtype=np.int32)      # not a multiple of 4: refused for the tensor-core modes
+    st = np.zeros(1, dtype=np.int32)
+    rc = ieti.lib.ieti_potrf_batched_f32(1, C.c_void_p(16), z.ctypes.data, n.ctypes.data, ld.ctypes.data,
+                                         n.ctypes.data, 2, st.ctypes.data, None)
+    assert rc == -1
+    rc = ieti.lib.ieti_potrf_batched_f32(1, C.c_void_p(16), z.ctypes.data, n.ctypes.data, ld.ctypes.data,
+                                         n.ctypes.data, 9, st.ctypes.data, None)
+    assert rc == -1
