@@ -10,14 +10,17 @@
 //      stacked panel buffer (rows ro[s] + r, TC_KP columns, zero padded) as two
 //      planes, hi = rna_tf32(L21) and lo = L21 - hi.
 //   2. k_syrk_tc: one persistent CTA per SM walks a host-built list of
-//      128 x 256 output tiles (patch-major, lower triangle only).  Warp 0 feeds
-//      the 128-byte-swizzled K-major operand tiles by TMA through a shared-memory
-//      ring, warp 1 issues the MMAs (hi*hi + hi*lo + lo*hi for the three-term
-//      split, which carries FP32 accuracy; hi*hi alone for the one-term
-//      ablation) into one of two TMEM accumulators, and warps 2-5 read the
-//      accumulator, subtract it from A22 in global memory (lower triangle, the
-//      patch's active rows, the AugLimits restrictions) while the next tile is
-//      multiplied.
+//      128 x 128 output tiles (patch-major, lower triangle only).  Warp 0 feeds
+//      the 128-byte-swizzled K-major operand tiles (one 32-wide K chunk per
+//      stage) by TMA through a shared-memory ring; warp 1 issues, per chunk,
+//      the MMAs hi*hi into one TMEM accumulator and (three-term split, FP32
+//      accuracy) hi*lo + lo*hi into a second, alternating between two chunk
+//      buffers; warps 2-9 add every chunk's accumulators to FP32 register sums
+//      (one row and half the tile's columns per thread) and finally subtract the sums from A22 in global
+//      memory (lower triangle, the patch's active rows, the AugLimits
+//      restrictions).  The tensor cores truncate when they accumulate; a fresh
+//      accumulator per chunk and round-to-nearest sums across chunks keep that
+//      error at the level of the SIMT FP32 update instead of growing with K.
 //
 // Every wait is bounded; a timeout sets *err_flag, stops the work loops, drains
 // the copies and MMAs in flight and frees the tensor memory before returning.
@@ -39,8 +42,9 @@ struct AugLimits {
 
 constexpr int TC_KP = 256;  // outer panel width = K of one trailing update
 constexpr int TC_BM = 128;  // tile rows (MMA M)
-constexpr int TC_BN = 256;  // tile columns (MMA N)
-constexpr int TC_THREADS = 192;
+constexpr int TC_BN = 128;  // tile columns (MMA N)
+constexpr int TC_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
+constexpr int TC_EPI_COLS = TC_BN / 2;  // columns per epilogue thread
 
 struct TcItem {
   int32_t s, R0, C0, t0, nk, pad;  // patch, tile origin, first trailing column, 32-wide K chunks
@@ -91,12 +95,15 @@ __global__ void k_panel_split(const float *base, const int64_t *off, const int32
 template <int X3>
 struct TcCfg {
   static constexpr int NPLANE = X3 ? 2 : 1;
-  static constexpr int NS = X3 ? 2 : 4;  // ring stages
+  static constexpr int NS = X3 ? 3 : 6;  // ring stages (one 32-wide K chunk each)
   static constexpr uint32_t A_BYTES = TC_BM * 128;  // one plane, 32 FP32 of K per row
   static constexpr uint32_t B_BYTES = TC_BN * 128;
   static constexpr uint32_t STAGE = NPLANE * (A_BYTES + B_BYTES);
   static constexpr uint32_t SMEM = NS * STAGE + 1024 /* alignment */ + 256 /* barriers */;
 };
+
+// TMEM: two chunk buffers of 2 * TC_BN columns: [hi*hi | hi*lo + lo*hi]
+constexpr uint32_t TC_TMEM_COLS = 4 * TC_BN;
 
 template <int X3>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -109,9 +116,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(sm + C::NS * C::STAGE);
   uint64_t *empty = full + C::NS;
-  uint64_t *tfull = empty + C::NS;  // [2] accumulator ready
-  uint64_t *tempty = tfull + 2;     // [2] accumulator drained by the epilogue
-  uint64_t *drain = tempty + 2;
+  uint64_t *cfull = empty + C::NS;  // [2] chunk accumulators ready
+  uint64_t *cempty = cfull + 2;     // [2] chunk accumulators drained by the epilogue
+  uint64_t *drain = cempty + 2;
   uint32_t *tbase = (uint32_t *)(drain + 1);
   volatile int *abort_ = (volatile int *)(tbase + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,15 +129,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(empty + i, 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(tfull + i, 1);
-      mbar_init(tempty + i, 4);
+      mbar_init(cfull + i, 1);
+      mbar_init(cempty + i, 8);
     }
     mbar_init(drain, 1);
     *abort_ = 0;
     mbar_fence_init();
   }
   if (warp == 1) {
-    tmem_alloc(tbase, 512);
+    tmem_alloc(tbase, TC_TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -161,11 +168,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_arrive_expect_tx(full + st, C::STAGE);
 #pragma unroll
           for (int pl = 0; pl < C::NPLANE; ++pl) {
-            unsigned char *a = sb + pl * C::A_BYTES;
-            unsigned char *b = sb + C::NPLANE * C::A_BYTES + pl * C::B_BYTES;
-            tma_load_3d(a, &tmap, kc * 32, ya, pl, full + st);
-            tma_load_3d(b, &tmap, kc * 32, yb, pl, full + st);
-            tma_load_3d(b + C::A_BYTES, &tmap, kc * 32, yb + TC_BM, pl, full + st);
+            tma_load_3d(sb + pl * C::A_BYTES, &tmap, kc * 32, ya, pl, full + st);
+            tma_load_3d(sb + C::NPLANE * C::A_BYTES + pl * C::B_BYTES, &tmap, kc * 32, yb, pl, full + st);
           }
         }
       }
@@ -176,19 +180,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      int it = 0, tile = 0;
-      for (int w = blockIdx.x; w < n_items && !*abort_; w += gridDim.x, ++tile) {
+      int it = 0;  // chunk counter (ring stage and chunk buffer)
+      for (int w = blockIdx.x; w < n_items && !*abort_; w += gridDim.x) {
         const TcItem t = items[w];
-        const int ab = tile & 1;
-        const unsigned tph = (unsigned)(tile >> 1) & 1u;
-        if (!mbar_wait(tempty + ab, tph ^ 1u)) {
-          give_up(3);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)(ab * TC_BN);
         bool ok = true;
         for (int kc = 0; kc < t.nk; ++kc, ++it) {
+          const int cb = it & 1;
+          const unsigned cph = (unsigned)(it >> 1) & 1u;
+          if (!mbar_wait(cempty + cb, cph ^ 1u)) {
+            give_up(3);
+            ok = false;
+            break;
+          }
           const int st = it % C::NS;
           const unsigned ph = (unsigned)(it / C::NS) & 1u;
           if (!mbar_wait(full + st, ph)) {
@@ -197,73 +200,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           tc_fence_after();
+          const uint32_t dh = tmem + (uint32_t)(cb * 2 * TC_BN), dc = dh + TC_BN;
           const uint32_t sa = smem_u32(sm + st * C::STAGE);
           const uint32_t sb = sa + C::NPLANE * C::A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {  // 4 x K=8 inside the 128-byte row
             const uint64_t ah = tc_desc_sw128(sa + kk * 32), bh = tc_desc_sw128(sb + kk * 32);
-            tc_mma<0>(dt, ah, bh, IDESC, (kc | kk) != 0);
+            tc_mma<0>(dh, ah, bh, IDESC, kk != 0);
             if constexpr (X3) {
               const uint64_t al = tc_desc_sw128(sa + C::A_BYTES + kk * 32);
               const uint64_t bl = tc_desc_sw128(sb + C::B_BYTES + kk * 32);
-              tc_mma<0>(dt, ah, bl, IDESC, 1u);
-              tc_mma<0>(dt, al, bh, IDESC, 1u);
+              tc_mma<0>(dc, ah, bl, IDESC, kk != 0);
+              tc_mma<0>(dc, al, bh, IDESC, 1u);
             }
           }
           tc_commit(empty + st);  // the stage is free once these MMAs have read it
+          tc_commit(cfull + cb);  // the chunk accumulators are complete
         }
         if (!ok) break;
-        tc_commit(tfull + ab);
       }
       tc_commit(drain);
       if (!mbar_wait(drain, 0)) give_up(5);
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (warps 2-5)
-    const int q = warp & 3;  // TMEM lane quarter of this warp
-    int tile = 0;
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x, ++tile) {
+    // ---------------------------------------------------------------- epilogue (warps 2-9)
+    // Every 32-wide K chunk is accumulated afresh in TMEM and added here to FP32
+    // register sums with round-to-nearest: the tensor-core accumulation then spans
+    // 4 MMAs of one chunk instead of a whole panel.
+    const int q = warp & 3;                    // TMEM lane quarter of this warp
+    const int c_off = ((warp - 2) >> 2) * TC_EPI_COLS;  // its half of the tile's columns
+    const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)c_off;
+    int it = 0;
+    bool dead = false;
+    for (int w = blockIdx.x; w < n_items && !dead; w += gridDim.x) {
       const TcItem t = items[w];
-      const int ab = tile & 1;
-      const unsigned tph = (unsigned)(tile >> 1) & 1u;
-      const bool ok = mbar_wait(tfull + ab, tph);
-      if (__any_sync(0xffffffffu, !ok || *abort_)) {
-        if (lane == 0) give_up(6);
-        break;
-      }
-      tc_fence_after();
-      const int s = t.s;
-      const int na = nact[s], sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
-      const int64_t ld = ldv[s];
-      const int rw0 = t.R0 + q * 32;  // first row of this warp
-      const int r = rw0 + lane;
-      const bool row_ok = r < na && !(r >= sk_lo && r < sk_hi);
-      const int cmax = min(r, (r >= rlim) ? clim - 1 : INT_MAX);  // last column this row updates
-      float *Arow = base + off[s] + (int64_t)r * ld;
-#pragma unroll 1
-      for (int c32 = 0; c32 < TC_BN / 32; ++c32) {
-        const int cb = t.C0 + c32 * 32;
-        if (cb > rw0 + 31 || cb >= na) break;  // warp-uniform: beyond every row of this warp
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * TC_BN + c32 * 32), v);
-        if (row_ok) {
+      float acc[TC_EPI_COLS];
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            const int c = cb + 4 * g;
-            if (c + 3 < t.t0 || c > cmax) continue;  // no updated column in this group
-            float4 *p = reinterpret_cast<float4 *>(Arow + c);
-            float4 x = *p;
-            if (c + 0 >= t.t0 && c + 0 <= cmax) x.x -= v[4 * g + 0];
-            if (c + 1 >= t.t0 && c + 1 <= cmax) x.y -= v[4 * g + 1];
-            if (c + 2 >= t.t0 && c + 2 <= cmax) x.z -= v[4 * g + 2];
-            if (c + 3 >= t.t0 && c + 3 <= cmax) x.w -= v[4 * g + 3];
-            *p = x;
+      for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0.f;
+      for (int kc = 0; kc < t.nk; ++kc, ++it) {
+        const int cb = it & 1;
+        const unsigned cph = (unsigned)(it >> 1) & 1u;
+        const bool ok = mbar_wait(cfull + cb, cph);
+        if (__any_sync(0xffffffffu, !ok || *abort_)) {
+          if (lane == 0) give_up(6);
+          dead = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dh = tmem + lane_off + (uint32_t)(cb * 2 * TC_BN);
+#pragma unroll
+        for (int g = 0; g < TC_EPI_COLS / 16; ++g) {
+          float h[16];
+          tmem_ld16(dh + g * 16, h);
+          if constexpr (X3) {
+            float c[16];
+            tmem_ld16(dh + TC_BN + g * 16, c);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[g * 16 + i] += h[i] + c[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[g * 16 + i] += h[i];
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(cempty + cb);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty + ab);
+      if (dead) break;
+      const int s = t.s;
+      const int na = nact[s], sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
+      const int r = t.R0 + q * 32 + lane;
+      if (r < na && !(r >= sk_lo && r < sk_hi)) {
+        const int cmax = min(r, (r >= rlim) ? clim - 1 : INT_MAX);  // last column this row updates
+        float *Arow = base + off[s] + (int64_t)r * ldv[s];
+#pragma unroll
+        for (int g = 0; g < TC_EPI_COLS / 4; ++g) {
+          const int c = t.C0 + c_off + 4 * g;
+          if (c + 3 < t.t0 || c > cmax) continue;  // no updated column in this group
+          float4 *p = reinterpret_cast<float4 *>(Arow + c);
+          float4 x = *p;
+          if (c + 0 >= t.t0 && c + 0 <= cmax) x.x -= acc[4 * g + 0];
+          if (c + 1 >= t.t0 && c + 1 <= cmax) x.y -= acc[4 * g + 1];
+          if (c + 2 >= t.t0 && c + 2 <= cmax) x.z -= acc[4 * g + 2];
+          if (c + 3 >= t.t0 && c + 3 <= cmax) x.w -= acc[4 * g + 3];
+          *p = x;
+        }
+      }
     }
   }
   __syncwarp();
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, TC_TMEM_COLS);
   }
 }
 

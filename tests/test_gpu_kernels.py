@@ -98,7 +98,7 @@ def _batch_f32(rng, sizes, pad=4):
 def _f32_errors(mats, offs, lds, sizes, piv, out, inp):
     errs = []
     for A, o, ld, n, kk in zip(mats, offs, lds, sizes, piv):
-        R = out[o:o + n * ld].reshape(n, ld).astype(np.float64)
+        R = out[o:o + n * ld].reshape(n, ld)[:, :n].astype(np.float64)
         R0 = inp[o:o + n * ld].reshape(n, ld)
         # the strict upper triangle and the padding columns are left bit-identical
         iu = np.triu_indices(n, 1)
@@ -130,6 +130,7 @@ def test_partial_cholesky_f32_modes(ieti, sizes, frac):
         st = ieti.potrf_batched_f32(base, offs, sizes, lds, piv, factor=mode)
         assert np.all(st == 0), (mode, st)
         err[mode] = _f32_errors(mats, offs, lds, sizes, piv, base.cpu().numpy(), flat)
+    print({k: v.max() for k, v in err.items()})
     # FP32 arithmetic (SIMT or three TF32 products) vs the exact factor of the FP32 input
     assert err["fp32"].max() <= 2e-5, err
     assert err["tf32x3"].max() <= 2e-5, err
