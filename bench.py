@@ -30,7 +30,8 @@ WORKLOAD = ("c2: unit cube, 4x4x4 curved patches (+-5% interior control points),
             "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3")
 OUTER_TOL = 1e-11
 OPTS = {
-    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20),
+    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20,
+                  factor="tf32x3"),
     "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, outer_tol=OUTER_TOL, max_sweeps=20),
 }
 
@@ -38,7 +39,7 @@ OPTS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -53,7 +54,23 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# nominal dense rates relative to bf16 (2.25 PFLOP/s): tf32 1.1 PFLOP/s, fp64 1.25 TFLOP/s
+NOMINAL_RATIO = {"tf32": 1.1 / 2.25, "fp64": 1.25e-3 / 2.25}
+
+
+def ncu_traffic(kernel_file):
+    """DRAM bytes per launch (read + write) recorded in a committed ncu summary."""
+    try:
+        with open(os.path.join(ROOT, "profiles", kernel_file)) as f:
+            for line in f:
+                if line.startswith("| DRAM traffic per launch"):
+                    return float(line.split("|")[2].split()[0]) * 1e9
+    except OSError:
+        pass
+    return None
 
 
 class Clocks:
@@ -231,6 +248,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot["mixed"], tot["fp64"], e2e_s = t.tolist()
     rm, rf = results["mixed"][1], results["fp64"][1]
+    im, iff = results["mixed"][0].info(), results["fp64"][0].info()
     # the two paths ran the same number of steps from a^0 = 0: compare states
     err = float(np.linalg.norm(rm["state"] - rf["state"]) / np.linalg.norm(rf["state"]))
     # roofline of the dominant kernel class (largest share of event time in the mixed run)
@@ -241,7 +259,29 @@ def run_ours(args):
     bytes_per = ks[dom]["bytes"] / max(ks[dom]["launches"], 1)
     achieved = bytes_per / (avg_ms * 1e-3) / 1e9
     step_ms = tot["mixed"] * 1e3 / K
-    info = results["mixed"][0].info()
+    info = im
+    # factorization (setup): the tensor-core trailing update of the mixed path against
+    # the TF32 peak, the FP64 factorization against the FP64 peak (both derived from the
+    # measured bf16 GEMM rate by the nominal ratios)
+    tf32_peak = pk["bf16_tflops"] * NOMINAL_RATIO["tf32"]
+    fp64_peak = pk["bf16_tflops"] * NOMINAL_RATIO["fp64"]
+    tc_tfs = im["tc_flops"] / max(im["tc_ms"], 1e-9) / 1e9
+    factor = {
+        "mixed": {"factor": OPTS["mixed"]["factor"], "t_factor_ms": im["t_factor_ms"],
+                  "useful_tflop": im["factor_flops"] / 1e12,
+                  "useful_tflops_per_s": im["factor_flops"] / max(im["t_factor_ms"], 1e-9) / 1e9,
+                  "tc_kernel": "k_syrk_tc", "tc_ms": im["tc_ms"], "tc_launches": im["tc_launches"],
+                  "tc_issued_tflops_per_s": tc_tfs,
+                  "tc_useful_tflops_per_s": im["tc_useful_flops"] / max(im["tc_ms"], 1e-9) / 1e9,
+                  "roofline": {"bound": "tensor", "achieved": tc_tfs, "peak": tf32_peak, "unit": "TFLOP/s",
+                               "frac": tc_tfs / tf32_peak,
+                               "peak_source": f"{pk_src} bf16_tflops x nominal tf32/bf16 ratio 1.1/2.25"}},
+        "fp64": {"factor": "fp64", "t_factor_ms": iff["t_factor_ms"], "useful_tflop": iff["factor_flops"] / 1e12,
+                 "useful_tflops_per_s": iff["factor_flops"] / max(iff["t_factor_ms"], 1e-9) / 1e9,
+                 "roofline": {"bound": "fp64", "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": iff["factor_flops"] / max(iff["t_factor_ms"], 1e-9) / 1e9 / fp64_peak,
+                              "peak_source": f"{pk_src} bf16_tflops x nominal fp64/bf16 ratio 1.25e-3/2.25"}},
+    }
     line = {
         "metric": METRIC,
         "value": world * K / tot["mixed"],
@@ -258,6 +298,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n_dofs": info["n_dofs"], "n_free": info["n_free"],
                    "n_lambda": info["n_lambda"], "n_coarse": info["n_coarse"],
                    "precond": "dirichlet_stiff", "inner_cg_tol": OPTS["mixed"]["cg_tol"],
+                   "mixed_factor": OPTS["mixed"]["factor"],
                    "outer_tol": OUTER_TOL, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "cg_its_per_s": world * rm["its"] / tot["mixed"],
@@ -274,10 +315,12 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * S.n},
         "gpu_launches": rm["launches"],
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic("k_ddsolve_c2_mixed.md"),
+                     "traffic_source": "profiles/k_ddsolve_c2_mixed.md (one ncu launch of ~19 PCG iterations)",
                      "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms,
                      "share_of_step": ks[dom]["total_ms"] / (tot["mixed"] * 1e3),
                      "peak_source": f"{pk_src} hbm_gbs (copy)"},
+        "factorization": factor,
         "kernel_classes_ms_per_step": {k: v["total_ms"] / K for k, v in ks.items() if v["launches"]},
         "pcg_phase_us": {"phases": ["P1 B^T p, [F;Psi^T]", "P2 coarse rhs", "P3 S_c^-1", "P4 Psi q",
                                     "P5 update+precond", "P6 jump+dot"],

@@ -140,6 +140,7 @@ typedef struct {
   double tc_flops;           /* tensor-core flops those updates issued (3 products per update for TF32X3) */
   double tc_useful_flops;    /* the multiply-adds of the updated entries, x 2 */
   int64_t tc_launches;       /* tensor-core update launches */
+  double factor_flops;       /* useful flops of the patch-block partial Cholesky (both phases) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -698,6 +698,7 @@ struct DeviceState {
   double t_factor_ms = 0;                 // both partial-Cholesky phases of the patch blocks
   double tc_ms = 0, tc_flops = 0, tc_useful_flops = 0;  // tensor-core trailing updates
   int64_t tc_launches = 0;
+  double factor_flops = 0;                // useful flops of both phases (all factor modes)
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -896,6 +897,31 @@ static void tc_plan(const TcHost &th, const std::vector<int32_t> &hkb, const std
     }
     pofs.push_back((int64_t)items.size());
   }
+}
+
+// Useful flops of a partial Cholesky phase: for every pivot k, the scaled column and the
+// rank-1 update of the active rows below it (rows in the skip range hold zeros there,
+// rows >= rlim stop at column clim).
+static double partial_chol_flops(const TcHost &th, const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
+                                 const std::vector<int32_t> &hna) {
+  double f = 0;
+  for (size_t s = 0; s < hkb.size(); ++s) {
+    const int sklo = th.sk_lo[s], skhi = th.sk_hi[s], rlim = th.rlim[s], clim = th.clim[s];
+    for (int k = hkb[s]; k < hke[s]; ++k) {
+      // active rows r in (k, na) outside [sklo, skhi)
+      const int lo = k + 1, hi = hna[s];
+      if (lo >= hi) continue;
+      int m = hi - lo - std::max(0, std::min(hi, skhi) - std::max(lo, sklo));
+      double upd = 0.5 * (double)m * (m + 1);  // lower-triangle entries (r, c), k < c <= r
+      if (rlim < hi && clim <= hi) {            // rows >= rlim only reach columns < clim
+        int mr = hi - std::max(lo, rlim);
+        int mc = std::max(0, hi - std::max(lo, clim));
+        upd -= 0.5 * (double)std::min(mr, mc) * (std::min(mr, mc) + 1);
+      }
+      f += (double)m + 2.0 * upd;
+    }
+  }
+  return f;
 }
 
 template <int X3>
@@ -1764,6 +1790,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   // one partial-Cholesky phase over all patches in the chosen factor precision
   auto factor_phase = [&](const std::vector<int32_t> &kb, const std::vector<int32_t> &ke,
                           const std::vector<int32_t> &na, AugLimits lm) -> int {
+    d->factor_flops += partial_chol_flops(th, kb, ke, na);
     switch (d->factor) {
       case IETI_FACTOR_FP64:
         return potrf_partial<double>(d, D, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
@@ -2156,6 +2183,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->tc_flops = d->tc_flops;
   info->tc_useful_flops = d->tc_useful_flops;
   info->tc_launches = d->tc_launches;
+  info->factor_flops = d->factor_flops;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

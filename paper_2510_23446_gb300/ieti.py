@@ -66,7 +66,7 @@ class ieti_info(C.Structure):
                 ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64),
                 ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64),
                 ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
-                ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64)]
+                ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double)]
 
 
 _ctx = C.c_void_p
