@@ -29,6 +29,7 @@ METRIC = "time steps/s and CG its/s, mixed+batched vs FP64 on GB300 at rel. L2 e
 WORKLOAD = ("c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
             "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3")
 OUTER_TOL = 1e-11
+HORIZON = 50   # the workload's run: 50 implicit-Euler steps from a^0 = 0, replayed for K > 50
 OPTS = {
     "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20,
                   factor="tf32x3"),
@@ -169,8 +170,10 @@ def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
     t_setup = S.info()
     j = S.load_vector(prob.coil)
     jd = torch.from_numpy(j).to(f"cuda:{dev}")
+    zero = torch.zeros(S.n, dtype=torch.float64, device=f"cuda:{dev}")
     for _ in range(W):
         S.step(jd)
+    S.set_state(zero)
     S.kernel_stats(reset=True)
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -178,6 +181,8 @@ def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
     if clocks:
         clocks.start()
     for k in range(K):
+        if k and k % HORIZON == 0:
+            S.set_state(zero)                  # replay the 50-step run (outside the timed events)
         flush_buf.zero_()                      # evict L2 between timed steps (256 MiB write)
         ev[k][0].record()
         st = S.step(jd)
@@ -231,16 +236,23 @@ def run_ours(args):
         clocks = Clocks(dev) if mode == "mixed" else None
         S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks)
         results[mode] = (S, r)
-    # end-to-end through the public API with host buffers (pinned), mixed path
+    # end-to-end through the public API with host buffers (pinned), mixed path: the same
+    # steps as the timed device run (same resets, same L2 flush between steps, both
+    # outside the timed segments); every step copies j in and the state out
     S, r = results["mixed"]
     jh = torch.from_numpy(r["j"]).pin_memory()
     ah = torch.empty(S.n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(K):
+    zero = torch.zeros(S.n, dtype=torch.float64, device=f"cuda:{dev}")
+    e2e_s = 0.0
+    for k in range(K):
+        if k % HORIZON == 0:
+            S.set_state(zero)
+        flush_buf.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         S.step(jh)
         S.solution(ah)
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
     # timing over ranks: max
     tot = {m: sum(results[m][1]["ms"]) / 1e3 for m in results}
     if world > 1:
@@ -300,6 +312,7 @@ def run_ours(args):
                    "precond": "dirichlet_stiff", "inner_cg_tol": OPTS["mixed"]["cg_tol"],
                    "mixed_factor": OPTS["mixed"]["factor"],
                    "outer_tol": OUTER_TOL, "l2": "flushed between timed steps (256 MiB write)",
+                   "steps": f"the 50-step run from a^0 = 0 (dt = 1e-3), replayed; state reset untimed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "cg_its_per_s": world * rm["its"] / tot["mixed"],
         "cg_its_per_step": rm["its"] / K,

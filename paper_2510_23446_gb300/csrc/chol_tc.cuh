@@ -15,8 +15,8 @@
 //      stage) by TMA through a shared-memory ring; warp 1 issues, per chunk,
 //      the MMAs hi*hi into one TMEM accumulator and (three-term split, FP32
 //      accuracy) hi*lo + lo*hi into a second, alternating between two chunk
-//      buffers; warps 2-9 add every chunk's accumulators to FP32 register sums
-//      (one row and half the tile's columns per thread) and finally subtract the sums from A22 in global
+//      buffers; 16 epilogue warps add every chunk's accumulators to FP32 register
+//      sums (one row and 32 of the tile's columns per thread) and finally subtract the sums from A22 in global
 //      memory (lower triangle, the patch's active rows, the AugLimits
 //      restrictions).  The tensor cores truncate when they accumulate; a fresh
 //      accumulator per chunk and round-to-nearest sums across chunks keep that
@@ -43,8 +43,9 @@ struct AugLimits {
 constexpr int TC_KP = 256;  // outer panel width = K of one trailing update
 constexpr int TC_BM = 128;  // tile rows (MMA M)
 constexpr int TC_BN = 128;  // tile columns (MMA N)
-constexpr int TC_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
-constexpr int TC_EPI_COLS = TC_BN / 2;  // columns per epilogue thread
+constexpr int TC_EPI_WARPS = 16;                          // 4 per TMEM lane quarter
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);        // producer, MMA issuer, epilogue
+constexpr int TC_EPI_COLS = TC_BN / (TC_EPI_WARPS / 4);    // columns per epilogue thread
 
 struct TcItem {
   int32_t s, R0, C0, t0, nk, pad;  // patch, tile origin, first trailing column, 32-wide K chunks
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(cfull + i, 1);
-      mbar_init(cempty + i, 8);
+      mbar_init(cempty + i, TC_EPI_WARPS);
     }
     mbar_init(drain, 1);
     *abort_ = 0;
@@ -223,17 +224,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!mbar_wait(drain, 0)) give_up(5);
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (warps 2-9)
+    // ---------------------------------------------------------------- epilogue (warps 2-17)
     // Every 32-wide K chunk is accumulated afresh in TMEM and added here to FP32
     // register sums with round-to-nearest: the tensor-core accumulation then spans
-    // 4 MMAs of one chunk instead of a whole panel.
-    const int q = warp & 3;                    // TMEM lane quarter of this warp
-    const int c_off = ((warp - 2) >> 2) * TC_EPI_COLS;  // its half of the tile's columns
+    // 4 MMAs of one chunk instead of a whole panel.  Each thread owns one row and
+    // TC_EPI_COLS columns of the tile; its part of A22 is loaded when the tile
+    // starts, so the read is in flight while the tile's chunks are multiplied.
+    const int q = warp & 3;                                      // TMEM lane quarter of this warp
+    const int c_off = ((warp - 2) >> 2) * TC_EPI_COLS;           // its columns of the tile
     const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)c_off;
     int it = 0;
     bool dead = false;
     for (int w = blockIdx.x; w < n_items && !dead; w += gridDim.x) {
       const TcItem t = items[w];
+      const int s = t.s;
+      const int na = nact[s], sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
+      const int r = t.R0 + q * 32 + lane;
+      const bool row_ok = r < na && !(r >= sk_lo && r < sk_hi);
+      const int cmax = row_ok ? min(r, (r >= rlim) ? clim - 1 : INT_MAX) : -1;  // last column this row updates
+      const int cb0 = t.C0 + c_off;
+      float4 *Arow = reinterpret_cast<float4 *>(base + off[s] + (int64_t)(row_ok ? r : 0) * ldv[s] + cb0);
+      float4 x[TC_EPI_COLS / 4];
+#pragma unroll
+      for (int g = 0; g < TC_EPI_COLS / 4; ++g) {
+        const int c = cb0 + 4 * g;
+        if (!(c + 3 < t.t0 || c > cmax)) x[g] = Arow[g];  // groups holding an updated column
+      }
       float acc[TC_EPI_COLS];
 #pragma unroll
       for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0.f;
@@ -249,17 +265,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         const uint32_t dh = tmem + lane_off + (uint32_t)(cb * 2 * TC_BN);
 #pragma unroll
-        for (int g = 0; g < TC_EPI_COLS / 16; ++g) {
-          float h[16];
-          tmem_ld16(dh + g * 16, h);
+        for (int g = 0; g < TC_EPI_COLS / 8; ++g) {
+          float h[8];
+          tmem_ld8(dh + g * 8, h);
           if constexpr (X3) {
-            float c[16];
-            tmem_ld16(dh + TC_BN + g * 16, c);
+            float c[8];
+            tmem_ld8(dh + TC_BN + g * 8, c);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[g * 16 + i] += h[i] + c[i];
+            for (int i = 0; i < 8; ++i) acc[g * 8 + i] += h[i] + c[i];
           } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[g * 16 + i] += h[i];
+            for (int i = 0; i < 8; ++i) acc[g * 8 + i] += h[i];
           }
         }
         tc_fence_before();
@@ -267,24 +283,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_arrive(cempty + cb);
       }
       if (dead) break;
-      const int s = t.s;
-      const int na = nact[s], sk_lo = lim.sk_lo[s], sk_hi = lim.sk_hi[s], rlim = lim.rlim[s], clim = lim.clim[s];
-      const int r = t.R0 + q * 32 + lane;
-      if (r < na && !(r >= sk_lo && r < sk_hi)) {
-        const int cmax = min(r, (r >= rlim) ? clim - 1 : INT_MAX);  // last column this row updates
-        float *Arow = base + off[s] + (int64_t)r * ldv[s];
 #pragma unroll
-        for (int g = 0; g < TC_EPI_COLS / 4; ++g) {
-          const int c = t.C0 + c_off + 4 * g;
-          if (c + 3 < t.t0 || c > cmax) continue;  // no updated column in this group
-          float4 *p = reinterpret_cast<float4 *>(Arow + c);
-          float4 x = *p;
-          if (c + 0 >= t.t0 && c + 0 <= cmax) x.x -= acc[4 * g + 0];
-          if (c + 1 >= t.t0 && c + 1 <= cmax) x.y -= acc[4 * g + 1];
-          if (c + 2 >= t.t0 && c + 2 <= cmax) x.z -= acc[4 * g + 2];
-          if (c + 3 >= t.t0 && c + 3 <= cmax) x.w -= acc[4 * g + 3];
-          *p = x;
-        }
+      for (int g = 0; g < TC_EPI_COLS / 4; ++g) {
+        const int c = cb0 + 4 * g;
+        if (c + 3 < t.t0 || c > cmax) continue;  // no updated column in this group
+        float4 v = x[g];
+        if (c + 0 >= t.t0 && c + 0 <= cmax) v.x -= acc[4 * g + 0];
+        if (c + 1 >= t.t0 && c + 1 <= cmax) v.y -= acc[4 * g + 1];
+        if (c + 2 >= t.t0 && c + 2 <= cmax) v.z -= acc[4 * g + 2];
+        if (c + 3 >= t.t0 && c + 3 <= cmax) v.w -= acc[4 * g + 3];
+        Arow[g] = v;
       }
     }
   }
