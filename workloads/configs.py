@@ -23,6 +23,9 @@ Data layout (mirrored by the C ABI in ``include/ieti.h``):
   with ``T_z = J0*(r_out - r)`` on ``r_in < r < r_out``, ``J0*(r_out - r_in)`` for
   ``r <= r_in`` and 0 beyond, ``r`` the distance to the axis ``x = xc, y = yc``.
   ``curl T`` is an azimuthal current of amplitude ``J0`` in the shell.
+* ``reluctivity``: ``None`` (linear: ``nu_el`` everywhere) or the parameters
+  ``nu0, k1, k2, k3`` of ``nu(|B|) = nu0 (k1 exp(k2 |B|^2) + k3)``, which then
+  replaces ``nu_el`` in the conducting elements (``sigma_el > 0``).
 """
 from __future__ import annotations
 
@@ -45,6 +48,7 @@ class Problem:
     cg_tol: float = 1e-10
     coil: dict = field(default_factory=dict)
     seed: int = 0
+    reluctivity: dict | None = None
 
     # ---- plain bookkeeping (sizes and offsets; no spline arithmetic) ----
     @property
@@ -121,7 +125,7 @@ def default_coil(J0: float = 1.0) -> dict:
 
 
 def build_problem(name, P, n_el, degree, *, sigma_fn, nu_fn, dt, n_steps, cg_tol=1e-10,
-                  perturb=0.0, coil=None, seed=0) -> Problem:
+                  perturb=0.0, coil=None, seed=0, reluctivity=None) -> Problem:
     """Lay out a problem.
 
     ``sigma_fn(s, centers)`` / ``nu_fn(s, centers)`` give per-element values from the
@@ -167,7 +171,8 @@ def build_problem(name, P, n_el, degree, *, sigma_fn, nu_fn, dt, n_steps, cg_tol
     return Problem(name=name, P=P, n_el=n_el, degree=degree, knots=knots,
                    ctrl=np.concatenate(ctrl), sigma_el=np.concatenate(sig),
                    nu_el=np.concatenate(nu), dt=float(dt), n_steps=int(n_steps),
-                   cg_tol=float(cg_tol), coil=coil or default_coil(), seed=seed)
+                   cg_tol=float(cg_tol), coil=coil or default_coil(), seed=seed,
+                   reluctivity=reluctivity)
 
 
 def _inside_box(centers, lo, hi):
@@ -232,8 +237,17 @@ def config4(seed=0, n_steps=100) -> Problem:
         coil=default_coil(1.0), seed=seed)
 
 
-def config5(patches_per_dir=4, seed=0, n_steps=200) -> Problem:
-    """k^3 p=3 patches of 8^3 elements, config-2 material layout (linear part)."""
+# nonlinear law of the scalability sweep: nu(|B|) = nu0 (k1 exp(k2 |B|^2) + k3)
+C5_RELUCTIVITY = dict(nu0=1.0, k1=0.5, k2=2.0, k3=0.5)
+# Coil amplitude of the nonlinear sweep.  With the config-2 amplitude (1e2) the field
+# in the conductor approaches |B| ~ 15, where exp(2 |B|^2) overflows; an amplitude of
+# 5 keeps |B| = O(1), the range in which the law above is a reluctivity curve.
+C5_J0 = 5.0
+
+
+def config5(patches_per_dir=4, seed=0, n_steps=200, nonlinear=True) -> Problem:
+    """k^3 p=3 patches of 8^3 elements, config-2 material layout, nonlinear
+    reluctivity in the conductor."""
     k = int(patches_per_dir)
     P = (k, k, k)
 
@@ -243,13 +257,13 @@ def config5(patches_per_dir=4, seed=0, n_steps=200) -> Problem:
     return build_problem(
         f"c5_{k}^3x8^3_p3", P, [[8] * k] * 3, [[3] * k] * 3, sigma_fn=sig,
         nu_fn=lambda s, C: 1.0, dt=5e-4, n_steps=n_steps, perturb=0.05,
-        coil=default_coil(1e2), seed=seed)
+        coil=default_coil(C5_J0), seed=seed, reluctivity=dict(C5_RELUCTIVITY) if nonlinear else None)
 
 
 def small_problem(P=(2, 2, 1), n_el=((2, 3), (3, 2), (2,)), degree=((1, 2), (2, 1), (2,)),
                   conductor=((0.0, 0.5), (0.0, 1.0), (0.0, 1.0)), sigma=1.0, nu=1.0,
                   dt=0.05, n_steps=3, perturb=0.05, J0=1.0, seed=0, elementwise=False,
-                  name="small") -> Problem:
+                  name="small", reluctivity=None) -> Problem:
     """Tiny uneven problems for brute-force pins and ragged-tile parity cases.
 
     ``conductor`` is an axis-aligned box; patches whose centre lies inside conduct
@@ -265,7 +279,7 @@ def small_problem(P=(2, 2, 1), n_el=((2, 3), (3, 2), (2,)), degree=((1, 2), (2, 
         return sigma if inside else 0.0
     return build_problem(name, P, [list(x) for x in n_el], [list(x) for x in degree],
                          sigma_fn=sig, nu_fn=lambda s, C: nu, dt=dt, n_steps=n_steps,
-                         perturb=perturb, coil=default_coil(J0), seed=seed)
+                         perturb=perturb, coil=default_coil(J0), seed=seed, reluctivity=reluctivity)
 
 
 CONFIGS = {
