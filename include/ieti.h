@@ -86,6 +86,11 @@ typedef struct {
   const double *nu_el;          /* per element, same layout; > 0 */
   double dt;                    /* implicit-Euler step (Eq. (11)), > 0 */
   int32_t primal_mode;          /* 0: tree DOFs on Gamma + cotree wirebasket edges of Omega_I (Sec. 3) */
+  const double *reluctivity;    /* NULL: linear (nu_el everywhere).  Else 4 values nu0, k1, k2, k3 of the law
+                                   nu(|B|) = nu0 (k1 exp(k2 |B|^2) + k3), which replaces nu_el in the
+                                   conducting elements (sigma_el > 0); nu0 > 0, k1, k2, k3 >= 0, k1 + k3 > 0.
+                                   The nonlinear material the paper names as an extension (Sec. 2): every
+                                   ieti_step then runs Newton's method (see ieti_options.refactor). */
 } ieti_problem;
 
 typedef struct {
@@ -103,7 +108,18 @@ typedef struct {
   int32_t l2_persist;    /* 1: keep the per-iteration operators in a persisting L2 carve-out during a step
                             (reset to normal at the end of every step); 0: plain streaming */
   int32_t factor;        /* IETI_FACTOR_* (MIXED precision only; must be IETI_FACTOR_FP64 with FP64) */
+  /* Newton's method for a nonlinear reluctivity (ignored for linear problems).  Each
+   * iteration evaluates the FP64 residual R(a) = W a + dt N(a) - f of the nonlinear
+   * system on the device and solves J d = -R with one dual-primal PCG solve (cg_tol);
+   * max_sweeps bounds the iterations.  The step stops when ||R|| <= outer_tol ||f|| or,
+   * with newton_tol > 0, when ||d|| <= newton_tol ||a|| after an update. */
+  int32_t refactor;      /* IETI_REFACTOR_*: when the nonlinear patches and the coarse block are refactored */
+  double newton_tol;     /* relative-update stop (0: residual test only) */
 } ieti_options;
+
+#define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
+#define IETI_REFACTOR_STEP 1   /* at the first iterate of every step, frozen within the step (modified Newton) */
+#define IETI_REFACTOR_NEVER 2  /* never after setup (the tangent at a = 0) */
 
 /* Coil source through its potential T = T_z(r) chi(|z - zc| < hz) e_z (J = curl T):
  * T_z = J0 (r_out - r) on r_in < r < r_out, J0 (r_out - r_in) for r <= r_in, 0 beyond;
@@ -119,6 +135,7 @@ typedef struct {
   double outer_res;      /* ||f - W a|| / ||f|| after the step (FP64) */
   double t_step_ms;      /* device time of the step (CUDA events) */
   int64_t kernel_launches; /* kernels this library launched for the step */
+  int32_t refactors;     /* refactorizations of the nonlinear patches in the step (nonlinear problems) */
 } ieti_stats;
 
 typedef struct {
@@ -141,6 +158,9 @@ typedef struct {
   double tc_useful_flops;    /* the multiply-adds of the updated entries, x 2 */
   int64_t tc_launches;       /* tensor-core update launches */
   double factor_flops;       /* useful flops of the patch-block partial Cholesky (both phases) */
+  int64_t nl_patches;        /* patches refactored by Newton (holding elements of the nonlinear law) */
+  int64_t nl_elements;       /* elements of the nonlinear law */
+  int64_t refactors;         /* refactorizations since setup */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -32,10 +32,12 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "chol_tc.cuh"
 #include "device.h"
+#include "nonlinear.cuh"
 #include "pcg_kernel.cuh"
 
 namespace ieti {
@@ -545,6 +547,22 @@ __global__ void k_dot_partial(int64_t n, const double *x, const double *y, doubl
 
 // sc[idx] = sum(part); op 1: sc[4] = sc[1]/sc[2] (alpha); op 2: sc[5] = sc[6]/sc[1], sc[1] = sc[6] (beta)
 enum { SC_DD = 0, SC_RZ = 1, SC_PQ = 2, SC_RR = 3, SC_ALPHA = 4, SC_BETA = 5, SC_RZNEW = 6, SC_TMP = 7 };
+// partial sums of sum_k own[k] x[k]^2 (each global DOF once)
+__global__ void k_owner_sq(int64_t n, const uint8_t *own, const double *x, double *part) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (own[i]) acc += x[i] * x[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
 __global__ void k_dot_final(int nparts, const double *part, double *sc, int idx, int op) {
   __shared__ double sh[32];
   double acc = 0;
@@ -699,6 +717,34 @@ struct DeviceState {
   double tc_ms = 0, tc_flops = 0, tc_useful_flops = 0;  // tensor-core trailing updates
   int64_t tc_launches = 0;
   double factor_flops = 0;                // useful flops of both phases (all factor modes)
+  // coarse factorization descriptors (one matrix), kept for refactorizations
+  int64_t *c_off = nullptr;
+  int32_t *c_ld = nullptr, *c_kb = nullptr, *c_ke = nullptr, *c_na = nullptr, *c_st = nullptr, *c_z = nullptr,
+          *c_big = nullptr;
+  // nonlinear reluctivity: Newton with refactorization of the patches holding
+  // nonlinear elements (the "nl batch") and of the coarse block
+  bool nonlinear = false;
+  NlLaw law{};
+  int nl_np = 0;
+  int64_t nl_ne = 0;
+  int nl_max_nloc = 0, nl_max_nq = 0;
+  double *nl_G = nullptr, *nl_cq = nullptr;
+  int32_t *nl_kept = nullptr, *nl_nloc = nullptr, *nl_nq = nullptr, *nl_bpos = nullptr;
+  int64_t *nl_glob = nullptr, *nl_goff = nullptr, *nl_qoff = nullptr, *nl_doff = nullptr;
+  float4 *nl_tq = nullptr;
+  void *nl_base = nullptr, *nl_work = nullptr;  // dense augmented blocks of the batch: W without the law, + dt K_t
+  std::vector<int32_t> nlh_ids, nlh_nn, nlh_n, nlh_ni, nlh_nb, nlh_np;
+  std::vector<int64_t> nlh_doff, nlh_pofs;
+  int64_t nl_arena = 0;
+  int64_t *nlb_doff = nullptr, *nlb_kofs = nullptr, *nlb_hoff = nullptr, *nlb_qoff = nullptr, *nlb_poff = nullptr,
+          *nlb_igoff = nullptr, *nlb_gtoff = nullptr;
+  int32_t *nlb_nn = nullptr, *nlb_ni = nullptr, *nlb_nb = nullptr, *nlb_np = nullptr, *nlb_ldb = nullptr,
+          *nlb_ldp = nullptr, *nlb_ldi = nullptr, *nlb_ldg = nullptr, *nlb_n = nullptr;
+  int32_t *nlb_kb = nullptr, *nlb_ke = nullptr, *nlb_na = nullptr, *nlb_st = nullptr, *nlb_sklo = nullptr,
+          *nlb_skhi = nullptr, *nlb_rlim = nullptr, *nlb_clim = nullptr;
+  double *sc_lin = nullptr, *sc_aug = nullptr;  // coarse: sum over the linear patches (nc x nc); work (2nc)^2
+  int64_t refactors = 0;
+  int32_t step_refactors = 0;
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -1078,6 +1124,198 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
   return IETI_OK;
 }
 
+// one partial-Cholesky phase of a batch in the context's factor arithmetic
+template <class TD>
+static int run_partial(DeviceState *d, TD *D, const int64_t *doff, const int32_t *ld, const TcHost &th,
+                       const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
+                       const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke, int32_t *dna, int32_t *dst,
+                       AugLimits lim, std::string &err) {
+  if constexpr (std::is_same<TD, double>::value) {
+    return potrf_partial<double>(d, D, doff, ld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+  } else {
+    switch (d->factor) {
+      case IETI_FACTOR_FP32:
+        return potrf_partial<float>(d, D, doff, ld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+      case IETI_FACTOR_TF32X3:
+        return potrf_partial_tc<1>(d, D, doff, ld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+      default:
+        return potrf_partial_tc<0>(d, D, doff, ld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+    }
+  }
+}
+
+// FP64 partial Cholesky of the assembled [[S_c, I], [I, 0]] (2 nc x 2 nc, row-major)
+// and extraction of S_c^{-1} into the per-iteration slot (FP32 (hi, lo) pairs in the
+// mixed path).  The descriptor words are allocated once and reused.
+static int coarse_factor(DeviceState *d, double *Sc, std::string &err) {
+  const int64_t nc = d->NC, ldc = 2 * nc;
+  int rc;
+  if (!d->c_off) {
+    std::vector<int64_t> hcoff{0};
+    std::vector<int32_t> hcld{(int32_t)ldc}, hckb{0}, hcke{(int32_t)nc}, hcna{(int32_t)ldc}, hz{0},
+        hbig{INT32_MAX};
+    if ((rc = upload(d, &d->c_off, hcoff, err)) || (rc = upload(d, &d->c_ld, hcld, err)) ||
+        (rc = upload(d, &d->c_kb, hckb, err)) || (rc = upload(d, &d->c_ke, hcke, err)) ||
+        (rc = upload(d, &d->c_na, hcna, err)) || (rc = upload(d, &d->c_st, hz, err)) ||
+        (rc = upload(d, &d->c_z, hz, err)) || (rc = upload(d, &d->c_big, hbig, err)))
+      return rc;
+  }
+  CK(cudaMemsetAsync(d->c_st, 0, 4, d->stream));
+  std::vector<int32_t> hckb{0}, hcke{(int32_t)nc}, hcna{(int32_t)ldc};
+  AugLimits clim_{d->c_z, d->c_z, d->c_big, d->c_z};
+  if ((rc = potrf_partial<double>(d, Sc, d->c_off, d->c_ld, hckb, hcke, hcna, d->c_kb, d->c_ke, d->c_na, d->c_st,
+                                  clim_, err)))
+    return rc;
+  int32_t cstat = 0;
+  CK(cudaMemcpyAsync(&cstat, d->c_st, 4, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  if (cstat) {
+    err = "coarse Schur complement is not positive definite (pivot " + std::to_string(cstat - 1) + ")";
+    return IETI_ERR_NOT_SPD;
+  }
+  if (!d->Sinv) {
+    if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * d->ldc), err))) return rc;
+    CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
+  }
+  k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
+  if (d->mixed) {
+    d->Sdf = d->Scoarse_slot;
+    k_split_pairs<<<grid_for(nc * d->ldc, 256), 256, 0, d->stream>>>(nc * d->ldc, d->Sinv, (float2 *)d->Sdf);
+  } else {
+    CK(cudaMemcpyAsync(d->Scoarse_slot, d->Sinv, (size_t)(nc * d->ldc) * sizeof(double), cudaMemcpyDeviceToDevice,
+                       d->stream));
+  }
+  d->launches_setup += 2;
+  CK(cudaGetLastError());
+  return IETI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Nonlinear reluctivity: refactorization of the patches holding nonlinear elements
+// at the current state d->a (their blocks W (without the law) + dt K_t(a)), then the
+// coarse block S_c = (sum over the linear patches, kept from setup) + theirs.
+template <class TD, class TO>  // dense arena type, operator type
+static int nl_refactor(DeviceState *d, std::string &err) {
+  cudaStream_t st = d->stream;
+  const int nb = d->nl_np;
+  TD *W = (TD *)d->nl_work;
+  CK(cudaMemcpyAsync(d->nl_work, d->nl_base, (size_t)d->nl_arena * sizeof(TD), cudaMemcpyDeviceToDevice, st));
+  {
+    size_t sm = (size_t)(d->nl_max_nloc + 4 * d->nl_max_nq) * sizeof(double);
+    k_nl_eval<<<(unsigned)d->nl_ne, 128, sm, st>>>(d->nl_G, d->nl_cq, d->nl_kept, d->nl_glob, d->nl_goff,
+                                                   d->nl_qoff, d->nl_doff, d->nl_nloc, d->nl_nq, d->nl_bpos,
+                                                   d->nlb_kofs, d->a, d->law, d->dt, nullptr, d->nl_tq, 2);
+    size_t sm2 = (size_t)NL_QC * d->nl_max_nloc * sizeof(float4);
+    k_nl_tangent<TD><<<(unsigned)d->nl_ne, NL_TB, sm2, st>>>(d->nl_G, d->nl_kept, d->nl_goff, d->nl_qoff,
+                                                             d->nl_doff, d->nl_nloc, d->nl_nq, d->nl_bpos, d->nl_tq,
+                                                             d->nlb_doff, d->nlb_nn, d->dt, W);
+    d->nlaunch += 2;
+  }
+  CK(cudaGetLastError());
+  // phase A: interior pivots; copy S_bb
+  std::vector<int32_t> hkb(nb), hke(nb), hna(nb);
+  TcHost th;
+  th.off = d->nlh_doff;
+  th.ld = d->nlh_nn;
+  th.sk_lo.resize(nb);
+  th.sk_hi.resize(nb);
+  th.rlim.assign(nb, INT32_MAX);
+  th.clim.assign(nb, 0);
+  for (int b = 0; b < nb; ++b) {
+    hkb[b] = 0;
+    hke[b] = d->nlh_ni[b];
+    hna[b] = d->nlh_nn[b];
+    th.sk_lo[b] = d->nlh_n[b];
+    th.sk_hi[b] = d->nlh_n[b] + d->nlh_nb[b];
+  }
+  auto put = [&](int32_t *dst, const std::vector<int32_t> &h) -> int {
+    CK(cudaMemcpyAsync(dst, h.data(), nb * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return IETI_OK;
+  };
+  int rc;
+  if ((rc = put(d->nlb_kb, hkb)) || (rc = put(d->nlb_ke, hke)) || (rc = put(d->nlb_na, hna)) ||
+      (rc = put(d->nlb_sklo, th.sk_lo)) || (rc = put(d->nlb_skhi, th.sk_hi)) || (rc = put(d->nlb_rlim, th.rlim)) ||
+      (rc = put(d->nlb_clim, th.clim)))
+    return rc;
+  CK(cudaMemsetAsync(d->nlb_st, 0, nb * 4, st));
+  AugLimits lim{d->nlb_sklo, d->nlb_skhi, d->nlb_rlim, d->nlb_clim};
+  if ((rc = run_partial<TD>(d, W, d->nlb_doff, d->nlb_nn, th, hkb, hke, hna, d->nlb_kb, d->nlb_ke, d->nlb_na,
+                            d->nlb_st, lim, err)))
+    return rc;
+  int maxnb = 1, maxnp = 1;
+  int64_t maxH = 1, maxIG = 1;
+  for (int b = 0; b < nb; ++b) {
+    maxnb = std::max(maxnb, d->nlh_nb[b]);
+    maxnp = std::max(maxnp, d->nlh_np[b]);
+    maxH = std::max(maxH, (int64_t)(d->nlh_nb[b] + d->nlh_np[b]) * d->nlh_nb[b]);
+    maxIG = std::max(maxIG, (int64_t)d->nlh_n[b] * d->nlh_ni[b]);
+  }
+  {
+    dim3 g(grid_for((int64_t)maxnb * maxnb, 256), nb);
+    k_extract_P<TD, TO><<<g, 256, 0, st>>>(W, d->nlb_doff, d->nlb_nn, d->nlb_ni, d->nlb_nb, d->nlb_ldb,
+                                           d->nlb_poff, (TO *)d->P);
+  }
+  // phase B: interface pivots
+  for (int b = 0; b < nb; ++b) {
+    hkb[b] = d->nlh_ni[b];
+    hke[b] = d->nlh_ni[b] + d->nlh_nb[b];
+    hna[b] = d->nlh_n[b] + d->nlh_nb[b];
+    th.sk_lo[b] = th.sk_hi[b] = 0;
+  }
+  if ((rc = put(d->nlb_kb, hkb)) || (rc = put(d->nlb_ke, hke)) || (rc = put(d->nlb_na, hna)) ||
+      (rc = put(d->nlb_sklo, th.sk_lo)) || (rc = put(d->nlb_skhi, th.sk_hi)))
+    return rc;
+  if ((rc = run_partial<TD>(d, W, d->nlb_doff, d->nlb_nn, th, hkb, hke, hna, d->nlb_kb, d->nlb_ke, d->nlb_na,
+                            d->nlb_st, lim, err)))
+    return rc;
+  {
+    std::vector<int32_t> hst(nb);
+    CK(cudaMemcpyAsync(hst.data(), d->nlb_st, nb * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b)
+      if (hst[b]) {
+        err = "Newton tangent block of patch " + std::to_string(d->nlh_ids[b]) +
+              " is not positive definite (pivot " + std::to_string(hst[b] - 1) + ")";
+        return IETI_ERR_NOT_SPD;
+      }
+  }
+  {
+    dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), nb);
+    k_extract_ops<TD, TO><<<g, 256, 0, st>>>(W, d->nlb_doff, d->nlb_nn, d->nlb_ni, d->nlb_nb, d->nlb_np, d->nlb_ldb,
+                                             d->nlb_ldp, d->nlb_hoff, d->nlb_qoff, (TO *)d->H, (TO *)d->Q);
+    dim3 g2((unsigned)std::min<int64_t>(grid_for(maxIG, 256), 4096), nb);
+    k_extract_IG<TD, TO><<<g2, 256, 0, st>>>(W, d->nlb_doff, d->nlb_nn, d->nlb_ni, d->nlb_nb, d->nlb_np, d->nlb_ldi,
+                                             d->nlb_ldg, d->nlb_igoff, d->nlb_gtoff, (TO *)d->IG, (TO *)d->GT);
+  }
+  // coarse: linear part + the refactored patches, then FP64 factorization
+  if (d->NC > 0) {
+    const int64_t nc = d->NC, ldc = 2 * nc;
+    CK(cudaMemsetAsync(d->sc_aug, 0, (size_t)(ldc * ldc) * sizeof(double), st));
+    CK(cudaMemcpy2DAsync(d->sc_aug, ldc * sizeof(double), d->sc_lin, nc * sizeof(double), nc * sizeof(double), nc,
+                         cudaMemcpyDeviceToDevice, st));
+    for (int b = 0; b < nb; ++b) {
+      if (d->nlh_np[b] == 0) continue;
+      int64_t cnt = (int64_t)d->nlh_np[b] * d->nlh_np[b];
+      k_coarse_add<TD><<<grid_for(cnt, 256), 256, 0, st>>>(W, d->nlh_doff[b], d->nlh_nn[b], d->nlh_ni[b],
+                                                           d->nlh_nb[b], d->nlh_np[b], d->pc + d->nlh_pofs[b],
+                                                           d->sc_aug, ldc);
+    }
+    k_coarse_identity<<<grid_for(nc, 256), 256, 0, st>>>((int)nc, d->sc_aug, ldc);
+    if ((rc = coarse_factor(d, d->sc_aug, err))) return rc;
+  }
+  CK(cudaGetLastError());
+  d->refactors++;
+  d->step_refactors++;
+  return IETI_OK;
+}
+
+static int nl_refactor_any(DeviceState *d, std::string &err) {
+  if (!d->mixed) return nl_refactor<double, double>(d, err);
+  if (d->factor == IETI_FACTOR_FP64) return nl_refactor<double, float>(d, err);
+  return nl_refactor<float, float>(d, err);
+}
+
 // ---------------------------------------------------------------------------
 // the condensed interface solve: given u (B-space) and gp (Pi-space, may be
 // null): bp[0:NBt] = F u - Psi q, q = S_c^{-1} sum_s A_s^T (gp - Psi^T u)
@@ -1394,6 +1632,9 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   int its_total = 0, sweeps = 0, cg_rc = IETI_OK;
   double rel = 0, ores = -1.0, prev = -1.0;
   int max_sweeps = std::max(1, d->opt.max_sweeps);
+  const bool newton = d->nl_np > 0;
+  bool update_small = false;
+  d->step_refactors = 0;
   for (int sweep = 0;; ++sweep) {
     // defect of the ASSEMBLED system at the current iterate, in FP64: r = f - W_g a,
     // redistributed over the patches with the 1/k weights (so that the local
@@ -1402,10 +1643,18 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     k_resid<<<grid_for(NK * 32, 256), 256, 0, st>>>(NK, d->wptr, d->wcol, d->wval, d->ka, d->kf, d->kr);
     d->nlaunch++;
     prof_end(d);
+    if (newton) {
+      // Newton residual of the nonlinear system: r -= dt N(a) over the nonlinear elements
+      size_t sm = (size_t)(d->nl_max_nloc + 4 * d->nl_max_nq) * sizeof(double);
+      k_nl_eval<<<(unsigned)d->nl_ne, 128, sm, st>>>(d->nl_G, d->nl_cq, d->nl_kept, d->nl_glob, d->nl_goff,
+                                                     d->nl_qoff, d->nl_doff, d->nl_nloc, d->nl_nq, d->nl_bpos,
+                                                     d->nlb_kofs, d->a, d->law, d->dt, d->kr, d->nl_tq, 1);
+      d->nlaunch++;
+    }
     double rn;
     if ((rc = assemble_norm(d, d->kr, &rn, err))) return rc;
     ores = fn > 0 ? rn / fn : 0.0;
-    if (ores <= d->opt.outer_tol || fn == 0.0) break;
+    if (ores <= d->opt.outer_tol || fn == 0.0 || update_small) break;
     if (sweep >= max_sweeps) {
       if (max_sweeps > 1 && cg_rc == IETI_OK) {
         err = "refinement did not reach outer_tol within max_sweeps";
@@ -1413,7 +1662,9 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
       }
       break;
     }
-    if (sweep >= 2 && rn > 0.9 * prev) {  // stagnation at the rounding floor of the FP64 defect
+    // stagnation at the rounding floor of the FP64 defect (Newton with a frozen tangent
+    // contracts linearly, possibly slowly: only a residual that stops falling ends it)
+    if (sweep >= (newton ? 6 : 2) && rn > (newton ? 1.0 : 0.9) * prev) {
       if (cg_rc == IETI_OK) {
         err = "refinement stagnated above outer_tol";
         cg_rc = IETI_ERR_CG_NOT_CONVERGED;
@@ -1421,6 +1672,8 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
       break;
     }
     prev = rn;
+    if (newton && (d->opt.refactor == IETI_REFACTOR_EVERY || (d->opt.refactor == IETI_REFACTOR_STEP && sweep == 0)))
+      if ((rc = nl_refactor_any(d, err))) return rc;
     k_distribute<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->kw, d->rglob, d->kr);
     d->nlaunch++;
     int its = 0;
@@ -1433,9 +1686,22 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     d->nlaunch++;
     k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
     d->nlaunch++;
+    if (newton && d->opt.newton_tol > 0.0) {
+      // relative update ||d|| / ||a|| of this Newton iteration
+      k_owner_sq<<<RED_BLOCKS, 256, 0, st>>>(NK, d->kown, d->kx, d->part);
+      k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_TMP, 0);
+      double dn2, an2;
+      if ((rc = read_scalar(d, SC_TMP, &dn2, err))) return rc;
+      k_owner_sq<<<RED_BLOCKS, 256, 0, st>>>(NK, d->kown, d->ka, d->part);
+      k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_TMP, 0);
+      if ((rc = read_scalar(d, SC_TMP, &an2, err))) return rc;
+      d->nlaunch += 4;
+      update_small = dn2 <= d->opt.newton_tol * d->opt.newton_tol * an2;
+    }
   }
   CK(cudaGetLastError());
   if (stats) {
+    stats->refactors = d->step_refactors;
     stats->cg_its = its_total;
     stats->sweeps = sweeps;
     stats->rel_res = rel;
@@ -1455,6 +1721,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->device = opt.device;
   d->mixed = opt.precision == IETI_PREC_MIXED;
   d->factor = d->mixed ? opt.factor : IETI_FACTOR_FP64;
+  d->nonlinear = hs.nonlinear;
+  d->law = NlLaw{hs.law[0], hs.law[1], hs.law[2], hs.law[3]};
   d->dt = hs.dt;
   auto fail = [&](int rc) {
     device_destroy(d);
@@ -1768,6 +2036,82 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     d->launches_setup += 2;
   }
   CK(cudaGetLastError());
+  if (d->nonlinear && !hs.nl.patches.empty()) {
+    // patches holding nonlinear elements: keep their blocks without the law (base of
+    // every refactorization) and the quadrature tables of their nonlinear elements
+    const NlTables &T = hs.nl;
+    const int nb = (int)T.patches.size();
+    d->nl_np = nb;
+    d->nl_ne = (int64_t)T.nloc.size();
+    d->nl_arena = 0;
+    for (int b = 0; b < nb; ++b) {
+      int sg = T.patches[b];
+      d->nlh_ids.push_back(sg);
+      d->nlh_nn.push_back(hnn[sg]);
+      d->nlh_n.push_back(hn[sg]);
+      d->nlh_ni.push_back(hni[sg]);
+      d->nlh_nb.push_back(hnb[sg]);
+      d->nlh_np.push_back(hnp[sg]);
+      d->nlh_doff.push_back(d->nl_arena);
+      d->nlh_pofs.push_back(hpofs[sg]);
+      d->nl_arena += (int64_t)hnn[sg] * hnn[sg];
+    }
+    for (int e = 0; e < (int)d->nl_ne; ++e) {
+      d->nl_max_nloc = std::max(d->nl_max_nloc, T.nloc[e]);
+      d->nl_max_nq = std::max(d->nl_max_nq, T.nq[e]);
+    }
+    if (NL_QC * d->nl_max_nloc * (int)sizeof(float4) > 48 * 1024 ||
+        (d->nl_max_nloc + 4 * d->nl_max_nq) * (int)sizeof(double) > 48 * 1024) {
+      err = "nonlinear elements too large for the element kernels' shared memory";
+      return fail(IETI_ERR_TOO_LARGE);
+    }
+    CK(cudaMalloc(&d->nl_base, (size_t)d->nl_arena * dsz));
+    d->allocs.push_back(d->nl_base);
+    CK(cudaMalloc(&d->nl_work, (size_t)d->nl_arena * dsz));
+    d->allocs.push_back(d->nl_work);
+    d->bytes += 2 * d->nl_arena * (int64_t)dsz;
+    for (int b = 0; b < nb; ++b) {
+      int sg = T.patches[b];
+      CK(cudaMemcpyAsync((char *)d->nl_base + d->nlh_doff[b] * dsz, (char *)Dv + hdoff[sg] * dsz,
+                         (size_t)hnn[sg] * hnn[sg] * dsz, cudaMemcpyDeviceToDevice, d->stream));
+    }
+    std::vector<int64_t> kofs_b, hoff_b, qoff_b, poff_b, igoff_b, gtoff_b;
+    std::vector<int32_t> ldb_b, ldp_b, ldi_b, ldg_b;
+    for (int b = 0; b < nb; ++b) {
+      int sg = T.patches[b];
+      kofs_b.push_back(hkofs[sg]);
+      hoff_b.push_back(hh[sg]);
+      qoff_b.push_back(hq[sg]);
+      poff_b.push_back(hp[sg]);
+      igoff_b.push_back(hig[sg]);
+      gtoff_b.push_back(hgt[sg]);
+      ldb_b.push_back(hldb[sg]);
+      ldp_b.push_back(hldp[sg]);
+      ldi_b.push_back(hldi[sg]);
+      ldg_b.push_back(hldg[sg]);
+    }
+    std::vector<int32_t> zeros(nb, 0);
+    std::vector<float4> tq0(std::max<size_t>(T.cq.size(), 1));
+    if ((rc = upload(d, &d->nlb_doff, d->nlh_doff, err)) || (rc = upload(d, &d->nlb_kofs, kofs_b, err)) ||
+        (rc = upload(d, &d->nlb_hoff, hoff_b, err)) || (rc = upload(d, &d->nlb_qoff, qoff_b, err)) ||
+        (rc = upload(d, &d->nlb_poff, poff_b, err)) || (rc = upload(d, &d->nlb_igoff, igoff_b, err)) ||
+        (rc = upload(d, &d->nlb_gtoff, gtoff_b, err)) || (rc = upload(d, &d->nlb_nn, d->nlh_nn, err)) ||
+        (rc = upload(d, &d->nlb_n, d->nlh_n, err)) || (rc = upload(d, &d->nlb_ni, d->nlh_ni, err)) ||
+        (rc = upload(d, &d->nlb_nb, d->nlh_nb, err)) || (rc = upload(d, &d->nlb_np, d->nlh_np, err)) ||
+        (rc = upload(d, &d->nlb_ldb, ldb_b, err)) || (rc = upload(d, &d->nlb_ldp, ldp_b, err)) ||
+        (rc = upload(d, &d->nlb_ldi, ldi_b, err)) || (rc = upload(d, &d->nlb_ldg, ldg_b, err)) ||
+        (rc = upload(d, &d->nlb_kb, zeros, err)) || (rc = upload(d, &d->nlb_ke, zeros, err)) ||
+        (rc = upload(d, &d->nlb_na, zeros, err)) || (rc = upload(d, &d->nlb_st, zeros, err)) ||
+        (rc = upload(d, &d->nlb_sklo, zeros, err)) || (rc = upload(d, &d->nlb_skhi, zeros, err)) ||
+        (rc = upload(d, &d->nlb_rlim, zeros, err)) || (rc = upload(d, &d->nlb_clim, zeros, err)) ||
+        (rc = upload(d, &d->nl_G, T.G, err)) || (rc = upload(d, &d->nl_cq, T.cq, err)) ||
+        (rc = upload(d, &d->nl_kept, T.kept, err)) || (rc = upload(d, &d->nl_glob, T.glob, err)) ||
+        (rc = upload(d, &d->nl_goff, T.g_off, err)) || (rc = upload(d, &d->nl_qoff, T.q_off, err)) ||
+        (rc = upload(d, &d->nl_doff, T.d_off, err)) || (rc = upload(d, &d->nl_nloc, T.nloc, err)) ||
+        (rc = upload(d, &d->nl_nq, T.nq, err)) || (rc = upload(d, &d->nl_bpos, T.el_batch, err)) ||
+        (rc = upload(d, &d->nl_tq, tq0, err)))
+      return fail(rc);
+  }
   // phase A: interior pivots -> trailing [b p b'] = Schur complement; copy S_bb
   std::vector<int32_t> hkb(np_), hke(np_), hna(np_);
   int32_t *dkb = nullptr, *dke = nullptr, *dna = nullptr, *dstat = nullptr;
@@ -1949,40 +2293,32 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       d->launches_setup++;
     }
     k_coarse_identity<<<grid_for(nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc);
-    int64_t *coff = nullptr;
-    int32_t *cld = nullptr, *ckb = nullptr, *cke = nullptr, *cna = nullptr, *cst = nullptr;
-    std::vector<int64_t> hcoff{0};
-    std::vector<int32_t> hcld{(int32_t)ldc}, hckb{0}, hcke{(int32_t)nc}, hcna{(int32_t)ldc}, hcst{0};
-    std::vector<int32_t> hz{0}, hbig{INT32_MAX};
-    int32_t *cz = nullptr, *cbig = nullptr;
-    if ((rc = upload(d, &coff, hcoff, err)) || (rc = upload(d, &cld, hcld, err)) || (rc = upload(d, &ckb, hckb, err)) ||
-        (rc = upload(d, &cke, hcke, err)) || (rc = upload(d, &cna, hcna, err)) || (rc = upload(d, &cst, hcst, err)) ||
-        (rc = upload(d, &cz, hz, err)) || (rc = upload(d, &cbig, hbig, err)))
-      return fail(rc);
-    AugLimits clim_{cz, cz, cbig, cz};
-    if ((rc = potrf_partial<double>(d, Sc, coff, cld, hckb, hcke, hcna, ckb, cke, cna, cst, clim_, err)))
-      return fail(rc);
-    int32_t cstat = 0;
-    CK(cudaMemcpyAsync(&cstat, cst, 4, cudaMemcpyDeviceToHost, d->stream));
-    CK(cudaStreamSynchronize(d->stream));
-    if (cstat) {
-      err = "coarse Schur complement is not positive definite (pivot " + std::to_string(cstat - 1) + ")";
-      return fail(IETI_ERR_NOT_SPD);
+    if (d->nl_np > 0) {
+      // the linear patches' part of S_c, kept for the refactorizations
+      if ((rc = dalloc(d, &d->sc_lin, (size_t)(nc * nc), err))) return fail(rc);
+      CK(cudaMemsetAsync(d->sc_lin, 0, (size_t)(nc * nc) * sizeof(double), d->stream));
+      std::vector<uint8_t> is_nl(np_, 0);
+      for (int sg : hs.nl.patches) is_nl[sg] = 1;
+      for (int s = 0; s < np_; ++s) {
+        if (hnp[s] == 0 || is_nl[s]) continue;
+        int64_t cnt = (int64_t)hnp[s] * hnp[s];
+        if (f32)
+          k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s],
+                                                                         hnp[s], d->pc + hpofs[s], d->sc_lin, nc);
+        else
+          k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
+                                                                          hnp[s], d->pc + hpofs[s], d->sc_lin, nc);
+      }
     }
-    if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * d->ldc), err))) return fail(rc);
-    CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
-    k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
-    if (d->mixed) {
-      d->Sdf = d->Scoarse_slot;
-      k_split_pairs<<<grid_for(nc * d->ldc, 256), 256, 0, d->stream>>>(nc * d->ldc, d->Sinv, (float2 *)d->Sdf);
+    if ((rc = coarse_factor(d, Sc, err))) return fail(rc);
+    CK(cudaStreamSynchronize(d->stream));
+    if (d->nl_np > 0) {
+      d->sc_aug = Sc;  // reused by every refactorization
     } else {
-      CK(cudaMemcpyAsync(d->Scoarse_slot, d->Sinv, (size_t)(nc * d->ldc) * sizeof(double), cudaMemcpyDeviceToDevice,
-                         d->stream));
+      cudaFree(Sc);
+      d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
+      d->bytes -= (int64_t)(ldc * ldc) * 8;
     }
-    CK(cudaStreamSynchronize(d->stream));
-    cudaFree(Sc);
-    d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
-    d->bytes -= (int64_t)(ldc * ldc) * 8;
   }
   CK(cudaStreamSynchronize(d->stream));
   CK(cudaGetLastError());
@@ -2119,6 +2455,12 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     d->bytes_sweep_alg = e * (2.0 * sy + sl) + 8.0 * 6 * (double)d->NK;
     d->gemv_bytes[IETI_K_SPMV] = 12.0 * (double)wval.size() + 8.0 * 3 * (double)d->NK;
   }
+  if (d->nl_np > 0) {
+    // operators of the nonlinear patches at the initial state a = 0 (the tangent there)
+    if ((rc = nl_refactor_any(d, err))) return fail(rc);
+    CK(cudaStreamSynchronize(d->stream));
+    d->refactors = 0;
+  }
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   (void)maxnp;
   *out = d;
@@ -2184,6 +2526,9 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->tc_useful_flops = d->tc_useful_flops;
   info->tc_launches = d->tc_launches;
   info->factor_flops = d->factor_flops;
+  info->nl_patches = d->nl_np;
+  info->nl_elements = d->nl_ne;
+  info->refactors = d->refactors;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

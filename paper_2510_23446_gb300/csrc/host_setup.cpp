@@ -202,6 +202,16 @@ int HostSetup::validate(const ieti_problem *pr, std::string &err) {
       return IETI_ERR_INVALID_ARG;
     }
   dt = pr->dt;
+  nonlinear = pr->reluctivity != nullptr;
+  if (nonlinear) {
+    for (int k = 0; k < 4; ++k) law[k] = pr->reluctivity[k];
+    bool ok = law[0] > 0.0 && law[1] >= 0.0 && law[2] >= 0.0 && law[3] >= 0.0 && law[1] + law[3] > 0.0;
+    for (int k = 0; k < 4; ++k) ok = ok && std::isfinite(law[k]);
+    if (!ok) {
+      err = "reluctivity law needs nu0 > 0, k1, k2, k3 >= 0 and k1 + k3 > 0";
+      return IETI_ERR_INVALID_ARG;
+    }
+  }
   return IETI_OK;
 }
 
@@ -519,7 +529,8 @@ void HostSetup::assemble_patch(Patch &pt) const {
       Ke.assign((size_t)nloc * nloc, 0.0);
       Me.assign((size_t)nloc * nloc, 0.0);
     }
-    double ck = nu[el] * w / det;
+    // the nonlinear law's stiffness is assembled on the device at every Newton iterate
+    double ck = nl_element(s, el) ? 0.0 : nu[el] * w / det;
     double cm = sig[el] * w * det;
     for (int a = 0; a < nloc; ++a) {
       const double *Ua = U + 3 * a, *Va = V + 3 * a;
@@ -852,6 +863,7 @@ void HostSetup::decompose() {
     order.insert(order.end(), pt.p_loc.begin(), pt.p_loc.end());
     std::vector<int32_t> perm(pt.n_dofs, -1);
     for (size_t k = 0; k < order.size(); ++k) perm[order[k]] = (int32_t)k;
+    pt.loc2kept = perm;
     restrict_reorder(pt.M, perm, order, &pt.K, dt, pt.Wk);
     restrict_reorder(pt.M, perm, order, nullptr, 0.0, pt.Mk);
     pt.kept_glob.resize(order.size());
@@ -876,6 +888,70 @@ void HostSetup::decompose() {
 }
 
 // -------------------------------------------------------------------- build
+void HostSetup::nl_tables() {
+  nl = NlTables();
+  for (int s = 0; s < n_patches(); ++s) {
+    const Patch &pt = patches[s];
+    int ne = pt.ne[0] * pt.ne[1] * pt.ne[2];
+    for (int e = 0; e < ne; ++e)
+      if (nl_element(s, e)) {
+        nl.patches.push_back(s);
+        break;
+      }
+  }
+  // per patch tables in parallel, then concatenated in patch order
+  const int nb = (int)nl.patches.size();
+  std::vector<NlTables> part(nb);
+  parallel_for(nb, threads, [&](int b) {
+    const int s = nl.patches[b];
+    const Patch &pt = patches[s];
+    DirData dd[3];
+    for (int d = 0; d < 3; ++d) {
+      int slab = d == 0 ? pt.a : (d == 1 ? pt.b : pt.c);
+      dd[d] = direction_data(knots[d][slab], pt.p[d], pt.ne[d]);
+    }
+    NlTables &t = part[b];
+    int cur = -1;
+    for_each_point(*this, pt, s, dd, [&](int el, int nloc, const int *lid, const double *, double det, double w,
+                                         const double *U, const double *) {
+      if (!nl_element(s, el)) return;
+      if (el != cur) {
+        cur = el;
+        t.el_batch.push_back(b);
+        t.nloc.push_back(nloc);
+        t.nq.push_back(0);
+        t.g_off.push_back((int64_t)t.G.size());
+        t.q_off.push_back((int64_t)t.cq.size());
+        t.d_off.push_back((int64_t)t.kept.size());
+        for (int a = 0; a < nloc; ++a) {
+          t.kept.push_back(pt.loc2kept[lid[a]]);
+          t.glob.push_back(pt.l2g[lid[a]]);
+        }
+      }
+      t.nq.back()++;
+      double g = std::sqrt(w / det);
+      for (int a = 0; a < 3 * nloc; ++a) t.G.push_back(U[a] * g);
+      t.cq.push_back(1.0 / std::sqrt(w * det));
+    });
+  });
+  for (int b = 0; b < nb; ++b) {
+    NlTables &t = part[b];
+    int64_t go = (int64_t)nl.G.size(), qo = (int64_t)nl.cq.size(), dof = (int64_t)nl.kept.size();
+    for (size_t e = 0; e < t.nloc.size(); ++e) {
+      nl.el_batch.push_back(t.el_batch[e]);
+      nl.nloc.push_back(t.nloc[e]);
+      nl.nq.push_back(t.nq[e]);
+      nl.g_off.push_back(go + t.g_off[e]);
+      nl.q_off.push_back(qo + t.q_off[e]);
+      nl.d_off.push_back(dof + t.d_off[e]);
+    }
+    nl.G.insert(nl.G.end(), t.G.begin(), t.G.end());
+    nl.cq.insert(nl.cq.end(), t.cq.begin(), t.cq.end());
+    nl.kept.insert(nl.kept.end(), t.kept.begin(), t.kept.end());
+    nl.glob.insert(nl.glob.end(), t.glob.begin(), t.glob.end());
+  }
+}
+
 int HostSetup::build(const ieti_problem *pr, int nthreads, std::string &err) {
   auto t0 = std::chrono::steady_clock::now();
   threads = nthreads;
@@ -887,6 +963,7 @@ int HostSetup::build(const ieti_problem *pr, int nthreads, std::string &err) {
   build_tree();
   classify();
   decompose();
+  if (nonlinear) nl_tables();
   t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return IETI_OK;
 }

@@ -31,6 +31,22 @@ struct Patch {
   Csr Wk, Mk;                      // W = M + dt K and M in the kept numbering
   std::vector<int64_t> kept_glob;  // kept index -> global edge
   std::vector<double> load_w;      // kept index -> 1/n_share
+  std::vector<int32_t> loc2kept;   // local DOF -> kept index (-1: eliminated)
+};
+
+// Quadrature tables of the elements with the nonlinear reluctivity (one entry per
+// element of a patch listed in `patches`): at point q of element e and its local
+// function a, G[q][a][:] = (DF c_hat_a) sqrt(w / det) and cq[q] = 1 / sqrt(w det),
+// so that B_q = cq[q] sum_a x_a G[q][a], the stiffness is sum_q nu G_a.G_b and
+// the residual sum_q nu (B_q . G[q][a]) / cq[q].
+struct NlTables {
+  std::vector<int32_t> patches;                 // global ids of the patches holding such elements
+  std::vector<int32_t> el_batch;                // element -> position in `patches`
+  std::vector<int32_t> nloc, nq;                // per element
+  std::vector<int64_t> g_off, q_off, d_off;     // per element offsets into G / cq / kept,glob
+  std::vector<double> G, cq;
+  std::vector<int32_t> kept;                    // per element function: kept index in its patch, -1 eliminated
+  std::vector<int64_t> glob;                    // per element function: global edge
 };
 
 struct Multiplier {                // lambda = (copy in s) - (copy in t), s < t
@@ -47,6 +63,9 @@ struct HostSetup {
   std::vector<int64_t> ctrl_off;                    // per patch offset (doubles)
   std::vector<double> sigma_el, nu_el;
   std::vector<int64_t> el_off;
+  bool nonlinear = false;                           // nu(|B|) law in the conducting elements
+  double law[4]{};                                  // nu0, k1, k2, k3
+  NlTables nl;
   double dt = 0;
   int threads = 0;
   // lattice
@@ -88,6 +107,8 @@ struct HostSetup {
                 const std::vector<int64_t> &u, const std::vector<int64_t> &v);
   void classify();
   void decompose();
+  void nl_tables();
+  bool nl_element(int s, int el) const { return nonlinear && sigma_el[el_off[s] + el] > 0.0; }
 };
 
 }  // namespace ieti

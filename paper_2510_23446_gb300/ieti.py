@@ -21,6 +21,7 @@ IETI_MEM_HOST, IETI_MEM_DEVICE = 0, 1
 PREC = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
 FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3}
+REFACTOR = {"every": 0, "step": 1, "never": 2}
 ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
           -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE"}
 
@@ -31,7 +32,7 @@ _dp = C.POINTER(C.c_double)
 class ieti_problem(C.Structure):
     _fields_ = [("n_patches", C.c_int32 * 3), ("n_el", _i32p * 3), ("degree", _i32p * 3),
                 ("knots", _dp * 3), ("ctrl_pts", _dp), ("sigma_el", _dp), ("nu_el", _dp),
-                ("dt", C.c_double), ("primal_mode", C.c_int32)]
+                ("dt", C.c_double), ("primal_mode", C.c_int32), ("reluctivity", _dp)]
 
 
 class ieti_options(C.Structure):
@@ -39,7 +40,7 @@ class ieti_options(C.Structure):
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
-                ("factor", C.c_int32)]
+                ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double)]
 
 
 class ieti_coil(C.Structure):
@@ -48,7 +49,8 @@ class ieti_coil(C.Structure):
 
 class ieti_stats(C.Structure):
     _fields_ = [("cg_its", C.c_int32), ("sweeps", C.c_int32), ("rel_res", C.c_double),
-                ("outer_res", C.c_double), ("t_step_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("outer_res", C.c_double), ("t_step_ms", C.c_double), ("kernel_launches", C.c_int64),
+                ("refactors", C.c_int32)]
 
 
 class ieti_kernel_stat(C.Structure):
@@ -66,7 +68,8 @@ class ieti_info(C.Structure):
                 ("t_setup_device_ms", C.c_double), ("kernel_launches_setup", C.c_int64),
                 ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64),
                 ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
-                ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double)]
+                ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double),
+                ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64)]
 
 
 _ctx = C.c_void_p
@@ -120,10 +123,10 @@ def _ptr(x):
 class Solver:
     """One IETI-DP context (ieti_setup ... ieti_destroy)."""
 
-    def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, device=0,
+    def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, reluctivity=None, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1,
-                 factor="fp64"):
+                 factor="fp64", refactor="every", newton_tol=0.0):
         self._keep = []
 
         def arr(x, dt_):
@@ -141,6 +144,11 @@ class Solver:
         pr.nu_el = arr(nu_el, np.float64).ctypes.data_as(_dp)
         pr.dt = float(dt)
         pr.primal_mode = 0
+        if reluctivity is not None:
+            law = reluctivity
+            if isinstance(law, dict):
+                law = [law["nu0"], law["k1"], law["k2"], law["k3"]]
+            pr.reluctivity = arr(law, np.float64).ctypes.data_as(_dp)
         op = ieti_options()
         op.device = int(device)
         op.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -157,6 +165,8 @@ class Solver:
         op.profile = int(profile)
         op.l2_persist = int(l2_persist)
         op.factor = FACTOR[factor] if isinstance(factor, str) else int(factor)
+        op.refactor = REFACTOR[refactor] if isinstance(refactor, str) else int(refactor)
+        op.newton_tol = float(newton_tol)
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
@@ -167,6 +177,7 @@ class Solver:
 
     @classmethod
     def from_problem(cls, prob, **kw):
+        kw.setdefault("reluctivity", getattr(prob, "reluctivity", None))
         return cls(prob.P, prob.n_el, prob.degree, prob.knots, prob.ctrl, prob.sigma_el,
                    prob.nu_el, prob.dt, **kw)
 

@@ -1,0 +1,129 @@
+"""GPU parity of the Newton path (nonlinear reluctivity nu(|B|) in the conductor,
+the extension the paper names in Sec. 2) against the oracle's Newton step.
+
+Tolerances (relative l2 of the global state, every step):
+  FP64 path  <= 1e-10  (PCG 1e-12, Newton stopped on the FP64 residual 1e-13)
+  mixed path <= 1e-8   (FP32 / TF32x3 factors of the tangent, PCG 1e-6, residual 1e-12)
+The oracle solves each step by Newton with SuperLU to a relative update of 1e-13."""
+import numpy as np
+import pytest
+
+from oracle.nonlinear import NewtonProblem
+from workloads import make_problem, small_problem
+
+pytestmark = pytest.mark.gpu
+
+LAW = dict(nu0=1.0, k1=0.5, k2=2.0, k3=0.5)
+TOL = {"fp64": 1e-10, "mixed": 1e-8}
+OPTS = {"fp64": dict(precision="fp64", cg_tol=1e-12, outer_tol=1e-13, max_sweeps=30),
+        "mixed": dict(precision="mixed", cg_tol=1e-6, outer_tol=1e-12, max_sweeps=40, factor="tf32x3")}
+
+
+@pytest.fixture(scope="module")
+def ieti():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_23446_gb300.build import build
+    build()
+    from paper_2510_23446_gb300 import ieti as mod
+    return mod
+
+
+def _c1():
+    prob = make_problem("c1")
+    prob.coil = dict(prob.coil, J0=15.0)
+    prob.reluctivity = dict(LAW)
+    return prob
+
+
+def _uneven():
+    return small_problem(P=(3, 2, 2), n_el=((2, 3, 2), (2, 3), (3, 2)), degree=((1, 2, 1), (2, 1), (1, 2)),
+                         conductor=((0.3, 0.7), (0.2, 0.8), (0.2, 0.8)), elementwise=True, J0=10.0,
+                         reluctivity=LAW, dt=0.02)
+
+
+CASES = {"c1_law": _c1, "uneven_law": _uneven}
+_REF = {}
+
+
+def oracle(name, steps):
+    key = (name, steps)
+    if key not in _REF:
+        prob = CASES[name]()
+        npb = NewtonProblem(prob)
+        a = np.zeros(npb.asm.lat.n_edges)
+        out, its = [], []
+        for _ in range(steps):
+            a, hist = npb.step(a, npb.asm.j_global, tol=1e-13)
+            out.append(a)
+            its.append(len(hist))
+        _REF[key] = (prob, npb, out, its)
+    return _REF[key]
+
+
+def gpu_run(ieti, prob, steps, **kw):
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", **kw)
+    j = S.load_vector(prob.coil)
+    out, stats = [], []
+    for _ in range(steps):
+        stats.append(S.step(j))
+        out.append(S.solution().copy())
+    info = S.info()
+    S.close()
+    return out, stats, info
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_newton_steps_match_oracle(ieti, name, mode):
+    steps = 3
+    prob, npb, ref, its = oracle(name, steps)
+    got, stats, info = gpu_run(ieti, prob, steps, **OPTS[mode])
+    assert info["nl_patches"] > 0 and info["nl_elements"] > 0
+    for l, (a, b) in enumerate(zip(ref, got)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(a)
+        assert err <= TOL[mode], (name, mode, l, err, stats[l])
+        assert stats[l]["refactors"] == stats[l]["sweeps"]      # Newton: a new tangent every iteration
+    # FP64 Newton takes the oracle's number of iterations (within one)
+    if mode == "fp64":
+        for s_, k in zip(stats, its):
+            assert abs(s_["sweeps"] - k) <= 1, (stats, its)
+
+
+@pytest.mark.parametrize("refactor", ["step", "never"])
+def test_frozen_tangents_reach_the_same_state(ieti, refactor):
+    """Modified Newton (tangent of the first iterate of each step) and the chord
+    method (tangent at a = 0) converge to the same solution, in more iterations."""
+    prob, npb, ref, its = oracle("c1_law", 2)
+    full, sf, _ = gpu_run(ieti, prob, 2, **OPTS["fp64"])
+    got, sg, _ = gpu_run(ieti, prob, 2, refactor=refactor, **dict(OPTS["fp64"], max_sweeps=400))
+    for l in range(2):
+        assert np.linalg.norm(got[l] - ref[l]) <= TOL["fp64"] * np.linalg.norm(ref[l])
+        assert sg[l]["sweeps"] >= sf[l]["sweeps"]
+        assert sg[l]["refactors"] == (1 if refactor == "step" else 0)
+
+
+def test_relative_update_stop(ieti):
+    """With newton_tol the step may stop on ||d|| <= tol ||a||; the state still meets
+    the FP64 tolerance against the oracle."""
+    prob, npb, ref, its = oracle("c1_law", 1)
+    opts = dict(OPTS["fp64"], outer_tol=1e-30, newton_tol=1e-11)
+    got, stats, _ = gpu_run(ieti, prob, 1, **opts)
+    assert stats[0]["rc"] == 0
+    assert np.linalg.norm(got[0] - ref[0]) <= TOL["fp64"] * np.linalg.norm(ref[0])
+
+
+def test_linear_law_equals_linear_solver(ieti):
+    """k1 = 0: the Newton path with nu = nu0 k3 gives the linear solver's state
+    with that nu in the conducting elements, after one Newton correction."""
+    law = dict(nu0=1.0, k1=0.0, k2=2.0, k3=0.7)
+    prob = _c1()
+    prob.reluctivity = law
+    got, stats, _ = gpu_run(ieti, prob, 2, **OPTS["fp64"])
+    lin = _c1()
+    lin.reluctivity = None
+    lin.nu_el = np.where(lin.sigma_el > 0, 0.7, lin.nu_el)
+    ref, _, _ = gpu_run(ieti, lin, 2, **OPTS["fp64"])
+    for a, b in zip(ref, got):
+        assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+    assert all(s["sweeps"] <= 2 for s in stats)
