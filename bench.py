@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--no-nonlinear", action="store_true", help="skip the nonlinear (Newton) workload")
+    ap.add_argument("--nl-steps", type=int, default=4, help="timed steps of the nonlinear workload")
     ap.add_argument("--profile-step", action="store_true",
                     help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
     return ap.parse_args()
@@ -201,6 +203,60 @@ def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
                    state=state, j=j, outer_res=st["outer_res"])
 
 
+NL_OPTS = {
+    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=40,
+                  factor="tf32x3", refactor="every"),
+    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, outer_tol=OUTER_TOL, max_sweeps=40,
+                 refactor="every"),
+}
+
+
+def nonlinear_leg(ieti, torch, dev, stream, flush_buf, K, W):
+    """The Newton workload: 64 curved p=3 patches of 8^3 elements, inner cube
+    conducting with nu(|B|) = nu0 (k1 exp(k2 |B|^2) + k3), dt = 5e-4; each step is
+    Newton with the nonlinear patches and the coarse block refactored every
+    iteration.  Mixed (TF32x3 tensor-core factors) vs FP64, same residual stop."""
+    from workloads import make_problem
+    import numpy as np
+    prob = make_problem("c5", patches_per_dir=4)
+    out = {}
+    for mode in ("mixed", "fp64"):
+        t0 = time.perf_counter()
+        S = ieti.Solver.from_problem(prob, device=dev, stream=stream, **NL_OPTS[mode])
+        t_setup = time.perf_counter() - t0
+        inf = S.info()
+        jd = torch.from_numpy(S.load_vector(prob.coil)).to(f"cuda:{dev}")
+        for _ in range(W):
+            S.step(jd)
+        S.set_state(torch.zeros(S.n, dtype=torch.float64, device=f"cuda:{dev}"))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        its = newton = refac = 0
+        for k in range(K):
+            flush_buf.zero_()
+            ev[k][0].record()
+            st = S.step(jd)
+            ev[k][1].record()
+            its += st["cg_its"]
+            newton += st["sweeps"]
+            refac += st["refactors"]
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        out[mode] = dict(value=1e3 * K / ms, unit="steps/s", ms_per_step=ms / K, newton_its_per_step=newton / K,
+                         refactors_per_step=refac / K, cg_its_per_step=its / K, cg_its_per_s=1e3 * its / ms,
+                         setup_s=t_setup, factor=NL_OPTS[mode].get("factor", "fp64"),
+                         state=S.solution().copy())
+        info = inf
+        S.close()
+        torch.cuda.empty_cache()
+    a, b = out["mixed"].pop("state"), out["fp64"].pop("state")
+    return {"workload": "c5: 4x4x4 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 "
+                        "sigma=1e2 with nu(|B|)=1*(0.5 exp(2|B|^2)+0.5), coil J0=5, dt=5e-4, Newton per step",
+            "n_dofs": info["n_dofs"], "n_coarse": info["n_coarse"], "nl_patches": info["nl_patches"],
+            "steps": K, "warmup": W, "mixed": out["mixed"], "fp64": out["fp64"],
+            "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+            "rel_err_vs_fp64": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -339,6 +395,12 @@ def run_ours(args):
                                     "P5 update+precond", "P6 jump+dot"],
                          "work": rm["phases"]["work_us"], "barrier_wait": rm["phases"]["wait_us"]},
     }
+    if not args.no_nonlinear and world == 1:
+        for m in results:
+            results[m][0].close()
+        results = {}
+        torch.cuda.empty_cache()
+        line["nonlinear"] = nonlinear_leg(ieti, torch, dev, stream, flush_buf, max(1, args.nl_steps), 1)
     if cb is not None:
         line["cpu_baseline"] = cb
     if rank == 0:

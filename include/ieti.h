@@ -161,6 +161,8 @@ typedef struct {
   int64_t nl_patches;        /* patches refactored by Newton (holding elements of the nonlinear law) */
   int64_t nl_elements;       /* elements of the nonlinear law */
   int64_t refactors;         /* refactorizations since setup */
+  int64_t nl_coarse_block;   /* coarse unknowns of those patches, updated by the block formula at every
+                                refactorization (0: the whole coarse block is refactored) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

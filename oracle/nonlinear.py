@@ -185,8 +185,11 @@ class NewtonProblem:
         jf = j_glob[self.free]
         a = a_prev.copy()
         hist = []
+        fn = np.linalg.norm(self.M @ a_prev + self.prob.dt * jf)
+        self.last_residuals = []       # ||R(a_k)|| / ||M a^l + dt j|| before every update
         for _ in range(max_it):
             R = self.residual(a, a_prev, jf)
+            self.last_residuals.append(np.linalg.norm(R) / fn)
             d = spla.spsolve(self.jacobian(a), -R)
             a = a + d
             rel = np.linalg.norm(d) / max(np.linalg.norm(a), 1e-300)

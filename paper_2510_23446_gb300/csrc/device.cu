@@ -361,6 +361,86 @@ __global__ void k_split_pairs(int64_t n, const double *x, float2 *out) {
   out[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
+// C = alpha op(A) op(B) + beta C (row-major FP64; op = identity or transpose), 64 x 64
+// tiles, 16-deep K slices in shared memory, 4 x 4 outputs per thread
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double *A, int64_t lda,
+                                               const double *B, int64_t ldb, double beta, double *C, int64_t ldc) {
+  __shared__ double As[16][64 + 1], Bs[16][64 + 1];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+      int kk = idx / 64, ii = idx % 64;
+      int k = k0 + kk, i = m0 + ii, j = n0 + ii;
+      double a = 0, b = 0;
+      if (k < K && i < M) a = TA ? A[(int64_t)k * lda + i] : A[(int64_t)i * lda + k];
+      if (k < K && j < N) b = TB ? B[(int64_t)j * ldb + k] : B[(int64_t)k * ldb + j];
+      As[kk][ii] = a;
+      Bs[kk][ii] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][tr + 16 * u];
+        b[u] = Bs[kk][tc + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int i = m0 + tr + 16 * u, j = n0 + tc + 16 * v;
+      if (i < M && j < N) {
+        double *c = C + (int64_t)i * ldc + j;
+        *c = alpha * acc[u][v] + (beta == 0.0 ? 0.0 : beta * *c);
+      }
+    }
+}
+
+// out[i][j] = S[ri[i]][ci[j]]  (gather of a sub-block of an ld-strided matrix)
+__global__ void k_gather_block(int nr, int ncol, const int32_t *ri, const int32_t *ci, const double *S, int64_t ld,
+                               double *out, int64_t ldo) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nr * ncol) return;
+  int i = (int)(idx / ncol), j = (int)(idx % ncol);
+  out[(int64_t)i * ldo + j] = S[(int64_t)ri[i] * ld + ci[j]];
+}
+
+// S[ri[i]][ci[j]] = sign * B[i][j]  (and, with tr, S[ci[j]][ri[i]] as well)
+__global__ void k_scatter_block(int nr, int ncol, const int32_t *ri, const int32_t *ci, const double *B, int64_t ldb,
+                                double sign, int tr, double *S, int64_t ld) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nr * ncol) return;
+  int i = (int)(idx / ncol), j = (int)(idx % ncol);
+  double v = sign * B[(int64_t)i * ldb + j];
+  S[(int64_t)ri[i] * ld + ci[j]] = v;
+  if (tr) S[(int64_t)ci[j] * ld + ri[i]] = v;
+}
+
+// aug = [[S, I], [I, 0]] (2n x 2n) from an n x n block S
+__global__ void k_aug_identity_block(int n, const double *S, int64_t lds, double *aug) {
+  int64_t ld = 2 * (int64_t)n;
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ld * ld) return;
+  int64_t r = idx / ld, c = idx % ld;
+  double v = 0;
+  if (r < n && c < n) v = S[r * lds + c];
+  else if (r >= n && c == r - n) v = 1.0;
+  else if (c >= n && r == c - n) v = 1.0;
+  aug[idx] = v;
+}
+
 __global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv, int ldo) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nc * nc) return;
@@ -745,6 +825,13 @@ struct DeviceState {
   double *sc_lin = nullptr, *sc_aug = nullptr;  // coarse: sum over the linear patches (nc x nc); work (2nc)^2
   int64_t refactors = 0;
   int32_t step_refactors = 0;
+  // coarse block update: coarse unknowns split into L (untouched by the nonlinear
+  // patches) and N; constants inv(S_LL), X = inv(S_LL) S_LN, Z0 = S_NN(linear) - S_NL X
+  int cL = 0, cN = 0;
+  int32_t *c_idxL = nullptr, *c_idxN = nullptr, *nl_pcN = nullptr;
+  std::vector<int64_t> nlh_pcN;     // per batch patch: offset into nl_pcN
+  double *c_SLLinv = nullptr, *c_X = nullptr, *c_Z0 = nullptr, *c_Zaug = nullptr, *c_Zinv = nullptr,
+         *c_Y = nullptr, *c_Ltmp = nullptr;
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -1144,6 +1231,8 @@ static int run_partial(DeviceState *d, TD *D, const int64_t *doff, const int32_t
   }
 }
 
+static int coarse_publish(DeviceState *d, std::string &err);
+
 // FP64 partial Cholesky of the assembled [[S_c, I], [I, 0]] (2 nc x 2 nc, row-major)
 // and extraction of S_c^{-1} into the per-iteration slot (FP32 (hi, lo) pairs in the
 // mixed path).  The descriptor words are allocated once and reused.
@@ -1178,6 +1267,12 @@ static int coarse_factor(DeviceState *d, double *Sc, std::string &err) {
     CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
   }
   k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
+  return coarse_publish(d, err);
+}
+
+// S_c^{-1} (d->Sinv) -> the per-iteration slot: FP32 (hi, lo) pairs (mixed) or FP64
+static int coarse_publish(DeviceState *d, std::string &err) {
+  const int64_t nc = d->NC;
   if (d->mixed) {
     d->Sdf = d->Scoarse_slot;
     k_split_pairs<<<grid_for(nc * d->ldc, 256), 256, 0, d->stream>>>(nc * d->ldc, d->Sinv, (float2 *)d->Sdf);
@@ -1188,6 +1283,154 @@ static int coarse_factor(DeviceState *d, double *Sc, std::string &err) {
   d->launches_setup += 2;
   CK(cudaGetLastError());
   return IETI_OK;
+}
+
+// inverse of an SPD n x n block from its assembled augmentation aug = [[S, I], [I, 0]]
+// (2n x 2n, row-major): FP64 partial Cholesky of the first n pivots leaves -S^{-1}
+// in the trailing block; out (n x n, leading dimension ldo) receives S^{-1}
+static int spd_inverse(DeviceState *d, double *aug, int n, double *out, int ldo, std::string &err) {
+  static_assert(sizeof(int64_t) == 8, "");
+  int64_t *off = nullptr;
+  int32_t *w = nullptr;
+  CK(cudaMalloc((void **)&off, sizeof(int64_t) + 8 * sizeof(int32_t)));
+  w = (int32_t *)(off + 1);
+  int32_t hw[8] = {2 * n, 0, n, 2 * n, 0, 0, INT32_MAX, 0};  // ld, kb, ke, na, status, zero, big, zero
+  int64_t h0 = 0;
+  cudaError_t e = cudaMemcpyAsync(off, &h0, 8, cudaMemcpyHostToDevice, d->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w, hw, sizeof(hw), cudaMemcpyHostToDevice, d->stream);
+  if (e != cudaSuccess) {
+    cudaFree(off);
+    err = "spd_inverse upload failed";
+    return IETI_ERR_CUDA;
+  }
+  std::vector<int32_t> hkb{0}, hke{n}, hna{2 * n};
+  AugLimits lim{w + 5, w + 5, w + 6, w + 7};
+  int rc = potrf_partial<double>(d, aug, off, w, hkb, hke, hna, w + 1, w + 2, w + 3, w + 4, lim, err);
+  int32_t st = 0;
+  if (rc == IETI_OK) {
+    e = cudaMemcpyAsync(&st, w + 4, 4, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) {
+      err = std::string("spd_inverse failed: ") + cudaGetErrorString(e);
+      rc = IETI_ERR_CUDA;
+    } else if (st) {
+      err = "coarse block is not positive definite (pivot " + std::to_string(st - 1) + ")";
+      rc = IETI_ERR_NOT_SPD;
+    }
+  }
+  if (rc == IETI_OK)
+    k_coarse_extract<<<grid_for((int64_t)n * n, 256), 256, 0, d->stream>>>(n, aug, 2 * n, out, ldo);
+  cudaStreamSynchronize(d->stream);
+  cudaFree(off);
+  return rc;
+}
+
+static void dgemm(DeviceState *d, bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int64_t lda,
+                  const double *B, int64_t ldb, double beta, double *C, int64_t ldc) {
+  dim3 g((N + 63) / 64, (M + 63) / 64);
+  if (!ta && !tb) k_dgemm<false, false><<<g, 256, 0, d->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta && !tb) k_dgemm<true, false><<<g, 256, 0, d->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!ta && tb) k_dgemm<false, true><<<g, 256, 0, d->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else k_dgemm<true, true><<<g, 256, 0, d->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// Split of the coarse unknowns for the Newton refactorizations: N = the primal
+// unknowns of the patches holding nonlinear elements (only S_NN changes between
+// refactorizations), L = the rest.  Precomputes inv(S_LL), X = inv(S_LL) S_LN and
+// Z0 = S_NN(linear part) - S_NL X from the linear patches' part of S_c.
+static int coarse_block_setup(DeviceState *d, const std::vector<int32_t> &hpc, std::string &err) {
+  const int64_t nc = d->NC;
+  std::vector<int32_t> posN(nc, -1), idxL, idxN, pcN;
+  for (int b = 0; b < d->nl_np; ++b)
+    for (int k = 0; k < d->nlh_np[b]; ++k) posN[hpc[d->nlh_pofs[b] + k]] = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (posN[c] == 0) {
+      posN[c] = (int32_t)idxN.size();
+      idxN.push_back((int32_t)c);
+    } else {
+      idxL.push_back((int32_t)c);
+    }
+  }
+  for (int b = 0; b < d->nl_np; ++b) {
+    d->nlh_pcN.push_back((int64_t)pcN.size());
+    for (int k = 0; k < d->nlh_np[b]; ++k) pcN.push_back(posN[hpc[d->nlh_pofs[b] + k]]);
+  }
+  const int cL = (int)idxL.size(), cN = (int)idxN.size();
+  if (cL == 0 || cN == 0) return IETI_OK;  // no split: full refactorizations
+  int rc;
+  if ((rc = upload(d, &d->c_idxL, idxL, err)) || (rc = upload(d, &d->c_idxN, idxN, err)) ||
+      (rc = upload(d, &d->nl_pcN, pcN, err)) || (rc = dalloc(d, &d->c_SLLinv, (size_t)cL * cL, err)) ||
+      (rc = dalloc(d, &d->c_X, (size_t)cL * cN, err)) || (rc = dalloc(d, &d->c_Z0, (size_t)cN * cN, err)) ||
+      (rc = dalloc(d, &d->c_Zaug, (size_t)4 * cN * cN, err)) || (rc = dalloc(d, &d->c_Zinv, (size_t)cN * cN, err)) ||
+      (rc = dalloc(d, &d->c_Y, (size_t)cL * cN, err)) || (rc = dalloc(d, &d->c_Ltmp, (size_t)cL * cL, err)))
+    return rc;
+  double *tmpL = nullptr, *augL = nullptr, *SLN = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(d->stream);
+    cudaFree(tmpL);
+    cudaFree(augL);
+    cudaFree(SLN);
+  };
+  if (cudaMalloc((void **)&tmpL, (size_t)cL * cL * 8) != cudaSuccess ||
+      cudaMalloc((void **)&augL, (size_t)4 * cL * cL * 8) != cudaSuccess ||
+      cudaMalloc((void **)&SLN, (size_t)cL * cN * 8) != cudaSuccess) {
+    cleanup();
+    err = "cudaMalloc failed for the coarse block split";
+    return IETI_ERR_OOM;
+  }
+  cudaStream_t st = d->stream;
+  k_gather_block<<<grid_for((int64_t)cL * cL, 256), 256, 0, st>>>(cL, cL, d->c_idxL, d->c_idxL, d->sc_lin, nc, tmpL,
+                                                                   cL);
+  k_aug_identity_block<<<grid_for((int64_t)4 * cL * cL, 256), 256, 0, st>>>(cL, tmpL, cL, augL);
+  if ((rc = spd_inverse(d, augL, cL, d->c_SLLinv, cL, err))) {
+    cleanup();
+    return rc;
+  }
+  k_gather_block<<<grid_for((int64_t)cL * cN, 256), 256, 0, st>>>(cL, cN, d->c_idxL, d->c_idxN, d->sc_lin, nc, SLN,
+                                                                   cN);
+  dgemm(d, false, false, cL, cN, cL, 1.0, d->c_SLLinv, cL, SLN, cN, 0.0, d->c_X, cN);
+  k_gather_block<<<grid_for((int64_t)cN * cN, 256), 256, 0, st>>>(cN, cN, d->c_idxN, d->c_idxN, d->sc_lin, nc,
+                                                                   d->c_Z0, cN);
+  dgemm(d, true, false, cN, cN, cL, -1.0, SLN, cN, d->c_X, cN, 1.0, d->c_Z0, cN);
+  cudaError_t e = cudaGetLastError();
+  cleanup();
+  if (e != cudaSuccess) {
+    err = std::string("coarse block split failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_CUDA;
+  }
+  d->cL = cL;
+  d->cN = cN;
+  return IETI_OK;
+}
+
+// S_c^{-1} after a refactorization of the nonlinear patches, by the block formula
+// with Z = Z0 + sum over those patches of their C_s (on N):
+// S^{-1} = [[inv(S_LL) + X inv(Z) X^T, -X inv(Z)], [-inv(Z) X^T, inv(Z)]]
+template <class TD>
+static int coarse_block_refactor(DeviceState *d, const TD *W, std::string &err) {
+  cudaStream_t st = d->stream;
+  const int cL = d->cL, cN = d->cN;
+  const int64_t ldz = 2 * (int64_t)cN;
+  k_aug_identity_block<<<grid_for(ldz * ldz, 256), 256, 0, st>>>(cN, d->c_Z0, cN, d->c_Zaug);
+  for (int b = 0; b < d->nl_np; ++b) {
+    if (d->nlh_np[b] == 0) continue;
+    int64_t cnt = (int64_t)d->nlh_np[b] * d->nlh_np[b];
+    k_coarse_add<TD><<<grid_for(cnt, 256), 256, 0, st>>>(W, d->nlh_doff[b], d->nlh_nn[b], d->nlh_ni[b], d->nlh_nb[b],
+                                                         d->nlh_np[b], d->nl_pcN + d->nlh_pcN[b], d->c_Zaug, ldz);
+  }
+  int rc;
+  if ((rc = spd_inverse(d, d->c_Zaug, cN, d->c_Zinv, cN, err))) return rc;
+  dgemm(d, false, false, cL, cN, cN, 1.0, d->c_X, cN, d->c_Zinv, cN, 0.0, d->c_Y, cN);
+  CK(cudaMemcpyAsync(d->c_Ltmp, d->c_SLLinv, (size_t)cL * cL * 8, cudaMemcpyDeviceToDevice, st));
+  dgemm(d, false, true, cL, cL, cN, 1.0, d->c_Y, cN, d->c_X, cN, 1.0, d->c_Ltmp, cL);
+  k_scatter_block<<<grid_for((int64_t)cL * cL, 256), 256, 0, st>>>(cL, cL, d->c_idxL, d->c_idxL, d->c_Ltmp, cL, 1.0,
+                                                                    0, d->Sinv, d->ldc);
+  k_scatter_block<<<grid_for((int64_t)cL * cN, 256), 256, 0, st>>>(cL, cN, d->c_idxL, d->c_idxN, d->c_Y, cN, -1.0,
+                                                                    1, d->Sinv, d->ldc);
+  k_scatter_block<<<grid_for((int64_t)cN * cN, 256), 256, 0, st>>>(cN, cN, d->c_idxN, d->c_idxN, d->c_Zinv, cN, 1.0,
+                                                                    0, d->Sinv, d->ldc);
+  CK(cudaGetLastError());
+  return coarse_publish(d, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -1288,8 +1531,11 @@ static int nl_refactor(DeviceState *d, std::string &err) {
     k_extract_IG<TD, TO><<<g2, 256, 0, st>>>(W, d->nlb_doff, d->nlb_nn, d->nlb_ni, d->nlb_nb, d->nlb_np, d->nlb_ldi,
                                              d->nlb_ldg, d->nlb_igoff, d->nlb_gtoff, (TO *)d->IG, (TO *)d->GT);
   }
-  // coarse: linear part + the refactored patches, then FP64 factorization
-  if (d->NC > 0) {
+  // coarse: by the block formula when the split exists, else linear part + the
+  // refactored patches and a full FP64 factorization
+  if (d->NC > 0 && d->cN > 0) {
+    if ((rc = coarse_block_refactor<TD>(d, W, err))) return rc;
+  } else if (d->NC > 0) {
     const int64_t nc = d->NC, ldc = 2 * nc;
     CK(cudaMemsetAsync(d->sc_aug, 0, (size_t)(ldc * ldc) * sizeof(double), st));
     CK(cudaMemcpy2DAsync(d->sc_aug, ldc * sizeof(double), d->sc_lin, nc * sizeof(double), nc * sizeof(double), nc,
@@ -2313,7 +2559,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     if ((rc = coarse_factor(d, Sc, err))) return fail(rc);
     CK(cudaStreamSynchronize(d->stream));
     if (d->nl_np > 0) {
-      d->sc_aug = Sc;  // reused by every refactorization
+      d->sc_aug = Sc;  // reused by the full refactorizations
+      if ((rc = coarse_block_setup(d, pc, err))) return fail(rc);
     } else {
       cudaFree(Sc);
       d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
@@ -2529,6 +2776,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->nl_patches = d->nl_np;
   info->nl_elements = d->nl_ne;
   info->refactors = d->refactors;
+  info->nl_coarse_block = d->cN;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

@@ -69,7 +69,8 @@ class ieti_info(C.Structure):
                 ("l2_window_bytes", C.c_int64), ("l2_hit_ratio", C.c_double), ("iter_operator_bytes", C.c_int64),
                 ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
                 ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double),
-                ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64)]
+                ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64),
+                ("nl_coarse_block", C.c_int64)]
 
 
 _ctx = C.c_void_p

@@ -29,11 +29,15 @@ def ieti():
     return mod
 
 
-def _c1():
+def _c1(J0=15.0):
     prob = make_problem("c1")
-    prob.coil = dict(prob.coil, J0=15.0)
+    prob.coil = dict(prob.coil, J0=J0)
     prob.reluctivity = dict(LAW)
     return prob
+
+
+def _c1_mild():
+    return _c1(J0=5.0)
 
 
 def _uneven():
@@ -42,7 +46,14 @@ def _uneven():
                          reluctivity=LAW, dt=0.02)
 
 
-CASES = {"c1_law": _c1, "uneven_law": _uneven}
+def _buried():
+    """Conductor in the centre patch of 3 x 3 x 3: the other patches stay linear, so
+    the coarse inverse is updated by the block formula."""
+    return small_problem(P=(3, 3, 3), n_el=((2, 2, 2),) * 3, degree=((1, 2, 1),) * 3,
+                         conductor=((0.4, 0.6),) * 3, J0=6.0, reluctivity=LAW, dt=0.02)
+
+
+CASES = {"c1_law": _c1, "uneven_law": _uneven, "c1_mild": _c1_mild, "buried_law": _buried}
 _REF = {}
 
 
@@ -56,7 +67,9 @@ def oracle(name, steps):
         for _ in range(steps):
             a, hist = npb.step(a, npb.asm.j_global, tol=1e-13)
             out.append(a)
-            its.append(len(hist))
+            # updates the oracle needed before its residual met the GPU's stop (1e-13)
+            res = npb.last_residuals
+            its.append(next((k for k, r in enumerate(res) if r <= 1e-13), len(res)))
         _REF[key] = (prob, npb, out, its)
     return _REF[key]
 
@@ -73,18 +86,20 @@ def gpu_run(ieti, prob, steps, **kw):
     return out, stats, info
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", ["c1_law", "uneven_law", "buried_law"])
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 def test_newton_steps_match_oracle(ieti, name, mode):
     steps = 3
     prob, npb, ref, its = oracle(name, steps)
     got, stats, info = gpu_run(ieti, prob, steps, **OPTS[mode])
     assert info["nl_patches"] > 0 and info["nl_elements"] > 0
+    if name == "buried_law":
+        assert 0 < info["nl_coarse_block"] < info["n_coarse"]     # block update of the coarse inverse
     for l, (a, b) in enumerate(zip(ref, got)):
         err = np.linalg.norm(a - b) / np.linalg.norm(a)
         assert err <= TOL[mode], (name, mode, l, err, stats[l])
         assert stats[l]["refactors"] == stats[l]["sweeps"]      # Newton: a new tangent every iteration
-    # FP64 Newton takes the oracle's number of iterations (within one)
+    # FP64 Newton needs the oracle's number of updates to reach the same residual (within one)
     if mode == "fp64":
         for s_, k in zip(stats, its):
             assert abs(s_["sweeps"] - k) <= 1, (stats, its)
@@ -93,8 +108,11 @@ def test_newton_steps_match_oracle(ieti, name, mode):
 @pytest.mark.parametrize("refactor", ["step", "never"])
 def test_frozen_tangents_reach_the_same_state(ieti, refactor):
     """Modified Newton (tangent of the first iterate of each step) and the chord
-    method (tangent at a = 0) converge to the same solution, in more iterations."""
-    prob, npb, ref, its = oracle("c1_law", 2)
+    method (tangent at a = 0) converge to the same solution, in more iterations.
+    A frozen tangent contracts only while it stays close to the true one, so this
+    runs the milder coil (nu varies by ~10%; with nu up to 3x the chord iteration
+    from the tangent at a = 0 diverges)."""
+    prob, npb, ref, its = oracle("c1_mild", 2)
     full, sf, _ = gpu_run(ieti, prob, 2, **OPTS["fp64"])
     got, sg, _ = gpu_run(ieti, prob, 2, refactor=refactor, **dict(OPTS["fp64"], max_sweeps=400))
     for l in range(2):
