@@ -163,6 +163,9 @@ typedef struct {
   int64_t refactors;         /* refactorizations since setup */
   int64_t nl_coarse_block;   /* coarse unknowns of those patches, updated by the block formula at every
                                 refactorization (0: the whole coarse block is refactored) */
+  double t_refactor_ms[4];   /* with options.profile = 1: device time of all refactorizations since setup in
+                                the tangent assembly, the local factorization + extraction, the coarse update,
+                                and in total (CUDA events) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

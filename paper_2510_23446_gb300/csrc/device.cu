@@ -441,12 +441,21 @@ __global__ void k_aug_identity_block(int n, const double *S, int64_t lds, double
   aug[idx] = v;
 }
 
-__global__ void k_coarse_extract(int nc, const double *Sc, int64_t ldc, double *Sinv, int ldo) {
+template <class TS>
+__global__ void k_coarse_extract(int nc, const TS *Sc, int64_t ldc, double *Sinv, int ldo) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nc * nc) return;
   int r = (int)(idx / nc), c = (int)(idx % nc);
   int hi = max(r, c), lo = min(r, c);
-  Sinv[(int64_t)r * ldo + c] = -Sc[(int64_t)(nc + hi) * ldc + nc + lo];
+  Sinv[(int64_t)r * ldo + c] = -(double)Sc[(int64_t)(nc + hi) * ldc + nc + lo];
+}
+
+// lower triangle of an FP64 matrix rounded to FP32 (leading dimensions ld, ldf)
+__global__ void k_round_lower(int64_t n, const double *A, int64_t ld, float *F, int64_t ldf) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int64_t r = idx / n, c = idx % n;
+  F[r * ldf + c] = c <= r ? (float)A[r * ld + c] : 0.f;
 }
 
 // =============================================================================
@@ -825,6 +834,9 @@ struct DeviceState {
   double *sc_lin = nullptr, *sc_aug = nullptr;  // coarse: sum over the linear patches (nc x nc); work (2nc)^2
   int64_t refactors = 0;
   int32_t step_refactors = 0;
+  double t_refactor_ms[4] = {};
+  float *sc_aug32 = nullptr;             // FP32 copy of the augmented coarse block (mixed Newton refactors)
+  int64_t ld32 = 0;          // tangent, local factorization + extraction, coarse, total (profile)
   // coarse block update: coarse unknowns split into L (untouched by the nonlinear
   // patches) and N; constants inv(S_LL), X = inv(S_LL) S_LN, Z0 = S_NN(linear) - S_NL X
   int cL = 0, cN = 0;
@@ -1266,7 +1278,7 @@ static int coarse_factor(DeviceState *d, double *Sc, std::string &err) {
     if ((rc = dalloc(d, &d->Sinv, (size_t)(nc * d->ldc), err))) return rc;
     CK(cudaMemsetAsync(d->Sinv, 0, (size_t)(nc * d->ldc) * sizeof(double), d->stream));
   }
-  k_coarse_extract<<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
+  k_coarse_extract<double><<<grid_for(nc * nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc, d->Sinv, d->ldc);
   return coarse_publish(d, err);
 }
 
@@ -1319,7 +1331,7 @@ static int spd_inverse(DeviceState *d, double *aug, int n, double *out, int ldo,
     }
   }
   if (rc == IETI_OK)
-    k_coarse_extract<<<grid_for((int64_t)n * n, 256), 256, 0, d->stream>>>(n, aug, 2 * n, out, ldo);
+    k_coarse_extract<double><<<grid_for((int64_t)n * n, 256), 256, 0, d->stream>>>(n, aug, 2 * n, out, ldo);
   cudaStreamSynchronize(d->stream);
   cudaFree(off);
   return rc;
@@ -1356,7 +1368,9 @@ static int coarse_block_setup(DeviceState *d, const std::vector<int32_t> &hpc, s
     for (int k = 0; k < d->nlh_np[b]; ++k) pcN.push_back(posN[hpc[d->nlh_pofs[b] + k]]);
   }
   const int cL = (int)idxL.size(), cN = (int)idxN.size();
-  if (cL == 0 || cN == 0) return IETI_OK;  // no split: full refactorizations
+  // the split pays only when the changing block is a minor part of S_c: its cost is
+  // that of inverting Z (cN) plus GEMMs of cL^2 cN, against a factorization of 2 nc
+  if (cL == 0 || cN == 0 || 2 * cN > nc) return IETI_OK;  // full refactorizations
   int rc;
   if ((rc = upload(d, &d->c_idxL, idxL, err)) || (rc = upload(d, &d->c_idxN, idxN, err)) ||
       (rc = upload(d, &d->nl_pcN, pcN, err)) || (rc = dalloc(d, &d->c_SLLinv, (size_t)cL * cL, err)) ||
@@ -1440,6 +1454,12 @@ static int coarse_block_refactor(DeviceState *d, const TD *W, std::string &err) 
 template <class TD, class TO>  // dense arena type, operator type
 static int nl_refactor(DeviceState *d, std::string &err) {
   cudaStream_t st = d->stream;
+  cudaEvent_t ev[4] = {};
+  if (d->opt.profile)
+    for (auto &e : ev) {
+      cudaEventCreate(&e);
+    }
+  if (ev[0]) cudaEventRecord(ev[0], st);
   const int nb = d->nl_np;
   TD *W = (TD *)d->nl_work;
   CK(cudaMemcpyAsync(d->nl_work, d->nl_base, (size_t)d->nl_arena * sizeof(TD), cudaMemcpyDeviceToDevice, st));
@@ -1455,6 +1475,7 @@ static int nl_refactor(DeviceState *d, std::string &err) {
     d->nlaunch += 2;
   }
   CK(cudaGetLastError());
+  if (ev[1]) cudaEventRecord(ev[1], st);
   // phase A: interior pivots; copy S_bb
   std::vector<int32_t> hkb(nb), hke(nb), hna(nb);
   TcHost th;
@@ -1531,10 +1552,61 @@ static int nl_refactor(DeviceState *d, std::string &err) {
     k_extract_IG<TD, TO><<<g2, 256, 0, st>>>(W, d->nlb_doff, d->nlb_nn, d->nlb_ni, d->nlb_nb, d->nlb_np, d->nlb_ldi,
                                              d->nlb_ldg, d->nlb_igoff, d->nlb_gtoff, (TO *)d->IG, (TO *)d->GT);
   }
+  if (ev[2]) cudaEventRecord(ev[2], st);
   // coarse: by the block formula when the split exists, else linear part + the
   // refactored patches and a full FP64 factorization
   if (d->NC > 0 && d->cN > 0) {
     if ((rc = coarse_block_refactor<TD>(d, W, err))) return rc;
+  } else if (d->NC > 0 && d->mixed && d->factor != IETI_FACTOR_FP64) {
+    // the Newton iterate's coarse block in the factor arithmetic of the patches (a
+    // Newton step is an inexact solve; its residual stays FP64): assembled in FP64,
+    // rounded, factored by the batched FP32 / tensor-core partial Cholesky
+    const int64_t nc = d->NC, ldc = 2 * nc;
+    CK(cudaMemsetAsync(d->sc_aug, 0, (size_t)(ldc * ldc) * sizeof(double), st));
+    CK(cudaMemcpy2DAsync(d->sc_aug, ldc * sizeof(double), d->sc_lin, nc * sizeof(double), nc * sizeof(double), nc,
+                         cudaMemcpyDeviceToDevice, st));
+    for (int b = 0; b < nb; ++b) {
+      if (d->nlh_np[b] == 0) continue;
+      int64_t cnt = (int64_t)d->nlh_np[b] * d->nlh_np[b];
+      k_coarse_add<TD><<<grid_for(cnt, 256), 256, 0, st>>>(W, d->nlh_doff[b], d->nlh_nn[b], d->nlh_ni[b],
+                                                           d->nlh_nb[b], d->nlh_np[b], d->pc + d->nlh_pofs[b],
+                                                           d->sc_aug, ldc);
+    }
+    k_coarse_identity<<<grid_for(nc, 256), 256, 0, st>>>((int)nc, d->sc_aug, ldc);
+    if (!d->sc_aug32) {
+      d->ld32 = (ldc + 3) / 4 * 4;
+      float *p = nullptr;
+      if ((rc = dalloc(d, &p, (size_t)(ldc * d->ld32), err))) return rc;
+      d->sc_aug32 = p;
+    }
+    k_round_lower<<<grid_for(ldc * ldc, 256), 256, 0, st>>>(ldc, d->sc_aug, ldc, d->sc_aug32, d->ld32);
+    std::vector<int32_t> ckb{0}, cke{(int32_t)nc}, cna{(int32_t)ldc};
+    TcHost cth;
+    cth.off = {0};
+    cth.ld = {(int32_t)d->ld32};
+    cth.sk_lo = {0};
+    cth.sk_hi = {0};
+    cth.rlim = {INT32_MAX};
+    cth.clim = {0};
+    int32_t hld = (int32_t)d->ld32;
+    CK(cudaMemcpyAsync(d->c_ld, &hld, 4, cudaMemcpyHostToDevice, st));  // coarse descriptor: FP32 leading dim
+    CK(cudaMemsetAsync(d->c_st, 0, 4, st));
+    AugLimits clim_{d->c_z, d->c_z, d->c_big, d->c_z};
+    rc = run_partial<float>(d, d->sc_aug32, d->c_off, d->c_ld, cth, ckb, cke, cna, d->c_kb, d->c_ke, d->c_na,
+                            d->c_st, clim_, err);
+    int32_t hld2 = (int32_t)ldc;
+    CK(cudaMemcpyAsync(d->c_ld, &hld2, 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    int32_t cstat = 0;
+    CK(cudaMemcpyAsync(&cstat, d->c_st, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (cstat) {
+      err = "Newton coarse block is not positive definite in FP32 (pivot " + std::to_string(cstat - 1) + ")";
+      return IETI_ERR_NOT_SPD;
+    }
+    k_coarse_extract<float><<<grid_for(nc * nc, 256), 256, 0, st>>>((int)nc, d->sc_aug32, d->ld32, d->Sinv, d->ldc);
+    if ((rc = coarse_publish(d, err))) return rc;
   } else if (d->NC > 0) {
     const int64_t nc = d->NC, ldc = 2 * nc;
     CK(cudaMemsetAsync(d->sc_aug, 0, (size_t)(ldc * ldc) * sizeof(double), st));
@@ -1551,6 +1623,19 @@ static int nl_refactor(DeviceState *d, std::string &err) {
     if ((rc = coarse_factor(d, d->sc_aug, err))) return rc;
   }
   CK(cudaGetLastError());
+  if (ev[3]) {
+    cudaEventRecord(ev[3], st);
+    cudaEventSynchronize(ev[3]);
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&c, ev[2], ev[3]);
+    d->t_refactor_ms[0] += a;
+    d->t_refactor_ms[1] += b;
+    d->t_refactor_ms[2] += c;
+    d->t_refactor_ms[3] += a + b + c;
+    for (auto &e : ev) cudaEventDestroy(e);
+  }
   d->refactors++;
   d->step_refactors++;
   return IETI_OK;
@@ -2777,6 +2862,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->nl_elements = d->nl_ne;
   info->refactors = d->refactors;
   info->nl_coarse_block = d->cN;
+  for (int k = 0; k < 4; ++k) info->t_refactor_ms[k] = d->t_refactor_ms[k];
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

@@ -70,7 +70,7 @@ class ieti_info(C.Structure):
                 ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
                 ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double),
                 ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64),
-                ("nl_coarse_block", C.c_int64)]
+                ("nl_coarse_block", C.c_int64), ("t_refactor_ms", C.c_double * 4)]
 
 
 _ctx = C.c_void_p
@@ -189,7 +189,9 @@ class Solver:
     def info(self):
         inf = ieti_info()
         self._check(lib.ieti_get_info(self.ctx, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in ieti_info._fields_}
+        out = {k: getattr(inf, k) for k, _ in ieti_info._fields_}
+        out["t_refactor_ms"] = list(out["t_refactor_ms"])
+        return out
 
     def load_vector(self, coil):
         c = ieti_coil(**{k: float(coil[k]) for k, _ in ieti_coil._fields_})

@@ -47,10 +47,12 @@ def _uneven():
 
 
 def _buried():
-    """Conductor in the centre patch of 3 x 3 x 3: the other patches stay linear, so
-    the coarse inverse is updated by the block formula."""
-    return small_problem(P=(3, 3, 3), n_el=((2, 2, 2),) * 3, degree=((1, 2, 1),) * 3,
-                         conductor=((0.4, 0.6),) * 3, J0=6.0, reluctivity=LAW, dt=0.02)
+    """Conductor in a corner patch of 4 x 4 x 2 (under the coil): few coarse unknowns
+    belong to the nonlinear patch, so the coarse inverse is updated by the block
+    formula."""
+    return small_problem(P=(4, 4, 2), n_el=((2, 3, 2, 2), (2, 2, 3, 2), (2, 2)),
+                         degree=((1, 2, 1, 1), (2, 1, 1, 2), (1, 2)),
+                         conductor=((0.0, 0.25), (0.0, 0.25), (0.0, 0.5)), J0=12.0, reluctivity=LAW, dt=0.02)
 
 
 CASES = {"c1_law": _c1, "uneven_law": _uneven, "c1_mild": _c1_mild, "buried_law": _buried}
