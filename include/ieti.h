@@ -115,6 +115,11 @@ typedef struct {
    * with newton_tol > 0, when ||d|| <= newton_tol ||a|| after an update. */
   int32_t refactor;      /* IETI_REFACTOR_*: when the nonlinear patches and the coarse block are refactored */
   double newton_tol;     /* relative-update stop (0: residual test only) */
+  /* Initial iterate of each step's refinement sweeps.  0: the previous state a^l.
+   * 1: the linear extrapolation in time 2 a^l - a^{l-1} (from the second step after
+   * setup or ieti_set_state on); the right-hand side M a^l + dt j^{l+1} and the stopping
+   * test are unchanged, so the step reaches the same outer_tol, usually in fewer sweeps. */
+  int32_t predictor;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -235,8 +240,12 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);
 /* Per-phase timing of the persistent PCG kernel (options.profile = 1): mean over the
  * traced iterations of the work time of CTA 0 in each of its six phases and of its
  * wait at the grid barrier that ends the phase, in microseconds (%globaltimer).
- * work_us and wait_us have 6 entries each.  reset != 0 clears the accumulators. */
-int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_t reset);
+ * work_us and wait_us have 6 entries each.  sub_us (NULL or 12 entries) splits the
+ * work of the four operator-streaming phases (the dual operator, the coarse solve,
+ * the primal correction, the preconditioner; 3 entries each): from the phase start to
+ * the staged first vector segment, from there to the first operator chunk in shared
+ * memory, and from there to the last row.  reset != 0 clears the accumulators. */
+int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, double *sub_us, int32_t reset);
 
 /* Batched dense partial Cholesky, the kernel family behind both Schur complements
  * of Sec. 3 (local W_rr eliminations and the coarse block), exposed for callers and

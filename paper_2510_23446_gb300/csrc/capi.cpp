@@ -31,6 +31,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->factor < IETI_FACTOR_FP64 || o->factor > IETI_FACTOR_TF32) { err = "bad factor"; return IETI_ERR_INVALID_ARG; }
   if (o->refactor < IETI_REFACTOR_EVERY || o->refactor > IETI_REFACTOR_NEVER) { err = "bad refactor"; return IETI_ERR_INVALID_ARG; }
   if (!(o->newton_tol >= 0.0)) { err = "newton_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->predictor != 0 && o->predictor != 1) { err = "predictor must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
     return IETI_ERR_INVALID_ARG;
@@ -152,10 +153,10 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset) {
   return IETI_OK;
 }
 
-int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, int32_t reset) {
+int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, double *sub_us, int32_t reset) {
   if (!ctx || !work_us || !wait_us) return IETI_ERR_INVALID_ARG;
   if (!ctx->dev) return IETI_ERR_NO_DEVICE;
-  ieti::device_pcg_trace(ctx->dev, work_us, wait_us, reset != 0);
+  ieti::device_pcg_trace(ctx->dev, work_us, wait_us, sub_us, reset != 0);
   return IETI_OK;
 }
 

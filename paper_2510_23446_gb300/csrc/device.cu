@@ -499,6 +499,13 @@ __global__ void k_gather_kept(int64_t nk, const int64_t *glob, const double *a, 
   if (k < nk) out[k] = a[glob[k]];
 }
 
+// initial iterate of a step by linear extrapolation in time: a = 2 a^l - a^{l-1}
+// (eliminated entries are 0 in both and stay 0)
+__global__ void k_extrapolate(int64_t n, const double *a_l, const double *a_lm1, double *a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = 2.0 * a_l[i] - a_lm1[i];
+}
+
 // f = M x + dt * w * j[glob]   (warp per CSR row)
 __global__ void k_rhs(int64_t nk, const int64_t *ptr, const int32_t *col, const double *val, const double *x,
                       const int64_t *glob, const double *w, const double *j, double dt, double *f) {
@@ -711,6 +718,8 @@ struct DevBuf {
 
 struct DeviceState {
   ieti_options opt{};
+  double *a_prev = nullptr, *a_old = nullptr;  // a^{l-1} and a^l of the step in progress (predictor)
+  bool have_prev = false;                      // a_prev holds the state before the current one
   int device = 0;
   cudaStream_t stream = nullptr;
   bool mixed = false;
@@ -786,6 +795,8 @@ struct DeviceState {
   unsigned long long *trace = nullptr;
   double trace_acc[8] = {};   // summed per-phase time (us) over traced iterations: work P1..P6, waits
   double trace_wait[8] = {};
+  double trace_sub[4][3] = {};  // P1, P3, P4, P5: staging, first chunk, rows (us)
+  int64_t trace_sub_n[4] = {};
   int64_t trace_n = 0;
   double *pcg_rr = nullptr, *pcg_dd = nullptr;
   double bytes_iter_alg = 0, bytes_sweep_alg = 0;
@@ -1796,7 +1807,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   a.stage_bytes = d->stage_bytes;
   a.xs_bytes = d->xs_bytes;
   a.n_stages = d->n_stages;
-  if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * 16 * sizeof(unsigned long long), st));
+  if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
   prof_begin(d, IETI_K_PCG, 0.0);
   {
@@ -1841,16 +1852,26 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   *its = h.its;
   prof_set_bytes(d, d->bytes_iter_alg * (h.its + 2) + d->bytes_sweep_alg);
   if (a.trace) {
-    unsigned long long tr[TRACE_IT * 16];
+    unsigned long long tr[TRACE_IT * TRACE_SLOTS];
     CK(cudaMemcpy(tr, d->trace, sizeof(tr), cudaMemcpyDeviceToHost));
     for (int i = 0; i < std::min(h.its - 1, TRACE_IT); ++i) {
-      unsigned long long *t = tr + i * 16;
+      unsigned long long *t = tr + i * TRACE_SLOTS;
       if (!t[14] || !t[11]) continue;
       unsigned long long prev = t[14];
+      // phase starts: P1 at the iteration start, P3 after the P2 wait, P4, P5 after theirs
+      const unsigned long long start_of[4] = {t[14], t[3], t[5], t[7]};
       for (int ph = 0; ph < 6; ++ph) {
         d->trace_acc[ph] += (t[2 * ph] - prev) * 1e-3;
         d->trace_wait[ph] += (t[2 * ph + 1] - t[2 * ph]) * 1e-3;
         prev = t[2 * ph + 1];
+      }
+      for (int k = 0; k < 4; ++k) {
+        const unsigned long long *u = t + 16 + 3 * k;
+        if (!u[0] || !u[1] || !u[2]) continue;
+        d->trace_sub[k][0] += (u[0] - start_of[k]) * 1e-3;
+        d->trace_sub[k][1] += (u[1] - u[0]) * 1e-3;
+        d->trace_sub[k][2] += (u[2] - u[1]) * 1e-3;
+        d->trace_sub_n[k]++;
       }
       d->trace_n++;
     }
@@ -1960,6 +1981,15 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   double fn = 0.0;
   int rc;
   if ((rc = assemble_norm(d, d->kf, &fn, err))) return rc;
+  if (d->opt.predictor) {
+    // keep a^l; with a^{l-1} known, start the sweeps from the extrapolated iterate
+    CK(cudaMemcpyAsync(d->a_old, d->a, d->n_edges * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (d->have_prev) {
+      k_extrapolate<<<grid_for(d->n_edges, 256), 256, 0, st>>>(d->n_edges, d->a_old, d->a_prev, d->a);
+      k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
+      d->nlaunch += 2;
+    }
+  }
   int its_total = 0, sweeps = 0, cg_rc = IETI_OK;
   double rel = 0, ores = -1.0, prev = -1.0;
   int max_sweeps = std::max(1, d->opt.max_sweeps);
@@ -2031,6 +2061,10 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
     }
   }
   CK(cudaGetLastError());
+  if (d->opt.predictor) {
+    std::swap(d->a_prev, d->a_old);  // a^l becomes the previous state
+    d->have_prev = true;
+  }
   if (stats) {
     stats->refactors = d->step_refactors;
     stats->cg_its = its_total;
@@ -2317,6 +2351,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   }
   // ---------------- work vectors
   if ((rc = dalloc(d, &d->a, hs.n_edges, err)) || (rc = dalloc(d, &d->j, hs.n_edges, err)) ||
+      (opt.predictor && ((rc = dalloc(d, &d->a_prev, hs.n_edges, err)) ||
+                         (rc = dalloc(d, &d->a_old, hs.n_edges, err)))) ||
       (rc = dalloc(d, &d->rglob, hs.n_edges, err)) ||
       (rc = dalloc(d, &d->kf, d->NK, err)) || (rc = dalloc(d, &d->kx, d->NK, err)) ||
       (rc = dalloc(d, &d->kr, d->NK, err)) || (rc = dalloc(d, &d->kz, d->NK, err)) ||
@@ -2744,7 +2780,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
         (rc = dalloc(d, &d->ccg, d->NC, err)) || (rc = dalloc(d, &d->ppart, 4 * (size_t)d->G, err)) ||
         (rc = dalloc(d, &d->bar, 4, err)) || (rc = dalloc(d, &d->pcg_its, 1, err)) ||
         (rc = dalloc(d, &d->pcg_rr, 1, err)) || (rc = dalloc(d, &d->pcg_dd, 1, err)) ||
-        (rc = dalloc(d, &d->trace, TRACE_IT * 16, err)))
+        (rc = dalloc(d, &d->trace, TRACE_IT * TRACE_SLOTS, err)))
       return fail(rc);
     CK(cudaMemsetAsync(d->p, 0, m * sizeof(double), d->stream));
     CK(cudaMemsetAsync(d->p1, 0, m * sizeof(double), d->stream));
@@ -2839,6 +2875,7 @@ int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std:
   CK(cudaMemsetAsync(d->a, 0, d->n_edges * sizeof(double), d->stream));
   k_owner_add<<<grid_for(d->NK, 256), 256, 0, d->stream>>>(d->NK, d->kglob, d->kown, d->kx, d->a);
   CK(cudaStreamSynchronize(d->stream));
+  d->have_prev = false;  // no history for the extrapolation of the next step
   return IETI_OK;
 }
 
@@ -2872,13 +2909,20 @@ void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
     for (int c = 0; c < IETI_K_NCLASS; ++c) d->kstat[c] = ieti_kernel_stat{};
 }
 
-void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, bool reset) {
+void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, double *sub_us, bool reset) {
   for (int ph = 0; ph < 6; ++ph) {
     work_us[ph] = d->trace_n ? d->trace_acc[ph] / d->trace_n : 0.0;
     wait_us[ph] = d->trace_n ? d->trace_wait[ph] / d->trace_n : 0.0;
   }
+  if (sub_us)
+    for (int k = 0; k < 4; ++k)
+      for (int j = 0; j < 3; ++j) sub_us[3 * k + j] = d->trace_sub_n[k] ? d->trace_sub[k][j] / d->trace_sub_n[k] : 0.0;
   if (reset) {
     for (int ph = 0; ph < 8; ++ph) d->trace_acc[ph] = d->trace_wait[ph] = 0;
+    for (int k = 0; k < 4; ++k) {
+      d->trace_sub[k][0] = d->trace_sub[k][1] = d->trace_sub[k][2] = 0;
+      d->trace_sub_n[k] = 0;
+    }
     d->trace_n = 0;
   }
 }

@@ -68,12 +68,17 @@ struct PcgArgs {
   unsigned *bar;       // arrival counter, error flag
   int *out_its;
   double *out_rr, *out_dd;
-  unsigned long long *trace;  // optional: CTA 0 phase timestamps, [TRACE_IT][16]
+  unsigned long long *trace;  // optional: CTA 0 phase timestamps, [TRACE_IT][TRACE_SLOTS]
   unsigned stage_bytes, xs_bytes;
   int n_stages;
 };
 
 constexpr int TRACE_IT = 16;
+// per traced iteration: [2 ph] end of the work of phase ph, [2 ph + 1] end of its
+// barrier wait (ph = 0..5), [14] start of the iteration, and for the streaming phases
+// (P1, P3, P4, P5 = sub 0..3) [16 + 3 sub + k]: k = 0 first segment staged, k = 1
+// first operator chunk arrived, k = 2 last row done
+constexpr int TRACE_SLOTS = 32;
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -339,7 +344,7 @@ __device__ __forceinline__ Cursor prefetch(Ring &ring, const OpRows<E> &op) {
 // Returns false (after setting the error flag and draining) when a wait timed out.
 template <int RW, class E, class Stage, class Out, class Pre = NoPre>
 __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, unsigned *errflag,
-                             Stage stage, Out out, Pre pre = Pre()) {
+                             Stage stage, Out out, Pre pre = Pre(), unsigned long long *ts = nullptr) {
   while (cur.issued - 0 < ring.ns && issue_next(ring, op, cur)) {
   }
   int nseg = op.nseg();
@@ -350,6 +355,7 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
     __syncthreads();
     stage(s, r0, r1);
     __syncthreads();
+    if (ts && k == 0 && threadIdx.x == 0) ts[0] = gtimer();
     if (ld == 0) {
       for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) out(s, r, 0.0, pre(s, r));
       continue;
@@ -366,6 +372,7 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
         ring.consumed = ring.issued;
         return false;
       }
+      if (ts && k == 0 && c0 == 0 && threadIdx.x == 0) ts[1] = gtimer();
       ring.consumed++;
       const E *buf = reinterpret_cast<const E *>(ring.stage + (size_t)st * ring.bytes);
       int cn = min(rpc, r1 - r0 - c0);
@@ -377,6 +384,7 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
       issue_next(ring, op, cur);
     }
   }
+  if (ts && threadIdx.x == 0) ts[2] = gtimer();
   return true;
 }
 
@@ -384,7 +392,7 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
 // (buffer, ld, first row, rows); stage() runs once before the first chunk
 template <class Stage, class Consume>
 __device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &cur, unsigned *errflag, Stage stage,
-                                 Consume consume) {
+                                 Consume consume, unsigned long long *ts = nullptr) {
   while (cur.issued < ring.ns && issue_next(ring, op, cur)) {
   }
   if (op.nseg() == 0) return true;
@@ -394,6 +402,7 @@ __device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &c
   __syncthreads();
   stage();
   __syncthreads();
+  if (ts && threadIdx.x == 0) ts[0] = gtimer();
   int rpc = rows_per_chunk<double>(ring, ld);
   for (int c0 = 0; r0 + c0 < r1; c0 += rpc) {
     int st = (int)(ring.consumed % ring.ns);
@@ -406,12 +415,14 @@ __device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &c
       ring.consumed = ring.issued;
       return false;
     }
+    if (ts && c0 == 0 && threadIdx.x == 0) ts[1] = gtimer();
     ring.consumed++;
     consume(reinterpret_cast<const double *>(ring.stage + (size_t)st * ring.bytes), ld, r0 + c0,
             min(rpc, r1 - r0 - c0));
     __syncthreads();
     issue_next(ring, op, cur);
   }
+  if (ts && threadIdx.x == 0) ts[2] = gtimer();
   return true;
 }
 
@@ -489,6 +500,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   auto jump = [&](const double *v, int64_t l) { return ldcg(v + a.lam_qp[l]) - ldcg(v + a.lam_qm[l]); };
   Cursor cur;  // producer cursor of the phase about to run (possibly prefetched)
   double *ub_old = a.ub1, *ub_new = a.ub;  // B^T p of the previous / current iteration
+  unsigned long long *tsub = nullptr;  // sub-phase timestamps of the traced iteration (or null)
+  auto tsp = [&](int k) { return tsub ? tsub + 3 * k : nullptr; };
   // H phase: [F; Psi^T] u_s -> zb, tpi, with a staging functor for u_s
   auto h_phase = [&](auto stage_u) -> bool {
     return stream_phase<4>(ring, opH, cur, xs, errflag, [&](int s, int r0, int r1) { stage_u(s, r0, r1); },
@@ -496,7 +509,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                              int nbs = a.nb[s];
                              if (r < nbs) a.zb[a.bofs[s] + r] = v;
                              else a.tpi[a.pofs[s] + (r - nbs)] = v;
-                           });
+                           },
+                           NoPre(), tsp(0));
   };
   // coarse right-hand side c = sum_copies (g_p - tpi), chunk per CTA
   auto coarse_rhs = [&](bool with_g) {
@@ -517,7 +531,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                                for (int k = threadIdx.x; k < a.ldc; k += nthr)
                                  ccs[k] = k < a.nc ? ldcg(a.cc + k) : 0.0;
                              },
-                             [&](int, int r, double v, double2) { a.q[r] = v; });
+                             [&](int, int r, double v, double2) { a.q[r] = v; }, NoPre(), tsp(1));
     } else {
       // rows of (hi, lo) pairs, streamed as doubles (8 bytes per entry), computed in
       // double-FP32 arithmetic by warp-per-row dots
@@ -537,7 +551,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                                   double v = row_dot_df(rows + (int64_t)r * ld, xp, a.nc);
                                   if (lane == 0) a.q[row0 + r] = v;
                                 }
-                              });
+                              },
+                              tsp(1));
     }
   };
   // zf = zb - Psi q on the interface rows; out(global B index, zf, ub)
@@ -552,11 +567,12 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         [&](int s, int r) {
           int64_t q = a.bofs[s] + r;
           return make_double2(ldcg(a.zb + q), ldcg(ub_new + q));
-        });
+        },
+        tsp(2));
   };
   auto precond_rows = [&](auto val) -> bool {
     return stream_phase<4>(ring, opP, cur, xs, errflag, [&](int s, int, int) { gather(s, wd, 0, 0, false, val); },
-                           [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; });
+                           [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
   };
   auto sync = [&](unsigned long long *tr) { return grid_sync(a.bar, G, target, tr); };
   // z on the multipliers from the preconditioned interface values (or r itself)
@@ -641,7 +657,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
     double *rcur = a.r0, *rnxt = a.r1, *pcur = a.p0, *pnxt = a.p1;
     for (it = 1; it <= a.max_it; ++it) {
       unsigned long long *tr =
-          (a.trace && cta == 0 && it <= TRACE_IT) ? a.trace + (size_t)(it - 1) * 16 : nullptr;
+          (a.trace && cta == 0 && it <= TRACE_IT) ? a.trace + (size_t)(it - 1) * TRACE_SLOTS : nullptr;
+      tsub = tr ? tr + 16 : nullptr;
       if (tr && threadIdx.x == 0) tr[14] = gtimer();
       // ---------------- P1: p_new, u = B^T p_new, [F; Psi^T] u
       double beta = 0.0;
@@ -723,6 +740,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       t = ub_old; ub_old = ub_new; ub_new = t;
     }
   }
+  tsub = nullptr;
   // ================= R: recovery with v_b = g_b - B^T lambda  (H rows prefetched)
   if (!h_phase([&](int s, int, int) {
         int64_t kb = a.kofs[s] + a.ni[s];

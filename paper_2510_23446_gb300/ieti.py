@@ -40,7 +40,8 @@ class ieti_options(C.Structure):
                 ("cg_tol", C.c_double), ("cg_max_it", C.c_int32), ("outer_tol", C.c_double),
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
-                ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double)]
+                ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
+                ("predictor", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -88,7 +89,7 @@ lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
 lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
-lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
+lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
 lib.ieti_potrf_batched_noalloc.argtypes = lib.ieti_potrf_batched.argtypes
@@ -127,7 +128,7 @@ class Solver:
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, reluctivity=None, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1,
-                 factor="fp64", refactor="every", newton_tol=0.0):
+                 factor="fp64", refactor="every", newton_tol=0.0, predictor=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -168,6 +169,7 @@ class Solver:
         op.factor = FACTOR[factor] if isinstance(factor, str) else int(factor)
         op.refactor = REFACTOR[refactor] if isinstance(refactor, str) else int(refactor)
         op.newton_tol = float(newton_tol)
+        op.predictor = int(predictor)
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
@@ -225,8 +227,10 @@ class Solver:
     def pcg_phase_times(self, reset=False):
         work = np.zeros(6)
         wait = np.zeros(6)
-        self._check(lib.ieti_pcg_phase_times(self.ctx, work.ctypes.data, wait.ctypes.data, int(reset)))
-        return {"work_us": work.tolist(), "wait_us": wait.tolist()}
+        sub = np.zeros(12)
+        self._check(lib.ieti_pcg_phase_times(self.ctx, work.ctypes.data, wait.ctypes.data, sub.ctypes.data,
+                                             int(reset)))
+        return {"work_us": work.tolist(), "wait_us": wait.tolist(), "sub_us": sub.reshape(4, 3).tolist()}
 
     def step(self, j, raise_on_error=True):
         p, mem = _ptr(j)
