@@ -116,9 +116,10 @@ typedef struct {
   int32_t refactor;      /* IETI_REFACTOR_*: when the nonlinear patches and the coarse block are refactored */
   double newton_tol;     /* relative-update stop (0: residual test only) */
   /* Initial iterate of each step's refinement sweeps.  0: the previous state a^l.
-   * 1: the linear extrapolation in time 2 a^l - a^{l-1} (from the second step after
-   * setup or ieti_set_state on); the right-hand side M a^l + dt j^{l+1} and the stopping
-   * test are unchanged, so the step reaches the same outer_tol, usually in fewer sweeps. */
+   * 1: the linear extrapolation in time 2 a^l - a^{l-1}; 2: the quadratic one
+   * 3 a^l - 3 a^{l-1} + a^{l-2} (lower orders while fewer states exist after setup or
+   * ieti_set_state).  The right-hand side M a^l + dt j^{l+1} and the stopping test are
+   * unchanged, so the step reaches the same outer_tol, usually in fewer sweeps. */
   int32_t predictor;
 } ieti_options;
 

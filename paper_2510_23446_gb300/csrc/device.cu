@@ -499,11 +499,13 @@ __global__ void k_gather_kept(int64_t nk, const int64_t *glob, const double *a, 
   if (k < nk) out[k] = a[glob[k]];
 }
 
-// initial iterate of a step by linear extrapolation in time: a = 2 a^l - a^{l-1}
-// (eliminated entries are 0 in both and stay 0)
-__global__ void k_extrapolate(int64_t n, const double *a_l, const double *a_lm1, double *a) {
+// initial iterate of a step by extrapolation in time through the last two or three
+// states: a = 2 a^l - a^{l-1}, or a = 3 a^l - 3 a^{l-1} + a^{l-2} (a_lm2 non-null);
+// eliminated entries are 0 in all of them and stay 0
+__global__ void k_extrapolate(int64_t n, const double *a_l, const double *a_lm1, const double *a_lm2, double *a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) a[i] = 2.0 * a_l[i] - a_lm1[i];
+  if (i >= n) return;
+  a[i] = a_lm2 ? 3.0 * (a_l[i] - a_lm1[i]) + a_lm2[i] : 2.0 * a_l[i] - a_lm1[i];
 }
 
 // f = M x + dt * w * j[glob]   (warp per CSR row)
@@ -719,7 +721,8 @@ struct DevBuf {
 struct DeviceState {
   ieti_options opt{};
   double *a_prev = nullptr, *a_old = nullptr;  // a^{l-1} and a^l of the step in progress (predictor)
-  bool have_prev = false;                      // a_prev holds the state before the current one
+  double *a_prev2 = nullptr;                   // a^{l-2} (quadratic predictor)
+  int n_hist = 0;                              // previous states held: a_prev (1), and a_prev2 (2)
   int device = 0;
   cudaStream_t stream = nullptr;
   bool mixed = false;
@@ -1984,8 +1987,9 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   if (d->opt.predictor) {
     // keep a^l; with a^{l-1} known, start the sweeps from the extrapolated iterate
     CK(cudaMemcpyAsync(d->a_old, d->a, d->n_edges * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (d->have_prev) {
-      k_extrapolate<<<grid_for(d->n_edges, 256), 256, 0, st>>>(d->n_edges, d->a_old, d->a_prev, d->a);
+    if (d->n_hist > 0) {
+      const double *a2 = (d->opt.predictor == 2 && d->n_hist > 1) ? d->a_prev2 : nullptr;
+      k_extrapolate<<<grid_for(d->n_edges, 256), 256, 0, st>>>(d->n_edges, d->a_old, d->a_prev, a2, d->a);
       k_gather_kept<<<grid_for(NK, 256), 256, 0, st>>>(NK, d->kglob, d->a, d->ka);
       d->nlaunch += 2;
     }
@@ -2062,8 +2066,10 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   }
   CK(cudaGetLastError());
   if (d->opt.predictor) {
-    std::swap(d->a_prev, d->a_old);  // a^l becomes the previous state
-    d->have_prev = true;
+    // a^l becomes the previous state, a^{l-1} the one before (quadratic predictor)
+    if (d->opt.predictor == 2) std::swap(d->a_prev2, d->a_prev);
+    std::swap(d->a_prev, d->a_old);
+    d->n_hist = std::min(d->n_hist + 1, d->opt.predictor);
   }
   if (stats) {
     stats->refactors = d->step_refactors;
@@ -2353,6 +2359,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   if ((rc = dalloc(d, &d->a, hs.n_edges, err)) || (rc = dalloc(d, &d->j, hs.n_edges, err)) ||
       (opt.predictor && ((rc = dalloc(d, &d->a_prev, hs.n_edges, err)) ||
                          (rc = dalloc(d, &d->a_old, hs.n_edges, err)))) ||
+      (opt.predictor == 2 && (rc = dalloc(d, &d->a_prev2, hs.n_edges, err))) ||
       (rc = dalloc(d, &d->rglob, hs.n_edges, err)) ||
       (rc = dalloc(d, &d->kf, d->NK, err)) || (rc = dalloc(d, &d->kx, d->NK, err)) ||
       (rc = dalloc(d, &d->kr, d->NK, err)) || (rc = dalloc(d, &d->kz, d->NK, err)) ||
@@ -2875,7 +2882,7 @@ int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std:
   CK(cudaMemsetAsync(d->a, 0, d->n_edges * sizeof(double), d->stream));
   k_owner_add<<<grid_for(d->NK, 256), 256, 0, d->stream>>>(d->NK, d->kglob, d->kown, d->kx, d->a);
   CK(cudaStreamSynchronize(d->stream));
-  d->have_prev = false;  // no history for the extrapolation of the next step
+  d->n_hist = 0;  // no history for the extrapolation of the next step
   return IETI_OK;
 }
 

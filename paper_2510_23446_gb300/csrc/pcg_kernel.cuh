@@ -293,10 +293,14 @@ struct Cursor {
   int seg = 0, chunk = 0, issued = 0;
 };
 
+// whole rows per chunk; from 32 rows on a multiple of 32, so that the 8 warps of a
+// CTA get the same number of 4-row groups from every chunk
 template <class E>
 __device__ __forceinline__ int rows_per_chunk(const Ring &ring, int ld) {
   unsigned rb = (unsigned)ld * sizeof(E);
-  return rb == 0 ? 1 << 30 : max(1, (int)(ring.bytes / rb));
+  if (rb == 0) return 1 << 30;
+  int r = (int)(ring.bytes / rb);
+  return r >= 32 ? r & ~31 : max(1, r);
 }
 
 // issue the next chunk of `op` (if any) into the next ring stage; returns false at the end

@@ -235,12 +235,13 @@ def test_pcg_modes_agree(ieti, mode):
 
 @pytest.mark.parametrize("name", ["c1", "ragged_p23"])
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_predictor_steps_match_oracle(ieti, name, mode):
-    """Sweeps started from the extrapolated iterate 2 a^l - a^{l-1}: same right-hand
-    side and stopping test, so every step still matches the oracle's solve."""
+@pytest.mark.parametrize("predictor", [1, 2])
+def test_predictor_steps_match_oracle(ieti, name, mode, predictor):
+    """Sweeps started from the iterate extrapolated in time (linear or quadratic): same
+    right-hand side and stopping test, so every step still matches the oracle's solve."""
     steps = 4
     prob, op, ref = oracle_run(name, steps)
-    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", predictor=1, **OPTS[mode])
+    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", predictor=predictor, **OPTS[mode])
     for l, (a, b) in enumerate(zip(ref, got)):
         err = np.linalg.norm(a - b) / np.linalg.norm(a)
         assert err <= TOL[mode], (name, mode, l, err, stats[l])
@@ -251,15 +252,15 @@ def test_predictor_history_reset_by_set_state(ieti):
     """A resumed context has no a^{l-1}: its first step starts from a^l and still
     reaches the state of the uninterrupted run within the tolerance."""
     prob = CASES["ragged_p23"]()
-    S = ieti.Solver.from_problem(prob, device=0, predictor=1, **OPTS["fp64"])
+    S = ieti.Solver.from_problem(prob, device=0, predictor=2, **OPTS["fp64"])
     j = S.load_vector(prob.coil)
-    for _ in range(2):
+    for _ in range(3):
         S.step(j)
     mid = S.solution().copy()
     S.step(j)
     end = S.solution().copy()
     S.close()
-    R = ieti.Solver.from_problem(prob, device=0, predictor=1, **OPTS["fp64"])
+    R = ieti.Solver.from_problem(prob, device=0, predictor=2, **OPTS["fp64"])
     R.set_state(mid)
     R.step(j)
     assert np.linalg.norm(R.solution() - end) <= TOL["fp64"] * np.linalg.norm(end)

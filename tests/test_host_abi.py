@@ -103,6 +103,7 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     dict(precision="fp64", factor="tf32x3"),   # the FP64 mode factors in FP64
     dict(precision="mixed", factor=7),
     dict(precision="mixed", pcg_mode=3),
+    dict(precision="fp64", predictor=3),
 ])
 def test_invalid_options_return_codes(ieti, kw):
     prob = make_problem("c1")
