@@ -2111,6 +2111,16 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   std::vector<int64_t> hkofs(np_ + 1, 0), hdoff(np_ + 1, 0), hig(np_ + 1, 0), hgt(np_ + 1, 0), hh(np_ + 1, 0),
       hq(np_ + 1, 0), hp(np_ + 1, 0), hbofs(np_ + 1, 0), hpofs(np_ + 1, 0);
   std::vector<int32_t> hldi(np_), hldg(np_);
+  // leading dimension of an operator block with n columns: whole 16-byte units, an
+  // odd number of them, so that lanes reading different rows at the same column hit
+  // distinct shared-memory banks (the row kernels of the dual-primal sweep)
+  const int esz_op = d->mixed ? 4 : 8;
+  auto op_ld = [&](int n) {
+    if (n <= 0) return 0;
+    int l = (n + 3) / 4 * 4;
+    if ((l * esz_op / 16) % 2 == 0) l += 16 / esz_op;
+    return l;
+  };
   for (int s = 0; s < np_; ++s) {
     const Patch &pt = hs.patches[s];
     hni[s] = pt.ni;
@@ -2120,11 +2130,11 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     hnn[s] = (hn[s] + pt.nb + pt.ni + 3) / 4 * 4;  // augmented [i b p | b' | i'], 16-byte rows (zero padded)
     hkofs[s + 1] = hkofs[s] + hn[s];
     hdoff[s + 1] = hdoff[s] + (int64_t)hnn[s] * hnn[s];
-    hldi[s] = (pt.ni + 3) / 4 * 4;
-    hldg[s] = (pt.nb + pt.np + 3) / 4 * 4;
+    hldi[s] = op_ld(pt.ni);
+    hldg[s] = op_ld(pt.nb + pt.np);
     hig[s + 1] = hig[s] + (int64_t)hn[s] * hldi[s];
     hgt[s + 1] = hgt[s] + (int64_t)pt.ni * hldg[s];
-    int ldb_s = (pt.nb + 3) / 4 * 4, ldp_s = (pt.np + 3) / 4 * 4;  // 16-byte aligned rows
+    int ldb_s = op_ld(pt.nb), ldp_s = op_ld(pt.np);
     hldb[s] = ldb_s;
     hldp[s] = ldp_s;
     hh[s + 1] = hh[s] + (int64_t)(pt.nb + pt.np) * ldb_s;
@@ -2715,7 +2725,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     for (int s = 0; s < np_; ++s) ldmax = std::max({ldmax, hldb[s], hldp[s], hldi[s], hldg[s]});
     // shared memory: staged x vector, then n_stages TMA stages (whole rows per stage)
     size_t xs_bytes = (std::max((size_t)ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
-    size_t budget = 220 * 1024, row_max = std::max((size_t)ldmax * esz, (size_t)d->ldc * sizeof(double));
+    // dynamic shared memory budget: 227 KB per CTA minus the kernel's static arrays
+    size_t budget = 212 * 1024, row_max = std::max((size_t)ldmax * esz, (size_t)d->ldc * sizeof(double));
     if (xs_bytes + 2 * row_max > budget) {
       err = "a patch block is too wide for the shared-memory staging of the dual-primal kernel";
       return fail(IETI_ERR_TOO_LARGE);

@@ -252,6 +252,42 @@ __device__ __forceinline__ void rows_gemv(const T *A, int ld, int r0, int r1, co
   }
 }
 
+constexpr int RPC_MAX = 512;  // operator rows per ring chunk at most (their results are staged)
+
+// y[r] = A_r . x for the rows of a chunk in shared memory (row-major, leading
+// dimension ld = an odd number of 16-byte units, zero-padded), G lanes per row:
+// lane j of a row group sums the 16-byte units j, j + G, ...; the G partial sums are
+// combined by log2(G) shuffles.  With the odd row pitch, the eight lanes of a
+// shared-memory wavefront read distinct banks both for G = 1 (eight rows) and for
+// G >= 8 (one row).
+template <class T, int G>
+__device__ __noinline__ void chunk_rows_g(const T *A, int ld, int cn, const T *xs, T *y) {
+  using V = typename V16<T>::t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sub = lane / G, j = lane % G;
+  const int nv = ld / V16<T>::n;
+  const V *x = reinterpret_cast<const V *>(xs);
+  for (int r0 = warp * (32 / G); r0 < cn; r0 += nw * (32 / G)) {
+    const int r = r0 + sub;
+    T s = 0;
+    if (r < cn) {
+      const V *row = reinterpret_cast<const V *>(A + (int64_t)r * ld);
+      T s0 = 0, s1 = 0;
+      int k = j;
+      for (; k + G < nv; k += 2 * G) {
+        V a = row[k], b = row[k + G], xa = x[k], xb = x[k + G];
+        s0 += dot16(a, xa);
+        s1 += dot16(b, xb);
+      }
+      if (k < nv) s0 += dot16(row[k], x[k]);
+      s = s0 + s1;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (j == 0 && r < cn) y[r] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // TMA ring.  The operator rows a CTA multiplies in a phase are fixed by the static
 // partition, independent of the iteration's vectors, so they are streamed HBM ->
@@ -299,7 +335,7 @@ template <class E>
 __device__ __forceinline__ int rows_per_chunk(const Ring &ring, int ld) {
   unsigned rb = (unsigned)ld * sizeof(E);
   if (rb == 0) return 1 << 30;
-  int r = (int)(ring.bytes / rb);
+  int r = min((int)(ring.bytes / rb), RPC_MAX);
   return r >= 32 ? r & ~31 : max(1, r);
 }
 
@@ -347,7 +383,7 @@ __device__ __forceinline__ Cursor prefetch(Ring &ring, const OpRows<E> &op) {
 // stage(s, r0, r1) runs with every thread of the CTA; out(s, r, value, pre) per row.
 // Returns false (after setting the error flag and draining) when a wait timed out.
 template <int RW, class E, class Stage, class Out, class Pre = NoPre>
-__device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, unsigned *errflag,
+__device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, E *y, unsigned *errflag,
                              Stage stage, Out out, Pre pre = Pre(), unsigned long long *ts = nullptr) {
   while (cur.issued - 0 < ring.ns && issue_next(ring, op, cur)) {
   }
@@ -379,13 +415,29 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
       if (ts && k == 0 && c0 == 0 && threadIdx.x == 0) ts[1] = gtimer();
       ring.consumed++;
       const E *buf = reinterpret_cast<const E *>(ring.stage + (size_t)st * ring.bytes);
-      int cn = min(rpc, r1 - r0 - c0);
-      int base_r = r0 + c0;
-      rows_gemv<RW, false>(buf, ld, 0, cn, xs,
-                           [&](int r, double v, double2 pv) { out(s, base_r + r, v, pv); },
-                           [&](int r) { return pre(s, base_r + r); });
-      __syncthreads();  // every warp is done with this stage
-      issue_next(ring, op, cur);
+      const int cn = min(rpc, r1 - r0 - c0), base_r = r0 + c0;
+      // row kernel per row length and operator precision (measured on the c2
+      // workload): short rows one per lane; long FP64 rows 8 lanes per row; long
+      // FP32 rows, and chunks of fewer than 16 rows, RW rows per warp
+      const int nv = ld / V16<E>::n;
+      const int split = nv <= 32 ? 1 : (sizeof(E) == 8 && cn >= 16 ? 8 : 0);
+      if (split) {
+        // row results into y (two buffers: the epilogues of the previous chunk may
+        // still read the other one), then one thread per row
+        E *yc = y + (ring.consumed & 1ull) * RPC_MAX;
+        if (split == 1) chunk_rows_g<E, 1>(buf, ld, cn, xs, yc);
+        else chunk_rows_g<E, 8>(buf, ld, cn, xs, yc);
+        __syncthreads();  // every warp is done with this stage; yc is complete
+        issue_next(ring, op, cur);
+        for (int r = threadIdx.x; r < cn; r += blockDim.x) out(s, base_r + r, (double)yc[r], pre(s, base_r + r));
+      } else {
+        // long rows: RW rows per warp, lane i of the group runs row i's epilogue
+        rows_gemv<RW, false>(buf, ld, 0, cn, xs,
+                             [&](int r, double v, double2 pv) { out(s, base_r + r, v, pv); },
+                             [&](int r) { return pre(s, base_r + r); });
+        __syncthreads();  // every warp is done with this stage
+        issue_next(ring, op, cur);
+      }
     }
   }
   if (ts && threadIdx.x == 0) ts[2] = gtimer();
@@ -434,6 +486,7 @@ template <class T>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constant__ PcgArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sh[32];
+  __shared__ __align__(16) T ybuf[2 * RPC_MAX];  // row results of the last two chunks
   __shared__ __align__(8) uint64_t ring_bar[NS_MAX];
   T *xs = reinterpret_cast<T *>(smem_raw);
   double *ccs = reinterpret_cast<double *>(smem_raw);
@@ -508,7 +561,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   auto tsp = [&](int k) { return tsub ? tsub + 3 * k : nullptr; };
   // H phase: [F; Psi^T] u_s -> zb, tpi, with a staging functor for u_s
   auto h_phase = [&](auto stage_u) -> bool {
-    return stream_phase<4>(ring, opH, cur, xs, errflag, [&](int s, int r0, int r1) { stage_u(s, r0, r1); },
+    return stream_phase<4>(ring, opH, cur, xs, ybuf, errflag, [&](int s, int r0, int r1) { stage_u(s, r0, r1); },
                            [&](int s, int r, double v, double2) {
                              int nbs = a.nb[s];
                              if (r < nbs) a.zb[a.bofs[s] + r] = v;
@@ -530,7 +583,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   };
   auto coarse_solve = [&]() -> bool {
     if constexpr (sizeof(T) == 8) {
-      return stream_phase<1>(ring, opS, cur, ccs, errflag,
+      return stream_phase<1>(ring, opS, cur, ccs, ybuf, errflag,
                              [&](int, int, int) {
                                for (int k = threadIdx.x; k < a.ldc; k += nthr)
                                  ccs[k] = k < a.nc ? ldcg(a.cc + k) : 0.0;
@@ -562,7 +615,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   // zf = zb - Psi q on the interface rows; out(global B index, zf, ub)
   auto psi_phase = [&](auto out) -> bool {
     return stream_phase<4>(
-        ring, opQ, cur, xs, errflag,
+        ring, opQ, cur, xs, ybuf, errflag,
         [&](int s, int, int) {
           const int32_t *pcs = a.pc + a.pofs[s];
           stage(a.np[s], a.ldp[s], [&](int k) { return ldcg(a.q + pcs[k]); });
@@ -575,7 +628,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         tsp(2));
   };
   auto precond_rows = [&](auto val) -> bool {
-    return stream_phase<4>(ring, opP, cur, xs, errflag, [&](int s, int, int) { gather(s, wd, 0, 0, false, val); },
+    return stream_phase<4>(ring, opP, cur, xs, ybuf, errflag, [&](int s, int, int) { gather(s, wd, 0, 0, false, val); },
                            [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
   };
   auto sync = [&](unsigned long long *tr) { return grid_sync(a.bar, G, target, tr); };
@@ -598,7 +651,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
 
   // ================= C: interior condensation  kg = [W_ii^{-1} f_i ; f_[bp] - G f_i]
   cur = prefetch(ring, opIG);
-  if (!stream_phase<4>(ring, opIG, cur, xs, errflag,
+  if (!stream_phase<4>(ring, opIG, cur, xs, ybuf, errflag,
                        [&](int s, int, int) {
                          int64_t ko = a.kofs[s];
                          stage(a.ni[s], a.ldi[s], [&](int k) { return a.rhs[ko + k]; });
@@ -783,7 +836,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   cur = prefetch(ring, opGT);
   if (!sync(nullptr)) return;
   // R5: a_i = z_i - G^T a_[bp]
-  if (!stream_phase<4>(ring, opGT, cur, xs, errflag,
+  if (!stream_phase<4>(ring, opGT, cur, xs, ybuf, errflag,
                        [&](int s, int, int) {
                          int64_t ko = a.kofs[s] + a.ni[s];
                          stage(a.nb[s] + a.np[s], a.ldg[s], [&](int k) { return ldcg(a.kx + ko + k); });
