@@ -210,6 +210,21 @@ int ieti_get_info(const ieti_ctx *ctx, ieti_info *info);
  * buffer of ieti_num_dofs() doubles.  Works on host-only contexts. */
 int ieti_load_vector(const ieti_ctx *ctx, const ieti_coil *coil, double *j_out);
 
+/* Quadrature points of the assembly, for sources given as functions of space
+ * (Sec. 2.2 load vector (j_i)_k = <J, w_k> with a general J): the physical coordinates
+ * (x, y, z) of every point, patch after patch, within a patch element after element
+ * (x fastest) and within an element the (p_d + 2)^3 Gauss points (x fastest).
+ * Two-call protocol: with xyz NULL only *n_points is written; otherwise xyz holds
+ * 3 * (*n_points) doubles (host) and *n_points must be at least the count.  Works on
+ * host-only contexts.  Errors: INVALID_ARG. */
+int ieti_quad_points(const ieti_ctx *ctx, double *xyz, int64_t *n_points);
+
+/* Load vector j_k = <J, w_k> of a current density J sampled at the quadrature points
+ * of ieti_quad_points (J_xyz: 3 doubles per point, same order; host), assembled into
+ * the global numbering (j_out: ieti_num_dofs() doubles, host).  For J = curl T of a
+ * coil, ieti_load_vector is the exact alternative.  Works on host-only contexts. */
+int ieti_load_vector_points(const ieti_ctx *ctx, const double *J_xyz, double *j_out);
+
 /* Host-side classification (works on host-only contexts): per global DOF,
  * cls[g] = 0 (e), 1 (p), 2 (r) and tree[g] = 1 for tree edges (Sec. 3).  Either
  * pointer may be NULL. */

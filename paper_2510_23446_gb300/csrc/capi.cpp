@@ -101,6 +101,31 @@ int ieti_load_vector(const ieti_ctx *ctx, const ieti_coil *coil, double *j_out) 
   return IETI_OK;
 }
 
+int ieti_quad_points(const ieti_ctx *ctx, double *xyz, int64_t *n_points) {
+  if (!ctx || !n_points) return IETI_ERR_INVALID_ARG;
+  try {
+    int64_t n = ctx->hs.quad_point_count();
+    if (xyz) {
+      if (*n_points < n) return IETI_ERR_INVALID_ARG;
+      ctx->hs.quad_points(xyz);
+    }
+    *n_points = n;
+  } catch (...) {
+    return IETI_ERR_OOM;
+  }
+  return IETI_OK;
+}
+
+int ieti_load_vector_points(const ieti_ctx *ctx, const double *J_xyz, double *j_out) {
+  if (!ctx || !J_xyz || !j_out) return IETI_ERR_INVALID_ARG;
+  try {
+    ctx->hs.points_load(J_xyz, j_out);
+  } catch (...) {
+    return IETI_ERR_OOM;
+  }
+  return IETI_OK;
+}
+
 int ieti_dof_classes(const ieti_ctx *ctx, int8_t *cls, int8_t *tree) {
   if (!ctx) return IETI_ERR_INVALID_ARG;
   for (int64_t g = 0; g < ctx->hs.n_edges; ++g) {

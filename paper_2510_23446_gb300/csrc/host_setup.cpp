@@ -576,6 +576,71 @@ void HostSetup::coil_load(const ieti_coil &coil, double *out) const {
     for (int l = 0; l < patches[s].n_dofs; ++l) out[patches[s].l2g[l]] += loc[s][l];
 }
 
+// Quadrature points of the assembly: per patch its elements (x fastest) and per
+// element its (p_d + 2)^3 Gauss points (x fastest), the order of for_each_point.
+int64_t HostSetup::quad_point_count(std::vector<int64_t> *patch_off) const {
+  int np = n_patches();
+  if (patch_off) patch_off->assign(np + 1, 0);
+  int64_t n = 0;
+  for (int s = 0; s < np; ++s) {
+    const Patch &pt = patches[s];
+    n += (int64_t)pt.ne[0] * pt.ne[1] * pt.ne[2] * (pt.p[0] + 2) * (pt.p[1] + 2) * (pt.p[2] + 2);
+    if (patch_off) (*patch_off)[s + 1] = n;
+  }
+  return n;
+}
+
+void HostSetup::quad_points(double *xyz) const {
+  std::vector<int64_t> off;
+  quad_point_count(&off);
+  parallel_for(n_patches(), threads, [&](int s) {
+    const Patch &pt = patches[s];
+    DirData dd[3];
+    for (int d = 0; d < 3; ++d) {
+      int slab = d == 0 ? pt.a : (d == 1 ? pt.b : pt.c);
+      dd[d] = direction_data(knots[d][slab], pt.p[d], pt.ne[d]);
+    }
+    int64_t k = off[s];
+    for_each_point(*this, pt, s, dd, [&](int, int, const int *, const double *F, double, double, const double *,
+                                         const double *) {
+      xyz[3 * k] = F[0];
+      xyz[3 * k + 1] = F[1];
+      xyz[3 * k + 2] = F[2];
+      ++k;
+    });
+  });
+}
+
+// j_k = <J, w_k> = sum over points of weight * det DF * J(x_q) . w_k(x_q)
+void HostSetup::points_load(const double *J, double *out) const {
+  std::vector<int64_t> off;
+  quad_point_count(&off);
+  int np = n_patches();
+  std::vector<std::vector<double>> loc(np);
+  parallel_for(np, threads, [&](int s) {
+    const Patch &pt = patches[s];
+    DirData dd[3];
+    for (int d = 0; d < 3; ++d) {
+      int slab = d == 0 ? pt.a : (d == 1 ? pt.b : pt.c);
+      dd[d] = direction_data(knots[d][slab], pt.p[d], pt.ne[d]);
+    }
+    loc[s].assign(pt.n_dofs, 0.0);
+    int64_t k = off[s];
+    for_each_point(*this, pt, s, dd, [&](int, int nloc, const int *lid, const double *, double det, double w,
+                                         const double *, const double *V) {
+      const double *Jq = J + 3 * k;
+      ++k;
+      double c = w * det;
+      if (Jq[0] == 0.0 && Jq[1] == 0.0 && Jq[2] == 0.0) return;
+      for (int a = 0; a < nloc; ++a)
+        loc[s][lid[a]] += c * (Jq[0] * V[3 * a] + Jq[1] * V[3 * a + 1] + Jq[2] * V[3 * a + 2]);
+    });
+  });
+  std::fill(out, out + n_edges, 0.0);
+  for (int s = 0; s < np; ++s)
+    for (int l = 0; l < patches[s].n_dofs; ++l) out[patches[s].l2g[l]] += loc[s][l];
+}
+
 // ----------------------------------------------------------------- regions
 // any(mask) over inclusive element boxes, via a 3-D prefix sum
 struct Prefix3 {

@@ -95,6 +95,11 @@ struct HostSetup {
   int n_patches() const { return P[0] * P[1] * P[2]; }
   // load vector of a coil potential, global numbering
   void coil_load(const ieti_coil &coil, double *out) const;
+  // quadrature points of the assembly (patch, element, point order): count, offsets
+  // per patch, physical coordinates; load vector of a field sampled at them
+  int64_t quad_point_count(std::vector<int64_t> *patch_off = nullptr) const;
+  void quad_points(double *xyz) const;
+  void points_load(const double *J, double *out) const;
 
  private:
   int validate(const ieti_problem *pr, std::string &err);

@@ -83,6 +83,8 @@ lib.ieti_num_dofs.restype = C.c_int64
 lib.ieti_get_info.argtypes = [_ctx, C.POINTER(ieti_info)]
 lib.ieti_load_vector.argtypes = [_ctx, C.POINTER(ieti_coil), C.c_void_p]
 lib.ieti_dof_classes.argtypes = [_ctx, C.c_void_p, C.c_void_p]
+lib.ieti_quad_points.argtypes = [_ctx, C.c_void_p, C.POINTER(C.c_int64)]
+lib.ieti_load_vector_points.argtypes = [_ctx, C.c_void_p, C.c_void_p]
 lib.ieti_patch_csr.argtypes = [_ctx, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                C.c_void_p, C.c_void_p, C.c_void_p]
 lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
@@ -103,7 +105,8 @@ lib.ieti_destroy.restype = None
 EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", "ieti_load_vector",
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
-            "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32"]
+            "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32",
+            "ieti_quad_points", "ieti_load_vector_points"]
 
 
 class IetiError(RuntimeError):
@@ -193,6 +196,19 @@ class Solver:
         self._check(lib.ieti_get_info(self.ctx, C.byref(inf)))
         out = {k: getattr(inf, k) for k, _ in ieti_info._fields_}
         out["t_refactor_ms"] = list(out["t_refactor_ms"])
+        return out
+
+    def quad_points(self):
+        n = C.c_int64(0)
+        self._check(lib.ieti_quad_points(self.ctx, None, C.byref(n)))
+        xyz = np.zeros((n.value, 3))
+        self._check(lib.ieti_quad_points(self.ctx, xyz.ctypes.data, C.byref(n)))
+        return xyz
+
+    def load_vector_points(self, J):
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        out = np.zeros(self.n)
+        self._check(lib.ieti_load_vector_points(self.ctx, J.ctypes.data, out.ctypes.data))
         return out
 
     def load_vector(self, coil):

@@ -44,6 +44,11 @@ CASES = {
     "all_insulating_but_one": lambda: small_problem(P=(3, 3, 2), n_el=((2, 3, 2), (3, 2, 2), (2, 2)),
                                                     degree=((2, 1, 2), (1, 2, 2), (2, 1)),
                                                     conductor=((0.34, 0.66), (0.34, 0.66), (0.0, 0.5))),
+    # smaller members of the 512-patch family (per-patch log-uniform sigma up to 1e4 in a
+    # ball, nu in [0.5, 2]) and of the 343-patch family (uneven slabs, p in {2, 3} per
+    # slab, random conductors with sigma = 1e3), from the same generators
+    "c3_family": lambda: make_problem("c3", patches_per_dir=3, n_el=2),
+    "c4_family": lambda: make_problem("c4", patches_per_dir=3, el_range=(2, 3)),
 }
 
 _ORACLE = {}

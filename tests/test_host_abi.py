@@ -125,3 +125,23 @@ def test_potrf_f32_rejects_bad_arguments_without_a_device(ieti):
     rc = ieti.lib.ieti_potrf_batched_f32(1, C.c_void_p(16), z.ctypes.data, n.ctypes.data, ld.ctypes.data,
                                          n.ctypes.data, 9, st.ctypes.data, None)
     assert rc == -1
+
+
+@pytest.mark.parametrize("name", ["uneven", "c3_slice"])
+def test_load_vector_from_points_matches_oracle(ieti, name):
+    """<J, w_k> from J sampled at the library's quadrature points equals the oracle's
+    quadrature of the same analytic field (curved patches, uneven degrees)."""
+    from oracle.manufactured import A_star, FieldEval
+    prob = CASES[name]()
+    op = OracleProblem(prob)
+    S = ieti.Solver.from_problem(prob, device=-1)
+    xyz = S.quad_points()
+    assert xyz.shape[0] == sum(int(np.prod(prob.patch_n_el(s))) * int(np.prod(np.asarray(prob.patch_degree(s)) + 2))
+                               for s in range(prob.n_patches))
+    field = lambda x: A_star(x) * (1.0 + x[..., :1])      # smooth, direction-dependent
+    got = S.load_vector_points(field(xyz))
+    ref = FieldEval(prob, op.asm).load(field)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    # the points lie in the unit cube and sample every element
+    assert xyz.min() > 0.0 and xyz.max() < 1.0
+    S.close()

@@ -207,9 +207,11 @@ def config2(seed=0, n_steps=50) -> Problem:
         dt=1e-3, n_steps=n_steps, perturb=0.05, coil=default_coil(1e2), seed=seed)
 
 
-def config3(seed=0, n_steps=100) -> Problem:
-    """512 p=2 patches of 6^3 elements; log-uniform sigma in a ball of radius 0.35."""
-    P = (8, 8, 8)
+def config3(seed=0, n_steps=100, patches_per_dir=8, n_el=6) -> Problem:
+    """512 p=2 patches of 6^3 elements; log-uniform sigma in a ball of radius 0.35.
+    (patches_per_dir, n_el) give smaller members of the same family."""
+    k = int(patches_per_dir)
+    P = (k, k, k)
     rng = np.random.default_rng(seed + 1000)
     n = P[0] * P[1] * P[2]
     logs = rng.uniform(0.0, 4.0, size=n)
@@ -219,20 +221,22 @@ def config3(seed=0, n_steps=100) -> Problem:
         _, ctr = _patch_center_inside(P, s, 0.0, 1.0)
         return 10.0 ** logs[s] if np.linalg.norm(ctr - 0.5) < 0.35 else 0.0
     return build_problem(
-        "c3_512x6^3_p2", P, [[6] * 8] * 3, [[2] * 8] * 3, sigma_fn=sig,
+        f"c3_{n}x{n_el}^3_p2", P, [[n_el] * k] * 3, [[2] * k] * 3, sigma_fn=sig,
         nu_fn=lambda s, C: nus[s], dt=1e-3, n_steps=n_steps, perturb=0.05,
         coil=default_coil(1.0), seed=seed)
 
 
-def config4(seed=0, n_steps=100) -> Problem:
-    """343 patches, per-slab elements in {4..12} and per-slab degrees in {2,3}."""
-    P = (7, 7, 7)
+def config4(seed=0, n_steps=100, patches_per_dir=7, el_range=(4, 12)) -> Problem:
+    """343 patches, per-slab elements in {4..12} and per-slab degrees in {2,3}.
+    (patches_per_dir, el_range) give smaller members of the same family."""
+    k = int(patches_per_dir)
+    P = (k, k, k)
     rng = np.random.default_rng(seed + 2000)
-    n_el = [rng.integers(4, 13, size=7) for _ in range(3)]
-    deg = [rng.integers(2, 4, size=7) for _ in range(3)]
-    cond = rng.uniform(size=343) < 0.5
+    n_el = [rng.integers(el_range[0], el_range[1] + 1, size=k) for _ in range(3)]
+    deg = [rng.integers(2, 4, size=k) for _ in range(3)]
+    cond = rng.uniform(size=k ** 3) < 0.5
     return build_problem(
-        "c4_343_uneven", P, n_el, deg, sigma_fn=lambda s, C: 1e3 if cond[s] else 0.0,
+        f"c4_{k ** 3}_uneven", P, n_el, deg, sigma_fn=lambda s, C: 1e3 if cond[s] else 0.0,
         nu_fn=lambda s, C: 1.0, dt=1e-3, n_steps=n_steps, perturb=0.05,
         coil=default_coil(1.0), seed=seed)
 
