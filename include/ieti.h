@@ -65,6 +65,9 @@ extern "C" {
 #define IETI_FACTOR_TF32X3 2  /* FP32 panels, trailing updates on the tensor cores as three TF32 products
                                  (hi*hi + hi*lo + lo*hi, FP32 accumulation): FP32-class accuracy */
 #define IETI_FACTOR_TF32 3    /* as TF32X3 with one TF32 product (ablation: 11-bit operands) */
+#define IETI_FACTOR_BF16X3 4  /* as TF32X3 with BF16 hi and lo planes (kind::f16 MMAs, FP32 accumulation):
+                                 about 16 significant bits per operand (ablation) */
+#define IETI_FACTOR_BF16 5    /* one BF16 product (ablation: 8-bit operands) */
 
 /* Dirichlet preconditioner variants (Sec. 4 uses it "without scaling"; Sec. 5 asks for scaling). */
 #define IETI_PRECOND_NONE 0
@@ -121,6 +124,17 @@ typedef struct {
    * ieti_set_state).  The right-hand side M a^l + dt j^{l+1} and the stopping test are
    * unchanged, so the step reaches the same outer_tol, usually in fewer sweeps. */
   int32_t predictor;
+  /* Schedule of the persistent dual-primal kernel (pcg_mode 0): CTAs per SM, TMA
+   * ring stages and bytes per stage.  0: the rule (one CTA per SM, three stages of
+   * at most 64 KB).  1: autotune at setup: every feasible schedule of a fixed
+   * candidate list runs a few PCG iterations on a synthetic right-hand side and the
+   * fastest is kept (results do not depend on the schedule beyond rounding order).
+   * tune_cache (NULL: none) names a text file of earlier choices keyed by device name,
+   * precision and problem sizes: a matching entry is used without timing, a new
+   * choice is added to it.  An unreadable or malformed cache is ignored (tuned
+   * afresh); a failed write leaves setup successful (ieti_info.pcg_sched_source). */
+  int32_t autotune;
+  const char *tune_cache;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -172,6 +186,13 @@ typedef struct {
   double t_refactor_ms[4];   /* with options.profile = 1: device time of all refactorizations since setup in
                                 the tangent assembly, the local factorization + extraction, the coarse update,
                                 and in total (CUDA events) */
+  int32_t pcg_grid;          /* CTAs of the persistent dual-primal kernel */
+  int32_t pcg_stages;        /* TMA ring stages per CTA */
+  int32_t pcg_stage_bytes;   /* bytes per stage */
+  int32_t pcg_sched_source;  /* 0: rule, 1: autotuned, 2: autotuned and written to tune_cache, 3: from tune_cache */
+  int32_t tune_candidates;   /* schedules timed by the autotuner */
+  double tune_ms;            /* host time of the autotuning */
+  double tune_us_per_it[2];  /* measured time per PCG iteration: the rule's schedule, the chosen one */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
@@ -280,12 +301,14 @@ int ieti_potrf_batched(int32_t batch, double *base_dev, const int64_t *offsets, 
                        const int32_t *n_pivots, int32_t *status_out, void *stream);
 
 /* The FP32 variant of ieti_potrf_batched in the arithmetic `factor` (IETI_FACTOR_FP32,
- * IETI_FACTOR_TF32X3 or IETI_FACTOR_TF32).  Matrix b is row-major n[b] x n[b] with
+ * IETI_FACTOR_TF32X3, IETI_FACTOR_TF32, IETI_FACTOR_BF16X3 or IETI_FACTOR_BF16: the
+ * data stays FP32, only the trailing-update operands are rounded).  Matrix b is
+ * row-major n[b] x n[b] with
  * leading dimension ld[b] >= n[b] at base_dev + offsets[b] (floats).  The tensor-core
  * variants need 16-byte rows and bases: ld[b] and offsets[b] multiples of 4.  Same
  * results, status and ownership rules as ieti_potrf_batched; the error is that of
- * the FP32 (or TF32) arithmetic.  Allocates its scratch (tile list, the panel buffer
- * of 2 x sum(n) x 256 floats) per call.  Returns 0, INVALID_ARG (also for a bad
+ * the FP32 (or TF32 / BF16) arithmetic.  Allocates its scratch (tile list, the panel
+ * buffer of 2 x sum(n) x 256 operand words) per call.  Returns 0, INVALID_ARG (also for a bad
  * factor or misaligned ld / offsets), CUDA or OOM. */
 int ieti_potrf_batched_f32(int32_t batch, float *base_dev, const int64_t *offsets, const int32_t *n,
                            const int32_t *ld, const int32_t *n_pivots, int32_t factor, int32_t *status_out,

@@ -28,10 +28,11 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->device < -1) { err = "device must be >= -1"; return IETI_ERR_INVALID_ARG; }
   if (o->pcg_mode != 0 && o->pcg_mode != 1) { err = "pcg_mode must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->l2_persist != 0 && o->l2_persist != 1) { err = "l2_persist must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
-  if (o->factor < IETI_FACTOR_FP64 || o->factor > IETI_FACTOR_TF32) { err = "bad factor"; return IETI_ERR_INVALID_ARG; }
+  if (o->factor < IETI_FACTOR_FP64 || o->factor > IETI_FACTOR_BF16) { err = "bad factor"; return IETI_ERR_INVALID_ARG; }
   if (o->refactor < IETI_REFACTOR_EVERY || o->refactor > IETI_REFACTOR_NEVER) { err = "bad refactor"; return IETI_ERR_INVALID_ARG; }
   if (!(o->newton_tol >= 0.0)) { err = "newton_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->predictor < 0 || o->predictor > 2) { err = "predictor must be 0, 1 or 2"; return IETI_ERR_INVALID_ARG; }
+  if (o->autotune != 0 && o->autotune != 1) { err = "autotune must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
     return IETI_ERR_INVALID_ARG;
@@ -211,7 +212,7 @@ int ieti_potrf_batched_f32(int32_t batch, float *base_dev, const int64_t *offset
                            void *stream) {
   g_setup_err.clear();
   if (batch < 1 || !base_dev || !offsets || !n || !ld || !n_pivots || !status_out ||
-      factor < IETI_FACTOR_FP32 || factor > IETI_FACTOR_TF32) {
+      factor < IETI_FACTOR_FP32 || factor > IETI_FACTOR_BF16) {
     g_setup_err = "ieti_potrf_batched_f32: invalid arguments";
     return IETI_ERR_INVALID_ARG;
   }

@@ -3,16 +3,19 @@
 // The right-looking blocked factorization of every augmented patch block (the
 // two Schur complements of Sec. 3) spends its flops in the trailing update
 // A22 -= L21 L21^T.  Here that update runs on the tcgen05 tensor cores in TF32
-// with FP32 accumulation in tensor memory, once per outer panel of TC_KP = 256
-// columns (the inner 32-column steps stay on the SIMT kernels):
+// (or, as an ablation, BF16) with FP32 accumulation in tensor memory, once per
+// outer panel of TC_KP = 256 columns (the inner 32-column steps stay on the SIMT
+// kernels):
 //
 //   1. k_panel_split writes the finished panel rows L21 of every patch into a
 //      stacked panel buffer (rows ro[s] + r, TC_KP columns, zero padded) as two
-//      planes, hi = rna_tf32(L21) and lo = L21 - hi.
+//      planes, hi = round(L21) and lo = round(L21 - hi), rounded to TF32 (kept in
+//      FP32 words) or to BF16 (16-bit words).
 //   2. k_syrk_tc: one persistent CTA per SM walks a host-built list of
 //      128 x 128 output tiles (patch-major, lower triangle only).  Warp 0 feeds
-//      the 128-byte-swizzled K-major operand tiles (one 32-wide K chunk per
-//      stage) by TMA through a shared-memory ring; warp 1 issues, per chunk,
+//      the 128-byte-swizzled K-major operand tiles (one K chunk of 128 bytes per
+//      row and stage: 32 TF32 or 64 BF16 values) by TMA through a shared-memory
+//      ring; warp 1 issues, per chunk,
 //      the MMAs hi*hi into one TMEM accumulator and (three-term split, FP32
 //      accuracy) hi*lo + lo*hi into a second, alternating between two chunk
 //      buffers; 16 epilogue warps add every chunk's accumulators to FP32 register
@@ -26,9 +29,11 @@
 // the copies and MMAs in flight and frees the tensor memory before returning.
 #pragma once
 #include <cuda.h>  // CUtensorMap
+#include <cuda_bf16.h>
 
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "tc.cuh"
 
@@ -48,13 +53,33 @@ constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);        // producer, MMA issu
 constexpr int TC_EPI_COLS = TC_BN / (TC_EPI_WARPS / 4);    // columns per epilogue thread
 
 struct TcItem {
-  int32_t s, R0, C0, t0, nk, pad;  // patch, tile origin, first trailing column, 32-wide K chunks
+  int32_t s, R0, C0, t0, nk, pad;  // patch, tile origin, first trailing column, K chunks
 };
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// Operand element of the trailing update: BF = 0 TF32 (FP32 words, kind::tf32, 8 K per
+// MMA), BF = 1 BF16 (kind::f16, 16 K per MMA).  Either way a K chunk fills one
+// 128-byte swizzle row and one MMA consumes 32 bytes of it.
+template <int BF>
+struct TcElem {
+  using T = typename std::conditional<BF != 0, __nv_bfloat16, float>::type;
+  static constexpr int KCH = 128 / (int)sizeof(T);  // K values per chunk
+  static constexpr uint32_t FMT = BF ? 1u : 2u;      // operand format in the instruction descriptor
+};
+
+__device__ __forceinline__ void split_store(float v, float *hi, float *lo, int k, bool x3) {
+  float h = 0.f;
+  {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    h = __uint_as_float(r);
+  }
+  hi[k] = h;
+  if (x3) lo[k] = v - h;
+}
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int k, bool x3) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[k] = h;
+  if (x3) lo[k] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -62,12 +87,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // Panel P of every patch: rows [t0, nact) x columns [J, J + jb) -> planes hi (and lo)
-// of the stacked panel buffer PB (plane stride R_total * TC_KP floats), zero padded
+// of the stacked panel buffer PB (plane stride R_total * TC_KP elements), zero padded
 // to TC_KP columns.  One warp per row.
-template <int X3>
+template <int X3, int BF>
 __global__ void k_panel_split(const float *base, const int64_t *off, const int32_t *ldv, const int32_t *kbeg,
                               const int32_t *kend, const int32_t *nact, int P, const int64_t *ro, int64_t R_total,
-                              float *PB) {
+                              typename TcElem<BF>::T *PB) {
   int s = blockIdx.y;
   int J = kbeg[s] + P * TC_KP;
   int ke = kend[s];
@@ -82,22 +107,17 @@ __global__ void k_panel_split(const float *base, const int64_t *off, const int32
   for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < m; rr += gridDim.x * wpb) {
     int r = t0 + rr;
     const float *src = A + (int64_t)r * ld + J;
-    float *hi = PB + (ro[s] + r) * (int64_t)TC_KP;
-    float *lo = hi + R_total * (int64_t)TC_KP;
-    for (int k = lane; k < TC_KP; k += 32) {
-      float v = k < jb ? src[k] : 0.f;
-      float h = tf32_rna(v);
-      hi[k] = h;
-      if (X3) lo[k] = v - h;
-    }
+    auto *hi = PB + (ro[s] + r) * (int64_t)TC_KP;
+    auto *lo = hi + R_total * (int64_t)TC_KP;
+    for (int k = lane; k < TC_KP; k += 32) split_store(k < jb ? src[k] : 0.f, hi, lo, k, X3 != 0);
   }
 }
 
 template <int X3>
 struct TcCfg {
   static constexpr int NPLANE = X3 ? 2 : 1;
-  static constexpr int NS = X3 ? 3 : 6;  // ring stages (one 32-wide K chunk each)
-  static constexpr uint32_t A_BYTES = TC_BM * 128;  // one plane, 32 FP32 of K per row
+  static constexpr int NS = X3 ? 3 : 6;  // ring stages (one K chunk each)
+  static constexpr uint32_t A_BYTES = TC_BM * 128;  // one plane, 128 bytes of K per row
   static constexpr uint32_t B_BYTES = TC_BN * 128;
   static constexpr uint32_t STAGE = NPLANE * (A_BYTES + B_BYTES);
   static constexpr uint32_t SMEM = NS * STAGE + 1024 /* alignment */ + 256 /* barriers */;
@@ -106,13 +126,14 @@ struct TcCfg {
 // TMEM: two chunk buffers of 2 * TC_BN columns: [hi*hi | hi*lo + lo*hi]
 constexpr uint32_t TC_TMEM_COLS = 4 * TC_BN;
 
-template <int X3>
+template <int X3, int BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmap, const TcItem *items, int n_items, float *base,
               const int64_t *off, const int32_t *ldv, const int64_t *ro, const int32_t *nact, AugLimits lim,
               int32_t *err_flag) {
   using C = TcCfg<X3>;
-  constexpr uint32_t IDESC = tc_idesc(2u /* TF32 */, TC_BM, TC_BN);
+  using E = TcElem<BF>;
+  constexpr uint32_t IDESC = tc_idesc(E::FMT, TC_BM, TC_BN);
   extern __shared__ unsigned char smraw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(sm + C::NS * C::STAGE);
@@ -169,8 +190,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_arrive_expect_tx(full + st, C::STAGE);
 #pragma unroll
           for (int pl = 0; pl < C::NPLANE; ++pl) {
-            tma_load_3d(sb + pl * C::A_BYTES, &tmap, kc * 32, ya, pl, full + st);
-            tma_load_3d(sb + C::NPLANE * C::A_BYTES + pl * C::B_BYTES, &tmap, kc * 32, yb, pl, full + st);
+            tma_load_3d(sb + pl * C::A_BYTES, &tmap, kc * E::KCH, ya, pl, full + st);
+            tma_load_3d(sb + C::NPLANE * C::A_BYTES + pl * C::B_BYTES, &tmap, kc * E::KCH, yb, pl, full + st);
           }
         }
       }
@@ -205,14 +226,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t sa = smem_u32(sm + st * C::STAGE);
           const uint32_t sb = sa + C::NPLANE * C::A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {  // 4 x K=8 inside the 128-byte row
+          for (int kk = 0; kk < 4; ++kk) {  // 4 MMAs of 32 bytes of K inside the 128-byte row
             const uint64_t ah = tc_desc_sw128(sa + kk * 32), bh = tc_desc_sw128(sb + kk * 32);
-            tc_mma<0>(dh, ah, bh, IDESC, kk != 0);
+            tc_mma<BF>(dh, ah, bh, IDESC, kk != 0);
             if constexpr (X3) {
               const uint64_t al = tc_desc_sw128(sa + C::A_BYTES + kk * 32);
               const uint64_t bl = tc_desc_sw128(sb + C::B_BYTES + kk * 32);
-              tc_mma<0>(dc, ah, bl, IDESC, kk != 0);
-              tc_mma<0>(dc, al, bh, IDESC, 1u);
+              tc_mma<BF>(dc, ah, bl, IDESC, kk != 0);
+              tc_mma<BF>(dc, al, bh, IDESC, 1u);
             }
           }
           tc_commit(empty + st);  // the stage is free once these MMAs have read it
@@ -225,7 +246,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue (warps 2-17)
-    // Every 32-wide K chunk is accumulated afresh in TMEM and added here to FP32
+    // Every K chunk is accumulated afresh in TMEM and added here to FP32
     // register sums with round-to-nearest: the tensor-core accumulation then spans
     // 4 MMAs of one chunk instead of a whole panel.  Each thread owns one row and
     // TC_EPI_COLS columns of the tile; its part of A22 is loaded when the tile

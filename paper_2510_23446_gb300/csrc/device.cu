@@ -30,10 +30,15 @@
 #include <climits>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
 #include <type_traits>
 #include <vector>
+
+#include <unistd.h>
 
 #include "chol_tc.cuh"
 #include "device.h"
@@ -804,6 +809,12 @@ struct DeviceState {
   double *pcg_rr = nullptr, *pcg_dd = nullptr;
   double bytes_iter_alg = 0, bytes_sweep_alg = 0;
   unsigned xs_bytes = 0, stage_bytes = 0;
+  // schedule of the persistent kernel: host copies of the per-patch row counts and
+  // leading dimensions of its four partitions (re-planned by the autotuner)
+  std::vector<int32_t> plan_rows[4], plan_ld[4];
+  int ldmax = 4, n_sm = 0, cps = 1;
+  int sched_source = 0, tune_candidates = 0;
+  double tune_ms = 0, tune_us[2] = {0, 0};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dt = 0;
   // kernel-class profiler (options.profile)
@@ -1020,7 +1031,7 @@ struct TcHost {
 // The output tiles of every outer panel (patch-major, lower triangle, restricted by
 // the limits), their useful flops, and each panel's slice of the list.
 static void tc_plan(const TcHost &th, const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
-                    const std::vector<int32_t> &hna, std::vector<TcItem> &items, std::vector<int64_t> &pofs,
+                    const std::vector<int32_t> &hna, int kch, std::vector<TcItem> &items, std::vector<int64_t> &pofs,
                     double &flops) {
   const int nb = (int)hkb.size();
   int max_outer = 0;
@@ -1034,7 +1045,7 @@ static void tc_plan(const TcHost &th, const std::vector<int32_t> &hkb, const std
       if (J >= hke[s]) continue;
       const int Je = std::min(J + TC_KP, hke[s]), t0 = Je, na = hna[s];
       if (t0 >= na) continue;
-      const int t0a = t0 & ~3, nk = (Je - J + 31) / 32;
+      const int t0a = t0 & ~3, nk = (Je - J + kch - 1) / kch;
       const int sklo = th.sk_lo[s], skhi = th.sk_hi[s], rlim = th.rlim[s], clim = th.clim[s];
       for (int R0 = t0; R0 < na; R0 += TC_BM) {
         const int Rend = std::min(R0 + TC_BM, na);
@@ -1083,7 +1094,7 @@ static double partial_chol_flops(const TcHost &th, const std::vector<int32_t> &h
   return f;
 }
 
-template <int X3>
+template <int X3, int BF>
 static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, const int32_t *ld, const TcHost &th,
                             const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
                             const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke, int32_t *dna,
@@ -1093,7 +1104,8 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
   std::vector<TcItem> items;
   std::vector<int64_t> pofs;
   double flops = 0;
-  tc_plan(th, hkb, hke, hna, items, pofs, flops);
+  using E = TcElem<BF>;
+  tc_plan(th, hkb, hke, hna, E::KCH, items, pofs, flops);
   const int max_outer = (int)pofs.size() - 1;
   if (max_outer <= 0) return IETI_OK;
   // stacked panel buffer: patch s owns rows [ro[s], ro[s] + nact[s])
@@ -1112,9 +1124,9 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
   int dev = 0, nsm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaFuncSetAttribute(k_syrk_tc<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<X3>::SMEM));
+  CK(cudaFuncSetAttribute(k_syrk_tc<X3, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<X3>::SMEM));
   // scratch: tile list, panel planes, row offsets, error word (freed before returning)
-  float *PB = nullptr;
+  typename E::T *PB = nullptr;
   TcItem *ditems = nullptr;
   int64_t *dro = nullptr;
   int32_t *derr = nullptr;
@@ -1125,7 +1137,7 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
     cudaFree(dro);
     cudaFree(derr);
   };
-  size_t pb_bytes = (size_t)2 * R * TC_KP * sizeof(float);
+  size_t pb_bytes = (size_t)2 * R * TC_KP * sizeof(typename E::T);
   if (cudaMalloc((void **)&PB, pb_bytes) != cudaSuccess ||
       cudaMalloc((void **)&ditems, std::max<size_t>(items.size(), 1) * sizeof(TcItem)) != cudaSuccess ||
       cudaMalloc((void **)&dro, nbatch * sizeof(int64_t)) != cudaSuccess ||
@@ -1146,11 +1158,13 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
   }
   CUtensorMap tm;
   {
+    const cuuint64_t esz = sizeof(typename E::T);
     cuuint64_t gdim[3] = {(cuuint64_t)TC_KP, (cuuint64_t)R, 2};
-    cuuint64_t gstr[2] = {(cuuint64_t)TC_KP * 4, (cuuint64_t)R * TC_KP * 4};
-    cuuint32_t box[3] = {32, (cuuint32_t)TC_BM, 1};
+    cuuint64_t gstr[2] = {(cuuint64_t)TC_KP * esz, (cuuint64_t)R * TC_KP * esz};
+    cuuint32_t box[3] = {(cuuint32_t)E::KCH, (cuuint32_t)TC_BM, 1};  // 128 bytes of K per row
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, PB, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = enc(&tm, BF ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, PB, gdim, gstr,
+                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -1199,7 +1213,7 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
       if (J < hke[s]) max_m = std::max(max_m, hna[s] - std::min(J + TC_KP, hke[s]));
     }
     dim3 gs(std::min<unsigned>(grid_for(max_m, 8), 512), nbatch);
-    k_panel_split<X3><<<gs, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, P, dro, R, PB);
+    k_panel_split<X3, BF><<<gs, 256, 0, d->stream>>>(base, off, ld, dkb, dke, dna, P, dro, R, PB);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1207,8 +1221,8 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
     evs.push_back(e1);
     cudaEventRecord(e0, d->stream);
     const unsigned grid = (unsigned)std::min<int64_t>(n_it, nsm);
-    k_syrk_tc<X3><<<grid, TC_THREADS, TcCfg<X3>::SMEM, d->stream>>>(tm, ditems + pofs[P], (int)n_it, base, off, ld,
-                                                                   dro, dna, lim, derr);
+    k_syrk_tc<X3, BF><<<grid, TC_THREADS, TcCfg<X3>::SMEM, d->stream>>>(tm, ditems + pofs[P], (int)n_it, base, off,
+                                                                       ld, dro, dna, lim, derr);
     cudaEventRecord(e1, d->stream);
     d->launches_setup += 2;
     d->tc_launches++;
@@ -1237,6 +1251,29 @@ static int potrf_partial_tc(DeviceState *d, float *base, const int64_t *off, con
   return IETI_OK;
 }
 
+// one partial-Cholesky phase of an FP32 batch in a reduced factor arithmetic
+// (IETI_FACTOR_FP32 on the SIMT pipe, the others with tensor-core trailing updates)
+static int potrf_partial_f32(DeviceState *d, int factor, float *base, const int64_t *off, const int32_t *ld,
+                             const TcHost &th, const std::vector<int32_t> &hkb, const std::vector<int32_t> &hke,
+                             const std::vector<int32_t> &hna, int32_t *dkb, int32_t *dke, int32_t *dna,
+                             int32_t *status, AugLimits lim, std::string &err) {
+  switch (factor) {
+    case IETI_FACTOR_FP32:
+      return potrf_partial<float>(d, base, off, ld, hkb, hke, hna, dkb, dke, dna, status, lim, err);
+    case IETI_FACTOR_TF32X3:
+      return potrf_partial_tc<1, 0>(d, base, off, ld, th, hkb, hke, hna, dkb, dke, dna, status, lim, err);
+    case IETI_FACTOR_TF32:
+      return potrf_partial_tc<0, 0>(d, base, off, ld, th, hkb, hke, hna, dkb, dke, dna, status, lim, err);
+    case IETI_FACTOR_BF16X3:
+      return potrf_partial_tc<1, 1>(d, base, off, ld, th, hkb, hke, hna, dkb, dke, dna, status, lim, err);
+    case IETI_FACTOR_BF16:
+      return potrf_partial_tc<0, 1>(d, base, off, ld, th, hkb, hke, hna, dkb, dke, dna, status, lim, err);
+    default:
+      err = "unknown factor arithmetic";
+      return IETI_ERR_INVALID_ARG;
+  }
+}
+
 // one partial-Cholesky phase of a batch in the context's factor arithmetic
 template <class TD>
 static int run_partial(DeviceState *d, TD *D, const int64_t *doff, const int32_t *ld, const TcHost &th,
@@ -1246,14 +1283,7 @@ static int run_partial(DeviceState *d, TD *D, const int64_t *doff, const int32_t
   if constexpr (std::is_same<TD, double>::value) {
     return potrf_partial<double>(d, D, doff, ld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
   } else {
-    switch (d->factor) {
-      case IETI_FACTOR_FP32:
-        return potrf_partial<float>(d, D, doff, ld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
-      case IETI_FACTOR_TF32X3:
-        return potrf_partial_tc<1>(d, D, doff, ld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
-      default:
-        return potrf_partial_tc<0>(d, D, doff, ld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
-    }
+    return potrf_partial_f32(d, d->factor, D, doff, ld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
   }
 }
 
@@ -2084,6 +2114,274 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
 // =============================================================================
 // Setup orchestration
 // =============================================================================
+// ---------------------------------------------------------------------------
+// Schedule of the persistent dual-primal kernel and its autotuner.
+//
+// A schedule fixes the CTAs per SM (grid = cps x SMs, every CTA resident: the launch
+// is cooperative), the number of TMA ring stages and the bytes per stage.  The
+// four row partitions of the kernel (H rows, interface rows, IG rows, GT rows) are
+// cut into cps x SMs byte-balanced ranges for it.  Results depend on the schedule
+// only through the rounding order of the cross-CTA reductions.
+constexpr int PCG_MAX_CPS = 2;
+
+struct PcgSched {
+  int cps = 1, ns = 3;
+  size_t stage = 0;
+};
+
+static size_t pcg_xs_bytes(const DeviceState *d) {
+  const size_t esz = d->mixed ? 4 : 8;
+  return (std::max((size_t)d->ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
+}
+static size_t pcg_row_max(const DeviceState *d) {
+  const size_t esz = d->mixed ? 4 : 8;
+  return (std::max((size_t)d->ldmax * esz, (size_t)d->ldc * sizeof(double)) + 127) / 128 * 128;
+}
+// dynamic shared memory per CTA at cps CTAs per SM (227 KB per CTA at most, the
+// kernel's static arrays and the per-CTA reservation taken off)
+static size_t pcg_budget(int cps) { return cps == 1 ? 212 * 1024 : 100 * 1024; }
+
+// the rule: one CTA per SM, three stages (two when three rows do not fit) of at most 64 KB
+static int pcg_rule(const DeviceState *d, PcgSched *out, std::string &err) {
+  const size_t xs = pcg_xs_bytes(d), row_max = pcg_row_max(d), budget = pcg_budget(1);
+  if (xs + 2 * row_max > budget) {
+    err = "a patch block is too wide for the shared-memory staging of the dual-primal kernel";
+    return IETI_ERR_TOO_LARGE;
+  }
+  out->cps = 1;
+  out->ns = (xs + 3 * row_max <= budget) ? 3 : 2;
+  size_t stage = std::min<size_t>(64 * 1024, (budget - xs) / out->ns) / 128 * 128;
+  out->stage = std::max(stage, row_max);
+  return IETI_OK;
+}
+
+template <class T>
+static int upload_cap(DeviceState *d, T **ptr, size_t cap, const std::vector<T> &h, std::string &err) {
+  if (!*ptr) {
+    int rc = dalloc(d, ptr, cap, err);
+    if (rc) return rc;
+  }
+  if (h.size() > cap) {
+    err = "persistent PCG plan exceeds its preallocated size";
+    return IETI_ERR_INVALID_ARG;
+  }
+  if (!h.empty()) CK(cudaMemcpyAsync(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return IETI_OK;
+}
+
+// apply a schedule: shared-memory layout, grid, row partitions.  IETI_ERR_TOO_LARGE
+// (state unchanged) when it does not fit the shared memory or the occupancy.
+static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
+  const size_t xs = pcg_xs_bytes(d), row_max = pcg_row_max(d);
+  if (sc.cps < 1 || sc.cps > PCG_MAX_CPS || sc.ns < 2 || sc.ns > NS_MAX || sc.stage % 128 || sc.stage < row_max ||
+      xs + sc.ns * sc.stage > pcg_budget(sc.cps)) {
+    err = "schedule does not fit the dual-primal kernel's shared memory";
+    return IETI_ERR_TOO_LARGE;
+  }
+  const size_t smem = xs + sc.ns * sc.stage;
+  const void *fn = d->mixed ? (const void *)k_ddsolve<float> : (const void *)k_ddsolve<double>;
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, smem));
+  if (per_sm < sc.cps) {
+    err = "schedule exceeds the occupancy of the dual-primal kernel";
+    return IETI_ERR_TOO_LARGE;
+  }
+  d->n_stages = sc.ns;
+  d->xs_bytes = (unsigned)xs;
+  d->stage_bytes = (unsigned)sc.stage;
+  d->pcg_smem = smem;
+  d->cps = sc.cps;
+  d->G = sc.cps * d->n_sm;
+  const size_t cap_ptr = (size_t)PCG_MAX_CPS * d->n_sm + 1, cap_seg = (size_t)PCG_MAX_CPS * d->n_sm + d->np_ + 1;
+  int32_t **ptrs[4][4] = {{&d->hseg_ptr, &d->hseg_s, &d->hseg_r0, &d->hseg_r1},
+                          {&d->bseg_ptr, &d->bseg_s, &d->bseg_r0, &d->bseg_r1},
+                          {&d->iseg_ptr, &d->iseg_s, &d->iseg_r0, &d->iseg_r1},
+                          {&d->tseg_ptr, &d->tseg_s, &d->tseg_r0, &d->tseg_r1}};
+  std::vector<int32_t> sp, ss, r0v, r1v;
+  for (int k = 0; k < 4; ++k) {
+    partition_rows(d->plan_rows[k], d->plan_ld[k], d->G, sp, ss, r0v, r1v);
+    int rc;
+    if ((rc = upload_cap(d, ptrs[k][0], cap_ptr, sp, err)) || (rc = upload_cap(d, ptrs[k][1], cap_seg, ss, err)) ||
+        (rc = upload_cap(d, ptrs[k][2], cap_seg, r0v, err)) || (rc = upload_cap(d, ptrs[k][3], cap_seg, r1v, err)))
+      return rc;
+  }
+  return IETI_OK;
+}
+
+// synthetic kept-space right-hand side of the tuning solves (a fixed bounded pattern)
+__global__ void k_tune_rhs(double *x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = (uint32_t)i * 2654435761u;
+    x[i] = (double)(h >> 8) * (1.0 / 16777216.0) - 0.5;
+  }
+}
+
+// time per PCG iteration (us) of the current schedule: `iters` iterations (no
+// convergence stop), the best of two runs after one untimed run
+template <class T>
+static int pcg_time(DeviceState *d, const double *rhs, int iters, double *us, std::string &err) {
+  const ieti_options keep = d->opt;
+  d->opt.profile = 0;
+  d->opt.cg_tol = 0.0;
+  d->opt.cg_max_it = iters;
+  double best = 1e300;
+  int rc = IETI_OK;
+  for (int rep = 0; rep < 3 && rc == IETI_OK; ++rep) {
+    int its = 0;
+    double rel = 0;
+    std::string e2;
+    cudaEventRecord(d->ev0, d->stream);
+    rc = pcg_persistent<T>(d, rhs, &its, &rel, e2);
+    cudaEventRecord(d->ev1, d->stream);
+    if (rc == IETI_ERR_CG_NOT_CONVERGED) rc = IETI_OK;  // the iteration count is fixed on purpose
+    if (rc != IETI_OK) {
+      err = "autotuning solve failed: " + e2;
+      break;
+    }
+    float ms = 0;
+    if (cudaEventSynchronize(d->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, d->ev0, d->ev1) != cudaSuccess) {
+      err = "autotuning: event timing failed";
+      rc = IETI_ERR_CUDA;
+      break;
+    }
+    if (rep > 0) best = std::min(best, 1e3 * ms / std::max(its + 2, 1));
+  }
+  d->opt = keep;
+  d->nlaunch = 0;
+  *us = best;
+  return rc;
+}
+
+static std::string tune_key(const DeviceState *d) {
+  cudaDeviceProp prop{};
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, d->device) == cudaSuccess) name = prop.name;
+  for (char &c : name)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  std::ostringstream k;
+  k << name << "|sm" << d->n_sm << "|" << (d->mixed ? "mixed" : "fp64") << "|np" << d->np_ << "|nk" << d->NK << "|nb"
+    << d->NBt << "|npi" << d->NPt << "|m" << d->M << "|nc" << d->NC << "|ld" << d->ldmax;
+  return k.str();
+}
+
+// cache lines: "ieti_tune1 <key> <cps> <stages> <stage bytes>"
+static bool tune_cache_lookup(const std::string &path, const std::string &key, PcgSched *out) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream ls(line);
+    std::string tag, k;
+    long cps = 0, ns = 0, stage = 0;
+    if (!(ls >> tag >> k >> cps >> ns >> stage) || tag != "ieti_tune1" || k != key) continue;
+    if (cps < 1 || cps > PCG_MAX_CPS || ns < 2 || ns > NS_MAX || stage < 128 || stage > 227 * 1024) continue;
+    out->cps = (int)cps;
+    out->ns = (int)ns;
+    out->stage = (size_t)stage;
+    found = true;  // the last valid entry of the key wins
+  }
+  return found;
+}
+
+static bool tune_cache_store(const std::string &path, const std::string &key, const PcgSched &sc) {
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (f && std::getline(f, line)) {
+      std::istringstream ls(line);
+      std::string tag, k;
+      if ((ls >> tag >> k) && tag == "ieti_tune1" && k == key) continue;
+      if (!line.empty()) keep.push_back(line);
+    }
+  }
+  const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    if (!f) return false;
+    for (auto &l : keep) f << l << "\n";
+    f << "ieti_tune1 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << "\n";
+    if (!f.good()) return false;
+  }
+  return std::rename(tmp.c_str(), path.c_str()) == 0;
+}
+
+// pick the schedule: from the cache, else by timing every feasible candidate
+template <class T>
+static int pcg_autotune(DeviceState *d, std::string &err) {
+  auto t0 = std::chrono::steady_clock::now();
+  const std::string key = tune_key(d);
+  const char *cache = d->opt.tune_cache;
+  PcgSched rule, best;
+  int rc = pcg_rule(d, &rule, err);
+  if (rc) return rc;
+  if (cache && *cache && tune_cache_lookup(cache, key, &best)) {
+    std::string e2;
+    if (pcg_plan(d, best, e2) == IETI_OK) {
+      d->sched_source = 3;
+      d->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      return IETI_OK;
+    }
+  }
+  double *rhs = nullptr;
+  if ((rc = dalloc(d, &rhs, (size_t)d->NK, err))) return rc;
+  k_tune_rhs<<<grid_for(d->NK, 256), 256, 0, d->stream>>>(rhs, d->NK);
+  CK(cudaGetLastError());
+  const int iters = 16;
+  std::vector<PcgSched> cand;
+  for (int cps = 1; cps <= PCG_MAX_CPS; ++cps)
+    for (int ns = 2; ns <= NS_MAX; ++ns)
+      for (size_t kb : {16, 24, 32, 48, 64, 96}) cand.push_back({cps, ns, kb * 1024});
+  cand.push_back(rule);
+  double best_us = 1e300, rule_us = 1e300;
+  best = rule;
+  PcgSched fastest = rule;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    std::string e2;
+    const int prc = pcg_plan(d, cand[c], e2);
+    if (prc == IETI_ERR_TOO_LARGE) continue;  // does not fit: not a candidate
+    if (prc) {
+      err = e2;
+      rc = prc;
+      break;
+    }
+    double us = 0;
+    if ((rc = pcg_time<T>(d, rhs, iters, &us, err))) break;
+    d->tune_candidates++;
+    if (c + 1 == cand.size()) rule_us = us;
+    if (us < best_us) {
+      best_us = us;
+      fastest = cand[c];
+    }
+  }
+  // the rule stays unless a candidate is faster by more than the timing noise (1%)
+  if (best_us < 0.99 * rule_us) {
+    best = fastest;
+  } else {
+    best_us = rule_us;
+  }
+  cudaStreamSynchronize(d->stream);
+  cudaFree(rhs);
+  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)rhs));
+  d->bytes -= d->NK * 8;
+  if (rc) return rc;
+  if ((rc = pcg_plan(d, best, err))) return rc;
+  // the tuning solves leave the iteration vectors non-zero: clear the ones a solve
+  // reads before writing
+  CK(cudaMemsetAsync(d->p, 0, d->M * sizeof(double), d->stream));
+  CK(cudaMemsetAsync(d->p1, 0, d->M * sizeof(double), d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  d->tune_us[0] = rule_us;
+  d->tune_us[1] = best_us;
+  d->sched_source = 1;
+  if (cache && *cache && tune_cache_store(cache, key, best)) d->sched_source = 2;
+  d->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return IETI_OK;
+}
+
 int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out, std::string &err) {
   auto t0 = std::chrono::steady_clock::now();
   DeviceState *d = new DeviceState();
@@ -2519,16 +2817,9 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   auto factor_phase = [&](const std::vector<int32_t> &kb, const std::vector<int32_t> &ke,
                           const std::vector<int32_t> &na, AugLimits lm) -> int {
     d->factor_flops += partial_chol_flops(th, kb, ke, na);
-    switch (d->factor) {
-      case IETI_FACTOR_FP64:
-        return potrf_partial<double>(d, D, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-      case IETI_FACTOR_FP32:
-        return potrf_partial<float>(d, Df, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-      case IETI_FACTOR_TF32X3:
-        return potrf_partial_tc<1>(d, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-      default:
-        return potrf_partial_tc<0>(d, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-    }
+    if (d->factor == IETI_FACTOR_FP64)
+      return potrf_partial<double>(d, D, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
+    return potrf_partial_f32(d, d->factor, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
   };
   for (int s = 0; s < np_; ++s) {
     hkb[s] = 0;
@@ -2720,53 +3011,27 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
                   8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
   {
-    // ---- persistent PCG plan: grid from occupancy, byte-balanced partitions
-    int ldmax = 4;
-    for (int s = 0; s < np_; ++s) ldmax = std::max({ldmax, hldb[s], hldp[s], hldi[s], hldg[s]});
-    // shared memory: staged x vector, then n_stages TMA stages (whole rows per stage)
-    size_t xs_bytes = (std::max((size_t)ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
-    // dynamic shared memory budget: 227 KB per CTA minus the kernel's static arrays
-    size_t budget = 212 * 1024, row_max = std::max((size_t)ldmax * esz, (size_t)d->ldc * sizeof(double));
-    if (xs_bytes + 2 * row_max > budget) {
-      err = "a patch block is too wide for the shared-memory staging of the dual-primal kernel";
-      return fail(IETI_ERR_TOO_LARGE);
-    }
-    d->n_stages = (xs_bytes + 3 * row_max <= budget) ? 3 : 2;
-    size_t stage = std::min<size_t>(64 * 1024, (budget - xs_bytes) / d->n_stages) / 128 * 128;
-    stage = std::max(stage, (row_max + 127) / 128 * 128);
-    d->xs_bytes = (unsigned)xs_bytes;
-    d->stage_bytes = (unsigned)stage;
-    d->pcg_smem = xs_bytes + d->n_stages * stage;
-    const void *fn = d->mixed ? (const void *)k_ddsolve<float> : (const void *)k_ddsolve<double>;
-    if (d->pcg_smem > 48 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->pcg_smem));
-    int per_sm = 0, n_sm = 0, coop = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, d->pcg_smem));
-    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, d->device));
+    // ---- persistent PCG plan: one CTA per SM, three TMA stages of at most 64 KB (the
+    // rule), or the autotuner's choice at the end of setup
+    for (int s = 0; s < np_; ++s) d->ldmax = std::max({d->ldmax, hldb[s], hldp[s], hldi[s], hldg[s]});
+    d->plan_ld[0] = hldb;  // H rows: [F_s; Psi_s^T]
+    d->plan_rows[0].resize(np_);
+    for (int s = 0; s < np_; ++s) d->plan_rows[0][s] = hnb[s] + hnp[s];
+    d->plan_rows[1] = hnb;  // interface rows (Psi and S_bb)
+    d->plan_ld[1] = hldb;
+    d->plan_rows[2] = hn;   // IG rows
+    d->plan_ld[2] = hldi;
+    d->plan_rows[3] = hni;  // GT rows
+    d->plan_ld[3] = hldg;
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&d->n_sm, cudaDevAttrMultiProcessorCount, d->device));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, d->device));
-    if (!coop || per_sm < 1) {
+    if (!coop) {
       err = "device cannot run the cooperative PCG kernel";
       return fail(IETI_ERR_CUDA);
     }
-    d->G = std::min(per_sm, 2) * n_sm;
-    std::vector<int32_t> hrows(np_);
-    for (int s = 0; s < np_; ++s) hrows[s] = hnb[s] + hnp[s];
-    std::vector<int32_t> sp, ss, r0v, r1v;
-    partition_rows(hrows, hldb, d->G, sp, ss, r0v, r1v);
-    if ((rc = upload(d, &d->hseg_ptr, sp, err)) || (rc = upload(d, &d->hseg_s, ss, err)) ||
-        (rc = upload(d, &d->hseg_r0, r0v, err)) || (rc = upload(d, &d->hseg_r1, r1v, err)))
-      return fail(rc);
-    partition_rows(hnb, hldb, d->G, sp, ss, r0v, r1v);
-    if ((rc = upload(d, &d->bseg_ptr, sp, err)) || (rc = upload(d, &d->bseg_s, ss, err)) ||
-        (rc = upload(d, &d->bseg_r0, r0v, err)) || (rc = upload(d, &d->bseg_r1, r1v, err)))
-      return fail(rc);
-    partition_rows(hn, hldi, d->G, sp, ss, r0v, r1v);
-    if ((rc = upload(d, &d->iseg_ptr, sp, err)) || (rc = upload(d, &d->iseg_s, ss, err)) ||
-        (rc = upload(d, &d->iseg_r0, r0v, err)) || (rc = upload(d, &d->iseg_r1, r1v, err)))
-      return fail(rc);
-    partition_rows(hni, hldg, d->G, sp, ss, r0v, r1v);
-    if ((rc = upload(d, &d->tseg_ptr, sp, err)) || (rc = upload(d, &d->tseg_s, ss, err)) ||
-        (rc = upload(d, &d->tseg_r0, r0v, err)) || (rc = upload(d, &d->tseg_r1, r1v, err)))
-      return fail(rc);
+    PcgSched rule;
+    if ((rc = pcg_rule(d, &rule, err)) || (rc = pcg_plan(d, rule, err))) return fail(rc);
     // fixed-width gather lists (an edge DOF is shared by at most 4 patches)
     std::vector<int32_t> ell_l(d->NBt * BT_W, -1), cpp(d->NC * CP_W, -1);
     std::vector<double> ell_s(d->NBt * BT_W, 0.0), ell_w(d->NBt * BT_W, 0.0);
@@ -2795,7 +3060,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
         (rc = dalloc(d, &d->zf, d->NBt, err)) || (rc = dalloc(d, &d->ubp, d->NBt, err)) ||
         (rc = dalloc(d, &d->ub1, d->NBt, err)) || (rc = dalloc(d, &d->uz, d->NBt, err)) ||
         (rc = dalloc(d, &d->tpi, d->NPt, err)) || (rc = dalloc(d, &d->zp, d->NBt, err)) ||
-        (rc = dalloc(d, &d->ccg, d->NC, err)) || (rc = dalloc(d, &d->ppart, 4 * (size_t)d->G, err)) ||
+        (rc = dalloc(d, &d->ccg, d->NC, err)) || (rc = dalloc(d, &d->ppart, 4 * (size_t)PCG_MAX_CPS * d->n_sm, err)) ||
         (rc = dalloc(d, &d->bar, 4, err)) || (rc = dalloc(d, &d->pcg_its, 1, err)) ||
         (rc = dalloc(d, &d->pcg_rr, 1, err)) || (rc = dalloc(d, &d->pcg_dd, 1, err)) ||
         (rc = dalloc(d, &d->trace, TRACE_IT * TRACE_SLOTS, err)))
@@ -2847,6 +3112,11 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     CK(cudaStreamSynchronize(d->stream));
     d->refactors = 0;
   }
+  if (opt.autotune && opt.pcg_mode == 0) {
+    rc = d->mixed ? pcg_autotune<float>(d, err) : pcg_autotune<double>(d, err);
+    if (rc) return fail(rc);
+  }
+  d->opt.tune_cache = nullptr;  // caller-owned, read during setup only
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   (void)maxnp;
   *out = d;
@@ -2918,6 +3188,14 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->refactors = d->refactors;
   info->nl_coarse_block = d->cN;
   for (int k = 0; k < 4; ++k) info->t_refactor_ms[k] = d->t_refactor_ms[k];
+  info->pcg_grid = d->G;
+  info->pcg_stages = d->n_stages;
+  info->pcg_stage_bytes = (int32_t)d->stage_bytes;
+  info->pcg_sched_source = d->sched_source;
+  info->tune_candidates = d->tune_candidates;
+  info->tune_ms = d->tune_ms;
+  info->tune_us_per_it[0] = d->tune_us[0];
+  info->tune_us_per_it[1] = d->tune_us[1];
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
@@ -3060,12 +3338,7 @@ int device_potrf_batched_f32(int batch, float *base, const int64_t *off, const i
     DeviceState tmp;
     tmp.stream = st;
     AugLimits lim{dz, dz2, dbig, dz};
-    if (factor == IETI_FACTOR_FP32)
-      rc = potrf_partial<float>(&tmp, base, doff, dld, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
-    else if (factor == IETI_FACTOR_TF32X3)
-      rc = potrf_partial_tc<1>(&tmp, base, doff, dld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
-    else
-      rc = potrf_partial_tc<0>(&tmp, base, doff, dld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+    rc = potrf_partial_f32(&tmp, factor, base, doff, dld, th, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
   }
   if (rc == IETI_OK) {
     if (cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -20,7 +20,7 @@ lib = C.CDLL(LIB_PATH)
 IETI_MEM_HOST, IETI_MEM_DEVICE = 0, 1
 PREC = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
-FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3}
+FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "bf16": 5}
 REFACTOR = {"every": 0, "step": 1, "never": 2}
 ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
           -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE"}
@@ -41,7 +41,7 @@ class ieti_options(C.Structure):
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
-                ("predictor", C.c_int32)]
+                ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 class ieti_coil(C.Structure):
@@ -71,7 +71,10 @@ class ieti_info(C.Structure):
                 ("t_factor_ms", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
                 ("tc_useful_flops", C.c_double), ("tc_launches", C.c_int64), ("factor_flops", C.c_double),
                 ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64),
-                ("nl_coarse_block", C.c_int64), ("t_refactor_ms", C.c_double * 4)]
+                ("nl_coarse_block", C.c_int64), ("t_refactor_ms", C.c_double * 4),
+                ("pcg_grid", C.c_int32), ("pcg_stages", C.c_int32), ("pcg_stage_bytes", C.c_int32),
+                ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
+                ("tune_us_per_it", C.c_double * 2)]
 
 
 _ctx = C.c_void_p
@@ -131,7 +134,7 @@ class Solver:
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, reluctivity=None, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1,
-                 factor="fp64", refactor="every", newton_tol=0.0, predictor=0):
+                 factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None):
         self._keep = []
 
         def arr(x, dt_):
@@ -173,6 +176,9 @@ class Solver:
         op.refactor = REFACTOR[refactor] if isinstance(refactor, str) else int(refactor)
         op.newton_tol = float(newton_tol)
         op.predictor = int(predictor)
+        op.autotune = int(autotune)
+        if tune_cache is not None:
+            op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
         self.options = op
         self.ctx = _ctx()
         rc = lib.ieti_setup(C.byref(pr), C.byref(op), C.byref(self.ctx))
@@ -196,6 +202,7 @@ class Solver:
         self._check(lib.ieti_get_info(self.ctx, C.byref(inf)))
         out = {k: getattr(inf, k) for k, _ in ieti_info._fields_}
         out["t_refactor_ms"] = list(out["t_refactor_ms"])
+        out["tune_us_per_it"] = list(out["tune_us_per_it"])
         return out
 
     def quad_points(self):

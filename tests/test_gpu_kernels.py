@@ -125,7 +125,7 @@ def test_partial_cholesky_f32_modes(ieti, sizes, frac):
     mats, offs, lds, flat = _batch_f32(rng, sizes)
     piv = [max(1, int(round(frac * n))) for n in sizes]
     err = {}
-    for mode in ("fp32", "tf32x3", "tf32"):
+    for mode in ("fp32", "tf32x3", "tf32", "bf16x3", "bf16"):
         base = torch.from_numpy(flat.copy()).cuda()
         st = ieti.potrf_batched_f32(base, offs, sizes, lds, piv, factor=mode)
         assert np.all(st == 0), (mode, st)
@@ -138,6 +138,12 @@ def test_partial_cholesky_f32_modes(ieti, sizes, frac):
     assert err["tf32"].max() <= 1e-2, err
     big = [i for i, n in enumerate(sizes) if piv[i] < n or n > 256]   # the tensor-core update ran
     assert err["tf32"][big].min() > 10 * err["tf32x3"][big].max(), err
+    # BF16 ablation: hi + lo planes carry ~16 significant bits (three products), one
+    # product 8 bits, i.e. 8x the TF32 operand rounding
+    assert err["bf16x3"].max() <= 2e-4, err
+    assert err["bf16"].max() <= 5e-2, err
+    assert err["bf16"][big].min() > 10 * err["bf16x3"][big].max(), err
+    assert err["bf16"][big].mean() > 2 * err["tf32"][big].mean(), err
 
 
 def test_partial_cholesky_f32_flags_indefinite(ieti):

@@ -88,7 +88,7 @@ def test_steps_match_oracle(ieti, name, mode):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("factor", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("factor", ["fp32", "tf32x3", "bf16x3"])
 def test_mixed_reduced_factors_match_oracle(ieti, name, factor):
     """Mixed path with the patch blocks factored in FP32 (SIMT, or tensor-core
     trailing updates as three TF32 products): the FP64 defect correction brings
@@ -102,12 +102,13 @@ def test_mixed_reduced_factors_match_oracle(ieti, name, factor):
         assert np.all(b[op.gauge.cls == 0] == 0.0)
 
 
-def test_tf32_ablation_factor_reaches_tolerance_or_reports(ieti):
-    """One-TF32-product factors (11-bit operands): the refinement either still reaches
-    the mixed tolerance (in more sweeps) or reports non-convergence; it never
-    returns a wrong state as converged."""
+@pytest.mark.parametrize("factor", ["tf32", "bf16"])
+def test_single_product_ablation_factor_reaches_tolerance_or_reports(ieti, factor):
+    """One-product tensor-core factors (TF32: 11-bit operands, BF16: 8-bit): the
+    refinement either still reaches the mixed tolerance (in more sweeps) or reports
+    non-convergence; it never returns a wrong state as converged."""
     prob, op, ref = oracle_run("c1", 2)
-    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", factor="tf32", **OPTS["mixed"])
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", factor=factor, **OPTS["mixed"])
     j = S.load_vector(prob.coil)
     for l in range(2):
         st = S.step(j, raise_on_error=False)

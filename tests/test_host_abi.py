@@ -104,6 +104,7 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     dict(precision="mixed", factor=7),
     dict(precision="mixed", pcg_mode=3),
     dict(precision="fp64", predictor=3),
+    dict(precision="mixed", factor="bf16", autotune=2),
 ])
 def test_invalid_options_return_codes(ieti, kw):
     prob = make_problem("c1")
@@ -125,6 +126,10 @@ def test_potrf_f32_rejects_bad_arguments_without_a_device(ieti):
     rc = ieti.lib.ieti_potrf_batched_f32(1, C.c_void_p(16), z.ctypes.data, n.ctypes.data, ld.ctypes.data,
                                          n.ctypes.data, 9, st.ctypes.data, None)
     assert rc == -1
+    for factor in (4, 5):                    # BF16 tensor-core modes: same 16-byte rule
+        rc = ieti.lib.ieti_potrf_batched_f32(1, C.c_void_p(16), z.ctypes.data, n.ctypes.data, ld.ctypes.data,
+                                             n.ctypes.data, factor, st.ctypes.data, None)
+        assert rc == -1
 
 
 @pytest.mark.parametrize("name", ["uneven", "c3_slice"])
