@@ -34,9 +34,9 @@ HORIZON = 50   # the workload's run: 50 implicit-Euler steps from a^0 = 0, repla
 # this workload); both start every step from the time-extrapolated iterate
 OPTS = {
     "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20,
-                  factor="tf32x3", predictor=2),
+                  factor="tf32x3", predictor=2, autotune=1, l2_persist=2),
     "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-11, outer_tol=OUTER_TOL, max_sweeps=20,
-                 predictor=2),
+                 predictor=2, autotune=1, l2_persist=2),
 }
 
 
@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-nonlinear", action="store_true", help="skip the nonlinear (Newton) workload")
     ap.add_argument("--nl-steps", type=int, default=4, help="timed steps of the nonlinear workload")
     ap.add_argument("--no-paper-case", action="store_true", help="skip the paper's two-subdomain timed run")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the factor-arithmetic ablation")
+    ap.add_argument("--configs", default="c3", help="comma-separated extra full-size workloads (c3, c5_4, c5_6; "
+                                                    "'' for none), each mixed vs FP64 over a few steps")
+    ap.add_argument("--config-steps", type=int, default=10, help="timed steps per extra workload and path")
     ap.add_argument("--profile-step", action="store_true",
                     help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
     return ap.parse_args()
@@ -308,6 +312,113 @@ def paper_case_leg(ieti, torch, dev, stream):
             "paper_total_s": 10.0, "paper_hardware": "laptop, MATLAB, not parallelized (Sec. 4)", **out}
 
 
+def factor_ablation_leg(ieti, torch, prob, dev, stream, n_steps=10):
+    """The mixed path with every factor arithmetic of the patch blocks (FP32 SIMT,
+    TF32x3 / TF32 / BF16x3 / BF16 tensor-core trailing updates) on the bench workload:
+    factorization time and rate, then n_steps implicit-Euler steps from a^0 = 0 with
+    the bench's outer stop, against the FP64 path's state after the same steps."""
+    import numpy as np
+
+    def run(opts):
+        S = ieti.Solver.from_problem(prob, device=dev, stream=stream, **opts)
+        inf = S.info()
+        jd = torch.from_numpy(S.load_vector(prob.coil)).to(f"cuda:{dev}")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = sweeps = 0
+        rc = 0
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        for _ in range(n_steps):
+            st = S.step(jd, raise_on_error=False)
+            its += st["cg_its"]
+            sweeps += st["sweeps"]
+            if st["rc"] != 0:
+                rc = st["rc"]
+                break
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        a = S.solution().copy()
+        S.close()
+        return inf, a, dict(ms=ev0.elapsed_time(ev1), its=its, sweeps=sweeps, rc=rc)
+
+    _, ref, _ = run(dict(OPTS["fp64"], autotune=0))
+    out = {}
+    for f in ("fp32", "tf32x3", "tf32", "bf16x3", "bf16"):
+        try:
+            inf, a, r = run(dict(OPTS["mixed"], factor=f, autotune=0))
+        except ieti.IetiError as e:   # e.g. a Schur complement that is no longer positive definite
+            out[f] = {"setup_failed": str(e), "converged": False}
+            torch.cuda.empty_cache()
+            continue
+        ok = r["rc"] == 0
+        out[f] = {"t_factor_ms": inf["t_factor_ms"],
+                  "useful_tflops_per_s": inf["factor_flops"] / max(inf["t_factor_ms"], 1e-9) / 1e9,
+                  "tc_ms": inf["tc_ms"], "converged": ok,
+                  "steps_per_s": 1e3 * n_steps / r["ms"] if ok else None,
+                  "sweeps_per_step": r["sweeps"] / n_steps if ok else None,
+                  "cg_its_per_step": r["its"] / n_steps if ok else None,
+                  "rel_err_vs_fp64": float(np.linalg.norm(a - ref) / np.linalg.norm(ref)) if ok else None}
+        torch.cuda.empty_cache()
+    return {"workload": "c2, mixed path, each factor arithmetic; " + f"{n_steps} steps from a^0 = 0, outer stop "
+                        f"{OUTER_TOL} (max 20 sweeps); error against the FP64 path after the same steps",
+            "factors": out}
+
+
+# extra workloads: (description, config, generator options, outer stop).  The 512-patch
+# workload's sigma contrast (1 .. 1e4) needs the outer stop at 1e-12 for the two paths
+# to agree to 1e-8
+EXTRA = {
+    "c3": ("c3: 8x8x8 curved patches, p=2, 6^3 elements per patch, sigma log-uniform in [1,1e4] per patch "
+           "within radius 0.35, nu in [0.5,2] per patch, dt=1e-3", "c3", {}, 1e-12),
+    "c5_4": ("c5 linear, 4x4x4 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
+             "dt=5e-4", "c5", dict(patches_per_dir=4, nonlinear=False), OUTER_TOL),
+    "c5_6": ("c5 linear, 6x6x6 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
+             "dt=5e-4", "c5", dict(patches_per_dir=6, nonlinear=False), OUTER_TOL),
+}
+
+
+def config_leg(ieti, torch, key, dev, stream, flush_buf, K, W=2):
+    """One extra full-size workload: mixed vs FP64 (the bench's options), W untimed
+    and K timed steps from a^0 = 0 (L2 flushed between timed steps), states compared."""
+    import numpy as np
+    from workloads import make_problem
+    desc, name, kw, outer = EXTRA[key]
+    prob = make_problem(name, **kw)
+    out, states = {}, {}
+    for mode in ("mixed", "fp64"):
+        t0 = time.perf_counter()
+        S = ieti.Solver.from_problem(prob, device=dev, stream=stream, **dict(OPTS[mode], outer_tol=outer, max_sweeps=30))
+        t_setup = time.perf_counter() - t0
+        inf = S.info()
+        jd = torch.from_numpy(S.load_vector(prob.coil)).to(f"cuda:{dev}")
+        for _ in range(W):
+            S.step(jd)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        its = sweeps = 0
+        for k in range(K):
+            flush_buf.zero_()
+            ev[k][0].record()
+            st = S.step(jd)
+            ev[k][1].record()
+            its += st["cg_its"]
+            sweeps += st["sweeps"]
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        out[mode] = {"value": 1e3 * K / ms, "unit": "steps/s", "ms_per_step": ms / K, "cg_its_per_step": its / K,
+                     "sweeps_per_step": sweeps / K, "cg_its_per_s": 1e3 * its / ms, "setup_s": t_setup,
+                     "t_factor_ms": inf["t_factor_ms"], "bytes_per_pcg_iteration": inf["bytes_iter"]}
+        states[mode] = S.solution().copy()
+        info = inf
+        S.close()
+        torch.cuda.empty_cache()
+    a, b = states["mixed"], states["fp64"]
+    return {"workload": desc, "outer_tol": outer, "n_patches": prob.n_patches, "n_dofs": info["n_dofs"],
+            "n_lambda": info["n_lambda"],
+            "n_coarse": info["n_coarse"], "steps": K, "warmup": W, **out,
+            "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+            "rel_err_vs_fp64": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -420,6 +531,8 @@ def run_ours(args):
                    "mixed_factor": OPTS["mixed"]["factor"],
                    "fp64_inner_cg_tol": OPTS["fp64"]["cg_tol"], "predictor": "3 a^l - 3 a^(l-1) + a^(l-2) (both paths)",
                    "outer_tol": OUTER_TOL, "l2": "flushed between timed steps (256 MiB write)",
+                   "l2_operator_policy": "per-iteration operators loaded with a fractional evict-last hint "
+                                         "(returned to normal priority at the end of every step)",
                    "steps": f"the 50-step run from a^0 = 0 (dt = 1e-3), replayed; state reset untimed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "cg_its_per_s": world * rm["its"] / tot["mixed"],
@@ -450,6 +563,9 @@ def run_ours(args):
                                    "parts": ["stage vector", "first chunk", "rows"],
                                    "us": rm["phases"]["sub_us"]}},
     }
+    line["config"]["schedule"] = {m: {k: results[m][0].info()[k] for k in (
+        "pcg_grid", "pcg_stages", "pcg_stage_bytes", "pcg_sched_source", "tune_candidates", "tune_ms",
+        "tune_us_per_it")} for m in results}
     if world == 1 and not args.no_paper_case:
         line["paper_case"] = paper_case_leg(ieti, torch, dev, stream)
     if not args.no_nonlinear and world == 1:
@@ -458,6 +574,20 @@ def run_ours(args):
         results = {}
         torch.cuda.empty_cache()
         line["nonlinear"] = nonlinear_leg(ieti, torch, dev, stream, flush_buf, max(1, args.nl_steps), 1)
+    if world == 1 and not args.no_ablation:
+        for m in results:
+            results[m][0].close()
+        results = {}
+        torch.cuda.empty_cache()
+        line["factor_ablation"] = factor_ablation_leg(ieti, torch, prob, dev, stream)
+    extra = [c for c in args.configs.split(",") if c] if world == 1 else []
+    if extra:
+        for m in results:
+            results[m][0].close()
+        results = {}
+        torch.cuda.empty_cache()
+        line["configs"] = {c: config_leg(ieti, torch, c, dev, stream, flush_buf, max(1, args.config_steps))
+                           for c in extra}
     if cb is not None:
         line["cpu_baseline"] = cb
     if rank == 0:

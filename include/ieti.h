@@ -108,8 +108,12 @@ typedef struct {
   int32_t host_threads;  /* threads for the host setup (0 = all cores) */
   void *cuda_stream;     /* cudaStream_t (0 = legacy default stream) */
   int32_t profile;       /* 1: time every launch of the operator kernels with CUDA events (ieti_kernel_stats) */
-  int32_t l2_persist;    /* 1: keep the per-iteration operators in a persisting L2 carve-out during a step
-                            (reset to normal at the end of every step); 0: plain streaming */
+  int32_t l2_persist;    /* L2 use by the per-iteration operators (H, Psi, S_bb, coarse), re-read every
+                            PCG iteration.  0: plain streaming.  1: a persisting L2 carve-out (access-policy
+                            window) during a step.  2: eviction-priority hints on their TMA loads: a fraction
+                            of the lines (about 60% of the L2 worth) loaded evict-last, the per-sweep operators
+                            evict-first.  Modes 1 and 2 return the lines to normal priority at the end of
+                            every step. */
   int32_t factor;        /* IETI_FACTOR_* (MIXED precision only; must be IETI_FACTOR_FP64 with FP64) */
   /* Newton's method for a nonlinear reluctivity (ignored for linear problems).  Each
    * iteration evaluates the FP64 residual R(a) = W a + dt N(a) - f of the nonlinear

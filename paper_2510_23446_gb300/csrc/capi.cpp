@@ -27,7 +27,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (!(o->outer_tol >= 0.0)) { err = "outer_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->device < -1) { err = "device must be >= -1"; return IETI_ERR_INVALID_ARG; }
   if (o->pcg_mode != 0 && o->pcg_mode != 1) { err = "pcg_mode must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
-  if (o->l2_persist != 0 && o->l2_persist != 1) { err = "l2_persist must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
+  if (o->l2_persist < 0 || o->l2_persist > 2) { err = "l2_persist must be 0, 1 or 2"; return IETI_ERR_INVALID_ARG; }
   if (o->factor < IETI_FACTOR_FP64 || o->factor > IETI_FACTOR_BF16) { err = "bad factor"; return IETI_ERR_INVALID_ARG; }
   if (o->refactor < IETI_REFACTOR_EVERY || o->refactor > IETI_REFACTOR_NEVER) { err = "bad refactor"; return IETI_ERR_INVALID_ARG; }
   if (!(o->newton_tol >= 0.0)) { err = "newton_tol must be >= 0"; return IETI_ERR_INVALID_ARG; }

@@ -791,11 +791,15 @@ struct DeviceState {
   double *Scoarse_slot = nullptr;  // coarse operator used by the PCG kernel (inside iter_arena)
   size_t iter_bytes = 0, l2_window = 0;
   float l2_hit_ratio = 0.f;
+  float l2_keep_frac = 0.f;  // l2_persist = 2: fraction of the arena's lines loaded evict-last
   bool l2_set = false;
   size_t l2_prev_limit = 0;
   int n_stages = 3;
   int32_t *ell_lam = nullptr, *cp_pos = nullptr;
   double *ell_sgn = nullptr, *ell_wd = nullptr;
+  int32_t *nb_idx = nullptr;               // [NBt][NB_W] interface-copy neighbours (self first)
+  double *nb_ca = nullptr, *nb_cb = nullptr;  // their B_D^T B and B^T B_D coefficients
+  double *yv0 = nullptr, *yv1 = nullptr;    // B_D^T r of the current / next PCG iterate
   double *p1 = nullptr, *r1 = nullptr, *zb = nullptr, *zf = nullptr, *ubp = nullptr, *tpi = nullptr, *zp = nullptr,
          *ccg = nullptr, *ppart = nullptr;
   unsigned *bar = nullptr;
@@ -1817,6 +1821,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   a.max_it = d->opt.cg_max_it;
   a.tol2 = d->opt.cg_tol * d->opt.cg_tol;
   a.bt_lam = d->ell_lam; a.bt_sgn = d->ell_sgn; a.bt_wd = d->ell_wd;
+  a.nb_idx = d->nb_idx; a.nb_ca = d->nb_ca; a.nb_cb = d->nb_cb; a.yv0 = d->yv0; a.yv1 = d->yv1;
   a.lam_qp = d->lam_qp; a.lam_qm = d->lam_qm;
   a.lam_wp = a.scaled ? d->lam_wp : nullptr;
   a.lam_wm = a.scaled ? d->lam_wm : nullptr;
@@ -1840,6 +1845,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   a.stage_bytes = d->stage_bytes;
   a.xs_bytes = d->xs_bytes;
   a.n_stages = d->n_stages;
+  a.l2_keep_frac = d->l2_keep_frac;
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
   prof_begin(d, IETI_K_PCG, 0.0);
@@ -2114,6 +2120,13 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
 // =============================================================================
 // Setup orchestration
 // =============================================================================
+// return the L2 lines of the per-iteration operator arena to normal eviction priority
+// (they were loaded evict-last during the step), so that later traffic can evict them
+__global__ void k_l2_demote(const unsigned char *base, int64_t lines) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lines; i += (int64_t)gridDim.x * blockDim.x)
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(base + 128 * i) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Schedule of the persistent dual-primal kernel and its autotuner.
 //
@@ -3056,6 +3069,40 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     if ((rc = upload(d, &d->ell_lam, ell_l, err)) || (rc = upload(d, &d->ell_sgn, ell_s, err)) ||
         (rc = upload(d, &d->ell_wd, ell_w, err)) || (rc = upload(d, &d->cp_pos, cpp, err)))
       return fail(rc);
+    {
+      // interface-copy neighbour lists of the two products through the multipliers the
+      // preconditioner needs every iteration: entry 0 is the copy itself, entries 1..3
+      // the other copies of its edge DOF (one multiplier joins the copy to each)
+      //   (B_D^T B v)_q = sum_t wd_qt (v[qp(l_t)] - v[qm(l_t)])          -> coefficients ca
+      //   (B^T B_D v)_q = sum_t sgn_qt (wp_l v[qp(l_t)] - wm_l v[qm(l_t)]) -> coefficients cb
+      const bool scaled = opt.precond == IETI_PRECOND_DIRICHLET_MULT || opt.precond == IETI_PRECOND_DIRICHLET_STIFF;
+      std::vector<int32_t> nidx(d->NBt * NB_W, -1);
+      std::vector<double> nca(d->NBt * NB_W, 0.0), ncb(d->NBt * NB_W, 0.0);
+      for (int64_t q = 0; q < d->NBt; ++q) {
+        nidx[q * NB_W] = (int32_t)q;
+        int e = 1;
+        for (int t = bt_ptr[q]; t < bt_ptr[q + 1]; ++t) {
+          const int32_t l = bt_lam[t];
+          const bool plus = qp[l] == (int32_t)q;
+          const int32_t other = plus ? qm[l] : qp[l];
+          const double wdq = scaled ? bt_wd[t] : bt_sgn[t], sg = bt_sgn[t];
+          const double wpl = scaled ? wp[l] : 1.0, wml = scaled ? wm[l] : 1.0;
+          // v[qp] carries +1 (ca) / +wp (cb), v[qm] carries -1 / -wm
+          const double a_self = plus ? wdq : -wdq, a_other = -a_self;
+          const double b_self = plus ? sg * wpl : -sg * wml, b_other = plus ? -sg * wml : sg * wpl;
+          nca[q * NB_W] += a_self;
+          ncb[q * NB_W] += b_self;
+          nidx[q * NB_W + e] = other;
+          nca[q * NB_W + e] = a_other;
+          ncb[q * NB_W + e] = b_other;
+          ++e;
+        }
+      }
+      if ((rc = upload(d, &d->nb_idx, nidx, err)) || (rc = upload(d, &d->nb_ca, nca, err)) ||
+          (rc = upload(d, &d->nb_cb, ncb, err)) || (rc = dalloc(d, &d->yv0, d->NBt, err)) ||
+          (rc = dalloc(d, &d->yv1, d->NBt, err)))
+        return fail(rc);
+    }
     if ((rc = dalloc(d, &d->p1, m, err)) || (rc = dalloc(d, &d->r1, m, err)) || (rc = dalloc(d, &d->zb, d->NBt, err)) ||
         (rc = dalloc(d, &d->zf, d->NBt, err)) || (rc = dalloc(d, &d->ubp, d->NBt, err)) ||
         (rc = dalloc(d, &d->ub1, d->NBt, err)) || (rc = dalloc(d, &d->uz, d->NBt, err)) ||
@@ -3067,7 +3114,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       return fail(rc);
     CK(cudaMemsetAsync(d->p, 0, m * sizeof(double), d->stream));
     CK(cudaMemsetAsync(d->p1, 0, m * sizeof(double), d->stream));
-    if (opt.l2_persist) {
+    if (opt.l2_persist == 2) {
+      // keep about 60% of the L2 for the per-iteration operators, the rest for the
+      // vectors and the per-sweep streams
+      int l2 = 0;
+      CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, d->device));
+      if (l2 > 0 && d->iter_bytes > 0)
+        d->l2_keep_frac = (float)std::min(1.0, 0.6 * (double)l2 / (double)d->iter_bytes);
+    } else if (opt.l2_persist == 1) {
       int max_persist = 0, max_window = 0;
       CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, d->device));
       CK(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, d->device));
@@ -3135,6 +3189,11 @@ int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std:
   // the carve-out only serves the iterations inside a step: return its lines to
   // normal so that whatever runs between steps can evict them
   if (d->l2_window > 0) CK(cudaCtxResetPersistingL2Cache());
+  if (d->l2_keep_frac > 0.f) {
+    const int64_t lines = (int64_t)(d->iter_bytes / 128);
+    k_l2_demote<<<grid_for(lines, 256), 256, 0, d->stream>>>(d->iter_arena, lines);
+    CK(cudaGetLastError());
+  }
   prof_collect(d);
   if (st) {
     float ms = 0;

@@ -33,6 +33,7 @@ namespace ieti {
 constexpr int PCG_THREADS = 256;
 constexpr int BT_W = 3;   // multipliers per interface copy (a DOF shared by at most 4 patches)
 constexpr int CP_W = 4;   // copies per coarse DOF
+constexpr int NB_W = 4;   // an interface copy and the other copies of its DOF
 
 template <class T>
 struct PcgArgs {
@@ -46,6 +47,11 @@ struct PcgArgs {
   const double *bt_sgn, *bt_wd;     // [NBt][BT_W]
   const int32_t *lam_qp, *lam_qm;
   const double *lam_wp, *lam_wm;
+  // interface-copy neighbour lists [NBt][NB_W] (self first, -1 = none) with the
+  // coefficients of B_D^T B (ca) and of B^T B_D (cb), and B_D^T r kept in B-space
+  const int32_t *nb_idx;
+  const double *nb_ca, *nb_cb;
+  double *yv0, *yv1;
   // per patch
   const int64_t *kofs, *bofs, *pofs, *hoff, *qoff, *poff, *igoff, *gtoff;
   const int32_t *ni, *nb, *np, *ldb, *ldp, *ldi, *ldg;
@@ -71,6 +77,7 @@ struct PcgArgs {
   unsigned long long *trace;  // optional: CTA 0 phase timestamps, [TRACE_IT][TRACE_SLOTS]
   unsigned stage_bytes, xs_bytes;
   int n_stages;
+  float l2_keep_frac;  // > 0: L2 eviction-priority hints on the operator streams
 };
 
 constexpr int TRACE_IT = 16;
@@ -314,6 +321,8 @@ struct OpRows {
   const int32_t *seg_s, *seg_r0, *seg_r1;
   int sb, se;
   int r0s, r1s, lds;
+  uint64_t policy;  // L2 eviction policy of the TMA loads (used when hint != 0)
+  int hint;
   __device__ int nseg() const { return seg_s ? se - sb : (r1s > r0s ? 1 : 0); }
   __device__ void seg(int k, int &s, int &r0, int &r1, int &l, const E *&A) const {
     if (seg_s) {
@@ -359,7 +368,11 @@ __device__ bool issue_next(Ring &ring, const OpRows<E> &op, Cursor &cur) {
       unsigned bytes = (unsigned)min(rpc, r1 - r0 - c0) * (unsigned)ld * sizeof(E);
       fence_proxy_async();
       mbar_arrive_expect_tx(ring.bar + st, bytes);
-      tma_load_1d(ring.stage + (size_t)st * ring.bytes, A + (int64_t)(r0 + c0) * ld, bytes, ring.bar + st);
+      if (op.hint)
+        tma_load_1d_hint(ring.stage + (size_t)st * ring.bytes, A + (int64_t)(r0 + c0) * ld, bytes, ring.bar + st,
+                         op.policy);
+      else
+        tma_load_1d(ring.stage + (size_t)st * ring.bytes, A + (int64_t)(r0 + c0) * ld, bytes, ring.bar + st);
     }
     ring.issued++;
     cur.chunk++;
@@ -506,19 +519,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   double *part_dd = a.part, *part_rz = a.part + G, *part_pq = a.part + 2 * G, *part_rr = a.part + 3 * G;
 
   // the operator rows of each phase (static per CTA)
-  const OpRows<T> opIG{a.IG, a.igoff, a.ldi, a.iseg_s, a.iseg_r0, a.iseg_r1, a.iseg_ptr[cta], a.iseg_ptr[cta + 1], 0, 0, 0};
-  const OpRows<T> opH{a.H, a.hoff, a.ldb, a.hseg_s, a.hseg_r0, a.hseg_r1, a.hseg_ptr[cta], a.hseg_ptr[cta + 1], 0, 0, 0};
-  const OpRows<T> opQ{a.Q, a.qoff, a.ldp, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1], 0, 0, 0};
-  const OpRows<T> opP{a.P, a.poff, a.ldb, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1], 0, 0, 0};
-  const OpRows<T> opGT{a.GT, a.gtoff, a.ldg, a.tseg_s, a.tseg_r0, a.tseg_r1, a.tseg_ptr[cta], a.tseg_ptr[cta + 1], 0, 0, 0};
-  const OpRows<double> opS{a.Sinv, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, (int)cb, (int)ce, a.ldc};
+  // L2 hints (l2_keep_frac > 0): the per-iteration operators (H, Psi, S_bb, coarse) are
+  // re-read every iteration, a fraction of their lines is kept in L2; the per-sweep
+  // operators (IG, GT) stream through
+  const int hint = a.l2_keep_frac > 0.f;
+  const uint64_t pk = hint ? l2_policy_keep(a.l2_keep_frac) : 0ull, ps = hint ? l2_policy_stream() : 0ull;
+  const OpRows<T> opIG{a.IG, a.igoff, a.ldi, a.iseg_s, a.iseg_r0, a.iseg_r1, a.iseg_ptr[cta], a.iseg_ptr[cta + 1],
+                       0, 0, 0, ps, hint};
+  const OpRows<T> opH{a.H, a.hoff, a.ldb, a.hseg_s, a.hseg_r0, a.hseg_r1, a.hseg_ptr[cta], a.hseg_ptr[cta + 1],
+                      0, 0, 0, pk, hint};
+  const OpRows<T> opQ{a.Q, a.qoff, a.ldp, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1],
+                      0, 0, 0, pk, hint};
+  const OpRows<T> opP{a.P, a.poff, a.ldb, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1],
+                      0, 0, 0, pk, hint};
+  const OpRows<T> opGT{a.GT, a.gtoff, a.ldg, a.tseg_s, a.tseg_r0, a.tseg_r1, a.tseg_ptr[cta], a.tseg_ptr[cta + 1],
+                       0, 0, 0, ps, hint};
+  const OpRows<double> opS{a.Sinv, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, (int)cb, (int)ce, a.ldc,
+                           pk, hint};
 
   // stage x_s[k] = f(k) (k < n), zero-padded to ld
   auto stage = [&](int n, int ld, auto f) {
     for (int k = threadIdx.x; k < ld; k += nthr) xs[k] = (T)(k < n ? f(k) : 0.0);
   };
   // stage u_s = B^T-type gather of patch s (ELL lists); keep it in ub for rows [r0, r1)
-  auto gather = [&](int s, const double *w, int r0, int r1, bool store_ub, auto val) {
+  auto gather = [&](int s, const double *w, int r0, int r1, double *store, auto val) {
     int nbs = a.nb[s], ld = a.ldb[s];
     int64_t b0 = a.bofs[s];
     constexpr int KP = 4;  // entries per thread per round, loads issued together
@@ -544,7 +568,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
 #pragma unroll
           for (int t = 0; t < BT_W; ++t)
             if (lidx[u][t] >= 0) acc += w[(b0 + k) * BT_W + t] * vals[u][t];
-          if (store_ub && k >= r0 && k < r1) a.ub[b0 + k] = acc;
+          if (store && k >= r0 && k < r1) store[b0 + k] = acc;
         }
         xs[k] = (T)acc;
       }
@@ -557,6 +581,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   auto jump = [&](const double *v, int64_t l) { return ldcg(v + a.lam_qp[l]) - ldcg(v + a.lam_qm[l]); };
   Cursor cur;  // producer cursor of the phase about to run (possibly prefetched)
   double *ub_old = a.ub1, *ub_new = a.ub;  // B^T p of the previous / current iteration
+  double *yv_old = a.yv0, *yv_new = a.yv1;  // B_D^T r of the current / next iterate
   unsigned long long *tsub = nullptr;  // sub-phase timestamps of the traced iteration (or null)
   auto tsp = [&](int k) { return tsub ? tsub + 3 * k : nullptr; };
   // H phase: [F; Psi^T] u_s -> zb, tpi, with a staging functor for u_s
@@ -627,15 +652,57 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         },
         tsp(2));
   };
-  auto precond_rows = [&](auto val) -> bool {
-    return stream_phase<4>(ring, opP, cur, xs, ybuf, errflag, [&](int s, int, int) { gather(s, wd, 0, 0, false, val); },
+  // S_bb rows against B_D^T r staged by gathering val(l) over the multipliers of each
+  // copy; the segment owner keeps B_D^T r (store, B-space) for the next iteration
+  auto precond_rows = [&](double *store, auto val) -> bool {
+    return stream_phase<4>(ring, opP, cur, xs, ybuf, errflag,
+                           [&](int s, int r0, int r1) { gather(s, wd, r0, r1, store, val); },
                            [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
   };
+  // the same with B_D^T r_new = B_D^T r_cur - alpha B_D^T B zf staged from the kept
+  // B-space copy yo and the neighbour lists (two dependent loads instead of three)
+  auto precond_rows_y = [&](double alpha, const double *yo, double *yn) -> bool {
+    return stream_phase<4>(
+        ring, opP, cur, xs, ybuf, errflag,
+        [&](int s, int r0, int r1) {
+          const int nbs = a.nb[s], ld = a.ldb[s];
+          const int64_t b0 = a.bofs[s];
+          for (int k = threadIdx.x; k < ld; k += nthr) {
+            double y = 0.0;
+            if (k < nbs) {
+              const int64_t q = b0 + k;
+              const int4 id = __ldg(reinterpret_cast<const int4 *>(a.nb_idx) + q);
+              const double2 c01 = __ldg(reinterpret_cast<const double2 *>(a.nb_ca) + 2 * q);
+              const double2 c23 = __ldg(reinterpret_cast<const double2 *>(a.nb_ca) + 2 * q + 1);
+              const double yq = ldcg(yo + q);
+              double acc = c01.x * ldcg(a.zf + id.x);
+              if (id.y >= 0) acc += c01.y * ldcg(a.zf + id.y);
+              if (id.z >= 0) acc += c23.x * ldcg(a.zf + id.z);
+              if (id.w >= 0) acc += c23.y * ldcg(a.zf + id.w);
+              y = yq - alpha * acc;
+              if (k >= r0 && k < r1) yn[q] = y;
+            }
+            xs[k] = (T)y;
+          }
+        },
+        [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
+  };
   auto sync = [&](unsigned long long *tr) { return grid_sync(a.bar, G, target, tr); };
-  // z on the multipliers from the preconditioned interface values (or r itself)
-  auto zval = [&](double rv, int l) { return a.precond_none ? rv : jumpD(a.zp, l); };
   // uz = B^T z on this CTA's chunk of interface copies (z recomputed on the fly)
   const int64_t qb = a.nbt * cta / G, qe = a.nbt * (cta + 1) / G;
+  // uz = B^T B_D zp on this CTA's chunk (preconditioned runs), by the neighbour lists
+  auto uz_chunk_nb = [&]() {
+    for (int64_t q = qb + threadIdx.x; q < qe; q += nthr) {
+      const int4 id = __ldg(reinterpret_cast<const int4 *>(a.nb_idx) + q);
+      const double2 c01 = __ldg(reinterpret_cast<const double2 *>(a.nb_cb) + 2 * q);
+      const double2 c23 = __ldg(reinterpret_cast<const double2 *>(a.nb_cb) + 2 * q + 1);
+      double u = c01.x * ldcg(a.zp + id.x);
+      if (id.y >= 0) u += c01.y * ldcg(a.zp + id.y);
+      if (id.z >= 0) u += c23.x * ldcg(a.zp + id.z);
+      if (id.w >= 0) u += c23.y * ldcg(a.zp + id.w);
+      a.uz[q] = u;
+    }
+  };
   auto uz_chunk = [&](auto zf_of) {
     for (int64_t q = qb + threadIdx.x; q < qe; q += nthr) {
       double u = 0.0;
@@ -691,7 +758,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part_dd[cta] = acc;
-  if (!a.precond_none && !precond_rows([&](int l) { return jump(a.zf, l); })) return;
+  if (!a.precond_none && !precond_rows(a.yv0, [&](int l) { return jump(a.zf, l); })) return;
   cur = prefetch(ring, opH);
   if (!sync(nullptr)) return;
   const double dd = reduce_slot(part_dd, G, sh);
@@ -708,7 +775,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
     }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) part_rz[cta] = acc;
-    uz_chunk([&](int l) { return zval(ldcg(a.r0 + l), l); });
+    if (a.precond_none) uz_chunk([&](int l) { return ldcg(a.r0 + l); });
+    else uz_chunk_nb();
     if (!sync(nullptr)) return;
     double rz_old = reduce_slot(part_rz, G, sh);
     double *rcur = a.r0, *rnxt = a.r1, *pcur = a.p0, *pnxt = a.p1;
@@ -773,9 +841,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       }
       acc = block_sum(acc, sh);
       if (threadIdx.x == 0) part_rr[cta] = acc;
-      if (!a.precond_none &&
-          !precond_rows([&](int l) { return ldcg(rcur + l) - alpha * jump(a.zf, l); }))
-        return;
+      if (!a.precond_none && !precond_rows_y(alpha, yv_old, yv_new)) return;
       cur = prefetch(ring, opH);
       if (!sync(tr ? tr + 8 : nullptr)) return;
       // ---------------- P6: convergence, z = B_D zp, (r, z)
@@ -790,11 +856,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       }
       acc = block_sum(acc, sh);
       if (threadIdx.x == 0) part_rz[cta] = acc;
-      uz_chunk([&](int l) { return zval(ldcg(rnxt + l), l); });
+      if (a.precond_none) uz_chunk([&](int l) { return ldcg(rnxt + l); });
+      else uz_chunk_nb();
       if (!sync(tr ? tr + 10 : nullptr)) return;
       double *t = rcur; rcur = rnxt; rnxt = t;
       t = pcur; pcur = pnxt; pnxt = t;
       t = ub_old; ub_old = ub_new; ub_new = t;
+      t = yv_old; yv_old = yv_new; yv_new = t;
     }
   }
   tsub = nullptr;

@@ -37,6 +37,29 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
       : "memory");
 }
 
+// the same with an L2 eviction-priority policy (from createpolicy) for the source lines
+__device__ __forceinline__ void tma_load_1d_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 policies: a fraction `frac` of the lines (chosen by address) evicted last, the
+// rest evicted first; and all lines evicted first
+__device__ __forceinline__ uint64_t l2_policy_keep(float frac) {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;" : "=l"(p) : "f"(frac));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   unsigned ok;
   asm volatile(

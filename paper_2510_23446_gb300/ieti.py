@@ -133,7 +133,7 @@ class Solver:
 
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, reluctivity=None, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
-                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=1,
+                 outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None):
         self._keep = []
 
