@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps per extra workload and path")
     ap.add_argument("--profile-step", action="store_true",
                     help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
+    ap.add_argument("--tune-cache", default=None,
+                    help="schedule cache file for --profile-step (a second run reads the first run's choice "
+                         "instead of launching the autotuner's timing solves)")
     return ap.parse_args()
 
 
@@ -608,12 +611,14 @@ def run_profile_step(args):
     build()
     from paper_2510_23446_gb300 import ieti
     prob = make_problem("c2")
-    S = ieti.Solver.from_problem(prob, device=0, **OPTS["mixed"])
+    S = ieti.Solver.from_problem(prob, device=0, tune_cache=args.tune_cache, **OPTS["mixed"])
     jd = torch.from_numpy(S.load_vector(prob.coil)).cuda()
     for _ in range(max(1, args.warmup) + 2):
         st = S.step(jd)
     torch.cuda.synchronize()
-    print("profile-step done:", st, flush=True)
+    inf = S.info()
+    print("profile-step done:", st, {k: inf[k] for k in ("pcg_grid", "pcg_stages", "pcg_stage_bytes",
+                                                           "pcg_sched_source", "tune_candidates")}, flush=True)
     S.close()
     return 0
 
