@@ -139,6 +139,13 @@ typedef struct {
    * afresh); a failed write leaves setup successful (ieti_info.pcg_sched_source). */
   int32_t autotune;
   const char *tune_cache;
+  /* 1: run the refinement sweeps of each step of a linear problem as one CUDA graph
+   * (a while node whose condition a device kernel sets from the assembled residual
+   * norm and the PCG status: no host round trip per sweep); 0: the host loop.  The
+   * graph is built at setup and needs pcg_mode 0, profile 0 and l2_persist != 1; if
+   * building it fails the host loop runs (ieti_info.step_graph).  Same sweeps, same
+   * stopping rules, same results. */
+  int32_t graph;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -197,6 +204,7 @@ typedef struct {
   int32_t tune_candidates;   /* schedules timed by the autotuner */
   double tune_ms;            /* host time of the autotuning */
   double tune_us_per_it[2];  /* measured time per PCG iteration: the rule's schedule, the chosen one */
+  int32_t step_graph;        /* 1: the sweeps of a step run as one CUDA graph (ieti_options.graph) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -649,7 +649,54 @@ __global__ void k_dot_partial(int64_t n, const double *x, const double *y, doubl
 }
 
 // sc[idx] = sum(part); op 1: sc[4] = sc[1]/sc[2] (alpha); op 2: sc[5] = sc[6]/sc[1], sc[1] = sc[6] (beta)
-enum { SC_DD = 0, SC_RZ = 1, SC_PQ = 2, SC_RR = 3, SC_ALPHA = 4, SC_BETA = 5, SC_RZNEW = 6, SC_TMP = 7 };
+enum { SC_DD = 0, SC_RZ = 1, SC_PQ = 2, SC_RR = 3, SC_ALPHA = 4, SC_BETA = 5, SC_RZNEW = 6, SC_TMP = 7, SC_FN = 8 };
+
+// Device-side control of a step's refinement sweeps (graph mode): the decisions the
+// host loop takes after reading the residual norm and the PCG status, taken on the
+// device so that the whole sweep loop runs as one CUDA graph with a while node.
+struct StepCtl {
+  double prev, ores, rel;
+  int sweeps, its, cg_fail, bar_err, status;  // status: 1 converged, 2 max sweeps, 3 stagnated, 4 barrier error
+};
+
+// after the residual norm of the current iterate: stop (converged, out of sweeps,
+// stagnated, barrier error) or run one more sweep (the while node's condition)
+__global__ void k_ctl_decide(StepCtl *c, const double *sc, cudaGraphConditionalHandle h, double outer_tol,
+                             int max_sweeps, int first) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (first) {
+    c->prev = -1.0;
+    c->rel = 0.0;
+    c->sweeps = c->its = c->cg_fail = c->bar_err = c->status = 0;
+  }
+  const double fn = sqrt(sc[SC_FN]), rn = sqrt(sc[SC_TMP]);
+  const double ores = fn > 0.0 ? rn / fn : 0.0;
+  c->ores = ores;
+  unsigned cont = 0;
+  if (c->bar_err) c->status = 4;
+  else if (ores <= outer_tol || fn == 0.0) c->status = 1;
+  else if (c->sweeps >= max_sweeps) c->status = 2;
+  else if (c->sweeps >= 2 && rn > 0.9 * c->prev) c->status = 3;
+  else {
+    cont = 1;
+    c->prev = rn;
+  }
+  cudaGraphSetConditional(h, cont);
+}
+
+// after a dual-primal solve: its iterations, barrier status and convergence
+__global__ void k_ctl_solved(StepCtl *c, const int *its, const unsigned *bar, const double *rr, const double *dd,
+                             double tol2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  c->sweeps++;
+  c->its += *its;
+  if (bar[1]) c->bar_err = 1;
+  const double r = *rr, q = *dd;
+  if (q > 0.0) {
+    c->rel = sqrt(r / q);
+    if (!isfinite(r) || r > tol2 * q) c->cg_fail = 1;
+  }
+}
 // partial sums of sum_k own[k] x[k]^2 (each global DOF once)
 __global__ void k_owner_sq(int64_t n, const uint8_t *own, const double *x, double *part) {
   __shared__ double sh[32];
@@ -813,6 +860,10 @@ struct DeviceState {
   double *pcg_rr = nullptr, *pcg_dd = nullptr;
   double bytes_iter_alg = 0, bytes_sweep_alg = 0;
   unsigned xs_bytes = 0, stage_bytes = 0;
+  // graph mode: the sweep loop of a step as one CUDA graph (while node)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  StepCtl *ctl = nullptr, *h_ctl = nullptr;
   // schedule of the persistent kernel: host copies of the per-patch row counts and
   // leading dimensions of its four partitions (re-planned by the autotuner)
   std::vector<int32_t> plan_rows[4], plan_ld[4];
@@ -1806,11 +1857,10 @@ static int pcg(DeviceState *d, int *its, double *rel, std::string &err) {
 
 // the whole dual-primal solve of a sweep as one persistent cooperative launch
 // (pcg_kernel.cuh): condensation, d, PCG, recovery
+// launch only (stream-ordered, no host synchronisation; usable under stream capture):
+// barrier reset, trace reset, the cooperative launch on stream st
 template <class T>
-static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
-  cudaStream_t st = d->stream;
-  *its = 0;
-  *rel = 0.0;
+static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::string &err) {
   CK(cudaMemsetAsync(d->bar, 0, 3 * sizeof(unsigned), st));
   PcgArgs<T> a;
   a.m = d->M;
@@ -1872,8 +1922,21 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
     cfg.numAttrs = nattr;
     CK(cudaLaunchKernelExC(&cfg, (const void *)k_ddsolve<T>, args));
   }
+  return IETI_OK;
+}
+
+template <class T>
+static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *rel, std::string &err) {
+  cudaStream_t st = d->stream;
+  *its = 0;
+  *rel = 0.0;
+  prof_begin(d, IETI_K_PCG, 0.0);
+  int lrc = pcg_launch<T>(d, rhs, st, err);
+  if (lrc) return lrc;
   d->nlaunch++;
   prof_end(d);
+  const double tol2 = d->opt.cg_tol * d->opt.cg_tol;
+  const bool traced = d->opt.profile != 0;
   struct {
     int its;
     unsigned bar[3];
@@ -1890,7 +1953,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   }
   *its = h.its;
   prof_set_bytes(d, d->bytes_iter_alg * (h.its + 2) + d->bytes_sweep_alg);
-  if (a.trace) {
+  if (traced) {
     unsigned long long tr[TRACE_IT * TRACE_SLOTS];
     CK(cudaMemcpy(tr, d->trace, sizeof(tr), cudaMemcpyDeviceToHost));
     for (int i = 0; i < std::min(h.its - 1, TRACE_IT); ++i) {
@@ -1921,7 +1984,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
     err = "PCG breakdown (non-finite residual)";
     return IETI_ERR_CG_NOT_CONVERGED;
   }
-  if (h.rr > a.tol2 * h.dd) {
+  if (h.rr > tol2 * h.dd) {
     err = "PCG did not reach cg_tol within cg_max_it";
     return IETI_ERR_CG_NOT_CONVERGED;
   }
@@ -2007,6 +2070,130 @@ static int assemble_norm(DeviceState *d, const double *v, double *out, std::stri
   return rc;
 }
 
+// residual of the assembled system at the current iterate and its squared norm
+// (kernels only, no host read): kr, rglob, sc[SC_TMP]
+static void resid_norm_launch(DeviceState *d, cudaStream_t st) {
+  k_resid<<<grid_for(d->NK * 32, 256), 256, 0, st>>>(d->NK, d->wptr, d->wcol, d->wval, d->ka, d->kf, d->kr);
+  k_assemble_free<<<RED_BLOCKS, 256, 0, st>>>(d->NF, d->fptr, d->fpos, d->fglob, d->kr, d->rglob, d->part);
+  k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_TMP, 0);
+}
+
+static void graph_release(DeviceState *d) {
+  if (d->gexec) cudaGraphExecDestroy(d->gexec);
+  if (d->graph) cudaGraphDestroy(d->graph);
+  d->gexec = nullptr;
+  d->graph = nullptr;
+}
+
+// Build the sweep loop of a linear step as one CUDA graph:
+//   residual + norm, decide  ->  while (condition) { distribute, dual-primal solve,
+//   solve status, owner update, gather, residual + norm, decide }
+// captured on a private stream (the legacy default stream cannot be captured).
+// Returns non-zero (graph mode off, state unchanged) when any graph call fails.
+template <class T>
+static int graph_build(DeviceState *d, std::string &err) {
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  auto bad = [&](const char *what, cudaError_t e) {
+    if (cs) {
+      cudaStreamCaptureStatus stt;
+      if (cudaStreamIsCapturing(cs, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+      }
+      cudaStreamDestroy(cs);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    err = std::string("graph mode unavailable: ") + what + ": " + cudaGetErrorString(e);
+    return IETI_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return bad("stream", e);
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return bad("graph", e);
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, 0)) != cudaSuccess) return bad("conditional handle", e);
+  const double outer_tol = d->opt.outer_tol, tol2 = d->opt.cg_tol * d->opt.cg_tol;
+  const int max_sweeps = std::max(1, d->opt.max_sweeps);
+  // the part before the loop
+  if ((e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return bad("capture", e);
+  resid_norm_launch(d, cs);
+  k_ctl_decide<<<1, 32, 0, cs>>>(d->ctl, d->sc, h, outer_tol, max_sweeps, 1);
+  if ((e = cudaStreamEndCapture(cs, &g)) != cudaSuccess) return bad("end capture", e);
+  // its last node (the part is a chain: the node without dependents)
+  size_t nn = 0;
+  if ((e = cudaGraphGetNodes(g, nullptr, &nn)) != cudaSuccess || nn == 0) return bad("nodes", e);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if ((e = cudaGraphGetNodes(g, nodes.data(), &nn)) != cudaSuccess) return bad("nodes", e);
+  cudaGraphNode_t leaf = nullptr;
+  for (cudaGraphNode_t x : nodes) {
+    size_t nd = 0;
+    if ((e = cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nd)) != cudaSuccess) return bad("dependents", e);
+    if (nd == 0) leaf = x;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  if ((e = cudaGraphAddNode(&cnode, g, &leaf, nullptr, 1, &cp)) != cudaSuccess) return bad("while node", e);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return bad("body capture", e);
+  k_distribute<<<grid_for(d->NK, 256), 256, 0, cs>>>(d->NK, d->kglob, d->kw, d->rglob, d->kr);
+  std::string e2;
+  if (pcg_launch<T>(d, d->kr, cs, e2) != IETI_OK) return bad("dual-primal launch", cudaGetLastError());
+  k_ctl_solved<<<1, 32, 0, cs>>>(d->ctl, d->pcg_its, d->bar, d->pcg_rr, d->pcg_dd, tol2);
+  k_owner_add<<<grid_for(d->NK, 256), 256, 0, cs>>>(d->NK, d->kglob, d->kown, d->kx, d->a);
+  k_gather_kept<<<grid_for(d->NK, 256), 256, 0, cs>>>(d->NK, d->kglob, d->a, d->ka);
+  resid_norm_launch(d, cs);
+  k_ctl_decide<<<1, 32, 0, cs>>>(d->ctl, d->sc, h, outer_tol, max_sweeps, 0);
+  if ((e = cudaStreamEndCapture(cs, &body)) != cudaSuccess) return bad("end body capture", e);
+  if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) return bad("instantiate", e);
+  cudaStreamDestroy(cs);
+  d->graph = g;
+  d->gexec = ge;
+  return IETI_OK;
+}
+
+// the sweep loop of a linear step through the graph: one launch, one read of the
+// control block afterwards
+static int graph_sweeps(DeviceState *d, int *its_total, int *sweeps, double *rel, double *ores, std::string &err) {
+  CK(cudaGraphLaunch(d->gexec, d->stream));
+  CK(cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  const StepCtl c = *d->h_ctl;
+  *its_total = c.its;
+  *sweeps = c.sweeps;
+  *rel = c.rel;
+  *ores = c.ores;
+  d->nlaunch += 4 + 9 * (int64_t)c.sweeps;
+  if (c.bar_err) {
+    err = "persistent PCG: a grid barrier timed out";
+    return IETI_ERR_CUDA;
+  }
+  if (c.status == 2 && d->opt.max_sweeps > 1 && !c.cg_fail) {
+    err = "refinement did not reach outer_tol within max_sweeps";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  if (c.status == 3) {
+    err = c.cg_fail ? "PCG did not reach cg_tol within cg_max_it" : "refinement stagnated above outer_tol";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  if (c.cg_fail) {
+    err = "PCG did not reach cg_tol within cg_max_it";
+    return IETI_ERR_CG_NOT_CONVERGED;
+  }
+  return IETI_OK;
+}
+
 template <class T>
 static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   cudaStream_t st = d->stream;
@@ -2019,7 +2206,14 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   d->nlaunch++;
   double fn = 0.0;
   int rc;
-  if ((rc = assemble_norm(d, d->kf, &fn, err))) return rc;
+  if (d->gexec) {
+    // ||f||^2 stays on the device (sc[SC_FN]) for the graph's decisions
+    k_assemble_free<<<RED_BLOCKS, 256, 0, st>>>(d->NF, d->fptr, d->fpos, d->fglob, d->kf, d->rglob, d->part);
+    k_dot_final<<<1, 256, 0, st>>>(RED_BLOCKS, d->part, d->sc, SC_FN, 0);
+    d->nlaunch += 2;
+  } else if ((rc = assemble_norm(d, d->kf, &fn, err))) {
+    return rc;
+  }
   if (d->opt.predictor) {
     // keep a^l; with a^{l-1} known, start the sweeps from the extrapolated iterate
     CK(cudaMemcpyAsync(d->a_old, d->a, d->n_edges * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -2036,7 +2230,11 @@ static int step_impl(DeviceState *d, ieti_stats *stats, std::string &err) {
   const bool newton = d->nl_np > 0;
   bool update_small = false;
   d->step_refactors = 0;
-  for (int sweep = 0;; ++sweep) {
+  if (d->gexec) {
+    cg_rc = graph_sweeps(d, &its_total, &sweeps, &rel, &ores, err);
+    if (cg_rc != IETI_OK && cg_rc != IETI_ERR_CG_NOT_CONVERGED) return cg_rc;
+  }
+  for (int sweep = 0; !d->gexec; ++sweep) {
     // defect of the ASSEMBLED system at the current iterate, in FP64: r = f - W_g a,
     // redistributed over the patches with the 1/k weights (so that the local
     // right-hand sides of the correction are as small as the defect itself)
@@ -3170,6 +3368,14 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     rc = d->mixed ? pcg_autotune<float>(d, err) : pcg_autotune<double>(d, err);
     if (rc) return fail(rc);
   }
+  if (opt.graph && opt.pcg_mode == 0 && d->nl_np == 0 && !opt.profile && d->l2_window == 0) {
+    // the sweep loop of every step as one CUDA graph; without it (a graph call that
+    // fails here) the host loop runs the same sweeps
+    if ((rc = dalloc(d, &d->ctl, 1, err))) return fail(rc);
+    CK(cudaMallocHost((void **)&d->h_ctl, sizeof(StepCtl)));
+    std::string gerr;
+    if ((d->mixed ? graph_build<float>(d, gerr) : graph_build<double>(d, gerr)) != IETI_OK) graph_release(d);
+  }
   d->opt.tune_cache = nullptr;  // caller-owned, read during setup only
   d->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   (void)maxnp;
@@ -3247,6 +3453,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->refactors = d->refactors;
   info->nl_coarse_block = d->cN;
   for (int k = 0; k < 4; ++k) info->t_refactor_ms[k] = d->t_refactor_ms[k];
+  info->step_graph = d->gexec != nullptr;
   info->pcg_grid = d->G;
   info->pcg_stages = d->n_stages;
   info->pcg_stage_bytes = (int32_t)d->stage_bytes;
@@ -3284,6 +3491,8 @@ void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, double *
 
 void device_destroy(DeviceState *d) {
   if (!d) return;
+  graph_release(d);
+  if (d->h_ctl) cudaFreeHost(d->h_ctl);
   if (d->l2_set) {
     if (d->device >= 0) cudaSetDevice(d->device);
     cudaCtxResetPersistingL2Cache();

@@ -41,7 +41,8 @@ class ieti_options(C.Structure):
                 ("max_sweeps", C.c_int32), ("pcg_mode", C.c_int32), ("host_threads", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
-                ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p)]
+                ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
+                ("graph", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -74,7 +75,7 @@ class ieti_info(C.Structure):
                 ("nl_coarse_block", C.c_int64), ("t_refactor_ms", C.c_double * 4),
                 ("pcg_grid", C.c_int32), ("pcg_stages", C.c_int32), ("pcg_stage_bytes", C.c_int32),
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
-                ("tune_us_per_it", C.c_double * 2)]
+                ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32)]
 
 
 _ctx = C.c_void_p
@@ -134,7 +135,8 @@ class Solver:
     def __init__(self, P, n_el, degree, knots, ctrl, sigma_el, nu_el, dt, *, reluctivity=None, device=0,
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
-                 factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None):
+                 factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
+                 graph=1):
         self._keep = []
 
         def arr(x, dt_):
@@ -177,6 +179,7 @@ class Solver:
         op.newton_tol = float(newton_tol)
         op.predictor = int(predictor)
         op.autotune = int(autotune)
+        op.graph = int(graph)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
         self.options = op

@@ -105,6 +105,8 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     dict(precision="mixed", pcg_mode=3),
     dict(precision="fp64", predictor=3),
     dict(precision="mixed", factor="bf16", autotune=2),
+    dict(precision="fp64", graph=2),
+    dict(precision="fp64", l2_persist=3),
 ])
 def test_invalid_options_return_codes(ieti, kw):
     prob = make_problem("c1")
