@@ -422,6 +422,42 @@ def config_leg(ieti, torch, key, dev, stream, flush_buf, K, W=2):
             "rel_err_vs_fp64": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
 
 
+def precond_study_leg(ieti, torch, dev, stream, n_t=8):
+    """Mean PCG iterations per step against the element count per subdomain for every
+    preconditioner variant (Sec. 4 uses the unscaled Dirichlet one; Sec. 5 asks for
+    scaling): the paper's two-subdomain problem (p = 3, left subdomain conducting,
+    sigma = nu = 1), n_t steps on (0, 1] of the zero-trace manufactured field, FP64
+    path, PCG tolerance 1e-6 (the paper's setting), one sweep per step."""
+    import numpy as np
+    from workloads import small_problem
+    p = 3
+    out = {}
+    for n in (2, 4, 8):
+        prob = small_problem(P=(2, 1, 1), n_el=((n, n), (n,), (n,)), degree=((p, p), (p,), (p,)),
+                             conductor=((0.0, 0.5), (0.0, 1.0), (0.0, 1.0)), sigma=1.0, nu=1.0, dt=1.0 / n_t,
+                             n_steps=n_t, perturb=0.0, J0=0.0, name="paper_two_subdomains")
+        row = {}
+        for pc in ("none", "dirichlet", "dirichlet_mult", "dirichlet_stiff"):
+            S = ieti.Solver.from_problem(prob, device=dev, stream=stream, precision="fp64", precond=pc,
+                                         cg_tol=1e-6, max_sweeps=1)
+            xyz = S.quad_points()
+            sx, sy, sz = (np.sin(np.pi * xyz[:, d]) for d in range(3))
+            Aq = np.stack([sy * sz, sz * sx, sx * sy], axis=1)
+            jA = S.load_vector_points(Aq)
+            jS = S.load_vector_points(Aq * (xyz[:, :1] < 0.5))
+            its = []
+            for l in range(1, n_t + 1):
+                t = l / n_t
+                its.append(S.step(2 * np.pi ** 2 * (1 - np.exp(-t)) * jA + np.exp(-t) * jS)["cg_its"])
+            row[pc] = float(np.mean(its))
+            n_dofs, n_coarse = S.n, S.info()["n_coarse"]
+            S.close()
+        out[f"h=1/{2 * n}"] = {"elements_per_subdomain": f"{n}^3", "n_dofs": n_dofs, "n_coarse": n_coarse,
+                               "mean_cg_its": row}
+    return {"workload": f"Sec. 4 geometry: 2 subdomains split at x = 0.5, p = 3, n_t = {n_t}, FP64 path, "
+                        "PCG tol 1e-6, one sweep per step", "by_h": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -577,6 +613,8 @@ def run_ours(args):
         results = {}
         torch.cuda.empty_cache()
         line["nonlinear"] = nonlinear_leg(ieti, torch, dev, stream, flush_buf, max(1, args.nl_steps), 1)
+    if world == 1 and not args.no_paper_case:
+        line["precond_study"] = precond_study_leg(ieti, torch, dev, stream)
     if world == 1 and not args.no_ablation:
         for m in results:
             results[m][0].close()
