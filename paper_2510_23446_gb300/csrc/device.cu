@@ -1898,7 +1898,6 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.l2_keep_frac = d->l2_keep_frac;
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
-  prof_begin(d, IETI_K_PCG, 0.0);
   {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(d->G);

@@ -82,3 +82,20 @@ def test_graph_mode_selection(ieti):
         if kw.get("l2_persist") == 1 and inf["l2_window_bytes"] == 0:
             want = 1      # no access-policy window on this device: nothing blocks the graph
         assert inf["step_graph"] == want, kw
+
+
+def test_profiled_steps_equal_unprofiled(ieti):
+    """Per-launch CUDA-event profiling (host loop) changes no result and fills the
+    kernel-class statistics."""
+    prob = make_problem("c1")
+    a, sa, _ = _run(ieti, prob, 2, **OPTS["mixed"])
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", profile=1, **OPTS["mixed"])
+    j = S.load_vector(prob.coil)
+    for x, s1 in zip(a, sa):
+        st = S.step(j)
+        assert (st["cg_its"], st["sweeps"]) == (s1["cg_its"], s1["sweeps"])
+        assert np.array_equal(S.solution(), x)
+    ks = S.kernel_stats()
+    assert ks["pcg"]["launches"] == sum(s["sweeps"] for s in sa) and ks["pcg"]["total_ms"] > 0
+    assert ks["spmv"]["launches"] > 0
+    S.close()
