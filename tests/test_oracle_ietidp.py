@@ -112,3 +112,29 @@ def test_unscaled_iterations_grow_with_h():
         its.append(np.mean(it))
     print("mean PCG iterations (unscaled Dirichlet, tol 1e-6):", its)
     assert its[1] >= its[0]
+
+
+def test_long_time_limit_is_the_magnetostatic_solve():
+    """With a constant load the implicit-Euler iterates approach the gauged
+    magnetostatic solution: the fixed point of W a^{l+1} = M a^l + dt j is K a = j on
+    the free DOFs (Eq. (11) with a^{l+1} = a^l).  Every step contracts the defect
+    K a^l - j by a fixed factor, so its norm falls geometrically; a wrong sign or a
+    misplaced dt in the step breaks that."""
+    prob = make_problem("c1")
+    prob.dt = 5.0                                  # long steps: few of them reach the limit
+    op = OracleProblem(prob)
+    mono = op.mono
+    K = (mono.W - mono.M) / prob.dt                # gauged stiffness on the free DOFs
+    jf = op.asm.j_global[mono.free]
+    defect = []
+    for a in op.run_monolithic(12):
+        defect.append(np.linalg.norm(K @ a[mono.free] - jf) / np.linalg.norm(jf))
+    assert defect[-1] < 1e-8, defect
+    # geometric decay down to the rounding floor of the sparse direct solves
+    d = np.array(defect)
+    above = d[:-1] > 1e-9
+    ratios = d[1:][above] / d[:-1][above]
+    assert above.sum() >= 3 and np.all(ratios < 0.5), (defect, ratios)
+    # the limit field is gradient-free against the load: (K a, a) = (j, a) at the end
+    a = op.run_monolithic(12)[-1][mono.free]
+    assert abs(a @ (K @ a) - jf @ a) <= 1e-8 * abs(jf @ a)
