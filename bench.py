@@ -652,7 +652,8 @@ def run_ours(args):
                                    "us": rm["phases"]["sub_us"]}},
     }
     line["config"]["schedule"] = {m: {k: results[m][0].info()[k] for k in (
-        "pcg_grid", "pcg_stages", "pcg_stage_bytes", "pcg_sched_source", "tune_candidates", "tune_ms",
+        "pcg_grid", "pcg_stages", "pcg_stage_bytes", "pcg_psi_partition", "pcg_sched_source", "tune_candidates",
+        "tune_ms",
         "tune_us_per_it")} for m in results}
     if world == 1 and not args.no_paper_case:
         line["paper_case"] = paper_case_leg(ieti, torch, dev, stream)

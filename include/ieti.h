@@ -132,7 +132,8 @@ typedef struct {
    * ring stages and bytes per stage.  0: the rule (one CTA per SM, three stages of
    * at most 64 KB).  1: autotune at setup: every feasible schedule of a fixed
    * candidate list runs a few PCG iterations on a synthetic right-hand side and the
-   * fastest is kept (results do not depend on the schedule beyond rounding order).
+   * fastest is kept, then partitions of the Psi rows of their own are tried on it
+   * (results do not depend on the schedule beyond rounding order).
    * tune_cache (NULL: none) names a text file of earlier choices keyed by device name,
    * precision and problem sizes: a matching entry is used without timing, a new
    * choice is added to it.  An unreadable or malformed cache is ignored (tuned
@@ -200,6 +201,8 @@ typedef struct {
   int32_t pcg_grid;          /* CTAs of the persistent dual-primal kernel */
   int32_t pcg_stages;        /* TMA ring stages per CTA */
   int32_t pcg_stage_bytes;   /* bytes per stage */
+  int32_t pcg_psi_partition; /* 0: the Psi rows share the S_bb rows' partition; > 0: their own, balanced with
+                                this per-row overhead (elements) */
   int32_t pcg_sched_source;  /* 0: rule, 1: autotuned, 2: autotuned and written to tune_cache, 3: from tune_cache */
   int32_t tune_candidates;   /* schedules timed by the autotuner */
   double tune_ms;            /* host time of the autotuning */

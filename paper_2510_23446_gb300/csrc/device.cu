@@ -829,6 +829,8 @@ struct DeviceState {
   int64_t *bofs_d = nullptr, *pofs_d = nullptr;
   int32_t *hseg_ptr = nullptr, *hseg_s = nullptr, *hseg_r0 = nullptr, *hseg_r1 = nullptr;
   int32_t *bseg_ptr = nullptr, *bseg_s = nullptr, *bseg_r0 = nullptr, *bseg_r1 = nullptr;
+  int32_t *qseg_ptr = nullptr, *qseg_s = nullptr, *qseg_r0 = nullptr, *qseg_r1 = nullptr;
+  int psi_overhead = 0;  // > 0: the Psi rows have their own partition (per-row overhead in elements)
   int32_t *iseg_ptr = nullptr, *iseg_s = nullptr, *iseg_r0 = nullptr, *iseg_r1 = nullptr;
   int32_t *tseg_ptr = nullptr, *tseg_s = nullptr, *tseg_r0 = nullptr, *tseg_r1 = nullptr;
   double *kg = nullptr, *ub1 = nullptr, *uz = nullptr;
@@ -866,7 +868,7 @@ struct DeviceState {
   StepCtl *ctl = nullptr, *h_ctl = nullptr;
   // schedule of the persistent kernel: host copies of the per-patch row counts and
   // leading dimensions of its four partitions (re-planned by the autotuner)
-  std::vector<int32_t> plan_rows[4], plan_ld[4];
+  std::vector<int32_t> plan_rows[5], plan_ld[5];
   int ldmax = 4, n_sm = 0, cps = 1;
   int sched_source = 0, tune_candidates = 0;
   double tune_ms = 0, tune_us[2] = {0, 0};
@@ -1883,6 +1885,11 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.H = (const T *)d->H; a.Q = (const T *)d->Q; a.P = (const T *)d->P; a.Sinv = d->Sinv;
   a.hseg_ptr = d->hseg_ptr; a.hseg_s = d->hseg_s; a.hseg_r0 = d->hseg_r0; a.hseg_r1 = d->hseg_r1;
   a.bseg_ptr = d->bseg_ptr; a.bseg_s = d->bseg_s; a.bseg_r0 = d->bseg_r0; a.bseg_r1 = d->bseg_r1;
+  if (d->psi_overhead > 0) {
+    a.qseg_ptr = d->qseg_ptr; a.qseg_s = d->qseg_s; a.qseg_r0 = d->qseg_r0; a.qseg_r1 = d->qseg_r1;
+  } else {
+    a.qseg_ptr = d->bseg_ptr; a.qseg_s = d->bseg_s; a.qseg_r0 = d->bseg_r0; a.qseg_r1 = d->bseg_r1;
+  }
   a.iseg_ptr = d->iseg_ptr; a.iseg_s = d->iseg_s; a.iseg_r0 = d->iseg_r0; a.iseg_r1 = d->iseg_r1;
   a.tseg_ptr = d->tseg_ptr; a.tseg_s = d->tseg_s; a.tseg_r0 = d->tseg_r0; a.tseg_r1 = d->tseg_r1;
   a.rhs = rhs; a.kg = d->kg; a.kx = d->kx; a.ub1 = d->ub1; a.uz = d->uz; a.nbt = d->NBt;
@@ -1991,12 +1998,13 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
 }
 
 // contiguous byte-balanced row ranges per CTA, split into per-patch segments
+// (a row weighs its leading dimension plus `overhead` elements: the per-row epilogue)
 static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std::vector<int32_t> &ld, int G,
                            std::vector<int32_t> &sptr, std::vector<int32_t> &ss, std::vector<int32_t> &r0,
-                           std::vector<int32_t> &r1) {
+                           std::vector<int32_t> &r1, int overhead = 16) {
   int np_ = (int)rows_per_patch.size();
   double W = 0;
-  for (int s = 0; s < np_; ++s) W += (double)rows_per_patch[s] * (ld[s] + 16);
+  for (int s = 0; s < np_; ++s) W += (double)rows_per_patch[s] * (ld[s] + overhead);
   sptr.assign(1, 0);
   ss.clear(); r0.clear(); r1.clear();
   int s = 0, r = 0;
@@ -2007,7 +2015,7 @@ static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std
       if (r >= rows_per_patch[s]) { ++s; r = 0; continue; }
       // take rows of patch s until the target is reached
       int take = rows_per_patch[s] - r;
-      double per = ld[s] + 16;
+      double per = ld[s] + overhead;
       if (c < G - 1) {
         int need = (int)std::ceil((target - acc) / per);
         take = std::max(1, std::min(take, need));
@@ -2337,6 +2345,7 @@ constexpr int PCG_MAX_CPS = 2;
 struct PcgSched {
   int cps = 1, ns = 3;
   size_t stage = 0;
+  int psi = 0;  // 0: the Psi rows share the S_bb partition; > 0: own partition, per-row overhead
 };
 
 static size_t pcg_xs_bytes(const DeviceState *d) {
@@ -2417,6 +2426,14 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
         (rc = upload_cap(d, ptrs[k][2], cap_seg, r0v, err)) || (rc = upload_cap(d, ptrs[k][3], cap_seg, r1v, err)))
       return rc;
   }
+  d->psi_overhead = sc.psi;
+  if (sc.psi > 0) {
+    partition_rows(d->plan_rows[4], d->plan_ld[4], d->G, sp, ss, r0v, r1v, sc.psi);
+    int rc;
+    if ((rc = upload_cap(d, &d->qseg_ptr, cap_ptr, sp, err)) || (rc = upload_cap(d, &d->qseg_s, cap_seg, ss, err)) ||
+        (rc = upload_cap(d, &d->qseg_r0, cap_seg, r0v, err)) || (rc = upload_cap(d, &d->qseg_r1, cap_seg, r1v, err)))
+      return rc;
+  }
   return IETI_OK;
 }
 
@@ -2476,7 +2493,7 @@ static std::string tune_key(const DeviceState *d) {
   return k.str();
 }
 
-// cache lines: "ieti_tune1 <key> <cps> <stages> <stage bytes>"
+// cache lines: "ieti_tune2 <key> <cps> <stages> <stage bytes> <psi overhead>"
 static bool tune_cache_lookup(const std::string &path, const std::string &key, PcgSched *out) {
   std::ifstream f(path);
   if (!f) return false;
@@ -2485,12 +2502,15 @@ static bool tune_cache_lookup(const std::string &path, const std::string &key, P
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string tag, k;
-    long cps = 0, ns = 0, stage = 0;
-    if (!(ls >> tag >> k >> cps >> ns >> stage) || tag != "ieti_tune1" || k != key) continue;
-    if (cps < 1 || cps > PCG_MAX_CPS || ns < 2 || ns > NS_MAX || stage < 128 || stage > 227 * 1024) continue;
+    long cps = 0, ns = 0, stage = 0, psi = -1;
+    if (!(ls >> tag >> k >> cps >> ns >> stage >> psi) || tag != "ieti_tune2" || k != key) continue;
+    if (cps < 1 || cps > PCG_MAX_CPS || ns < 2 || ns > NS_MAX || stage < 128 || stage > 227 * 1024 || psi < 0 ||
+        psi > 4096)
+      continue;
     out->cps = (int)cps;
     out->ns = (int)ns;
     out->stage = (size_t)stage;
+    out->psi = (int)psi;
     found = true;  // the last valid entry of the key wins
   }
   return found;
@@ -2504,7 +2524,7 @@ static bool tune_cache_store(const std::string &path, const std::string &key, co
     while (f && std::getline(f, line)) {
       std::istringstream ls(line);
       std::string tag, k;
-      if ((ls >> tag >> k) && tag == "ieti_tune1" && k == key) continue;
+      if ((ls >> tag >> k) && tag == "ieti_tune2" && k == key) continue;
       if (!line.empty()) keep.push_back(line);
     }
   }
@@ -2513,7 +2533,7 @@ static bool tune_cache_store(const std::string &path, const std::string &key, co
     std::ofstream f(tmp, std::ios::trunc);
     if (!f) return false;
     for (auto &l : keep) f << l << "\n";
-    f << "ieti_tune1 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << "\n";
+    f << "ieti_tune2 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << " " << sc.psi << "\n";
     if (!f.good()) return false;
   }
   return std::rename(tmp.c_str(), path.c_str()) == 0;
@@ -2572,6 +2592,26 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
     best = fastest;
   } else {
     best_us = rule_us;
+  }
+  // then the Psi rows on their own partition, for a few per-row overheads
+  for (int psi : {16, 64, 256}) {
+    if (rc) break;
+    PcgSched c = best;
+    c.psi = psi;
+    std::string e2;
+    const int prc = pcg_plan(d, c, e2);
+    if (prc) {
+      err = e2;
+      rc = prc;
+      break;
+    }
+    double us = 0;
+    if ((rc = pcg_time<T>(d, rhs, iters, &us, err))) break;
+    d->tune_candidates++;
+    if (us < 0.99 * best_us) {
+      best_us = us;
+      best = c;
+    }
   }
   cudaStreamSynchronize(d->stream);
   cudaFree(rhs);
@@ -3233,6 +3273,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     d->plan_ld[2] = hldi;
     d->plan_rows[3] = hni;  // GT rows
     d->plan_ld[3] = hldg;
+    d->plan_rows[4] = hnb;  // interface rows for Psi (own partition when the autotuner picks one)
+    d->plan_ld[4] = hldp;
     int coop = 0;
     CK(cudaDeviceGetAttribute(&d->n_sm, cudaDevAttrMultiProcessorCount, d->device));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, d->device));
@@ -3456,6 +3498,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->pcg_grid = d->G;
   info->pcg_stages = d->n_stages;
   info->pcg_stage_bytes = (int32_t)d->stage_bytes;
+  info->pcg_psi_partition = d->psi_overhead;
   info->pcg_sched_source = d->sched_source;
   info->tune_candidates = d->tune_candidates;
   info->tune_ms = d->tune_ms;

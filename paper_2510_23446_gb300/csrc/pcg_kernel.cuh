@@ -64,7 +64,8 @@ struct PcgArgs {
   // work partitions (per CTA): patch segments of operator rows
   const int32_t *iseg_ptr, *iseg_s, *iseg_r0, *iseg_r1;   // IG rows
   const int32_t *hseg_ptr, *hseg_s, *hseg_r0, *hseg_r1;   // H rows
-  const int32_t *bseg_ptr, *bseg_s, *bseg_r0, *bseg_r1;   // interface rows (Psi and P)
+  const int32_t *bseg_ptr, *bseg_s, *bseg_r0, *bseg_r1;   // interface rows (S_bb)
+  const int32_t *qseg_ptr, *qseg_s, *qseg_r0, *qseg_r1;   // interface rows (Psi; the S_bb ones or their own)
   const int32_t *tseg_ptr, *tseg_s, *tseg_r0, *tseg_r1;   // GT rows
   // vectors
   const double *rhs;                // kept space
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                        0, 0, 0, ps, hint};
   const OpRows<T> opH{a.H, a.hoff, a.ldb, a.hseg_s, a.hseg_r0, a.hseg_r1, a.hseg_ptr[cta], a.hseg_ptr[cta + 1],
                       0, 0, 0, pk, hint};
-  const OpRows<T> opQ{a.Q, a.qoff, a.ldp, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1],
+  const OpRows<T> opQ{a.Q, a.qoff, a.ldp, a.qseg_s, a.qseg_r0, a.qseg_r1, a.qseg_ptr[cta], a.qseg_ptr[cta + 1],
                       0, 0, 0, pk, hint};
   const OpRows<T> opP{a.P, a.poff, a.ldb, a.bseg_s, a.bseg_r0, a.bseg_r1, a.bseg_ptr[cta], a.bseg_ptr[cta + 1],
                       0, 0, 0, pk, hint};

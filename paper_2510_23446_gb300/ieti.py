@@ -74,6 +74,7 @@ class ieti_info(C.Structure):
                 ("nl_patches", C.c_int64), ("nl_elements", C.c_int64), ("refactors", C.c_int64),
                 ("nl_coarse_block", C.c_int64), ("t_refactor_ms", C.c_double * 4),
                 ("pcg_grid", C.c_int32), ("pcg_stages", C.c_int32), ("pcg_stage_bytes", C.c_int32),
+                ("pcg_psi_partition", C.c_int32),
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
                 ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32)]
 

@@ -67,27 +67,30 @@ def test_autotuned_schedule_gives_the_rule_state(ieti, mode, case):
 
 def test_tune_cache_round_trip_and_forced_schedules(ieti, tmp_path):
     """A tuned choice is written to the cache and read back without timing; cache
-    entries edited to other feasible schedules (two stages of 16 KB, two CTAs per
-    SM) are used as given and reach the same state; malformed lines are ignored."""
+    entries edited to other schedules (two stages of 16 KB; three of 32 KB with the Psi
+    rows on their own partition; two CTAs per SM, infeasible with this kernel's
+    registers) are used as given where feasible and reach the same state; malformed
+    lines are ignored."""
     prob = _ragged()
     cache = tmp_path / "tune.txt"
-    cache.write_text("garbage line\nieti_tune1 other-key 1 3 65536\n")
+    cache.write_text("garbage line\nieti_tune2 other-key 1 3 65536 0\nieti_tune2 short-line 1 3\n")
     ref, inf1 = _run(ieti, prob, 2, autotune=1, tune_cache=str(cache), **OPTS["mixed"])
     assert inf1["pcg_sched_source"] == 2
     lines = cache.read_text().splitlines()
-    ours = [l for l in lines if l.startswith("ieti_tune1 ") and "other-key" not in l]
+    ours = [l for l in lines if l.startswith("ieti_tune2 ") and "other-key" not in l and "short-line" not in l]
     assert len(ours) == 1 and "garbage line" in lines and any("other-key" in l for l in lines)
     key = ours[0].split()[1]
     _, inf2 = _run(ieti, prob, 1, autotune=1, tune_cache=str(cache), **OPTS["mixed"])
     assert inf2["pcg_sched_source"] == 3 and inf2["tune_candidates"] == 0
     assert (inf2["pcg_grid"], inf2["pcg_stages"], inf2["pcg_stage_bytes"]) == \
         (inf1["pcg_grid"], inf1["pcg_stages"], inf1["pcg_stage_bytes"])
-    for cps, ns, stage in [(1, 2, 16384), (2, 2, 16384)]:
-        cache.write_text(f"ieti_tune1 {key} {cps} {ns} {stage}\n")
+    for cps, ns, stage, psi in [(1, 2, 16384, 0), (1, 3, 32768, 64), (2, 2, 16384, 0)]:
+        cache.write_text(f"ieti_tune2 {key} {cps} {ns} {stage} {psi}\n")
         got, inf = _run(ieti, prob, 2, autotune=1, tune_cache=str(cache), **OPTS["mixed"])
         if inf["pcg_sched_source"] != 3:        # not feasible on this device: tuned afresh instead
             assert cps == 2 and inf["pcg_sched_source"] == 2
             continue
-        assert (inf["pcg_grid"], inf["pcg_stages"], inf["pcg_stage_bytes"]) == (cps * _n_sm(), ns, stage)
+        assert (inf["pcg_grid"], inf["pcg_stages"], inf["pcg_stage_bytes"], inf["pcg_psi_partition"]) == \
+            (cps * _n_sm(), ns, stage, psi)
         for a, b in zip(ref, got):
             assert np.linalg.norm(a - b) <= TOL["mixed"] * np.linalg.norm(a)
