@@ -699,7 +699,9 @@ def run_profile_step(args):
     build()
     from paper_2510_23446_gb300 import ieti
     prob = make_problem("c2")
-    S = ieti.Solver.from_problem(prob, device=0, tune_cache=args.tune_cache, **OPTS["mixed"])
+    # host loop (graph=0): ncu lists the kernels launched from the host, not the kernel
+    # nodes inside the step graph's while-loop body
+    S = ieti.Solver.from_problem(prob, device=0, tune_cache=args.tune_cache, graph=0, **OPTS["mixed"])
     jd = torch.from_numpy(S.load_vector(prob.coil)).cuda()
     for _ in range(max(1, args.warmup) + 2):
         st = S.step(jd)
