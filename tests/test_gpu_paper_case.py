@@ -112,3 +112,70 @@ def test_paper_case_rates_and_iterations(ieti):
     assert res[(2, 64)][0] / res[(4, 64)][0] > 4.0, res            # B: better than h^2
     assert res[(4, 16)][1] / res[(4, 64)][1] > 3.0, res            # E: first order in time
     assert res[(4, 64)][2] > res[(2, 64)][2], res                  # iterations grow with 1/h
+
+
+# ----------------------------------------------------------------------------- Eq. (13)
+def _eq13(n, p, n_t):
+    """The paper's own field A = e^{-t} A13 with its inhomogeneous tangential boundary
+    data lifted by the oracle (boundary L2 projection), its source
+    J = (3 nu - sigma) A (curl curl A13 = 3 A13) and its initial state; the library
+    solves for the homogeneous part with the lifting's terms in the load vector."""
+    from oracle.lifting import A13, LiftedRun
+    prob = two_subdomains(n, p, n_t)
+    op = OracleProblem(prob, with_load=False)
+    sig = lambda x: (x[..., 0] < 0.5).astype(float)
+    run = LiftedRun(op, A13, lambda x: (3.0 - sig(x))[..., None] * A13(x), sig)
+    return prob, op, run
+
+
+def _gpu_eq13(ieti, prob, run, n_t, **kw):
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet", **kw)
+    S.set_state(run.a0)
+    out, its = [], []
+    for l in range(1, n_t + 1):
+        st = S.step(run.j_step(l))
+        its.append(st["cg_its"])
+        out.append(S.solution().copy())
+    S.close()
+    return out, its
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_eq13_lifted_run_matches_oracle(ieti, mode):
+    """Every step of the Eq. (13) run (inhomogeneous data, non-zero initial state)
+    equals the oracle's monolithic solve of the same lifted system."""
+    n, p, n_t = 2, 3, 8
+    prob, op, run = _eq13(n, p, n_t)
+    ref = run.run_monolithic(n_t)
+    kw = (dict(precision="fp64", cg_tol=1e-12, max_sweeps=1) if mode == "fp64" else
+          dict(precision="mixed", cg_tol=1e-6, outer_tol=1e-12, max_sweeps=20))
+    got, _ = _gpu_eq13(ieti, prob, run, n_t, **kw)
+    tol = 1e-10 if mode == "fp64" else 1e-8
+    for l, (a, b) in enumerate(zip(ref, got)):
+        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(a), (mode, l)
+
+
+def test_eq13_rates_on_the_gpu_path(ieti):
+    """Sec. 4 with its own field: eps_B = O(h^p) (p = 2, 2^3 -> 4^3 elements per
+    subdomain, order ~2), eps_E = O(1/n_t), from GPU states with the paper's solver
+    settings (unscaled Dirichlet, PCG tol 1e-6), equal to the oracle's errors."""
+    from oracle.lifting import A13, curl_A13
+    p = 2
+    res = {}
+    for n, n_t in ((2, 64), (4, 64), (4, 16)):
+        prob, op, run = _eq13(n, p, n_t)
+        got, its = _gpu_eq13(ieti, prob, run, n_t, precision="fp64", cg_tol=1e-6, max_sweeps=1)
+        fe = FieldEval(prob, op.asm)
+        A1, A0 = run.total(got[-1], 1.0), run.total(got[-2], 1.0 - 1.0 / n_t)
+        _, eB = fe.errors(A1, lambda x: np.exp(-1.0) * A13(x), lambda x: np.exp(-1.0) * curl_A13(x))
+        eE, _ = fe.errors(-(A1 - A0) * n_t, lambda x: np.exp(-1.0) * A13(x), lambda x: 0 * x)
+        res[(n, n_t)] = (eB, eE, float(np.mean(its)))
+        if (n, n_t) == (4, 64):
+            ref = run.run_monolithic(n_t)
+            R1, R0 = run.total(ref[-1], 1.0), run.total(ref[-2], 1.0 - 1.0 / n_t)
+            _, rB = fe.errors(R1, lambda x: np.exp(-1.0) * A13(x), lambda x: np.exp(-1.0) * curl_A13(x))
+            rE, _ = fe.errors(-(R1 - R0) * n_t, lambda x: np.exp(-1.0) * A13(x), lambda x: 0 * x)
+            assert abs(eB - rB) <= 1e-3 * rB and abs(eE - rE) <= 1e-3 * rE, (eB, rB, eE, rE)
+    print(res)
+    assert res[(2, 64)][0] / res[(4, 64)][0] > 3.0, res            # B: order ~p = 2 in h
+    assert 3.0 < res[(4, 16)][1] / res[(4, 64)][1] < 5.5, res      # E: first order in time

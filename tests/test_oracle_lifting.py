@@ -84,3 +84,20 @@ def test_lifted_run_rates():
     _, eE16 = _lifted_errors(4, 2, 16)
     _, eE64 = _lifted_errors(4, 2, 64)
     assert 3.0 < eE16 / eE64 < 5.5, (eE16, eE64)             # first order in time
+
+
+def test_lifted_run_dual_primal_equals_monolithic():
+    """The lifting enters only through the initial state and the load vectors, so the
+    oracle's IETI-DP solve of the lifted run (what the library is given) equals the
+    monolithic solve step by step."""
+    from oracle.ietidp import PRECOND_DIRICHLET
+    n, p, n_t = 2, 2, 4
+    prob = two_subdomains(n, p, n_t)
+    op = OracleProblem(prob, with_load=False)
+    sig = lambda x: (x[..., 0] < 0.5).astype(float)
+    run = LiftedRun(op, A13, lambda x: (3.0 - sig(x))[..., None] * A13(x), sig)
+    ref = run.run_monolithic(n_t)
+    got, _ = op.run_ietidp(n_t, 1e-12, PRECOND_DIRICHLET, j_of_step=run.j_step, a0=run.a0)
+    for a, b in zip(ref, got):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
+    assert np.linalg.norm(run.a0) > 0 and np.linalg.norm(run.aD_star) > 0
