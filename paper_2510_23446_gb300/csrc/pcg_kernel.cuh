@@ -173,6 +173,11 @@ template <> struct V16<double> { using t = double2; static constexpr int n = 2; 
 
 __device__ __forceinline__ float dot16(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 __device__ __forceinline__ double dot16(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+// s + a . b for one 16-byte unit.  FP32: the dot of the unit, then the add (the FP32
+// pipe is not the limit of any row kernel).  FP64: two chained FMAs, two FP64
+// instructions per unit instead of three (GB300's FP64 pipe bounds the FP64 rows).
+__device__ __forceinline__ float fma16(float4 a, float4 b, float s) { return s + dot16(a, b); }
+__device__ __forceinline__ double fma16(double2 a, double2 b, double s) { return fma(a.y, b.y, fma(a.x, b.x, s)); }
 
 // R padded (16-byte aligned, zero-padded) rows against the staged x, by one warp.
 // Every lane issues its loads of a 32*U-vector chunk of all R rows before using
@@ -205,7 +210,7 @@ __device__ __forceinline__ void rows_dot(const T *A, int64_t ld, int r, int nval
         V xv = x[k];
 #pragma unroll
         for (int i = 0; i < R; ++i)
-          if (i < nvalid) out[i] += dot16(va[i][u], xv);
+          if (i < nvalid) out[i] = fma16(va[i][u], xv, out[i]);
       }
     }
   }
@@ -284,10 +289,10 @@ __device__ __noinline__ void chunk_rows_g(const T *A, int ld, int cn, const T *x
       int k = j;
       for (; k + G < nv; k += 2 * G) {
         V a = row[k], b = row[k + G], xa = x[k], xb = x[k + G];
-        s0 += dot16(a, xa);
-        s1 += dot16(b, xb);
+        s0 = fma16(a, xa, s0);
+        s1 = fma16(b, xb, s1);
       }
-      if (k < nv) s0 += dot16(row[k], x[k]);
+      if (k < nv) s0 = fma16(row[k], x[k], s0);
       s = s0 + s1;
     }
 #pragma unroll
