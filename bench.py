@@ -356,7 +356,7 @@ def paper_case_leg(ieti, torch, dev, stream):
         S.close()
     return {"workload": "Sec. 4 run: 2 subdomains x 8^3 elements, p=3, 7260 DOFs, n_t=32, PCG tol 1e-6, "
                         "unscaled Dirichlet, manufactured (1 - e^-t) A*",
-            "paper_total_s": 10.0, "paper_hardware": "laptop, MATLAB, not parallelized (Sec. 4)", **out}
+            "paper_total_s": 10.0, "paper_hardware": "laptop, MATLAB, serial (Sec. 4)", **out}
 
 
 def factor_ablation_leg(ieti, torch, prob, dev, stream, n_steps=10):

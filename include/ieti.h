@@ -69,7 +69,7 @@ extern "C" {
                                  about 16 significant bits per operand (ablation) */
 #define IETI_FACTOR_BF16 5    /* one BF16 product (ablation: 8-bit operands) */
 
-/* Dirichlet preconditioner variants (Sec. 4 uses it "without scaling"; Sec. 5 asks for scaling). */
+/* Dirichlet preconditioner variants (Sec. 4 uses the unscaled one; Sec. 5 asks for scaling). */
 #define IETI_PRECOND_NONE 0
 #define IETI_PRECOND_DIRICHLET 1       /* unscaled: B_D = B (the paper's experiments) */
 #define IETI_PRECOND_DIRICHLET_MULT 2  /* multiplicity scaling delta = 1/|N_x| */

@@ -17,8 +17,8 @@ are shared, as a written specification, with the library):
 * Graph: nodes and non-Dirichlet edges of Omega_I; all nodes on the outer boundary
   are merged into one ROOT (the PEC boundary is one connected conductor).
 * Gamma-type edges: graph edges whose two end nodes are conductor nodes (this
-  includes every Gamma edge).  Consistency (Sec. 3: the coupled tree DOFs on Gamma
-  "have to take the corresponding value from Omega_C") needs the tree restricted to
+  includes every Gamma edge).  Consistency (Sec. 3: tree DOFs coupled across Gamma
+  take their values from the conducting side) needs the tree restricted to
   Gamma to be connected: otherwise a path of eliminated edges joins two Gamma nodes
   and a_e = 0 forces a gauge-invariant line integral of A to zero.  In the paper's
   two-subdomain test Gamma touches the boundary and this holds through ROOT; with

@@ -4,7 +4,7 @@ Sec. 2.2 requires pairwise matching basis functions on interfaces; with open kno
 vectors that match across each shared face, the control points of all patches form
 one global lattice (I, J, K) in which neighbouring patches share the lattice planes
 of their common face.  An edge DOF of the spline edge space is then a lattice edge
-(Sec. 3: "the underlying (control) mesh"); a node is a lattice point.
+(Sec. 3 puts the tree on the control mesh); a node is a lattice point.
 
 Numbering (the library uses the same published convention, written separately):
 * node id  = I + N0*(J + N1*K);
