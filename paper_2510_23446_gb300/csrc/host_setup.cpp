@@ -496,6 +496,32 @@ static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const Di
       }
 }
 
+// out[a][b] = sum_k Ws[a][k] Ut[k][b] (n x n, row-major): the upper triangle by blocks
+// of eight rows and 32 terms (the row block and the terms' slice of Ut stay in the
+// first-level cache), the inner loop an axpy over b that vectorises without
+// reordering any sum; then mirrored
+static void gram_upper(const double *Ws, const double *Ut, int n, int K, double *out) {
+  constexpr int AB = 8, KC = 32;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int k1 = std::min(K, k0 + KC);
+    for (int a0 = 0; a0 < n; a0 += AB) {
+      const int a1 = std::min(n, a0 + AB);
+      for (int a = a0; a < a1; ++a) {
+        double *o = out + (size_t)a * n;
+        const double *ws = Ws + (size_t)a * K;
+        for (int k = k0; k < k1; ++k) {
+          const double w = ws[k];
+          if (w == 0.0) continue;
+          const double *ut = Ut + (size_t)k * n;
+          for (int b = a0; b < n; ++b) o[b] += w * ut[b];
+        }
+      }
+    }
+  }
+  for (int a = 1; a < n; ++a)
+    for (int b = 0; b < a; ++b) out[(size_t)a * n + b] = out[(size_t)b * n + a];
+}
+
 void HostSetup::assemble_patch(Patch &pt) const {
   int s = pt.a + P[0] * (pt.b + P[1] * pt.c);
   DirData dd[3];
@@ -507,16 +533,52 @@ void HostSetup::assemble_patch(Patch &pt) const {
   pt.M = pt.K;
   const double *sig = sigma_el.data() + el_off[s];
   const double *nu = nu_el.data() + el_off[s];
-  int cur_el = -1, cur_n = 0;
-  std::vector<double> Ke, Me;
+  // K_e = sum over the element's points of (nu w / det) (DF c_hat_a) . (DF c_hat_b) and
+  // M_e = sum of (sigma w det) w_a . w_b, formed per element as K_e = Ws Ut with the
+  // weighted values Ws (n x 3Q) and the plain values transposed Ut (3Q x n)
+  const int K3 = 3 * dd[0].q * dd[1].q * dd[2].q;
+  // element-local function index of the first function of every (component, c, b)
+  // group and the group's length (the a-run), in the order the element lists them
+  std::vector<std::pair<int, int>> groups;
+  {
+    int t = 0;
+    for (int comp = 0; comp < 3; ++comp) {
+      const int na = (comp == 0) ? pt.p[0] : pt.p[0] + 1, nb = (comp == 1) ? pt.p[1] : pt.p[1] + 1,
+                nc = (comp == 2) ? pt.p[2] : pt.p[2] + 1;
+      for (int c = 0; c < nc; ++c)
+        for (int b = 0; b < nb; ++b) {
+          groups.push_back({t, na});
+          t += na;
+        }
+    }
+  }
+  int cur_el = -1, cur_n = 0, qi = 0;
+  bool any_m = false;
+  std::vector<double> Ws, Ut, Vs, Vt, Ke, Me;
   std::vector<int> cur_lid;
   auto flush = [&]() {
     if (cur_el < 0) return;
-    for (int a = 0; a < cur_n; ++a)
-      for (int b = 0; b < cur_n; ++b) {
-        int pos = csr_find(pt.K, cur_lid[a], cur_lid[b]);
-        pt.K.val[pos] += Ke[(size_t)a * cur_n + b];
-        pt.M.val[pos] += Me[(size_t)a * cur_n + b];
+    const int n = cur_n;
+    Ke.assign((size_t)n * n, 0.0);
+    gram_upper(Ws.data(), Ut.data(), n, K3, Ke.data());
+    if (any_m) {
+      Me.assign((size_t)n * n, 0.0);
+      gram_upper(Vs.data(), Vt.data(), n, K3, Me.data());
+    }
+    // the element's columns of one (component, c, b) group are consecutive DOF ids
+    // whose CSR entries are consecutive in every row (a row's columns of one
+    // component form a box of lattice indices): one search per row and group
+    for (int a = 0; a < n; ++a)
+      for (const auto &g : groups) {
+        const int pos = csr_find(pt.K, cur_lid[a], cur_lid[g.first]);
+        const double *kr = &Ke[(size_t)a * n + g.first];
+        double *kv = &pt.K.val[pos];
+        for (int u = 0; u < g.second; ++u) kv[u] += kr[u];
+        if (any_m) {
+          const double *mr = &Me[(size_t)a * n + g.first];
+          double *mv = &pt.M.val[pos];
+          for (int u = 0; u < g.second; ++u) mv[u] += mr[u];
+        }
       }
   };
   for_each_point(*this, pt, s, dd, [&](int el, int nloc, const int *lid, const double *, double det, double w,
@@ -526,21 +588,26 @@ void HostSetup::assemble_patch(Patch &pt) const {
       cur_el = el;
       cur_n = nloc;
       cur_lid.assign(lid, lid + nloc);
-      Ke.assign((size_t)nloc * nloc, 0.0);
-      Me.assign((size_t)nloc * nloc, 0.0);
+      qi = 0;
+      any_m = false;
+      Ws.assign((size_t)nloc * K3, 0.0);
+      Ut.assign((size_t)K3 * nloc, 0.0);
+      Vs.assign((size_t)nloc * K3, 0.0);
+      Vt.assign((size_t)K3 * nloc, 0.0);
     }
     // the nonlinear law's stiffness is assembled on the device at every Newton iterate
-    double ck = nl_element(s, el) ? 0.0 : nu[el] * w / det;
-    double cm = sig[el] * w * det;
-    for (int a = 0; a < nloc; ++a) {
-      const double *Ua = U + 3 * a, *Va = V + 3 * a;
-      double *kr = &Ke[(size_t)a * nloc], *mr = &Me[(size_t)a * nloc];
-      for (int b = 0; b < nloc; ++b) {
-        const double *Ub = U + 3 * b, *Vb = V + 3 * b;
-        kr[b] += ck * (Ua[0] * Ub[0] + Ua[1] * Ub[1] + Ua[2] * Ub[2]);
-        if (cm != 0.0) mr[b] += cm * (Va[0] * Vb[0] + Va[1] * Vb[1] + Va[2] * Vb[2]);
+    const double ck = nl_element(s, el) ? 0.0 : nu[el] * w / det;
+    const double cm = sig[el] * w * det;
+    if (cm != 0.0) any_m = true;
+    for (int a = 0; a < nloc; ++a)
+      for (int r = 0; r < 3; ++r) {
+        const int k = 3 * qi + r;
+        Ws[(size_t)a * K3 + k] = ck * U[3 * a + r];
+        Ut[(size_t)k * nloc + a] = U[3 * a + r];
+        Vs[(size_t)a * K3 + k] = cm * V[3 * a + r];
+        Vt[(size_t)k * nloc + a] = V[3 * a + r];
       }
-    }
+    ++qi;
   });
   flush();
 }
@@ -910,7 +977,7 @@ void HostSetup::decompose() {
     if (cls[g] == CLS_P) coarse_of_edge[g] = n_coarse++;
     if (cls[g] != CLS_E) free_edges.push_back(g);
   }
-  for (int s = 0; s < np; ++s) {
+  parallel_for(np, threads, [&](int s) {
     Patch &pt = patches[s];
     pt.i_loc.clear(); pt.b_loc.clear(); pt.p_loc.clear();
     for (int l = 0; l < pt.n_dofs; ++l) {
@@ -937,6 +1004,9 @@ void HostSetup::decompose() {
       pt.kept_glob[k] = pt.l2g[order[k]];
       pt.load_w[k] = 1.0 / n_share[pt.kept_glob[k]];
     }
+  });
+  for (int s = 0; s < np; ++s) {
+    const Patch &pt = patches[s];
     for (int k = 0; k < pt.nb; ++k) copies.emplace_back(pt.l2g[pt.b_loc[k]], s, k);
   }
   std::sort(copies.begin(), copies.end());
