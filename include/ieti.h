@@ -339,11 +339,13 @@ int ieti_potrf_batched_f32(int32_t batch, float *base_dev, const int64_t *offset
  * descriptor copies and status words, 40 bytes per matrix) lives in one static
  * device array of IETI_NOALLOC_MAX_BATCH entries, which every device that loads the
  * library holds until the process exits; batch > IETI_NOALLOC_MAX_BATCH returns
- * IETI_ERR_TOO_LARGE.  It calls no cudaMalloc or cudaFree.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
- * shares the one array (the status words are cleared at each call), so calls
- * whose GPU work overlaps, on different streams or threads, race. */
+ * IETI_ERR_TOO_LARGE.  It calls no cudaMalloc or cudaFree.  Every call looks up
+ * the array's device address in the current device's context
+ * (cudaGetSymbolAddress).  The call copies its descriptors from pageable host
+ * memory and waits for its stream, so it cannot be called on a stream that is
+ * being captured into a CUDA graph.  Every call shares the one array (the status
+ * words are cleared at each call), so calls whose GPU work overlaps, on different
+ * streams or threads, race. */
 #define IETI_NOALLOC_MAX_BATCH 4096
 int ieti_potrf_batched_noalloc(int32_t batch, double *base_dev, const int64_t *offsets, const int32_t *n,
                                const int32_t *n_pivots, int32_t *status_out, void *stream);

@@ -247,8 +247,13 @@ int ieti_potrf_batched_noalloc(int32_t batch, double *base_dev, const int64_t *o
       g_setup_err = "ieti_potrf_batched_noalloc: bad size, pivot count or offset of matrix " + std::to_string(b);
       return IETI_ERR_INVALID_ARG;
     }
-  return ieti::device_potrf_batched_noalloc(batch, base_dev, offsets, n, n_pivots, status_out,
-                                            (cudaStream_t)stream, g_setup_err);
+  try {
+    return ieti::device_potrf_batched_noalloc(batch, base_dev, offsets, n, n_pivots, status_out,
+                                              (cudaStream_t)stream, g_setup_err);
+  } catch (...) {
+    g_setup_err = "ieti_potrf_batched_noalloc: host allocation failed";
+    return IETI_ERR_OOM;
+  }
 }
 
 const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

@@ -3672,25 +3672,17 @@ namespace ieti {
 constexpr int NOALLOC_MAX = IETI_NOALLOC_MAX_BATCH;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * (8 + 8 * 4)];
 
-// device address of the scratch array, looked up once per device (with it current)
-static void *noalloc_scratch_address(int dev, std::string &err) {
-  static std::mutex mu;
-  static void *addr[256] = {};
-  if (dev < 0 || dev >= 256) {
-    err = "device ordinal out of range";
+// device address of the scratch array in the current device's context.  Looked up
+// on every call (a host-side table lookup): a cached address would go stale when the
+// primary context is destroyed and re-created (cudaDeviceReset).
+static void *noalloc_scratch_address(std::string &err) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    err = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
     return nullptr;
   }
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      err = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-      return nullptr;
-    }
-    addr[dev] = p;
-  }
-  return addr[dev];
+  return p;
 }
 
 int device_potrf_batched_noalloc(int batch, double *base, const int64_t *off, const int32_t *n,
@@ -3700,12 +3692,7 @@ int device_potrf_batched_noalloc(int batch, double *base, const int64_t *off, co
           std::to_string(NOALLOC_MAX) + ")";
     return IETI_ERR_TOO_LARGE;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    err = "cudaGetDevice failed";
-    return IETI_ERR_CUDA;
-  }
-  unsigned char *blk = (unsigned char *)noalloc_scratch_address(dev, err);
+  unsigned char *blk = (unsigned char *)noalloc_scratch_address(err);
   if (!blk) return IETI_ERR_CUDA;
   int64_t *doff = (int64_t *)blk;
   int32_t *dn = (int32_t *)(blk + 8 * NOALLOC_MAX);
@@ -3722,31 +3709,15 @@ int device_potrf_batched_noalloc(int batch, double *base, const int64_t *off, co
     err = std::string("scratch upload failed: ") + cudaGetErrorString(cudaGetLastError());
     return IETI_ERR_CUDA;
   }
+  // the same panel loop as ieti_potrf_batched (host copies of the sizes; a
+  // DeviceState that owns no device memory carries the stream)
+  std::vector<int32_t> hkb(batch, 0), hke(npiv, npiv + batch), hna(n, n + batch);
+  DeviceState tmp;
+  tmp.stream = st;
   AugLimits lim{dz, dz2, dbig, dz};
-  int max_panels = 0;
-  for (int b = 0; b < batch; ++b) max_panels = std::max(max_panels, (npiv[b] + NB - 1) / NB);
-  for (int j = 0; j < max_panels; ++j) {
-    int max_rows = 0, max_tiles = 0;
-    for (int b = 0; b < batch; ++b) {
-      int j0 = j * NB;
-      if (j0 >= npiv[b]) continue;
-      int jb = std::min(NB, npiv[b] - j0);
-      int m = n[b] - (j0 + jb);
-      if (m <= 0) continue;
-      max_rows = std::max(max_rows, m);
-      int T64 = (m + 63) / 64;
-      max_tiles = std::max(max_tiles, T64 * (T64 + 1) / 2);
-    }
-    k_potrf_diag<double><<<batch, 256, 0, st>>>(base, doff, dn, dkb, dke, j, dst);
-    if (max_rows > 0) {
-      dim3 g1(grid_for(max_rows, 128), batch);
-      k_trsm_panel<double><<<g1, 128, 0, st>>>(base, doff, dn, dkb, dke, dna, j, lim);
-      dim3 g2(max_tiles, batch);
-      k_syrk_update<double><<<g2, 256, 0, st>>>(base, doff, dn, dkb, dke, dna, j, lim);
-    }
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st);
+  int rc = potrf_partial<double>(&tmp, base, doff, dn, hkb, hke, hna, dkb, dke, dna, dst, lim, err);
+  if (rc != IETI_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(status, dst, batch * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     err = std::string("batched partial Cholesky failed: ") + cudaGetErrorString(e);
