@@ -48,6 +48,8 @@ extern "C" {
 #define IETI_ERR_OOM -6             /* device or host allocation failed */
 #define IETI_ERR_NO_DEVICE -7       /* compute requested on a host-only context */
 #define IETI_ERR_TOO_LARGE -8       /* size beyond a documented fixed maximum */
+#define IETI_ERR_TIMEOUT -9         /* a bounded device wait (grid barrier of the dual-primal kernel) ran out;
+                                       the launch ended cleanly and the context stays usable */
 
 #define IETI_MEM_HOST 0
 #define IETI_MEM_DEVICE 1
@@ -147,6 +149,11 @@ typedef struct {
    * building it fails the host loop runs (ieti_info.step_graph).  Same sweeps, same
    * stopping rules, same results. */
   int32_t graph;
+  /* Bound of every grid-barrier wait of the persistent dual-primal kernel, in polls of
+   * the arrival counter.  0: the default (about 1-3 s).  A wait that runs out sets an
+   * error flag, every CTA waits for its own copies in flight and returns, and the step
+   * returns IETI_ERR_TIMEOUT.  Small values exist to test that path. */
+  int32_t wait_limit;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */

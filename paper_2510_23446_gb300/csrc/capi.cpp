@@ -34,6 +34,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->predictor < 0 || o->predictor > 2) { err = "predictor must be 0, 1 or 2"; return IETI_ERR_INVALID_ARG; }
   if (o->autotune != 0 && o->autotune != 1) { err = "autotune must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->graph != 0 && o->graph != 1) { err = "graph must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
+  if (o->wait_limit < 0) { err = "wait_limit must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
     return IETI_ERR_INVALID_ARG;

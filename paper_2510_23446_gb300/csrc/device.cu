@@ -1903,6 +1903,7 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.xs_bytes = d->xs_bytes;
   a.n_stages = d->n_stages;
   a.l2_keep_frac = d->l2_keep_frac;
+  a.spin_max = d->opt.wait_limit > 0 ? (long long)d->opt.wait_limit : (1ll << 25);
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
   {
@@ -1955,7 +1956,7 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
   CK(cudaStreamSynchronize(st));
   if (h.bar[1]) {
     err = "persistent PCG: a grid barrier timed out";
-    return IETI_ERR_CUDA;
+    return IETI_ERR_TIMEOUT;
   }
   *its = h.its;
   prof_set_bytes(d, d->bytes_iter_alg * (h.its + 2) + d->bytes_sweep_alg);
@@ -2184,7 +2185,7 @@ static int graph_sweeps(DeviceState *d, int *its_total, int *sweeps, double *rel
   d->nlaunch += 4 + 9 * (int64_t)c.sweeps;
   if (c.bar_err) {
     err = "persistent PCG: a grid barrier timed out";
-    return IETI_ERR_CUDA;
+    return IETI_ERR_TIMEOUT;
   }
   if (c.status == 2 && d->opt.max_sweeps > 1 && !c.cg_fail) {
     err = "refinement did not reach outer_tol within max_sweeps";

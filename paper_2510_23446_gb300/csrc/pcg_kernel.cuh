@@ -79,6 +79,7 @@ struct PcgArgs {
   unsigned stage_bytes, xs_bytes;
   int n_stages;
   float l2_keep_frac;  // > 0: L2 eviction-priority hints on the operator streams
+  long long spin_max;  // polls of a grid-barrier wait before it gives up (~1-3 s by default)
 };
 
 constexpr int TRACE_IT = 16;
@@ -102,8 +103,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 }
 
 // grid barrier: every CTA adds 1 to a counter that only grows; barrier k completes
-// when it reaches k * G.  Bounded wait; returns false when any CTA gave up.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned G, unsigned &target,
+// when it reaches k * G.  Bounded wait (spin_max polls); returns false when any CTA
+// gave up.
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned G, unsigned &target, long long spin_max,
                                           unsigned long long *tr = nullptr) {
   __syncthreads();
   __shared__ int ok;
@@ -116,7 +118,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned G, unsigned &t
     long long spins = 0;
     while (ld_acquire(bar) < target) {
       if (++spins > 64) __nanosleep(32);
-      if (spins > (1ll << 25)) {  // ~1-3 s
+      if (spins > spin_max) {
         atomicExch(bar + 1, 1u);
         good = 0;
         break;
@@ -693,7 +695,17 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         },
         [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
   };
-  auto sync = [&](unsigned long long *tr) { return grid_sync(a.bar, G, target, tr); };
+  // a barrier that gave up ends the launch: first the chunks this CTA still has in
+  // flight into its shared memory are waited for (bounded), then every CTA returns
+  auto sync = [&](unsigned long long *tr) {
+    if (grid_sync(a.bar, G, target, a.spin_max, tr)) return true;
+    if (threadIdx.x == 0)
+      for (unsigned long long g = ring.consumed; g < ring.issued; ++g)
+        mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
+    ring.consumed = ring.issued;
+    __syncthreads();
+    return false;
+  };
   // uz = B^T z on this CTA's chunk of interface copies (z recomputed on the fly)
   const int64_t qb = a.nbt * cta / G, qe = a.nbt * (cta + 1) / G;
   // uz = B^T B_D zp on this CTA's chunk (preconditioned runs), by the neighbour lists

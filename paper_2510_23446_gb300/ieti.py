@@ -23,7 +23,7 @@ PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
 FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "bf16": 5}
 REFACTOR = {"every": 0, "step": 1, "never": 2}
 ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
-          -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE"}
+          -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE", -9: "TIMEOUT"}
 
 _i32p = C.POINTER(C.c_int32)
 _dp = C.POINTER(C.c_double)
@@ -42,7 +42,7 @@ class ieti_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
                 ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
-                ("graph", C.c_int32)]
+                ("graph", C.c_int32), ("wait_limit", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -137,7 +137,7 @@ class Solver:
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
-                 graph=1):
+                 graph=1, wait_limit=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -181,6 +181,7 @@ class Solver:
         op.predictor = int(predictor)
         op.autotune = int(autotune)
         op.graph = int(graph)
+        op.wait_limit = int(wait_limit)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
         self.options = op
