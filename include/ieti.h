@@ -71,6 +71,16 @@ extern "C" {
                                  about 16 significant bits per operand (ablation) */
 #define IETI_FACTOR_BF16 5    /* one BF16 product (ablation: 8-bit operands) */
 
+/* Solve of the primal coarse problem S_c q = c (Sec. 3, the second Schur complement) in
+ * every PCG iteration.  DENSE: S_c^{-1} is formed at setup (FP64 partial Cholesky of
+ * [[S_c, I], [I, 0]]) and applied as dense rows (8 nc^2 bytes per solve).  ND: S_c is
+ * factored along a nested dissection of the patch grid (multifrontal, FP64) and solved by
+ * one forward and one backward sweep over the tree levels (bytes ~ the factor's entries).
+ * AUTO: ND once the dense inverse exceeds 64 MB, for linear problems with pcg_mode 0. */
+#define IETI_COARSE_AUTO 0
+#define IETI_COARSE_DENSE 1
+#define IETI_COARSE_ND 2
+
 /* Dirichlet preconditioner variants (Sec. 4 uses the unscaled one; Sec. 5 asks for scaling). */
 #define IETI_PRECOND_NONE 0
 #define IETI_PRECOND_DIRICHLET 1       /* unscaled: B_D = B (the paper's experiments) */
@@ -154,6 +164,9 @@ typedef struct {
    * error flag, every CTA waits for its own copies in flight and returns, and the step
    * returns IETI_ERR_TIMEOUT.  Small values exist to test that path. */
   int32_t wait_limit;
+  int32_t coarse;        /* IETI_COARSE_*: solve of the coarse problem (ND: linear problems, pcg_mode 0) */
+  int32_t coarse_leaf;   /* nested dissection: boxes of at most this many patches are not cut further
+                            (0: 8) */
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -215,6 +228,11 @@ typedef struct {
   double tune_ms;            /* host time of the autotuning */
   double tune_us_per_it[2];  /* measured time per PCG iteration: the rule's schedule, the chosen one */
   int32_t step_graph;        /* 1: the sweeps of a step run as one CUDA graph (ieti_options.graph) */
+  int32_t coarse_mode;       /* IETI_COARSE_DENSE or IETI_COARSE_ND (0 without coarse unknowns) */
+  int32_t coarse_nodes;      /* nodes of the nested-dissection tree */
+  int32_t coarse_levels;     /* grid-synchronised phases of one coarse solve */
+  double coarse_bytes;       /* algorithmic bytes of one coarse solve */
+  double t_coarse_ms;        /* host time of the coarse assembly and factorization at setup */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
@@ -291,6 +309,17 @@ int ieti_solution(const ieti_ctx *ctx, double *a_out, int64_t len, int32_t out_m
 
 /* Replace the state a^l (checkpoint resume); e entries are ignored. */
 int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem);
+
+/* Nested-dissection tree of the coarse problem (host query; built for every context
+ * with coarse unknowns, with options.coarse_leaf).  Nodes in postorder; node p owns the
+ * coarse unknowns at elimination positions [k0[p], k0[p] + nk[p]) and couples to the
+ * ancestor positions s_idx[s_off[p] .. s_off[p+1]); parent[p] = -1 for a root.
+ * elim_pos[g] (ieti_num_dofs() entries) is the elimination position of the primal edge
+ * g, -1 for other edges.  Two-call protocol: with the arrays NULL only *n_nodes and
+ * *n_s are written; otherwise k0, nk, parent hold *n_nodes entries, s_off *n_nodes + 1,
+ * s_idx *n_s.  Any array may be NULL.  Errors: INVALID_ARG. */
+int ieti_coarse_tree(const ieti_ctx *ctx, int32_t *n_nodes, int64_t *n_s, int32_t *elim_pos, int32_t *k0,
+                     int32_t *nk, int32_t *parent, int64_t *s_off, int32_t *s_idx);
 
 /* Per-class kernel statistics accumulated since the last reset (options.profile = 1);
  * out has IETI_K_NCLASS entries.  reset != 0 clears the counters after reading. */

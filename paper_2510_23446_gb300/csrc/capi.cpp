@@ -1,5 +1,6 @@
 // C ABI of the solver (declared in include/ieti.h).  Marshals arguments, keeps
 // the error text, and never lets an exception cross the boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,6 +11,7 @@
 
 struct ieti_ctx {
   ieti::HostSetup hs;
+  ieti::CoarseTree tree;
   ieti_options opt{};
   ieti::DeviceState *dev = nullptr;
   std::string err;
@@ -35,6 +37,8 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->autotune != 0 && o->autotune != 1) { err = "autotune must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->graph != 0 && o->graph != 1) { err = "graph must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->wait_limit < 0) { err = "wait_limit must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->coarse < IETI_COARSE_AUTO || o->coarse > IETI_COARSE_ND) { err = "bad coarse"; return IETI_ERR_INVALID_ARG; }
+  if (o->coarse_leaf < 0) { err = "coarse_leaf must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
     return IETI_ERR_INVALID_ARG;
@@ -55,7 +59,11 @@ int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ct
     ctx = new ieti_ctx();
     ctx->opt = *options;
     rc = ctx->hs.build(problem, options->host_threads, g_setup_err);
-    if (rc == IETI_OK && options->device >= 0) rc = ieti::device_setup(ctx->hs, ctx->opt, &ctx->dev, g_setup_err);
+    if (rc == IETI_OK)
+      rc = ieti::build_coarse_tree(ctx->hs, options->coarse_leaf > 0 ? options->coarse_leaf : 8, ctx->tree,
+                                   g_setup_err);
+    if (rc == IETI_OK && options->device >= 0)
+      rc = ieti::device_setup(ctx->hs, &ctx->tree, ctx->opt, &ctx->dev, g_setup_err);
   } catch (const std::bad_alloc &) {
     g_setup_err = "host allocation failed";
     rc = IETI_ERR_OOM;
@@ -255,6 +263,28 @@ int ieti_potrf_batched_noalloc(int32_t batch, double *base_dev, const int64_t *o
     g_setup_err = "ieti_potrf_batched_noalloc: host allocation failed";
     return IETI_ERR_OOM;
   }
+}
+
+int ieti_coarse_tree(const ieti_ctx *ctx, int32_t *n_nodes, int64_t *n_s, int32_t *elim_pos, int32_t *k0,
+                     int32_t *nk, int32_t *parent, int64_t *s_off, int32_t *s_idx) {
+  if (!ctx) return IETI_ERR_INVALID_ARG;
+  const ieti::CoarseTree &t = ctx->tree;
+  if (n_nodes) *n_nodes = t.n_nodes;
+  if (n_s) *n_s = (int64_t)t.s_idx.size();
+  if (elim_pos)
+    for (int64_t g = 0; g < ctx->hs.n_edges; ++g) {
+      const int64_t c = ctx->hs.coarse_of_edge[g];
+      elim_pos[g] = c < 0 || t.perm.empty() ? -1 : t.perm[c];
+    }
+  for (int p = 0; p < t.n_nodes; ++p) {
+    if (k0) k0[p] = t.k0[p];
+    if (nk) nk[p] = t.nk[p];
+    if (parent) parent[p] = t.parent[p];
+  }
+  if (s_off)
+    for (int p = 0; p <= t.n_nodes; ++p) s_off[p] = t.n_nodes ? t.s_off[p] : 0;
+  if (s_idx) std::copy(t.s_idx.begin(), t.s_idx.end(), s_idx);
+  return IETI_OK;
 }
 
 const char *ieti_last_error(const ieti_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

@@ -1,0 +1,45 @@
+// Nested-dissection structure of the primal coarse problem (Sec. 3: the coarse Schur
+// complement S_c = sum_s A_s^T C_s A_s).  Two primal unknowns couple only when some
+// patch holds copies of both, and every primal unknown sits on patch interfaces, so
+// the patch grid itself gives a nested dissection: a box of patches is cut in the
+// middle of its longest side and the unknowns whose patches lie on both sides of the
+// cut form that node's separator block K_p.  The tree is stored in postorder; the
+// unknowns are renumbered in elimination order, so that each node's block is the
+// contiguous range [k0, k0 + nk) and every unknown of an ancestor comes later.
+//
+// Fill (multifrontal view): the factor's column block of node p couples to the
+// ancestor unknowns that touch a patch of p's box, S_p (ascending).  A child's S set
+// is contained in its parent's front [K_p; S_p], which is what the extend-add and
+// the solves use.  Pure host code.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "host_setup.h"
+
+namespace ieti {
+
+struct CoarseTree {
+  int64_t nc = 0;
+  int n_nodes = 0;
+  int leaf_max = 1;
+  std::vector<int32_t> perm;            // coarse id -> position in elimination order
+  // per node, postorder (children before their parent)
+  std::vector<int32_t> k0, nk, ns;      // own block [k0, k0 + nk), |S_p|
+  std::vector<int32_t> parent;          // -1 for a root
+  std::vector<int32_t> height, depth;   // leaves have height 0, roots depth 0
+  std::vector<int32_t> box;             // [6 * p]: lo0, hi0, lo1, hi1, lo2, hi2 (patch index ranges, hi exclusive)
+  std::vector<int64_t> s_off;           // S_p = s_idx[s_off[p] .. s_off[p + 1])
+  std::vector<int32_t> s_idx;
+  std::vector<int32_t> child_ptr, child_idx;
+  int n_height = 0, n_depth = 0;        // levels of the forward (by height) and backward (by depth) sweeps
+  // index of a position x of the parent's front [K_p; S_p] (x = global elimination position)
+  int front_index(int p, int32_t x) const;
+};
+
+// Build the tree for the coarse unknowns of `hs` (boxes of leaf_max patches or fewer
+// are not cut further; empty nodes are removed and their children re-attached).
+int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::string &err);
+
+}  // namespace ieti

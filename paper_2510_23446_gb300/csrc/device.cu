@@ -44,6 +44,7 @@
 #include "device.h"
 #include "nonlinear.cuh"
 #include "pcg_kernel.cuh"
+#include "coarse_nd.h"
 
 namespace ieti {
 
@@ -461,6 +462,55 @@ __global__ void k_round_lower(int64_t n, const double *A, int64_t ld, float *F, 
   if (idx >= n * n) return;
   int64_t r = idx / n, c = idx % n;
   F[r * ldf + c] = c <= r ? (float)A[r * ld + c] : 0.f;
+}
+
+// ---- nested-dissection coarse factorization (multifrontal; fronts row-major, lower
+// triangle, leading dimension na = 2 nk + ns: [K | S | K'] with K' = identity rows)
+
+// original entries of S_c in the K columns of the front (rows K and S), identity rows K'
+__global__ void k_front_init(const double *Sc, int64_t nc, const int32_t *fid, int nk, int ns, double *F,
+                             int64_t ld) {
+  const int m = nk + ns;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx < (int64_t)m * nk) {
+    const int i = (int)(idx / nk), j = (int)(idx % nk);
+    if (i >= j) F[(int64_t)i * ld + j] = Sc[(int64_t)fid[i] * nc + fid[j]];
+  }
+  if (idx < nk) F[(int64_t)(m + idx) * ld + idx] = 1.0;
+}
+
+// F_parent[map[a]][map[b]] += U_child[a][b] (lower triangle; map ascending)
+__global__ void k_extend_add(const double *Fc, int64_t ldc, int nkc, int nsc, const int32_t *map, double *Fp,
+                             int64_t ldp) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nsc * nsc) return;
+  const int a = (int)(idx / nsc), b = (int)(idx % nsc);
+  if (b > a) return;
+  Fp[(int64_t)map[a] * ldp + map[b]] += Fc[(int64_t)(nkc + a) * ldc + nkc + b];
+}
+
+// after the nk pivots: trailing [K' K'] = -D^{-1}, [K' S] = -Lbar^T.  Z = [D^{-1}; Lbar],
+// Lt = Lbar^T (padding columns stay zero)
+__global__ void k_front_extract(const double *F, int64_t ld, int nk, int ns, double *Z, int zld, double *Lt,
+                                int ltld) {
+  const int m = nk + ns;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nz = (int64_t)m * nk;
+  if (idx < nz) {
+    const int r = (int)(idx / nk), c = (int)(idx % nk);
+    double v;
+    if (r < nk) {
+      const int hi = max(r, c), lo = min(r, c);
+      v = -F[(int64_t)(m + hi) * ld + m + lo];
+    } else {
+      v = -F[(int64_t)(m + c) * ld + r];
+    }
+    Z[(int64_t)r * zld + c] = v;
+  } else if (idx < nz + (int64_t)nk * ns) {
+    const int64_t t = idx - nz;
+    const int r = (int)(t / ns), j = (int)(t % ns);
+    Lt[(int64_t)r * ltld + j] = -F[(int64_t)(m + r) * ld + nk + j];
+  }
 }
 
 // =============================================================================
@@ -926,6 +976,21 @@ struct DeviceState {
   std::vector<int64_t> nlh_pcN;     // per batch patch: offset into nl_pcN
   double *c_SLLinv = nullptr, *c_X = nullptr, *c_Z0 = nullptr, *c_Zaug = nullptr, *c_Zinv = nullptr,
          *c_Y = nullptr, *c_Ltmp = nullptr;
+  // coarse solve by nested dissection of the patch grid (coarse_nd = 1): per node the
+  // operators Z = [D^{-1}; Lbar] and Lt = Lbar^T in the per-iteration arena, the
+  // update buffer, the gather lists, and the rows of every level per CTA
+  int coarse_nd = 0, nd_cw = 1, nd_H = 0, nd_D = 0, nd_nodes = 0, nd_zmax = 0;
+  int32_t *nd_k0 = nullptr, *nd_nk = nullptr, *nd_ns = nullptr, *nd_zld = nullptr, *nd_ltld = nullptr,
+          *nd_sidx = nullptr, *nd_src = nullptr;
+  int64_t *nd_zoff = nullptr, *nd_ltoff = nullptr, *nd_soff = nullptr, *nd_uoff = nullptr, *nd_srcoff = nullptr;
+  double *nd_Z = nullptr, *nd_Lt = nullptr, *nd_u = nullptr;
+  int32_t *ndf_ptr = nullptr, *ndf_s = nullptr, *ndf_r0 = nullptr, *ndf_r1 = nullptr;
+  int32_t *ndb_ptr = nullptr, *ndb_s = nullptr, *ndb_r0 = nullptr, *ndb_r1 = nullptr;
+  std::vector<std::vector<int32_t>> ndh_fwd, ndh_bwd;   // node ids per forward / backward level
+  std::vector<int32_t> ndh_nk, ndh_ns, ndh_zld, ndh_ltld;
+  int64_t nd_z_elems = 0, nd_lt_elems = 0;              // padded sizes of the two operator blocks
+  double nd_bytes = 0;                                  // algorithmic bytes of one coarse solve
+  double t_coarse_ms = 0;                               // device time of the coarse factorization
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -1345,6 +1410,229 @@ static int run_partial(DeviceState *d, TD *D, const int64_t *doff, const int32_t
 }
 
 static int coarse_publish(DeviceState *d, std::string &err);
+
+static int nd_ld(int n) {  // leading dimension of an FP64 operator block: an odd number of 16-byte units
+  if (n <= 0) return 0;
+  int l = (n + 3) / 4 * 4;
+  if ((l / 2) % 2 == 0) l += 2;
+  return l;
+}
+
+// Host part of the nested-dissection coarse solve: node tables, the gather lists of
+// the child updates, the per-level node lists and the operator layout (Z and Lt
+// blocks, offsets into d->nd_Z / d->nd_Lt).  Sizes only; the operators come from
+// coarse_nd_factor.
+static int coarse_nd_tables(DeviceState *d, const CoarseTree &t, std::string &err) {
+  const int NN = t.n_nodes;
+  d->nd_nodes = NN;
+  d->nd_H = t.n_height;
+  d->nd_D = t.n_depth;
+  d->ndh_nk.assign(t.nk.begin(), t.nk.end());
+  d->ndh_ns.assign(t.ns.begin(), t.ns.end());
+  d->ndh_zld.resize(NN);
+  d->ndh_ltld.resize(NN);
+  std::vector<int64_t> zoff(NN), ltoff(NN), uoff(NN), srcoff(NN);
+  int64_t z = 0, lt = 0, u = 0, sr = 0;
+  d->nd_zmax = 4;
+  d->nd_bytes = 0;
+  for (int p = 0; p < NN; ++p) {
+    const int nk = t.nk[p], ns = t.ns[p];
+    d->ndh_zld[p] = nd_ld(nk);
+    d->ndh_ltld[p] = nd_ld(ns);
+    zoff[p] = z;
+    ltoff[p] = lt;
+    uoff[p] = u;
+    srcoff[p] = sr;
+    z += (int64_t)(nk + ns) * d->ndh_zld[p];
+    lt += (int64_t)nk * d->ndh_ltld[p];
+    u += ns;
+    sr += nk + ns;
+    d->nd_zmax = std::max({d->nd_zmax, d->ndh_zld[p], d->ndh_ltld[p]});
+    // every entry of Z read once forward, of Lt once backward; the staged vectors once per node
+    d->nd_bytes += 8.0 * ((double)(nk + ns) * nk + (double)nk * ns) + 8.0 * (3.0 * nk + 2.0 * ns);
+  }
+  d->nd_z_elems = z;
+  d->nd_lt_elems = lt;
+  // child updates per front position
+  std::vector<std::vector<int32_t>> lists(sr);
+  int cw = 1;
+  for (int p = 0; p < NN; ++p)
+    for (int k = t.child_ptr[p]; k < t.child_ptr[p + 1]; ++k) {
+      const int ch = t.child_idx[k];
+      for (int j = 0; j < t.ns[ch]; ++j) {
+        const int i = t.front_index(p, t.s_idx[t.s_off[ch] + j]);
+        if (i < 0) {
+          err = "nested dissection: a child update has no place in its parent's front";
+          return IETI_ERR_INVALID_ARG;
+        }
+        auto &L = lists[srcoff[p] + i];
+        L.push_back((int32_t)(uoff[ch] + j));
+        cw = std::max(cw, (int)L.size());
+      }
+    }
+  if (u >= (int64_t)INT32_MAX || z >= ((int64_t)1 << 40)) {
+    err = "coarse problem too large for the nested-dissection solver";
+    return IETI_ERR_TOO_LARGE;
+  }
+  d->nd_cw = cw;
+  std::vector<int32_t> src((size_t)sr * cw, -1);
+  for (int64_t i = 0; i < sr; ++i)
+    for (size_t w = 0; w < lists[i].size(); ++w) src[(size_t)i * cw + w] = lists[i][w];
+  std::vector<int64_t> srcoff_w(NN), soff(t.s_off.begin(), t.s_off.end() - 1);
+  for (int p = 0; p < NN; ++p) srcoff_w[p] = srcoff[p] * cw;
+  d->ndh_fwd.assign(d->nd_H, {});
+  d->ndh_bwd.assign(std::max(d->nd_D - 1, 0), {});
+  for (int p = 0; p < NN; ++p) {
+    d->ndh_fwd[t.height[p]].push_back(p);
+    if (t.depth[p] > 0 && t.ns[p] > 0 && t.nk[p] > 0) d->ndh_bwd[t.depth[p] - 1].push_back(p);
+  }
+  std::vector<int32_t> sidx(t.s_idx);
+  if (sidx.empty()) sidx.push_back(0);
+  int rc;
+  if ((rc = upload(d, &d->nd_k0, t.k0, err)) || (rc = upload(d, &d->nd_nk, d->ndh_nk, err)) ||
+      (rc = upload(d, &d->nd_ns, d->ndh_ns, err)) || (rc = upload(d, &d->nd_zld, d->ndh_zld, err)) ||
+      (rc = upload(d, &d->nd_ltld, d->ndh_ltld, err)) || (rc = upload(d, &d->nd_sidx, sidx, err)) ||
+      (rc = upload(d, &d->nd_src, src, err)) || (rc = upload(d, &d->nd_zoff, zoff, err)) ||
+      (rc = upload(d, &d->nd_ltoff, ltoff, err)) || (rc = upload(d, &d->nd_soff, soff, err)) ||
+      (rc = upload(d, &d->nd_uoff, uoff, err)) || (rc = upload(d, &d->nd_srcoff, srcoff_w, err)) ||
+      (rc = dalloc(d, &d->nd_u, (size_t)std::max<int64_t>(u, 1), err)))
+    return rc;
+  return IETI_OK;
+}
+
+// Multifrontal FP64 factorization of S_c (nc x nc, rows and columns in elimination
+// order) along the tree, level by level in height: each node's front [K | S | K'] is
+// the original K columns of S_c, the children's update matrices added (in child
+// order: deterministic), and identity rows K'; one batched partial Cholesky of the
+// nk pivots of all fronts of a level leaves the update matrix in [S S], -Lbar^T in
+// [K' S] and -D^{-1} in [K' K'], which are extracted into d->nd_Z / d->nd_Lt.
+static int coarse_nd_factor(DeviceState *d, const CoarseTree &t, const double *Sc, std::string &err) {
+  const int NN = t.n_nodes;
+  const int64_t nc = d->NC;
+  cudaStream_t st = d->stream;
+  std::vector<int64_t> foff(NN + 1, 0), fidoff(NN + 1, 0), eaoff(NN + 1, 0);
+  std::vector<int32_t> na(NN), fid, ea;
+  for (int p = 0; p < NN; ++p) {
+    na[p] = 2 * t.nk[p] + t.ns[p];
+    foff[p + 1] = foff[p] + (int64_t)na[p] * na[p];
+    for (int k = 0; k < t.nk[p]; ++k) fid.push_back(t.k0[p] + k);
+    for (int64_t k = t.s_off[p]; k < t.s_off[p + 1]; ++k) fid.push_back(t.s_idx[k]);
+    fidoff[p + 1] = (int64_t)fid.size();
+    if (t.parent[p] >= 0)
+      for (int64_t k = t.s_off[p]; k < t.s_off[p + 1]; ++k) ea.push_back(t.front_index(t.parent[p], t.s_idx[k]));
+    eaoff[p + 1] = (int64_t)ea.size();
+  }
+  if (fid.empty()) fid.push_back(0);
+  if (ea.empty()) ea.push_back(0);
+  double *F = nullptr;
+  int32_t *dfid = nullptr, *dea = nullptr;
+  unsigned char *blk = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(F);
+    cudaFree(dfid);
+    cudaFree(dea);
+    cudaFree(blk);
+  };
+  const size_t fbytes = (size_t)std::max<int64_t>(foff[NN], 1) * sizeof(double);
+  if (cudaMalloc((void **)&F, fbytes) != cudaSuccess || cudaMalloc((void **)&dfid, fid.size() * 4) != cudaSuccess ||
+      cudaMalloc((void **)&dea, ea.size() * 4) != cudaSuccess ||
+      cudaMalloc((void **)&blk, (size_t)NN * (8 + 9 * 4)) != cudaSuccess) {
+    cleanup();
+    err = "cudaMalloc failed for the nested-dissection fronts (" + std::to_string(fbytes >> 20) + " MiB)";
+    return IETI_ERR_OOM;
+  }
+  int64_t *doff = (int64_t *)blk;
+  int32_t *dld = (int32_t *)(doff + NN), *dkb = dld + NN, *dke = dkb + NN, *dna = dke + NN, *dstat = dna + NN,
+          *dz = dstat + NN, *dbig = dz + NN, *dz2 = dbig + NN;
+  cudaError_t e = cudaMemsetAsync(F, 0, fbytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dfid, fid.data(), fid.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dea, ea.data(), ea.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dstat, 0, (size_t)NN * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dz, 0, (size_t)NN * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dz2, 0, (size_t)NN * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dbig, 0x7f, (size_t)NN * 4, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    err = std::string("nested-dissection setup failed: ") + cudaGetErrorString(e);
+    return IETI_ERR_CUDA;
+  }
+  for (int p = 0; p < NN; ++p) {
+    const int64_t cnt = std::max<int64_t>((int64_t)(t.nk[p] + t.ns[p]) * t.nk[p], t.nk[p]);
+    if (cnt > 0)
+      k_front_init<<<grid_for(cnt, 256), 256, 0, st>>>(Sc, nc, dfid + fidoff[p], t.nk[p], t.ns[p], F + foff[p],
+                                                       na[p]);
+    d->launches_setup++;
+  }
+  AugLimits lim{dz, dz2, dbig, dz};
+  int rc = IETI_OK;
+  for (int h = 0; h < d->nd_H && rc == IETI_OK; ++h) {
+    const std::vector<int32_t> &L = d->ndh_fwd[h];
+    std::vector<int64_t> hoff;
+    std::vector<int32_t> hld, hkb, hke, hna;
+    for (int p : L) {
+      for (int k = t.child_ptr[p]; k < t.child_ptr[p + 1]; ++k) {
+        const int ch = t.child_idx[k];
+        const int64_t cnt = (int64_t)t.ns[ch] * t.ns[ch];
+        if (cnt == 0) continue;
+        k_extend_add<<<grid_for(cnt, 256), 256, 0, st>>>(F + foff[ch], na[ch], t.nk[ch], t.ns[ch], dea + eaoff[ch],
+                                                         F + foff[p], na[p]);
+        d->launches_setup++;
+      }
+      hoff.push_back(foff[p]);
+      hld.push_back(na[p]);
+      hkb.push_back(0);
+      hke.push_back(t.nk[p]);
+      hna.push_back(na[p]);
+    }
+    const int nb = (int)L.size();
+    e = cudaMemcpyAsync(doff, hoff.data(), nb * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dld, hld.data(), nb * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dkb, hkb.data(), nb * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dke, hke.data(), nb * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dna, hna.data(), nb * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      err = std::string("nested-dissection setup failed: ") + cudaGetErrorString(e);
+      rc = IETI_ERR_CUDA;
+      break;
+    }
+    rc = potrf_partial<double>(d, F, doff, dld, hkb, hke, hna, dkb, dke, dna, dstat, lim, err);
+    if (rc == IETI_OK) {
+      std::vector<int32_t> hst(nb);
+      e = cudaMemcpyAsync(hst.data(), dstat, nb * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        err = std::string("nested-dissection factorization failed: ") + cudaGetErrorString(e);
+        rc = IETI_ERR_CUDA;
+      }
+      for (int b = 0; b < nb && rc == IETI_OK; ++b)
+        if (hst[b]) {
+          err = "coarse Schur complement is not positive definite (nested-dissection node " + std::to_string(L[b]) +
+                ", pivot " + std::to_string(hst[b] - 1) + ")";
+          rc = IETI_ERR_NOT_SPD;
+        }
+    }
+  }
+  if (rc == IETI_OK) {
+    int64_t zo = 0, lo = 0;
+    for (int p = 0; p < NN; ++p) {
+      const int64_t cnt = (int64_t)(t.nk[p] + t.ns[p]) * t.nk[p] + (int64_t)t.nk[p] * t.ns[p];
+      if (cnt > 0)
+        k_front_extract<<<grid_for(cnt, 256), 256, 0, st>>>(F + foff[p], na[p], t.nk[p], t.ns[p], d->nd_Z + zo,
+                                                            d->ndh_zld[p], d->nd_Lt + lo, d->ndh_ltld[p]);
+      d->launches_setup++;
+      zo += (int64_t)(t.nk[p] + t.ns[p]) * d->ndh_zld[p];
+      lo += (int64_t)t.nk[p] * d->ndh_ltld[p];
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      err = std::string("nested-dissection extraction failed: ") + cudaGetErrorString(e);
+      rc = IETI_ERR_CUDA;
+    }
+  }
+  cleanup();
+  return rc;
+}
 
 // FP64 partial Cholesky of the assembled [[S_c, I], [I, 0]] (2 nc x 2 nc, row-major)
 // and extraction of S_c^{-1} into the per-iteration slot (FP32 (hi, lo) pairs in the
@@ -1904,6 +2192,15 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.n_stages = d->n_stages;
   a.l2_keep_frac = d->l2_keep_frac;
   a.spin_max = d->opt.wait_limit > 0 ? (long long)d->opt.wait_limit : (1ll << 25);
+  a.coarse_nd = d->coarse_nd;
+  a.nd_cw = d->nd_cw; a.nd_H = d->nd_H; a.nd_D = d->nd_D;
+  a.nd_k0 = d->nd_k0; a.nd_nk = d->nd_nk; a.nd_ns = d->nd_ns; a.nd_zld = d->nd_zld; a.nd_ltld = d->nd_ltld;
+  a.nd_sidx = d->nd_sidx; a.nd_src = d->nd_src;
+  a.nd_zoff = d->nd_zoff; a.nd_ltoff = d->nd_ltoff; a.nd_soff = d->nd_soff; a.nd_uoff = d->nd_uoff;
+  a.nd_srcoff = d->nd_srcoff;
+  a.nd_Z = d->nd_Z; a.nd_Lt = d->nd_Lt; a.nd_u = d->nd_u;
+  a.ndf_ptr = d->ndf_ptr; a.ndf_s = d->ndf_s; a.ndf_r0 = d->ndf_r0; a.ndf_r1 = d->ndf_r1;
+  a.ndb_ptr = d->ndb_ptr; a.ndb_s = d->ndb_s; a.ndb_r0 = d->ndb_r0; a.ndb_r1 = d->ndb_r1;
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
   {
@@ -1927,7 +2224,8 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
     }
     cfg.attrs = attr;
     cfg.numAttrs = nattr;
-    CK(cudaLaunchKernelExC(&cfg, (const void *)k_ddsolve<T>, args));
+    const void *fn = d->coarse_nd ? (const void *)k_ddsolve<T, true> : (const void *)k_ddsolve<T, false>;
+    CK(cudaLaunchKernelExC(&cfg, fn, args));
   }
   return IETI_OK;
 }
@@ -2349,13 +2647,18 @@ struct PcgSched {
   int psi = 0;  // 0: the Psi rows share the S_bb partition; > 0: own partition, per-row overhead
 };
 
+// widest FP64 coarse row / staged coarse vector: the dense S_c^{-1} row, or the widest
+// nested-dissection block
+static size_t pcg_coarse_width(const DeviceState *d) {
+  return (size_t)(d->coarse_nd ? d->nd_zmax : std::max(d->ldc, 4));
+}
 static size_t pcg_xs_bytes(const DeviceState *d) {
   const size_t esz = d->mixed ? 4 : 8;
-  return (std::max((size_t)d->ldmax * esz, (size_t)std::max(d->ldc, 4) * sizeof(double)) + 127) / 128 * 128;
+  return (std::max((size_t)d->ldmax * esz, pcg_coarse_width(d) * sizeof(double)) + 127) / 128 * 128;
 }
 static size_t pcg_row_max(const DeviceState *d) {
   const size_t esz = d->mixed ? 4 : 8;
-  return (std::max((size_t)d->ldmax * esz, (size_t)d->ldc * sizeof(double)) + 127) / 128 * 128;
+  return (std::max((size_t)d->ldmax * esz, pcg_coarse_width(d) * sizeof(double)) + 127) / 128 * 128;
 }
 // dynamic shared memory per CTA at cps CTAs per SM (227 KB per CTA at most, the
 // kernel's static arrays and the per-CTA reservation taken off)
@@ -2400,7 +2703,8 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
     return IETI_ERR_TOO_LARGE;
   }
   const size_t smem = xs + sc.ns * sc.stage;
-  const void *fn = d->mixed ? (const void *)k_ddsolve<float> : (const void *)k_ddsolve<double>;
+  const void *fn = d->mixed ? (d->coarse_nd ? (const void *)k_ddsolve<float, true> : (const void *)k_ddsolve<float, false>)
+                            : (d->coarse_nd ? (const void *)k_ddsolve<double, true> : (const void *)k_ddsolve<double, false>);
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_THREADS, smem));
@@ -2426,6 +2730,36 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
     if ((rc = upload_cap(d, ptrs[k][0], cap_ptr, sp, err)) || (rc = upload_cap(d, ptrs[k][1], cap_seg, ss, err)) ||
         (rc = upload_cap(d, ptrs[k][2], cap_seg, r0v, err)) || (rc = upload_cap(d, ptrs[k][3], cap_seg, r1v, err)))
       return rc;
+  }
+  if (d->coarse_nd) {
+    // rows of every nested-dissection level, partitioned like the patch operators
+    // (segment s = node id); pointer rows of all levels concatenated
+    for (int dir = 0; dir < 2; ++dir) {
+      const auto &levels = dir == 0 ? d->ndh_fwd : d->ndh_bwd;
+      std::vector<int32_t> P, S, R0, R1;
+      for (const auto &L : levels) {
+        std::vector<int32_t> rows, ld;
+        for (int nd : L) {
+          rows.push_back(dir == 0 ? d->ndh_nk[nd] + d->ndh_ns[nd] : d->ndh_nk[nd]);
+          ld.push_back(dir == 0 ? d->ndh_zld[nd] : d->ndh_ltld[nd]);
+        }
+        partition_rows(rows, ld, d->G, sp, ss, r0v, r1v);
+        const int32_t base = (int32_t)S.size();
+        for (int32_t v : sp) P.push_back(base + v);
+        for (int32_t v : ss) S.push_back(L[v]);
+        R0.insert(R0.end(), r0v.begin(), r0v.end());
+        R1.insert(R1.end(), r1v.begin(), r1v.end());
+      }
+      const size_t nl = std::max<size_t>(levels.size(), 1);
+      const size_t cp = nl * ((size_t)PCG_MAX_CPS * d->n_sm + 1), cs = nl * (size_t)PCG_MAX_CPS * d->n_sm + d->nd_nodes + 1;
+      if (P.empty()) P.push_back(0);
+      int rc;
+      if (dir == 0 ? ((rc = upload_cap(d, &d->ndf_ptr, cp, P, err)) || (rc = upload_cap(d, &d->ndf_s, cs, S, err)) ||
+                      (rc = upload_cap(d, &d->ndf_r0, cs, R0, err)) || (rc = upload_cap(d, &d->ndf_r1, cs, R1, err)))
+                   : ((rc = upload_cap(d, &d->ndb_ptr, cp, P, err)) || (rc = upload_cap(d, &d->ndb_s, cs, S, err)) ||
+                      (rc = upload_cap(d, &d->ndb_r0, cs, R0, err)) || (rc = upload_cap(d, &d->ndb_r1, cs, R1, err))))
+        return rc;
+    }
   }
   d->psi_overhead = sc.psi;
   if (sc.psi > 0) {
@@ -2633,7 +2967,8 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
   return IETI_OK;
 }
 
-int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out, std::string &err) {
+int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options &opt, DeviceState **out,
+                 std::string &err) {
   auto t0 = std::chrono::steady_clock::now();
   DeviceState *d = new DeviceState();
   *out = nullptr;
@@ -2650,6 +2985,19 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   };
   CK(cudaSetDevice(d->device));
   d->stream = (cudaStream_t)opt.cuda_stream;
+  // coarse solve: dense S_c^{-1} rows, or the nested-dissection factor; auto takes the
+  // factor once the dense inverse passes 64 MB (its bytes per iteration grow as nc^2)
+  {
+    const double nc0 = (double)hs.n_coarse;
+    bool nd = opt.coarse == IETI_COARSE_ND;
+    if (opt.coarse == IETI_COARSE_AUTO)
+      nd = tree && tree->n_nodes > 0 && !hs.nonlinear && opt.pcg_mode == 0 && 8.0 * nc0 * nc0 > 64e6;
+    if (nd && (hs.nonlinear || opt.pcg_mode != 0 || !tree)) {
+      err = "the nested-dissection coarse solve needs a linear problem and pcg_mode 0";
+      return fail(IETI_ERR_INVALID_ARG);
+    }
+    d->coarse_nd = nd && hs.n_coarse > 0 && tree->n_nodes > 0;
+  }
   CK(cudaEventCreate(&d->ev0));
   CK(cudaEventCreate(&d->ev1));
   const int np_ = hs.n_patches();
@@ -2784,6 +3132,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     const Patch &pt = hs.patches[s];
     for (int k = 0; k < pt.np; ++k) {
       int64_t c = hs.coarse_of_edge[pt.kept_glob[pt.ni + pt.nb + k]];
+      if (d->coarse_nd) c = tree->perm[c];  // elimination order of the nested dissection
       pc[hpofs[s] + k] = (int32_t)c;
       copies[c].push_back((int32_t)(hpofs[s] + k));
     }
@@ -2914,6 +3263,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     }
     if ((rc = upload_desc(d, d->dS, ao, xo, yi, nc, err))) return fail(rc);
   }
+  if (d->coarse_nd && (rc = coarse_nd_tables(d, *tree, err))) return fail(rc);
   // ---------------- work vectors
   if ((rc = dalloc(d, &d->a, hs.n_edges, err)) || (rc = dalloc(d, &d->j, hs.n_edges, err)) ||
       (opt.predictor && ((rc = dalloc(d, &d->a_prev, hs.n_edges, err)) ||
@@ -3113,7 +3463,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     // H, Q, P and the coarse inverse are re-read every PCG iteration: one arena
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     size_t bH = al(std::max<int64_t>(hh[np_], 1) * esz), bQ = al(std::max<int64_t>(hq[np_], 1) * esz),
-           bP = al(std::max<int64_t>(hp[np_], 1) * esz), bS = al(std::max<int64_t>(d->NC * d->ldc, 1) * 8);
+           bP = al(std::max<int64_t>(hp[np_], 1) * esz),
+           bS = al(std::max<int64_t>(d->coarse_nd ? d->nd_z_elems + d->nd_lt_elems : d->NC * d->ldc, 1) * 8);
     d->iter_bytes = bH + bQ + bP + bS;
     cudaError_t e = cudaMalloc((void **)&d->iter_arena, d->iter_bytes);
     if (e != cudaSuccess) {
@@ -3126,6 +3477,11 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
     d->Q = d->iter_arena + bH;
     d->P = d->iter_arena + bH + bQ;
     d->Scoarse_slot = (double *)(d->iter_arena + bH + bQ + bP);
+    if (d->coarse_nd) {
+      d->nd_Z = d->Scoarse_slot;
+      d->nd_Lt = d->nd_Z + d->nd_z_elems;
+      CK(cudaMemsetAsync(d->Scoarse_slot, 0, bS, d->stream));  // row padding stays zero
+    }
   }
   if ((rc = alloc_op(&d->IG, hig[np_])) || (rc = alloc_op(&d->GT, hgt[np_]))) return fail(rc);
   CK(cudaMemsetAsync(d->IG, 0, std::max<int64_t>(hig[np_], 1) * esz, d->stream));
@@ -3201,8 +3557,35 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
                                                              d->igoff, d->gtoff, (double *)d->IG, (double *)d->GT);
     d->launches_setup++;
   }
-  // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, inverted through [[S_c, I], [I, 0]]
-  if (d->NC > 0) {
+  // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, factored along the nested
+  // dissection, or inverted through [[S_c, I], [I, 0]]
+  if (d->NC > 0 && d->coarse_nd) {
+    auto tc0 = std::chrono::steady_clock::now();
+    const int64_t nc = d->NC;
+    double *Sc = nullptr;
+    if (cudaMalloc((void **)&Sc, (size_t)(nc * nc) * sizeof(double)) != cudaSuccess) {
+      err = "cudaMalloc failed for the assembled coarse matrix";
+      return fail(IETI_ERR_OOM);
+    }
+    cudaError_t e0 = cudaMemsetAsync(Sc, 0, (size_t)(nc * nc) * sizeof(double), d->stream);
+    for (int s = 0; s < np_ && e0 == cudaSuccess; ++s) {
+      if (hnp[s] == 0) continue;
+      int64_t cnt = (int64_t)hnp[s] * hnp[s];
+      if (f32)
+        k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
+                                                                       d->pc + hpofs[s], Sc, nc);
+      else
+        k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
+                                                                        hnp[s], d->pc + hpofs[s], Sc, nc);
+      d->launches_setup++;
+    }
+    rc = e0 == cudaSuccess ? coarse_nd_factor(d, *tree, Sc, err) : IETI_ERR_CUDA;
+    if (e0 != cudaSuccess) err = std::string("coarse assembly failed: ") + cudaGetErrorString(e0);
+    cudaStreamSynchronize(d->stream);
+    cudaFree(Sc);
+    if (rc) return fail(rc);
+    d->t_coarse_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
+  } else if (d->NC > 0) {
     int64_t nc = d->NC, ldc = 2 * nc;
     double *Sc = nullptr;
     if ((rc = dalloc(d, &Sc, (size_t)(ldc * ldc), err))) return fail(rc);
@@ -3259,7 +3642,8 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
   d->bytes -= hdoff[np_] * (int64_t)dsz;
   // algorithmic bytes of one PCG iteration: H and Psi once each (F apply), P once
   // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
-  d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) + 8 * d->NC * d->NC +
+  d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) +
+                  (d->coarse_nd ? (int64_t)d->nd_bytes : 8 * d->NC * d->NC) +
                   8 * (12 * d->M + 6 * d->NBt + 4 * d->NPt);
   {
     // ---- persistent PCG plan: one CTA per SM, three TMA stages of at most 64 KB (the
@@ -3380,7 +3764,7 @@ int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out
       sQ += (int64_t)hnb[s] * hnp[s];
       sP += (int64_t)hnb[s] * hnb[s];
     }
-    d->bytes_iter_alg = (double)esz * (sH + sQ + sP) + 8.0 * (double)d->NC * d->NC +
+    d->bytes_iter_alg = (double)esz * (sH + sQ + sP) + (d->coarse_nd ? d->nd_bytes : 8.0 * (double)d->NC * d->NC) +
                         8.0 * (14.0 * d->M + 8.0 * d->NBt + 2.0 * d->NPt + 2.0 * d->NC);
   }
   {
@@ -3505,6 +3889,11 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->tune_ms = d->tune_ms;
   info->tune_us_per_it[0] = d->tune_us[0];
   info->tune_us_per_it[1] = d->tune_us[1];
+  info->coarse_mode = d->NC == 0 ? 0 : (d->coarse_nd ? IETI_COARSE_ND : IETI_COARSE_DENSE);
+  info->coarse_nodes = d->nd_nodes;
+  info->coarse_levels = d->coarse_nd ? d->nd_H + std::max(d->nd_D - 1, 0) : (d->NC > 0 ? 1 : 0);
+  info->coarse_bytes = d->coarse_nd ? d->nd_bytes : 8.0 * (double)d->NC * d->NC;
+  info->t_coarse_ms = d->t_coarse_ms;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

@@ -5,13 +5,15 @@
 
 #include <cuda_runtime.h>
 
+#include "coarse_nd.h"
 #include "host_setup.h"
 
 namespace ieti {
 
 struct DeviceState;
 
-int device_setup(const HostSetup &hs, const ieti_options &opt, DeviceState **out, std::string &err);
+int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options &opt, DeviceState **out,
+                 std::string &err);
 int device_step(DeviceState *d, const double *j, int j_mem, ieti_stats *st, std::string &err);
 int device_solution(DeviceState *d, double *a, int64_t len, int mem, std::string &err);
 int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std::string &err);

@@ -25,6 +25,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "tma.cuh"
 
@@ -80,6 +81,21 @@ struct PcgArgs {
   int n_stages;
   float l2_keep_frac;  // > 0: L2 eviction-priority hints on the operator streams
   long long spin_max;  // polls of a grid-barrier wait before it gives up (~1-3 s by default)
+  // coarse solve by nested dissection (coarse_nd = 1; else the dense S_c^{-1} rows above).
+  // Node p owns the coarse unknowns [k0, k0 + nk) and couples to the ns ancestor
+  // unknowns sidx[soff .. soff + ns).  Z_p = [D_p^{-1}; Lbar_p] ((nk + ns) x nk, leading
+  // dimension zld) with D_p the node's pivot block after the updates of its subtree and
+  // Lbar_p = F_SK D_p^{-1}; Lt_p = Lbar_p^T (nk x ns, ltld).  Forward, by height:
+  // f_K = c_K + child updates, q_K = D^{-1} f_K, u_p = f_S + child updates - Lbar f_K
+  // (u_p in ubuf at uoff, the child updates gathered through src: cw entries per front
+  // position, -1 = none).  Backward, by depth: q_K -= Lt_p q_S.
+  int coarse_nd, nd_cw, nd_H, nd_D;
+  const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_src;
+  const int64_t *nd_zoff, *nd_ltoff, *nd_soff, *nd_uoff, *nd_srcoff;
+  const double *nd_Z, *nd_Lt;
+  double *nd_u;
+  const int32_t *ndf_ptr, *ndf_s, *ndf_r0, *ndf_r1;   // forward rows per level: ptr [H][G + 1]
+  const int32_t *ndb_ptr, *ndb_s, *ndb_r0, *ndb_r1;   // backward rows per level (depth 1 ..): ptr [D][G + 1]
 };
 
 constexpr int TRACE_IT = 16;
@@ -503,11 +519,15 @@ __device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &c
   return true;
 }
 
-template <class T>
+// ND: the coarse solve by nested dissection (a separate instantiation, so that the
+// dense-coarse kernel carries none of its code or registers)
+template <class T, bool ND>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constant__ PcgArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sh[32];
-  __shared__ __align__(16) T ybuf[2 * RPC_MAX];  // row results of the last two chunks
+  using YB = typename std::conditional<ND, double, T>::type;  // the FP64 coarse rows stage their results too
+  __shared__ __align__(16) YB ybuf_raw[2 * RPC_MAX];  // row results of the last two chunks
+  T *ybuf = reinterpret_cast<T *>(ybuf_raw);
   __shared__ __align__(8) uint64_t ring_bar[NS_MAX];
   T *xs = reinterpret_cast<T *>(smem_raw);
   double *ccs = reinterpret_cast<double *>(smem_raw);
@@ -544,6 +564,23 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                        0, 0, 0, ps, hint};
   const OpRows<double> opS{a.Sinv, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, (int)cb, (int)ce, a.ldc,
                            pk, hint};
+  // nested-dissection levels: 0 .. H-1 forward (Z rows), H .. H+D-2 backward (Lt rows, depth 1 ..)
+  auto nd_op = [&](int lv) {
+    if (lv < a.nd_H) {
+      const int32_t *pp = a.ndf_ptr + (size_t)lv * (G + 1);
+      return OpRows<double>{a.nd_Z, a.nd_zoff, a.nd_zld, a.ndf_s, a.ndf_r0, a.ndf_r1, pp[cta], pp[cta + 1],
+                            0, 0, 0, pk, hint};
+    }
+    const int32_t *pp = a.ndb_ptr + (size_t)(lv - a.nd_H) * (G + 1);
+    return OpRows<double>{a.nd_Lt, a.nd_ltoff, a.nd_ltld, a.ndb_s, a.ndb_r0, a.ndb_r1, pp[cta], pp[cta + 1],
+                          0, 0, 0, pk, hint};
+  };
+  const int nd_levels = ND ? a.nd_H + max(a.nd_D - 1, 0) : 0;
+  // the first coarse phase's rows (prefetched before the barrier that precedes it)
+  auto coarse_first = [&]() {
+    if constexpr (ND) return nd_op(0);
+    else return opS;
+  };
 
   // stage x_s[k] = f(k) (k < n), zero-padded to ld
   auto stage = [&](int n, int ld, auto f) {
@@ -592,6 +629,17 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   double *yv_old = a.yv0, *yv_new = a.yv1;  // B_D^T r of the current / next iterate
   unsigned long long *tsub = nullptr;  // sub-phase timestamps of the traced iteration (or null)
   auto tsp = [&](int k) { return tsub ? tsub + 3 * k : nullptr; };
+  // a barrier that gave up ends the launch: first the chunks this CTA still has in
+  // flight into its shared memory are waited for (bounded), then every CTA returns
+  auto sync = [&](unsigned long long *tr) {
+    if (grid_sync(a.bar, G, target, a.spin_max, tr)) return true;
+    if (threadIdx.x == 0)
+      for (unsigned long long g = ring.consumed; g < ring.issued; ++g)
+        mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
+    ring.consumed = ring.issued;
+    __syncthreads();
+    return false;
+  };
   // H phase: [F; Psi^T] u_s -> zb, tpi, with a staging functor for u_s
   auto h_phase = [&](auto stage_u) -> bool {
     return stream_phase<4>(ring, opH, cur, xs, ybuf, errflag, [&](int s, int r0, int r1) { stage_u(s, r0, r1); },
@@ -614,8 +662,62 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       a.cc[k] = c;
     }
   };
+  // the child updates gathered into front position i of node p
+  auto nd_gather = [&](int p, int i) {
+    const int32_t *src = a.nd_src + a.nd_srcoff[p] + (int64_t)i * a.nd_cw;
+    double v = 0.0;
+    for (int w = 0; w < a.nd_cw; ++w) {
+      const int32_t u = src[w];
+      if (u >= 0) v += ldcg(a.nd_u + u);
+    }
+    return v;
+  };
+  // nested-dissection solve q = S_c^{-1} c: one phase per level, a grid barrier between
+  // levels; the next level's rows are issued before the barrier
+  auto coarse_solve_nd = [&]() -> bool {
+    double *xd = reinterpret_cast<double *>(smem_raw);
+    double *yd = reinterpret_cast<double *>(ybuf_raw);
+    for (int lv = 0; lv < nd_levels; ++lv) {
+      const OpRows<double> op = nd_op(lv);
+      bool ok;
+      if (lv < a.nd_H) {
+        ok = stream_phase<4>(
+            ring, op, cur, xd, yd, errflag,
+            [&](int p, int, int) {
+              const int nk = a.nd_nk[p], ld = a.nd_zld[p], k0 = a.nd_k0[p];
+              for (int k = threadIdx.x; k < ld; k += nthr)
+                xd[k] = k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0;
+            },
+            [&](int p, int r, double v, double2 pv) {
+              const int nk = a.nd_nk[p];
+              if (r < nk) a.q[a.nd_k0[p] + r] = v;
+              else a.nd_u[a.nd_uoff[p] + (r - nk)] = pv.x - v;
+            },
+            [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); },
+            lv == 0 ? tsp(1) : nullptr);
+      } else {
+        ok = stream_phase<4>(
+            ring, op, cur, xd, yd, errflag,
+            [&](int p, int, int) {
+              const int ns = a.nd_ns[p], ld = a.nd_ltld[p];
+              const int32_t *si = a.nd_sidx + a.nd_soff[p];
+              for (int k = threadIdx.x; k < ld; k += nthr) xd[k] = k < ns ? ldcg(a.q + si[k]) : 0.0;
+            },
+            [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; },
+            [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); });
+      }
+      if (!ok) return false;
+      if (lv + 1 < nd_levels) {
+        cur = prefetch(ring, nd_op(lv + 1));
+        if (!sync(nullptr)) return false;
+      }
+    }
+    return true;
+  };
   auto coarse_solve = [&]() -> bool {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (ND) {
+      return coarse_solve_nd();
+    } else if constexpr (sizeof(T) == 8) {
       return stream_phase<1>(ring, opS, cur, ccs, ybuf, errflag,
                              [&](int, int, int) {
                                for (int k = threadIdx.x; k < a.ldc; k += nthr)
@@ -695,17 +797,6 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         },
         [&](int s, int r, double v, double2) { a.zp[a.bofs[s] + r] = v; }, NoPre(), tsp(3));
   };
-  // a barrier that gave up ends the launch: first the chunks this CTA still has in
-  // flight into its shared memory are waited for (bounded), then every CTA returns
-  auto sync = [&](unsigned long long *tr) {
-    if (grid_sync(a.bar, G, target, a.spin_max, tr)) return true;
-    if (threadIdx.x == 0)
-      for (unsigned long long g = ring.consumed; g < ring.issued; ++g)
-        mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
-    ring.consumed = ring.issued;
-    __syncthreads();
-    return false;
-  };
   // uz = B^T z on this CTA's chunk of interface copies (z recomputed on the fly)
   const int64_t qb = a.nbt * cta / G, qe = a.nbt * (cta + 1) / G;
   // uz = B^T B_D zp on this CTA's chunk (preconditioned runs), by the neighbour lists
@@ -754,7 +845,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         stage(a.nb[s], a.ldb[s], [&](int k) { return ldcg(a.kg + kb + k); });
       }))
     return;
-  Cursor curS = prefetch(ring, opS);
+  Cursor curS = prefetch(ring, coarse_first());
   if (!sync(nullptr)) return;
   coarse_rhs(true);
   if (!sync(nullptr)) return;
@@ -826,7 +917,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
             }
           }))
         return;
-      curS = prefetch(ring, opS);
+      curS = prefetch(ring, coarse_first());
       if (!sync(tr ? tr + 0 : nullptr)) return;
       // ---------------- P2, P3: coarse
       coarse_rhs(false);
@@ -903,7 +994,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         }
       }))
     return;
-  curS = prefetch(ring, opS);
+  curS = prefetch(ring, coarse_first());
   if (!sync(nullptr)) return;
   coarse_rhs(true);
   if (!sync(nullptr)) return;

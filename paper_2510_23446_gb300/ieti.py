@@ -22,6 +22,7 @@ PREC = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "dirichlet": 1, "dirichlet_mult": 2, "dirichlet_stiff": 3}
 FACTOR = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "bf16": 5}
 REFACTOR = {"every": 0, "step": 1, "never": 2}
+COARSE = {"auto": 0, "dense": 1, "nd": 2}
 ERRORS = {-1: "INVALID_ARG", -2: "NONCONFORMING", -3: "NOT_SPD", -4: "CG_NOT_CONVERGED", -5: "CUDA",
           -6: "OOM", -7: "NO_DEVICE", -8: "TOO_LARGE", -9: "TIMEOUT"}
 
@@ -42,7 +43,8 @@ class ieti_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("profile", C.c_int32), ("l2_persist", C.c_int32),
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
                 ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
-                ("graph", C.c_int32), ("wait_limit", C.c_int32)]
+                ("graph", C.c_int32), ("wait_limit", C.c_int32), ("coarse", C.c_int32),
+                ("coarse_leaf", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -76,7 +78,9 @@ class ieti_info(C.Structure):
                 ("pcg_grid", C.c_int32), ("pcg_stages", C.c_int32), ("pcg_stage_bytes", C.c_int32),
                 ("pcg_psi_partition", C.c_int32),
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
-                ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32)]
+                ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32), ("coarse_mode", C.c_int32),
+                ("coarse_nodes", C.c_int32), ("coarse_levels", C.c_int32), ("coarse_bytes", C.c_double),
+                ("t_coarse_ms", C.c_double)]
 
 
 _ctx = C.c_void_p
@@ -96,6 +100,7 @@ lib.ieti_step.argtypes = [_ctx, C.c_void_p, C.c_int32, C.POINTER(ieti_stats)]
 lib.ieti_solution.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
+lib.ieti_coarse_tree.argtypes = [_ctx, C.POINTER(C.c_int32), C.POINTER(C.c_int64)] + [C.c_void_p] * 6
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
@@ -111,7 +116,7 @@ EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", 
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
             "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32",
-            "ieti_quad_points", "ieti_load_vector_points"]
+            "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree"]
 
 
 class IetiError(RuntimeError):
@@ -137,7 +142,7 @@ class Solver:
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
-                 graph=1, wait_limit=0):
+                 graph=1, wait_limit=0, coarse="auto", coarse_leaf=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -182,6 +187,8 @@ class Solver:
         op.autotune = int(autotune)
         op.graph = int(graph)
         op.wait_limit = int(wait_limit)
+        op.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
+        op.coarse_leaf = int(coarse_leaf)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
         self.options = op
@@ -245,6 +252,21 @@ class Solver:
         self._check(lib.ieti_patch_csr(self.ctx, s, which, None, None, ptr.ctypes.data,
                                        col.ctypes.data, val.ctypes.data))
         return ptr, col, val
+
+    def coarse_tree(self):
+        """ieti_coarse_tree: the nested-dissection tree of the coarse problem."""
+        nn = C.c_int32()
+        ns = C.c_int64()
+        self._check(lib.ieti_coarse_tree(self.ctx, C.byref(nn), C.byref(ns), None, None, None, None, None, None))
+        elim = np.zeros(self.n, dtype=np.int32)
+        k0 = np.zeros(nn.value, dtype=np.int32)
+        nk = np.zeros(nn.value, dtype=np.int32)
+        parent = np.zeros(nn.value, dtype=np.int32)
+        s_off = np.zeros(nn.value + 1, dtype=np.int64)
+        s_idx = np.zeros(max(ns.value, 1), dtype=np.int32)
+        self._check(lib.ieti_coarse_tree(self.ctx, C.byref(nn), C.byref(ns), elim.ctypes.data, k0.ctypes.data,
+                                         nk.ctypes.data, parent.ctypes.data, s_off.ctypes.data, s_idx.ctypes.data))
+        return dict(elim_pos=elim, k0=k0, nk=nk, parent=parent, s_off=s_off, s_idx=s_idx[:ns.value])
 
     def kernel_stats(self, reset=False):
         arr = (ieti_kernel_stat * len(KERNEL_CLASSES))()
