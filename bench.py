@@ -1,7 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 tree-cotree IETI-DP solver: implicit-Euler time steps/s and
-PCG iterations/s on the 64-patch curved p=2 workload (4x4x4 patches of 8^3 elements,
-inner cube sigma = 1e2, coil J0 = 1e2, dt = 1e-3), mixed+batched vs FP64.
+PCG iterations/s, mixed+batched vs FP64, on the 343-patch workload of uneven patches
+(7x7x7 curved patches, per-slab elements in {4..12} and degrees in {2,3}, random
+conductor/air patches with sigma = 1e3, dt = 1e-3; --workload picks another one).
 
 One bench "step" = one implicit-Euler step of Eq. (11) through the C ABI: RHS,
 interior condensation, dual-primal PCG, recovery, FP64 defect correction of the
@@ -26,18 +27,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time steps/s and CG its/s, mixed+batched vs FP64 on GB300 at rel. L2 err ≤1e-8"
-WORKLOAD = ("c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
-            "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3")
 OUTER_TOL = 1e-11
-HORIZON = 50   # the workload's run: 50 implicit-Euler steps from a^0 = 0, replayed for K > 50
+# workloads: description, generator, the run's length (steps from a^0 = 0, replayed for
+# longer timed runs), the outer stop both paths share
+WORKLOADS = {
+    "c4": dict(desc="c4: unit cube, 7x7x7 curved patches (+-5% interior control points), per-slab elements "
+                    "uniform in {4..12} and per-slab degrees in {2,3} (local sizes ~400..9000), conductor or air "
+                    "per patch with probability 1/2 (sigma=1e3), nu=1, coil J0=1, dt=1e-3",
+               gen=("c4", {}), horizon=100, outer=OUTER_TOL),
+    "c3": dict(desc="c3: unit cube, 8x8x8 curved patches, p=2, 6^3 elements per patch, sigma log-uniform in "
+                    "[1,1e4] per patch within radius 0.35, nu uniform in [0.5,2] per patch, coil J0=1, dt=1e-3",
+               gen=("c3", {}), horizon=100, outer=1e-12),
+    "c2": dict(desc="c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
+                    "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3",
+               gen=("c2", {}), horizon=50, outer=OUTER_TOL),
+}
+HEADLINE = "c4"
 # each path with its fastest inner PCG tolerance for the common outer stop (measured on
-# this workload); both start every step from the time-extrapolated iterate
+# these workloads); both start every step from the time-extrapolated iterate
 OPTS = {
-    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=20,
+    "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=30,
                   factor="tf32x3", predictor=2, autotune=1, l2_persist=2),
-    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-11, outer_tol=OUTER_TOL, max_sweeps=20,
+    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-11, outer_tol=OUTER_TOL, max_sweeps=30,
                  predictor=2, autotune=1, l2_persist=2),
 }
+
+
+def workload_problem(key):
+    from workloads import make_problem
+    name, kw = WORKLOADS[key]["gen"]
+    return make_problem(name, **kw)
 
 
 def parse():
@@ -52,8 +71,9 @@ def parse():
     ap.add_argument("--nl-steps", type=int, default=4, help="timed steps of the nonlinear workload")
     ap.add_argument("--no-paper-case", action="store_true", help="skip the paper's two-subdomain timed run")
     ap.add_argument("--no-ablation", action="store_true", help="skip the factor-arithmetic ablation")
-    ap.add_argument("--configs", default="c3", help="comma-separated extra full-size workloads (c3, c5_4, c5_6; "
-                                                    "'' for none), each mixed vs FP64 over a few steps")
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS), help="the headline workload")
+    ap.add_argument("--configs", default="c3,c2", help="comma-separated extra full-size workloads (c2, c3, c4, "
+                                                       "c5_4, c5_6; '' for none), each mixed vs FP64 over a few steps")
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps per extra workload and path")
     ap.add_argument("--profile-step", action="store_true",
                     help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
@@ -71,8 +91,31 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# nominal dense rates relative to bf16 (2.25 PFLOP/s): tf32 1.1 PFLOP/s, fp64 1.25 TFLOP/s
-NOMINAL_RATIO = {"tf32": 1.1 / 2.25, "fp64": 1.25e-3 / 2.25}
+def matmul_peaks(torch, dev):
+    """Dense matmul rates of this GPU in TF32 (FP32 operands, TF32 tensor cores) and in
+    FP64 (torch.matmul = cuBLAS), TFLOP/s: the best of a few CUDA-event-timed products
+    after one untimed; the denominators of the factorization rooflines."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, n, reps in (("tf32", torch.float32, 8192, 8), ("fp64", torch.float64, 4096, 3)):
+        torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+        a = torch.randn(n, n, device=f"cuda:{dev}", dtype=dt)
+        b = torch.randn(n, n, device=f"cuda:{dev}", dtype=dt)
+        torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        out[name] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
 
 
 def ncu_traffic(kernel_file):
@@ -143,31 +186,51 @@ def _blas_threads():
     return os.cpu_count()
 
 
-def cpu_baseline(prob, budget_s, tol=1e-10):
-    """The oracle's dual-primal step (as it stands) on the same workload, on the host
-    cores: setup first (not part of the rate), then as many whole time steps as fit
-    in the budget (at least one)."""
+def cpu_sample_problem(key):
+    """The bounded CPU sample of a workload: its central 2x2x2 block of patches as a
+    problem of its own (same slabs, control nets, materials, coil and time step)."""
+    from workloads import sub_problem
+    prob = workload_problem(key)
+    if prob.n_patches <= 8:
+        return prob, prob
+    lo = [max(0, p // 2 - 1) for p in prob.P]
+    return prob, sub_problem(prob, lo, [l + 2 for l in lo], name=f"{prob.name}_center8")
+
+
+def cpu_baseline(key, budget_s, max_steps=20, tol=1e-10):
+    """The oracle's dual-primal step (as it stands) on the host cores, on a bounded
+    sample of the workload: the central 2x2x2 patches (the whole problem when it has
+    no more); setup first (not part of the rate), then as many whole time steps from
+    a^0 = 0 as fit in the budget (at least one).  The rate is scaled to the whole
+    workload by its DOF count (the work of a step grows with the DOFs at a similar
+    PCG iteration count)."""
     from oracle.stepping import OracleProblem
     from oracle.ietidp import PRECOND_STIFF, local_rhs, gather_global
     import numpy as np
+    full, prob = cpu_sample_problem(key)
     t0 = time.perf_counter()
     op = OracleProblem(prob)
     I = op.ietidp(PRECOND_STIFF)
     t_setup = time.perf_counter() - t0
+    n_sample = op.asm.lat.n_edges
+    from oracle.lattice import Lattice
+    n_full = Lattice(full).n_edges
+    scale = n_sample / n_full
     a = np.zeros(op.asm.lat.n_edges)
     steps, its, t = 0, 0, 0.0
-    while steps == 0 or t < budget_s:
+    while steps == 0 or (t < budget_s and steps < max_steps):
         t1 = time.perf_counter()
         a_loc, lam, it, res = I.solve(local_rhs(op.dec, a, op.asm.j_global), tol)
         a = gather_global(op.dec, a_loc)
         t += time.perf_counter() - t1
         steps += 1
         its += it
-        if steps >= 20:
-            break
-    return {"value": steps / t, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
+    what = ("the whole workload" if prob is full else
+            f"its central 2x2x2 patches ({n_sample} of {n_full} DOFs), rate scaled by that DOF ratio")
+    return {"value": scale * steps / t, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
             "cg_its_per_s": its / t, "setup_s": t_setup, "steps": steps, "warmup": 0, "seconds": t,
-            "sample": f"{steps} whole time step(s) of the c2 workload (oracle IETI-DP, dense LAPACK local "
+            "sample_steps_per_s": steps / t, "dof_scale": scale,
+            "sample": f"{steps} whole time step(s) from a^0 = 0 of {what} (oracle IETI-DP, dense LAPACK local "
                       f"solves, PCG tol {tol}, stiffness-scaled Dirichlet); oracle setup {t_setup:.1f} s excluded"}
 
 
@@ -176,20 +239,19 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from workloads import make_problem
-    prob = make_problem("c2")
-    cb = cpu_baseline(prob, budget_s=args.cpu_seconds)
+    cb = cpu_baseline(args.workload, budget_s=args.cpu_seconds, max_steps=max(1, args.steps))
+    W = WORKLOADS[args.workload]
     # the oracle's steps are ~10^4 times slower than the GPU arm's: it times the whole
     # steps that fit its budget (from a^0 = 0, no warm-up) and reports those counts
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
             "n_gpus": args.gpus, "steps": cb["steps"], "warmup": cb["warmup"],
             "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": "oracle IETI-DP (CPU, FP64)",
-                       "steps": f"the first {cb['steps']} step(s) of the run from a^0 = 0 (dt = 1e-3), "
-                                f"no warm-up; --steps {args.steps} --warmup {args.warmup} asked for more than "
-                                f"the {args.cpu_seconds:.0f} s CPU budget holds" if cb["steps"] < args.steps
-                                else f"the first {cb['steps']} steps of the run from a^0 = 0, no warm-up"},
+            "config": {"workload": W["desc"], "solver": "oracle IETI-DP (CPU, FP64)",
+                       "sample": cb["sample"],
+                       "steps": f"the first {cb['steps']} step(s) of the run from a^0 = 0, no warm-up"
+                                + (f"; --steps {args.steps} --warmup {args.warmup} asked for more than the "
+                                   f"{args.cpu_seconds:.0f} s CPU budget holds" if cb["steps"] < args.steps else "")},
             "cg_its_per_s": cb["cg_its_per_s"],
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -197,13 +259,13 @@ def run_reference(args):
     return 0
 
 
-def _steps(S, torch, jd, zero, K, flush_buf, ev=None):
-    """K steps of the 50-step run (replayed from a^0 = 0 outside the timed events), the
+def _steps(S, torch, jd, zero, K, flush_buf, horizon, ev=None):
+    """K steps of the workload's run (replayed from a^0 = 0 outside the timed events), the
     L2 flushed before every step; returns (PCG iterations, kernel launches, sweeps, last stats)."""
     its = launches = sweeps = 0
     st = None
     for k in range(K):
-        if k and k % HORIZON == 0:
+        if k and k % horizon == 0:
             S.set_state(zero)
         flush_buf.zero_()
         if ev:
@@ -217,15 +279,18 @@ def _steps(S, torch, jd, zero, K, flush_buf, ev=None):
     return its, launches, sweeps, st
 
 
-def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
+def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer):
     """The timed run (the library as a user runs it: each step's sweep loop as one CUDA
     graph), then the same K steps on a second context with per-launch CUDA events for
     the kernel-class times and the phase trace (those need the host loop).  Both
     contexts share the autotuner's choice through a cache file."""
     tmpdir = tempfile.mkdtemp(prefix="ieti_bench_")
     cache = os.path.join(tmpdir, "schedule.txt")
-    S = ieti.Solver.from_problem(prob, device=dev, stream=stream, tune_cache=cache, **OPTS[mode])
+    opts = dict(OPTS[mode], outer_tol=outer)
+    t0 = time.perf_counter()
+    S = ieti.Solver.from_problem(prob, device=dev, stream=stream, tune_cache=cache, **opts)
     t_setup = S.info()
+    t_setup["setup_wall_s"] = time.perf_counter() - t0
     j = S.load_vector(prob.coil)
     jd = torch.from_numpy(j).to(f"cuda:{dev}")
     zero = torch.zeros(S.n, dtype=torch.float64, device=f"cuda:{dev}")
@@ -236,19 +301,19 @@ def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     if clocks:
         clocks.start()
-    its, launches, sweeps, st = _steps(S, torch, jd, zero, K, flush_buf, ev)
+    its, launches, sweeps, st = _steps(S, torch, jd, zero, K, flush_buf, horizon, ev)
     torch.cuda.synchronize(dev)
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
     state = S.solution()
     # profiled pass
-    P = ieti.Solver.from_problem(prob, device=dev, stream=stream, profile=1, tune_cache=cache, **OPTS[mode])
+    P = ieti.Solver.from_problem(prob, device=dev, stream=stream, profile=1, tune_cache=cache, **opts)
     for _ in range(W):
         P.step(jd)
     P.set_state(zero)
     P.kernel_stats(reset=True)
     P.pcg_phase_times(reset=True)
-    p_its, _, _, _ = _steps(P, torch, jd, zero, K, flush_buf)
+    p_its, _, _, _ = _steps(P, torch, jd, zero, K, flush_buf, horizon)
     torch.cuda.synchronize(dev)
     kst = P.kernel_stats(reset=True)
     phases = P.pcg_phase_times(reset=True)
@@ -421,8 +486,7 @@ def factor_ablation_leg(ieti, torch, prob, dev, stream, n_steps=10):
 # workload's sigma contrast (1 .. 1e4) needs the outer stop at 1e-12 for the two paths
 # to agree to 1e-8
 EXTRA = {
-    "c3": ("c3: 8x8x8 curved patches, p=2, 6^3 elements per patch, sigma log-uniform in [1,1e4] per patch "
-           "within radius 0.35, nu in [0.5,2] per patch, dt=1e-3", "c3", {}, 1e-12),
+    **{k: (v["desc"], v["gen"][0], v["gen"][1], v["outer"]) for k, v in WORKLOADS.items()},
     "c5_4": ("c5 linear, 4x4x4 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
              "dt=5e-4", "c5", dict(patches_per_dir=4, nonlinear=False), OUTER_TOL),
     "c5_6": ("c5 linear, 6x6x6 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
@@ -459,7 +523,9 @@ def config_leg(ieti, torch, key, dev, stream, flush_buf, K, W=2):
         ms = sum(a.elapsed_time(b) for a, b in ev)
         out[mode] = {"value": 1e3 * K / ms, "unit": "steps/s", "ms_per_step": ms / K, "cg_its_per_step": its / K,
                      "sweeps_per_step": sweeps / K, "cg_its_per_s": 1e3 * its / ms, "setup_s": t_setup,
-                     "t_factor_ms": inf["t_factor_ms"], "bytes_per_pcg_iteration": inf["bytes_iter"]}
+                     "t_factor_ms": inf["t_factor_ms"], "bytes_per_pcg_iteration": inf["bytes_iter"],
+                     "coarse": {1: "dense inverse", 2: "nested dissection"}.get(inf["coarse_mode"], "none"),
+                     "coarse_levels": inf["coarse_levels"], "coarse_bytes": inf["coarse_bytes"]}
         states[mode] = S.solution().copy()
         info = inf
         S.close()
@@ -534,12 +600,12 @@ def run_ours(args):
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    from workloads import make_problem
-    prob = make_problem("c2")
+    WL = WORKLOADS[args.workload]
+    prob = workload_problem(args.workload)
     # the CPU oracle leg runs before the library touches the GPU
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(prob, budget_s=args.cpu_seconds)
+        cb = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     from paper_2510_23446_gb300.build import build
     if rank == 0:
         build()
@@ -551,12 +617,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev).cuda_stream
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     K, W = args.steps, max(3, args.warmup)
+    horizon, outer = WL["horizon"], WL["outer"]
+    mm_peaks = matmul_peaks(torch, dev)
     results = {}
     for mode in ("fp64", "mixed"):
         if world > 1:
             dist.barrier()
         clocks = Clocks(dev) if mode == "mixed" else None
-        S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks)
+        S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer)
         results[mode] = (S, r)
     # end-to-end through the public API with host buffers (pinned), mixed path: the same
     # steps as the timed device run (same resets, same L2 flush between steps, both
@@ -567,7 +635,7 @@ def run_ours(args):
     zero = torch.zeros(S.n, dtype=torch.float64, device=f"cuda:{dev}")
     e2e_s = 0.0
     for k in range(K):
-        if k % HORIZON == 0:
+        if k % horizon == 0:
             S.set_state(zero)
         flush_buf.zero_()
         torch.cuda.synchronize(dev)
@@ -593,10 +661,10 @@ def run_ours(args):
     step_ms = tot["mixed"] * 1e3 / K
     info = im
     # factorization (setup): the tensor-core trailing update of the mixed path against
-    # the TF32 peak, the FP64 factorization against the FP64 peak (both derived from the
-    # measured bf16 GEMM rate by the nominal ratios)
-    tf32_peak = pk["bf16_tflops"] * NOMINAL_RATIO["tf32"]
-    fp64_peak = pk["bf16_tflops"] * NOMINAL_RATIO["fp64"]
+    # the TF32 matmul rate, the FP64 factorization against the FP64 matmul rate (both
+    # measured in this run)
+    tf32_peak = mm_peaks["tf32"]
+    fp64_peak = mm_peaks["fp64"]
     tc_tfs = im["tc_flops"] / max(im["tc_ms"], 1e-9) / 1e9
     factor = {
         "mixed": {"factor": OPTS["mixed"]["factor"], "t_factor_ms": im["t_factor_ms"],
@@ -607,12 +675,12 @@ def run_ours(args):
                   "tc_useful_tflops_per_s": im["tc_useful_flops"] / max(im["tc_ms"], 1e-9) / 1e9,
                   "roofline": {"bound": "tensor", "achieved": tc_tfs, "peak": tf32_peak, "unit": "TFLOP/s",
                                "frac": tc_tfs / tf32_peak,
-                               "peak_source": f"{pk_src} bf16_tflops x nominal tf32/bf16 ratio 1.1/2.25"}},
+                               "peak_source": "torch.matmul FP32 with TF32 tensor cores, 8192^3, measured in this run"}},
         "fp64": {"factor": "fp64", "t_factor_ms": iff["t_factor_ms"], "useful_tflop": iff["factor_flops"] / 1e12,
                  "useful_tflops_per_s": iff["factor_flops"] / max(iff["t_factor_ms"], 1e-9) / 1e9,
                  "roofline": {"bound": "fp64", "peak": fp64_peak, "unit": "TFLOP/s",
                               "frac": iff["factor_flops"] / max(iff["t_factor_ms"], 1e-9) / 1e9 / fp64_peak,
-                              "peak_source": f"{pk_src} bf16_tflops x nominal fp64/bf16 ratio 1.25e-3/2.25"}},
+                              "peak_source": "torch.matmul FP64, 4096^3, measured in this run"}},
     }
     line = {
         "metric": METRIC,
@@ -627,15 +695,18 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_dofs": info["n_dofs"], "n_free": info["n_free"],
+        "config": {"workload": WL["desc"], "n_dofs": info["n_dofs"], "n_free": info["n_free"],
                    "n_lambda": info["n_lambda"], "n_coarse": info["n_coarse"],
                    "precond": "dirichlet_stiff", "inner_cg_tol": OPTS["mixed"]["cg_tol"],
                    "mixed_factor": OPTS["mixed"]["factor"],
                    "fp64_inner_cg_tol": OPTS["fp64"]["cg_tol"], "predictor": "3 a^l - 3 a^(l-1) + a^(l-2) (both paths)",
-                   "outer_tol": OUTER_TOL, "l2": "flushed between timed steps (256 MiB write)",
+                   "outer_tol": outer, "l2": "flushed between timed steps (256 MiB write)",
+                   "coarse_solve": {m: {1: "dense inverse", 2: "nested dissection"}.get(results[m][0].info()["coarse_mode"],
+                                                                                         "none") for m in results},
+                   "coarse_levels": im["coarse_levels"], "n_patches": prob.n_patches,
                    "l2_operator_policy": "per-iteration operators loaded with a fractional evict-last hint "
                                          "(returned to normal priority at the end of every step)",
-                   "steps": f"the 50-step run from a^0 = 0 (dt = 1e-3), replayed; state reset untimed",
+                   "steps": f"the {horizon}-step run from a^0 = 0 (dt = {prob.dt:g}), replayed; state reset untimed",
                    "step_loop": "one CUDA graph per step (device-side while node over the sweeps)"
                                 if rm["step_graph"] else "host loop",
                    "kernel_times": "kernel classes, roofline and phase trace from a second pass of the same steps "
@@ -656,8 +727,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * S.n},
         "gpu_launches": rm["launches"],
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic("k_ddsolve_c2_mixed.md"),
-                     "traffic_source": "profiles/k_ddsolve_c2_mixed.md (one ncu launch of ~19 PCG iterations)",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(f"k_ddsolve_{args.workload}_mixed.md"),
+                     "traffic_source": f"DRAM bytes per launch from the committed ncu capture "
+                                       f"profiles/k_ddsolve_{args.workload}_mixed.md (not measured in this run; "
+                                       f"null when no capture of this kernel and workload is committed)",
                      "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms,
                      "share_of_step": ks[dom]["total_ms"] / (tot["mixed"] * 1e3),
                      "peak_source": f"{pk_src} hbm_gbs (copy)"},
@@ -689,8 +762,8 @@ def run_ours(args):
             results[m][0].close()
         results = {}
         torch.cuda.empty_cache()
-        line["factor_ablation"] = factor_ablation_leg(ieti, torch, prob, dev, stream)
-    extra = [c for c in args.configs.split(",") if c] if world == 1 else []
+        line["factor_ablation"] = factor_ablation_leg(ieti, torch, workload_problem("c2"), dev, stream)
+    extra = [c for c in args.configs.split(",") if c and c != args.workload] if world == 1 else []
     if extra:
         for m in results:
             results[m][0].close()
@@ -713,14 +786,14 @@ def run_ours(args):
 def run_profile_step(args):
     """Set up the mixed path on the bench workload and run a few steps (for ncu)."""
     import torch
-    from workloads import make_problem
     from paper_2510_23446_gb300.build import build
     build()
     from paper_2510_23446_gb300 import ieti
-    prob = make_problem("c2")
+    prob = workload_problem(args.workload)
     # host loop (graph=0): ncu lists the kernels launched from the host, not the kernel
     # nodes inside the step graph's while-loop body
-    S = ieti.Solver.from_problem(prob, device=0, tune_cache=args.tune_cache, graph=0, **OPTS["mixed"])
+    S = ieti.Solver.from_problem(prob, device=0, tune_cache=args.tune_cache, graph=0,
+                                 **dict(OPTS["mixed"], outer_tol=WORKLOADS[args.workload]["outer"]))
     jd = torch.from_numpy(S.load_vector(prob.coil)).cuda()
     for _ in range(max(1, args.warmup) + 2):
         st = S.step(jd)

@@ -319,6 +319,40 @@ __device__ __noinline__ void chunk_rows_g(const T *A, int ld, int cn, const T *x
   }
 }
 
+// y[r] = A_r . x for a chunk of fewer than 16 long rows (more than 32 16-byte units
+// each): every thread of the CTA takes a stride of the units of up to 4 rows at a time
+// (a warp reads 512 contiguous bytes of a row: no bank conflicts), partial sums are
+// reduced over the warp and then over the warps through part[] (32 entries).
+template <class T>
+__device__ __noinline__ void chunk_rows_wide(const T *A, int ld, int cn, const T *xs, T *y, T *part) {
+  using V = typename V16<T>::t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nv = ld / V16<T>::n;
+  const V *x = reinterpret_cast<const V *>(xs);
+  for (int r0 = 0; r0 < cn; r0 += 4) {
+    const int nr = min(4, cn - r0);
+    T acc[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      const V xv = x[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < nr) acc[i] = fma16(reinterpret_cast<const V *>(A + (int64_t)(r0 + i) * ld)[k], xv, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T v = warp_red_t(acc[i]);
+      if (lane == 0) part[warp * 4 + i] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nr) {
+      T t = 0;
+      for (int w = 0; w < nw; ++w) t += part[w * 4 + threadIdx.x];
+      y[r0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // TMA ring.  The operator rows a CTA multiplies in a phase are fixed by the static
 // partition, independent of the iteration's vectors, so they are streamed HBM ->
@@ -455,15 +489,17 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
       const int cn = min(rpc, r1 - r0 - c0), base_r = r0 + c0;
       // row kernel per row length and operator precision (measured on the c2
       // workload): short rows one per lane; long FP64 rows 8 lanes per row; long
-      // FP32 rows, and chunks of fewer than 16 rows, RW rows per warp
+      // FP32 rows RW rows per warp; chunks of fewer than 16 long rows (wide patches:
+      // a stage holds a few rows) spread over the whole CTA
       const int nv = ld / V16<E>::n;
-      const int split = nv <= 32 ? 1 : (sizeof(E) == 8 && cn >= 16 ? 8 : 0);
+      const int split = nv <= 32 ? 1 : (cn < 16 ? 2 : (sizeof(E) == 8 ? 8 : 0));
       if (split) {
         // row results into y (two buffers: the epilogues of the previous chunk may
         // still read the other one), then one thread per row
         E *yc = y + (ring.consumed & 1ull) * RPC_MAX;
         if (split == 1) chunk_rows_g<E, 1>(buf, ld, cn, xs, yc);
-        else chunk_rows_g<E, 8>(buf, ld, cn, xs, yc);
+        else if (split == 8) chunk_rows_g<E, 8>(buf, ld, cn, xs, yc);
+        else chunk_rows_wide<E>(buf, ld, cn, xs, yc, yc + RPC_MAX / 2);
         __syncthreads();  // every warp is done with this stage; yc is complete
         issue_next(ring, op, cur);
         for (int r = threadIdx.x; r < cn; r += blockDim.x) out(s, base_r + r, (double)yc[r], pre(s, base_r + r));

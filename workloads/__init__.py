@@ -6,4 +6,4 @@ and the coil-source parameters.  Everything that involves B-splines, assembly,
 gauging or solving lives separately in ``oracle/`` (the CPU checker) and in the
 CUDA library.
 """
-from .configs import Problem, make_problem, CONFIGS, small_problem  # noqa: F401
+from .configs import Problem, make_problem, CONFIGS, small_problem, sub_problem  # noqa: F401

@@ -286,6 +286,32 @@ def small_problem(P=(2, 2, 1), n_el=((2, 3), (3, 2), (2,)), degree=((1, 2), (2, 
                          perturb=perturb, coil=default_coil(J0), seed=seed, reluctivity=reluctivity)
 
 
+def sub_problem(prob: Problem, lo, hi, name=None) -> Problem:
+    """The patches [lo_d, hi_d) of a problem's patch grid as a problem of its own (same
+    slabs, knot vectors, control nets, materials, coil and time step; its outer faces
+    become the Dirichlet boundary).  Bookkeeping only: used to take a bounded sample
+    of a workload's per-patch work."""
+    lo = [int(x) for x in lo]
+    hi = [int(x) for x in hi]
+    P = tuple(hi[d] - lo[d] for d in range(3))
+    n_el = [np.asarray(prob.n_el[d][lo[d]:hi[d]], dtype=np.int32) for d in range(3)]
+    degree = [np.asarray(prob.degree[d][lo[d]:hi[d]], dtype=np.int32) for d in range(3)]
+    knots = [np.concatenate([prob.knot_vector(d, a) for a in range(lo[d], hi[d])]) for d in range(3)]
+    c_off, e_off = prob.ctrl_offsets(), prob.el_offsets()
+    ctrl, sig, nu = [], [], []
+    for c in range(lo[2], hi[2]):
+        for b in range(lo[1], hi[1]):
+            for a in range(lo[0], hi[0]):
+                s = a + prob.P[0] * (b + prob.P[1] * c)
+                ctrl.append(prob.ctrl[c_off[s]:c_off[s + 1]])
+                sig.append(prob.sigma_el[e_off[s]:e_off[s + 1]])
+                nu.append(prob.nu_el[e_off[s]:e_off[s + 1]])
+    return Problem(name=name or f"{prob.name}_sub", P=P, n_el=n_el, degree=degree, knots=knots,
+                   ctrl=np.concatenate(ctrl), sigma_el=np.concatenate(sig), nu_el=np.concatenate(nu),
+                   dt=prob.dt, n_steps=prob.n_steps, cg_tol=prob.cg_tol, coil=dict(prob.coil), seed=prob.seed,
+                   reluctivity=prob.reluctivity)
+
+
 CONFIGS = {
     "c1": config1,
     "c2": config2,
