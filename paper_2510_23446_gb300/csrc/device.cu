@@ -3580,6 +3580,12 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
       d->launches_setup++;
     }
     rc = e0 == cudaSuccess ? coarse_nd_factor(d, *tree, Sc, err) : IETI_ERR_CUDA;
+    if (rc == IETI_OK && d->mixed) {
+      // the mixed path streams the blocks as (hi, lo) FP32 pairs (in place: same 8 bytes)
+      const int64_t n = d->nd_z_elems + d->nd_lt_elems;
+      k_split_pairs<<<grid_for(n, 256), 256, 0, d->stream>>>(n, d->nd_Z, (float2 *)d->nd_Z);
+      d->launches_setup++;
+    }
     if (e0 != cudaSuccess) err = std::string("coarse assembly failed: ") + cudaGetErrorString(e0);
     cudaStreamSynchronize(d->stream);
     cudaFree(Sc);

@@ -353,6 +353,81 @@ __device__ __noinline__ void chunk_rows_wide(const T *A, int ld, int cn, const T
   }
 }
 
+// Double-FP32 rows: entries stored as (hi, lo) FP32 pairs of FP64 values, dotted with
+// staged (hi, lo) pairs by exact FP32 products (TwoProd by FMA) accumulated with TwoSum;
+// the cross terms hi*lo + lo*hi go into the compensation, lo*lo (2^-48) is dropped.
+// About 2^-46 relative per dot, on the FP32 pipe (GB300's FP64 pipe is ~1/64 of it).
+// One 16-byte unit = two pairs.
+__device__ __forceinline__ void df_acc(float &S, float &c, float4 a, float4 x) {
+  const float p0 = a.x * x.x, e0 = fmaf(a.x, x.x, -p0), t0 = fmaf(a.x, x.y, a.y * x.x);
+  const float p1 = a.z * x.z, e1 = fmaf(a.z, x.z, -p1), t1 = fmaf(a.z, x.w, a.w * x.z);
+  float s = S + p0, bb = s - S;
+  c += ((S - (s - bb)) + (p0 - bb)) + (e0 + t0);
+  S = s;
+  s = S + p1;
+  bb = s - S;
+  c += ((S - (s - bb)) + (p1 - bb)) + (e1 + t1);
+  S = s;
+}
+
+// y[r] = A_r . x (FP64 results) for the rows of a chunk of (hi, lo) pairs, G lanes per
+// row, two accumulators per lane; ld in pairs (even)
+template <int G>
+__device__ __noinline__ void chunk_rows_df(const float2 *A, int ld, int cn, const float2 *xs, double *y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sub = lane / G, j = lane % G;
+  const int nv = ld / 2;
+  const float4 *x = reinterpret_cast<const float4 *>(xs);
+  for (int r0 = warp * (32 / G); r0 < cn; r0 += nw * (32 / G)) {
+    const int r = r0 + sub;
+    double v = 0.0;
+    if (r < cn) {
+      const float4 *row = reinterpret_cast<const float4 *>(A + (int64_t)r * ld);
+      float S0 = 0.f, c0 = 0.f, S1 = 0.f, c1 = 0.f;
+      int k = j;
+      for (; k + G < nv; k += 2 * G) {
+        df_acc(S0, c0, row[k], x[k]);
+        df_acc(S1, c1, row[k + G], x[k + G]);
+      }
+      if (k < nv) df_acc(S0, c0, row[k], x[k]);
+      v = ((double)S0 + (double)c0) + ((double)S1 + (double)c1);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (j == 0 && r < cn) y[r] = v;
+  }
+}
+
+// the same for chunks of fewer than 16 long rows: the whole CTA on up to 4 rows at a time
+__device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn, const float2 *xs, double *y,
+                                                double *part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nv = ld / 2;
+  const float4 *x = reinterpret_cast<const float4 *>(xs);
+  for (int r0 = 0; r0 < cn; r0 += 4) {
+    const int nr = min(4, cn - r0);
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      const float4 xv = x[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < nr) df_acc(S[i], c[i], reinterpret_cast<const float4 *>(A + (int64_t)(r0 + i) * ld)[k], xv);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double v = warp_red((double)S[i] + (double)c[i]);
+      if (lane == 0) part[warp * 4 + i] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nr) {
+      double t = 0;
+      for (int w = 0; w < nw; ++w) t += part[w * 4 + threadIdx.x];
+      y[r0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // TMA ring.  The operator rows a CTA multiplies in a phase are fixed by the static
 // partition, independent of the iteration's vectors, so they are streamed HBM ->
@@ -453,7 +528,9 @@ __device__ __forceinline__ Cursor prefetch(Ring &ring, const OpRows<E> &op) {
 // chunks may have been prefetched): before the first chunk of each segment,
 // stage(s, r0, r1) runs with every thread of the CTA; out(s, r, value, pre) per row.
 // Returns false (after setting the error flag and draining) when a wait timed out.
-template <int RW, class E, class Stage, class Out, class Pre = NoPre>
+// DF: the rows hold (hi, lo) FP32 pairs (E = double only sizes them), xs holds staged
+// pairs, y receives FP64 results (double-FP32 row kernels)
+template <int RW, class E, bool DF = false, class Stage, class Out, class Pre = NoPre>
 __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, E *y, unsigned *errflag,
                              Stage stage, Out out, Pre pre = Pre(), unsigned long long *ts = nullptr) {
   while (cur.issued - 0 < ring.ns && issue_next(ring, op, cur)) {
@@ -493,7 +570,18 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
       // a stage holds a few rows) spread over the whole CTA
       const int nv = ld / V16<E>::n;
       const int split = nv <= 32 ? 1 : (cn < 16 ? 2 : (sizeof(E) == 8 ? 8 : 0));
-      if (split) {
+      if constexpr (DF) {
+        static_assert(sizeof(E) == 8, "double-FP32 rows are sized as 8-byte entries");
+        double *yc = reinterpret_cast<double *>(y) + (ring.consumed & 1ull) * RPC_MAX;
+        const float2 *ap = reinterpret_cast<const float2 *>(buf);
+        const float2 *xp = reinterpret_cast<const float2 *>(xs);
+        if (split == 1) chunk_rows_df<1>(ap, ld, cn, xp, yc);
+        else if (split == 2) chunk_rows_df_wide(ap, ld, cn, xp, yc, yc + RPC_MAX / 2);
+        else chunk_rows_df<8>(ap, ld, cn, xp, yc);
+        __syncthreads();
+        issue_next(ring, op, cur);
+        for (int r = threadIdx.x; r < cn; r += blockDim.x) out(s, base_r + r, yc[r], pre(s, base_r + r));
+      } else if (split) {
         // row results into y (two buffers: the epilogues of the previous chunk may
         // still read the other one), then one thread per row
         E *yc = y + (ring.consumed & 1ull) * RPC_MAX;
@@ -710,19 +798,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   };
   // nested-dissection solve q = S_c^{-1} c: one phase per level, a grid barrier between
   // levels; the next level's rows are issued before the barrier
+  // the mixed path's blocks are (hi, lo) FP32 pairs (double-FP32 rows), the FP64 path's FP64
+  constexpr bool NDF = sizeof(T) == 4;
   auto coarse_solve_nd = [&]() -> bool {
     double *xd = reinterpret_cast<double *>(smem_raw);
+    float2 *xp = reinterpret_cast<float2 *>(smem_raw);
     double *yd = reinterpret_cast<double *>(ybuf_raw);
+    auto put = [&](int k, double v) {
+      if constexpr (NDF) {
+        const float hi = (float)v;
+        xp[k] = make_float2(hi, (float)(v - (double)hi));
+      } else {
+        xd[k] = v;
+      }
+    };
     for (int lv = 0; lv < nd_levels; ++lv) {
       const OpRows<double> op = nd_op(lv);
       bool ok;
       if (lv < a.nd_H) {
-        ok = stream_phase<4>(
+        ok = stream_phase<4, double, NDF>(
             ring, op, cur, xd, yd, errflag,
             [&](int p, int, int) {
               const int nk = a.nd_nk[p], ld = a.nd_zld[p], k0 = a.nd_k0[p];
               for (int k = threadIdx.x; k < ld; k += nthr)
-                xd[k] = k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0;
+                put(k, k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0);
             },
             [&](int p, int r, double v, double2 pv) {
               const int nk = a.nd_nk[p];
@@ -732,12 +831,12 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
             [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); },
             lv == 0 ? tsp(1) : nullptr);
       } else {
-        ok = stream_phase<4>(
+        ok = stream_phase<4, double, NDF>(
             ring, op, cur, xd, yd, errflag,
             [&](int p, int, int) {
               const int ns = a.nd_ns[p], ld = a.nd_ltld[p];
               const int32_t *si = a.nd_sidx + a.nd_soff[p];
-              for (int k = threadIdx.x; k < ld; k += nthr) xd[k] = k < ns ? ldcg(a.q + si[k]) : 0.0;
+              for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < ns ? ldcg(a.q + si[k]) : 0.0);
             },
             [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; },
             [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); });
