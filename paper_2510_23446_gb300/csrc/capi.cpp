@@ -59,9 +59,12 @@ int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ct
     ctx = new ieti_ctx();
     ctx->opt = *options;
     rc = ctx->hs.build(problem, options->host_threads, g_setup_err);
+    // nested-dissection tree of the coarse problem: the given leaf size, or the shape of
+    // least modelled solve time (~4 TB/s streaming, ~12 us per grid-synchronised level)
     if (rc == IETI_OK)
-      rc = ieti::build_coarse_tree(ctx->hs, options->coarse_leaf > 0 ? options->coarse_leaf : 8, ctx->tree,
-                                   g_setup_err);
+      rc = options->coarse_leaf > 0
+               ? ieti::build_coarse_tree(ctx->hs, options->coarse_leaf, 0, ctx->tree, g_setup_err)
+               : ieti::choose_coarse_tree(ctx->hs, 4e12, 12e-6, ctx->tree, g_setup_err);
     if (rc == IETI_OK && options->device >= 0)
       rc = ieti::device_setup(ctx->hs, &ctx->tree, ctx->opt, &ctx->dev, g_setup_err);
   } catch (const std::bad_alloc &) {

@@ -11,7 +11,7 @@ namespace {
 struct RawNode {
   int box[6];
   std::vector<int32_t> dofs;   // coarse ids, ascending
-  int parent = -1;
+  int parent = -1, depth = 0;
   std::vector<int> kids;
 };
 
@@ -25,10 +25,11 @@ int CoarseTree::front_index(int p, int32_t x) const {
   return nk[p] + (int)(it - b);
 }
 
-int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::string &err) {
+int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err) {
   t = CoarseTree();
   t.nc = hs.n_coarse;
   t.leaf_max = std::max(1, leaf_max);
+  t.top = std::max(0, top);
   const int64_t nc = hs.n_coarse;
   if (nc == 0) return IETI_OK;
   if (nc >= (int64_t)INT32_MAX) {
@@ -60,6 +61,7 @@ int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::str
     raw.emplace_back();
     std::copy(box, box + 6, raw[k].box);
     raw[k].parent = parent;
+    raw[k].depth = parent < 0 ? 0 : raw[parent].depth + 1;
     int ext[3] = {box[1] - box[0], box[3] - box[2], box[5] - box[4]};
     if ((int64_t)ext[0] * ext[1] * ext[2] <= t.leaf_max) {
       raw[k].dofs = std::move(alive);
@@ -92,6 +94,15 @@ int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::str
     for (int64_t c = 0; c < nc; ++c) all[c] = (int32_t)c;
     const int root_box[6] = {0, hs.P[0], 0, hs.P[1], 0, hs.P[2]};
     rec(root_box, -1, std::move(all));
+  }
+  // the separators of the top levels (depth < top) form one dense root block
+  if (t.top > 1) {
+    for (size_t k = 1; k < raw.size(); ++k)
+      if (raw[k].depth < t.top) {
+        raw[0].dofs.insert(raw[0].dofs.end(), raw[k].dofs.begin(), raw[k].dofs.end());
+        raw[k].dofs.clear();
+      }
+    std::sort(raw[0].dofs.begin(), raw[0].dofs.end());
   }
   // remove empty nodes (their children move up to the nearest non-empty ancestor)
   std::vector<int> roots;
@@ -183,6 +194,34 @@ int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::str
         return IETI_ERR_INVALID_ARG;
       }
   }
+  return IETI_OK;
+}
+
+double coarse_tree_bytes(const CoarseTree &t) {
+  double b = 0;
+  for (int p = 0; p < t.n_nodes; ++p) b += 8.0 * ((double)(t.nk[p] + t.ns[p]) * t.nk[p] + (double)t.nk[p] * t.ns[p]);
+  return b;
+}
+
+int coarse_tree_levels(const CoarseTree &t) { return t.n_nodes ? t.n_height + std::max(t.n_depth - 1, 0) : 0; }
+
+int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTree &t, std::string &err) {
+  const int leaves[] = {1, 8, 16, 27, 64, 125};
+  const int tops[] = {0, 2, 3};
+  double best = 1e300;
+  bool any = false;
+  for (int leaf : leaves)
+    for (int top : tops) {
+      CoarseTree c;
+      int rc = build_coarse_tree(hs, leaf, top, c, err);
+      if (rc) return rc;
+      const double model = coarse_tree_bytes(c) / bw + coarse_tree_levels(c) * latency;
+      if (!any || model < best * (1.0 - 1e-9)) {
+        best = model;
+        t = std::move(c);
+        any = true;
+      }
+    }
   return IETI_OK;
 }
 

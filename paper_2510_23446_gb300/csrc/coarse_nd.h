@@ -24,6 +24,7 @@ struct CoarseTree {
   int64_t nc = 0;
   int n_nodes = 0;
   int leaf_max = 1;
+  int top = 0;                          // separators of depth < top merged into the root
   std::vector<int32_t> perm;            // coarse id -> position in elimination order
   // per node, postorder (children before their parent)
   std::vector<int32_t> k0, nk, ns;      // own block [k0, k0 + nk), |S_p|
@@ -39,7 +40,17 @@ struct CoarseTree {
 };
 
 // Build the tree for the coarse unknowns of `hs` (boxes of leaf_max patches or fewer
-// are not cut further; empty nodes are removed and their children re-attached).
-int build_coarse_tree(const HostSetup &hs, int leaf_max, CoarseTree &t, std::string &err);
+// are not cut further; with top > 1 the separators of the top `top` levels form one
+// root block; empty nodes are removed and their children re-attached).
+int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err);
+
+// Algorithmic bytes of one coarse solve on the tree (Z rows forward, Lt rows backward)
+// and its grid-synchronised phases (levels by height, then by depth below the roots).
+double coarse_tree_bytes(const CoarseTree &t);
+int coarse_tree_levels(const CoarseTree &t);
+
+// Tree shape of least modelled solve time over a fixed candidate list of leaf sizes
+// and top merges: bytes / bw + phases * latency.
+int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTree &t, std::string &err);
 
 }  // namespace ieti

@@ -570,6 +570,17 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
       // a stage holds a few rows) spread over the whole CTA
       const int nv = ld / V16<E>::n;
       const int split = nv <= 32 ? 1 : (cn < 16 ? 2 : (sizeof(E) == 8 ? 8 : 0));
+      // epilogue inputs of the chunk's rows (one thread per row, at most two rows per
+      // thread: RPC_MAX = 2 x 256), loaded before the row kernel so that their latency
+      // overlaps it
+      double2 pv[RPC_MAX / PCG_THREADS];
+      if (DF || split) {
+#pragma unroll
+        for (int i = 0; i < RPC_MAX / PCG_THREADS; ++i) {
+          const int r = threadIdx.x + i * PCG_THREADS;
+          if (r < cn) pv[i] = pre(s, base_r + r);
+        }
+      }
       if constexpr (DF) {
         static_assert(sizeof(E) == 8, "double-FP32 rows are sized as 8-byte entries");
         double *yc = reinterpret_cast<double *>(y) + (ring.consumed & 1ull) * RPC_MAX;
@@ -580,7 +591,11 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
         else chunk_rows_df<8>(ap, ld, cn, xp, yc);
         __syncthreads();
         issue_next(ring, op, cur);
-        for (int r = threadIdx.x; r < cn; r += blockDim.x) out(s, base_r + r, yc[r], pre(s, base_r + r));
+#pragma unroll
+        for (int i = 0; i < RPC_MAX / PCG_THREADS; ++i) {
+          const int r = threadIdx.x + i * PCG_THREADS;
+          if (r < cn) out(s, base_r + r, yc[r], pv[i]);
+        }
       } else if (split) {
         // row results into y (two buffers: the epilogues of the previous chunk may
         // still read the other one), then one thread per row
@@ -590,7 +605,11 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
         else chunk_rows_wide<E>(buf, ld, cn, xs, yc, yc + RPC_MAX / 2);
         __syncthreads();  // every warp is done with this stage; yc is complete
         issue_next(ring, op, cur);
-        for (int r = threadIdx.x; r < cn; r += blockDim.x) out(s, base_r + r, (double)yc[r], pre(s, base_r + r));
+#pragma unroll
+        for (int i = 0; i < RPC_MAX / PCG_THREADS; ++i) {
+          const int r = threadIdx.x + i * PCG_THREADS;
+          if (r < cn) out(s, base_r + r, (double)yc[r], pv[i]);
+        }
       } else {
         // long rows: RW rows per warp, lane i of the group runs row i's epilogue
         rows_gemv<RW, false>(buf, ld, 0, cn, xs,

@@ -47,6 +47,15 @@ CASES = {
     # smaller members of the 512-patch family (per-patch log-uniform sigma up to 1e4 in a
     # ball, nu in [0.5, 2]) and of the 343-patch family (uneven slabs, p in {2, 3} per
     # slab, random conductors with sigma = 1e3), from the same generators
+    # degenerate material layouts: no insulator (no tree, no primal unknowns: the dual
+    # problem has no coarse space) and no conductor (W = dt K, the whole domain gauged,
+    # the coarse space only the wirebasket cotree edges)
+    "all_conducting": lambda: small_problem(P=(2, 2, 2), n_el=((2, 3), (3, 2), (2, 2)),
+                                            degree=((1, 2), (2, 1), (2, 2)), conductor=((0.0, 1.0),) * 3,
+                                            sigma=5.0, dt=0.05),
+    "all_insulating": lambda: small_problem(P=(2, 2, 2), n_el=((2, 3), (3, 2), (2, 2)),
+                                            degree=((1, 2), (2, 1), (2, 2)), conductor=((2.0, 3.0),) * 3,
+                                            sigma=5.0, dt=0.05),
     "c3_family": lambda: make_problem("c3", patches_per_dir=3, n_el=2),
     "c4_family": lambda: make_problem("c4", patches_per_dir=3, el_range=(2, 3)),
 }
