@@ -166,7 +166,10 @@ typedef struct {
   int32_t wait_limit;
   int32_t coarse;        /* IETI_COARSE_*: solve of the coarse problem (ND: linear problems, pcg_mode 0) */
   int32_t coarse_leaf;   /* nested dissection: boxes of at most this many patches are not cut further
-                            (0: 8) */
+                            (0: the tree shape of least modelled solve time over a candidate list) */
+  int32_t factor_arena_mb; /* budget of the setup factorization's arena of dense patch blocks, MiB: the
+                              patches are factored in batches that fit it (0: 64 GB or 40% of the free
+                              device memory, whichever is smaller) */
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -233,6 +236,7 @@ typedef struct {
   int32_t coarse_levels;     /* grid-synchronised phases of one coarse solve */
   double coarse_bytes;       /* algorithmic bytes of one coarse solve */
   double t_coarse_ms;        /* host time of the coarse assembly and factorization at setup */
+  int32_t factor_batches;    /* patch batches of the setup factorization */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
@@ -334,6 +338,14 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);
  * the staged first vector segment, from there to the first operator chunk in shared
  * memory, and from there to the last row.  reset != 0 clears the accumulators. */
 int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, double *sub_us, int32_t reset);
+
+/* Per-level timing of the nested-dissection coarse solve (options.profile = 1, coarse
+ * mode ND): mean over the traced PCG iterations of CTA 0's time in each level of one
+ * coarse solve (forward levels by height, then backward levels by depth), from the end
+ * of the previous level's grid barrier to the end of this level's, in microseconds
+ * (%globaltimer).  us receives n entries (0 beyond the tree's levels).  reset != 0 clears
+ * the accumulators.  Errors: INVALID_ARG, NO_DEVICE. */
+int ieti_coarse_level_times(ieti_ctx *ctx, double *us, int32_t n, int32_t reset);
 
 /* Batched dense partial Cholesky, the kernel family behind both Schur complements
  * of Sec. 3 (local W_rr eliminations and the coarse block), exposed for callers and

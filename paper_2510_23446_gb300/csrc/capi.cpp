@@ -39,6 +39,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->wait_limit < 0) { err = "wait_limit must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse < IETI_COARSE_AUTO || o->coarse > IETI_COARSE_ND) { err = "bad coarse"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse_leaf < 0) { err = "coarse_leaf must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->factor_arena_mb < 0) { err = "factor_arena_mb must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
     return IETI_ERR_INVALID_ARG;
@@ -189,6 +190,13 @@ int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset) {
   if (!ctx || !out) return IETI_ERR_INVALID_ARG;
   if (!ctx->dev) return IETI_ERR_NO_DEVICE;
   ieti::device_kernel_stats(ctx->dev, out, reset != 0);
+  return IETI_OK;
+}
+
+int ieti_coarse_level_times(ieti_ctx *ctx, double *us, int32_t n, int32_t reset) {
+  if (!ctx || (!us && n > 0) || n < 0) return IETI_ERR_INVALID_ARG;
+  if (!ctx->dev) return IETI_ERR_NO_DEVICE;
+  ieti::device_coarse_level_times(ctx->dev, us, n, reset != 0);
   return IETI_OK;
 }
 

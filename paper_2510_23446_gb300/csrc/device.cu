@@ -907,6 +907,8 @@ struct DeviceState {
   double trace_acc[8] = {};   // summed per-phase time (us) over traced iterations: work P1..P6, waits
   double trace_wait[8] = {};
   double trace_sub[4][3] = {};  // P1, P3, P4, P5: staging, first chunk, rows (us)
+  double trace_nd[TRACE_ND] = {};  // nested-dissection levels of the coarse solve (us, incl. barrier)
+  int64_t trace_nd_n = 0;
   int64_t trace_sub_n[4] = {};
   int64_t trace_n = 0;
   double *pcg_rr = nullptr, *pcg_dd = nullptr;
@@ -991,6 +993,7 @@ struct DeviceState {
   int64_t nd_z_elems = 0, nd_lt_elems = 0;              // padded sizes of the two operator blocks
   double nd_bytes = 0;                                  // algorithmic bytes of one coarse solve
   double t_coarse_ms = 0;                               // device time of the coarse factorization
+  int factor_batches = 1;                               // patch batches of the setup factorization
 };
 
 // event pair around one launch of a kernel class (no-op unless profiling)
@@ -2272,6 +2275,15 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
         d->trace_wait[ph] += (t[2 * ph + 1] - t[2 * ph]) * 1e-3;
         prev = t[2 * ph + 1];
       }
+      if (d->coarse_nd && t[32]) {
+        unsigned long long prev_nd = t[3];  // the coarse phase starts after the P2 barrier
+        const int nl = std::min(TRACE_ND, d->nd_H + std::max(d->nd_D - 1, 0));
+        for (int lv = 0; lv < nl && t[32 + lv]; ++lv) {
+          d->trace_nd[lv] += (t[32 + lv] - prev_nd) * 1e-3;
+          prev_nd = t[32 + lv];
+        }
+        d->trace_nd_n++;
+      }
       for (int k = 0; k < 4; ++k) {
         const unsigned long long *u = t + 16 + 3 * k;
         if (!u[0] || !u[1] || !u[2]) continue;
@@ -3152,13 +3164,12 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
   }
   // ---------------- upload index data
   int rc;
-  std::vector<int64_t> hkofs_v(hkofs.begin(), hkofs.end() - 1), hdoff_v(hdoff.begin(), hdoff.end() - 1),
+  std::vector<int64_t> hkofs_v(hkofs.begin(), hkofs.end() - 1),
       hig_v(hig.begin(), hig.end() - 1), hgt_v(hgt.begin(), hgt.end() - 1), hh_v(hh.begin(), hh.end() - 1),
       hq_v(hq.begin(), hq.end() - 1), hp_v(hp.begin(), hp.end() - 1);
-  int64_t *ddoff = nullptr;
   int32_t *dnn = nullptr, *dn = nullptr, *drowpatch = nullptr, *drowlocal = nullptr;
   if ((rc = upload(d, &d->ni, hni, err)) || (rc = upload(d, &d->nb, hnb, err)) || (rc = upload(d, &d->npp, hnp, err)) ||
-      (rc = upload(d, &d->kofs, hkofs_v, err)) || (rc = upload(d, &ddoff, hdoff_v, err)) ||
+      (rc = upload(d, &d->kofs, hkofs_v, err)) ||
       (rc = upload(d, &d->igoff, hig_v, err)) || (rc = upload(d, &d->gtoff, hgt_v, err)) ||
       (rc = upload(d, &d->hoff, hh_v, err)) ||
       (rc = upload(d, &d->qoff, hq_v, err)) || (rc = upload(d, &d->poff, hp_v, err)) ||
@@ -3287,38 +3298,46 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
   CK(cudaMemsetAsync(d->j, 0, hs.n_edges * sizeof(double), d->stream));
   CK(cudaMemsetAsync(d->rglob, 0, hs.n_edges * sizeof(double), d->stream));
   // ---------------- dense augmented blocks, partial Cholesky (FP64, or FP32 with
-  // SIMT or tensor-core trailing updates)
+  // SIMT or tensor-core trailing updates), in batches of patches whose blocks fit one
+  // arena (all patches at once when they fit in 64 GB and 40% of the free memory)
   const bool f32 = d->factor != IETI_FACTOR_FP64;
   const size_t dsz = f32 ? sizeof(float) : sizeof(double);
+  size_t esz = d->mixed ? sizeof(float) : sizeof(double);
+  std::vector<int> bstart{0};
+  int64_t arena_elems = 0;
+  {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double cap = (opt.factor_arena_mb > 0 ? (double)opt.factor_arena_mb * 1048576.0
+                                                 : std::min(64e9, 0.4 * (double)free_b)) / (double)dsz;
+    int64_t acc = 0;
+    for (int s = 0; s < np_; ++s) {
+      const int64_t e = (int64_t)hnn[s] * hnn[s];
+      if (acc > 0 && (double)(acc + e) > cap) {
+        bstart.push_back(s);
+        acc = 0;
+      }
+      acc += e;
+      arena_elems = std::max(arena_elems, acc);
+    }
+    bstart.push_back(np_);
+  }
+  const int n_batches = (int)bstart.size() - 1;
+  d->factor_batches = n_batches;
   double *D = nullptr;  // FP64 arena
   float *Df = nullptr;  // FP32 arena
   if (f32) {
-    if ((rc = dalloc(d, &Df, hdoff[np_], err))) return fail(rc);
-  } else if ((rc = dalloc(d, &D, hdoff[np_], err))) {
+    if ((rc = dalloc(d, &Df, arena_elems, err))) return fail(rc);
+  } else if ((rc = dalloc(d, &D, arena_elems, err))) {
     return fail(rc);
   }
   void *Dv = f32 ? (void *)Df : (void *)D;
-  CK(cudaMemsetAsync(Dv, 0, hdoff[np_] * dsz, d->stream));
-  {
-    int64_t nrows = d->NK;
-    unsigned g0 = grid_for(nrows * 32, 256);
-    if (f32)
-      k_csr_to_dense<float><<<g0, 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol, d->wval,
-                                                       d->kofs, ddoff, dnn, Df);
-    else
-      k_csr_to_dense<double><<<g0, 256, 0, d->stream>>>(nrows, drowpatch, drowlocal, d->wptr, d->wcol, d->wval,
-                                                        d->kofs, ddoff, dnn, D);
-    int maxaug = std::max(*std::max_element(hnb.begin(), hnb.end()), d->max_ni);
-    if (maxaug > 0) {
-      dim3 g(grid_for(maxaug, 128), np_);
-      if (f32)
-        k_augment<float><<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, Df);
-      else
-        k_augment<double><<<g, 128, 0, d->stream>>>(np_, d->ni, d->nb, dn, dnn, ddoff, D);
-    }
-    d->launches_setup += 2;
-  }
-  CK(cudaGetLastError());
+  // offsets of the blocks inside the arena, relative to their batch's first block
+  std::vector<int64_t> hboff(np_);
+  for (int b = 0; b < n_batches; ++b)
+    for (int s = bstart[b]; s < bstart[b + 1]; ++s) hboff[s] = hdoff[s] - hdoff[bstart[b]];
+  int64_t *dboff = nullptr;
+  if ((rc = upload(d, &dboff, hboff, err))) return fail(rc);
   if (d->nonlinear && !hs.nl.patches.empty()) {
     // patches holding nonlinear elements: keep their blocks without the law (base of
     // every refactorization) and the quadrature tables of their nonlinear elements
@@ -3353,11 +3372,6 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     CK(cudaMalloc(&d->nl_work, (size_t)d->nl_arena * dsz));
     d->allocs.push_back(d->nl_work);
     d->bytes += 2 * d->nl_arena * (int64_t)dsz;
-    for (int b = 0; b < nb; ++b) {
-      int sg = T.patches[b];
-      CK(cudaMemcpyAsync((char *)d->nl_base + d->nlh_doff[b] * dsz, (char *)Dv + hdoff[sg] * dsz,
-                         (size_t)hnn[sg] * hnn[sg] * dsz, cudaMemcpyDeviceToDevice, d->stream));
-    }
     std::vector<int64_t> kofs_b, hoff_b, qoff_b, poff_b, igoff_b, gtoff_b;
     std::vector<int32_t> ldb_b, ldp_b, ldi_b, ldg_b;
     for (int b = 0; b < nb; ++b) {
@@ -3395,7 +3409,8 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
         (rc = upload(d, &d->nl_tq, tq0, err)))
       return fail(rc);
   }
-  // phase A: interior pivots -> trailing [b p b'] = Schur complement; copy S_bb
+  // per-patch factorization controls (device copies; the kernels see a batch through
+  // pointers offset to its first patch)
   std::vector<int32_t> hkb(np_), hke(np_), hna(np_);
   int32_t *dkb = nullptr, *dke = nullptr, *dna = nullptr, *dstat = nullptr;
   int32_t *dsklo = nullptr, *dskhi = nullptr, *drlim = nullptr, *dclim = nullptr;
@@ -3410,36 +3425,6 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     CK(cudaStreamSynchronize(d->stream));
     return IETI_OK;
   };
-  AugLimits lim{dsklo, dskhi, drlim, dclim};
-  TcHost th;
-  th.off = hdoff;
-  th.ld = hnn;
-  // one partial-Cholesky phase over all patches in the chosen factor precision
-  auto factor_phase = [&](const std::vector<int32_t> &kb, const std::vector<int32_t> &ke,
-                          const std::vector<int32_t> &na, AugLimits lm) -> int {
-    d->factor_flops += partial_chol_flops(th, kb, ke, na);
-    if (d->factor == IETI_FACTOR_FP64)
-      return potrf_partial<double>(d, D, ddoff, dnn, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-    return potrf_partial_f32(d, d->factor, Df, ddoff, dnn, th, kb, ke, na, dkb, dke, dna, dstat, lm, err);
-  };
-  for (int s = 0; s < np_; ++s) {
-    hkb[s] = 0;
-    hke[s] = hni[s];
-    hna[s] = hnn[s];
-    hsklo[s] = hn[s];              // b' rows: zero in the interior columns
-    hskhi[s] = hn[s] + hnb[s];
-    hrlim[s] = INT32_MAX;          // i' rows: full updates (W_ii^{-1} and G^T come out of them)
-    hclim[s] = 0;
-  }
-  if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
-      (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
-    return fail(rc);
-  th.sk_lo = hsklo;
-  th.sk_hi = hskhi;
-  th.rlim = hrlim;
-  th.clim = hclim;
-  CK(cudaEventRecord(d->ev0, d->stream));
-  if ((rc = factor_phase(hkb, hke, hna, lim))) return fail(rc);
   int maxnb = *std::max_element(hnb.begin(), hnb.end());
   int maxnp = *std::max_element(hnp.begin(), hnp.end());
   int64_t maxP = (int64_t)maxnb * maxnb;
@@ -3448,7 +3433,6 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     maxH = std::max(maxH, (int64_t)(hnb[s] + hnp[s]) * hnb[s]);
     maxIG = std::max(maxIG, (int64_t)hn[s] * hni[s]);
   }
-  size_t esz = d->mixed ? sizeof(float) : sizeof(double);
   auto alloc_op = [&](void **ptr, int64_t n) -> int {
     cudaError_t e = cudaMalloc(ptr, std::max<int64_t>(n, 1) * esz);
     if (e != cudaSuccess) {
@@ -3460,7 +3444,7 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     return IETI_OK;
   };
   {
-    // H, Q, P and the coarse inverse are re-read every PCG iteration: one arena
+    // H, Q, P and the coarse operators are re-read every PCG iteration: one arena
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     size_t bH = al(std::max<int64_t>(hh[np_], 1) * esz), bQ = al(std::max<int64_t>(hq[np_], 1) * esz),
            bP = al(std::max<int64_t>(hp[np_], 1) * esz),
@@ -3489,142 +3473,201 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
   CK(cudaMemsetAsync(d->P, 0, std::max<int64_t>(hp[np_], 1) * esz, d->stream));
   CK(cudaMemsetAsync(d->H, 0, std::max<int64_t>(hh[np_], 1) * esz, d->stream));
   CK(cudaMemsetAsync(d->Q, 0, std::max<int64_t>(hq[np_], 1) * esz, d->stream));
-  if (maxP > 0) {
-    dim3 g(grid_for(maxP, 256), np_);
-    if (f32)
-      k_extract_P<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
-                                                          (float *)d->P);
-    else if (d->mixed)
-      k_extract_P<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
-                                                           (float *)d->P);
-    else
-      k_extract_P<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->ldb, d->poff,
-                                                            (double *)d->P);
-    d->launches_setup++;
-  }
-  // phase B: interface pivots -> trailing [p b'] = [[C_s, -Psi^T], [-Psi, -F_s]]
-  for (int s = 0; s < np_; ++s) {
-    hkb[s] = hni[s];
-    hke[s] = hni[s] + hnb[s];
-    hna[s] = hn[s] + hnb[s];       // the i' rows are done
-    hsklo[s] = hskhi[s] = 0;
-    hrlim[s] = INT32_MAX;
-    hclim[s] = 0;
-  }
-  if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
-      (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
-    return fail(rc);
-  th.sk_lo = hsklo;
-  th.sk_hi = hskhi;
-  th.rlim = hrlim;
-  th.clim = hclim;
-  if ((rc = factor_phase(hkb, hke, hna, lim))) return fail(rc);
-  CK(cudaEventRecord(d->ev1, d->stream));
-  {
-    std::vector<int32_t> hstat(np_);
-    CK(cudaMemcpyAsync(hstat.data(), dstat, np_ * 4, cudaMemcpyDeviceToHost, d->stream));
-    CK(cudaStreamSynchronize(d->stream));
-    for (int s = 0; s < np_; ++s)
-      if (hstat[s]) {
-        err = "local block of patch " + std::to_string(s) + " is not positive definite (pivot " +
-              std::to_string(hstat[s] - 1) + ")";
-        return fail(IETI_ERR_NOT_SPD);
-      }
-  }
-  if (maxH > 0) {
-    dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), np_);
-    if (f32)
-      k_extract_ops<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
-                                                            d->hoff, d->qoff, (float *)d->H, (float *)d->Q);
-    else if (d->mixed)
-      k_extract_ops<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
-                                                             d->hoff, d->qoff, (float *)d->H, (float *)d->Q);
-    else
-      k_extract_ops<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldb, d->ldp,
-                                                              d->hoff, d->qoff, (double *)d->H, (double *)d->Q);
-    d->launches_setup++;
-  }
-  if (maxIG > 0) {
-    dim3 g((unsigned)std::min<int64_t>(grid_for(maxIG, 256), 4096), np_);
-    if (f32)
-      k_extract_IG<float, float><<<g, 256, 0, d->stream>>>(Df, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
-                                                           d->igoff, d->gtoff, (float *)d->IG, (float *)d->GT);
-    else if (d->mixed)
-      k_extract_IG<double, float><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
-                                                            d->igoff, d->gtoff, (float *)d->IG, (float *)d->GT);
-    else
-      k_extract_IG<double, double><<<g, 256, 0, d->stream>>>(D, ddoff, dnn, d->ni, d->nb, d->npp, d->ldi, d->ldg,
-                                                             d->igoff, d->gtoff, (double *)d->IG, (double *)d->GT);
-    d->launches_setup++;
-  }
-  // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, factored along the nested
-  // dissection, or inverted through [[S_c, I], [I, 0]]
-  if (d->NC > 0 && d->coarse_nd) {
-    auto tc0 = std::chrono::steady_clock::now();
-    const int64_t nc = d->NC;
-    double *Sc = nullptr;
-    if (cudaMalloc((void **)&Sc, (size_t)(nc * nc) * sizeof(double)) != cudaSuccess) {
-      err = "cudaMalloc failed for the assembled coarse matrix";
-      return fail(IETI_ERR_OOM);
+  // coarse accumulators: S_c (nested dissection) or [[S_c, I], [I, 0]] (dense inverse),
+  // and for Newton the linear patches' part of S_c
+  const int64_t nc = d->NC, ldS = d->coarse_nd ? nc : 2 * nc;
+  double *Sc = nullptr;
+  std::vector<uint8_t> is_nl(np_, 0);
+  for (int sg : hs.nl.patches) is_nl[sg] = 1;
+  if (nc > 0) {
+    if ((rc = dalloc(d, &Sc, (size_t)(ldS * ldS), err))) return fail(rc);
+    CK(cudaMemsetAsync(Sc, 0, (size_t)(ldS * ldS) * sizeof(double), d->stream));
+    if (d->nl_np > 0) {
+      if ((rc = dalloc(d, &d->sc_lin, (size_t)(nc * nc), err))) return fail(rc);
+      CK(cudaMemsetAsync(d->sc_lin, 0, (size_t)(nc * nc) * sizeof(double), d->stream));
     }
-    cudaError_t e0 = cudaMemsetAsync(Sc, 0, (size_t)(nc * nc) * sizeof(double), d->stream);
-    for (int s = 0; s < np_ && e0 == cudaSuccess; ++s) {
-      if (hnp[s] == 0) continue;
-      int64_t cnt = (int64_t)hnp[s] * hnp[s];
+  }
+  d->t_factor_ms = 0;
+  for (int bt = 0; bt < n_batches; ++bt) {
+    const int s0 = bstart[bt], s1 = bstart[bt + 1], nbt = s1 - s0;
+    const int64_t a0 = hdoff[s0], belems = hdoff[s1] - a0;
+    CK(cudaMemsetAsync(Dv, 0, (size_t)belems * dsz, d->stream));
+    {
+      const int64_t r0 = hkofs[s0], nrows = hkofs[s1] - r0;
+      unsigned g0 = grid_for(nrows * 32, 256);
       if (f32)
-        k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
-                                                                       d->pc + hpofs[s], Sc, nc);
+        k_csr_to_dense<float><<<g0, 256, 0, d->stream>>>(nrows, drowpatch + r0, drowlocal + r0, d->wptr + r0,
+                                                         d->wcol, d->wval, d->kofs, dboff, dnn, Df);
       else
-        k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
-                                                                        hnp[s], d->pc + hpofs[s], Sc, nc);
+        k_csr_to_dense<double><<<g0, 256, 0, d->stream>>>(nrows, drowpatch + r0, drowlocal + r0, d->wptr + r0,
+                                                          d->wcol, d->wval, d->kofs, dboff, dnn, D);
+      int maxaug = 0;
+      for (int s = s0; s < s1; ++s) maxaug = std::max({maxaug, hnb[s], hni[s]});
+      if (maxaug > 0) {
+        dim3 g(grid_for(maxaug, 128), nbt);
+        if (f32)
+          k_augment<float><<<g, 128, 0, d->stream>>>(nbt, d->ni + s0, d->nb + s0, dn + s0, dnn + s0, dboff + s0, Df);
+        else
+          k_augment<double><<<g, 128, 0, d->stream>>>(nbt, d->ni + s0, d->nb + s0, dn + s0, dnn + s0, dboff + s0, D);
+      }
+      d->launches_setup += 2;
+    }
+    CK(cudaGetLastError());
+    // the nonlinear patches' blocks without the law: base of every refactorization
+    for (int b = 0; b < d->nl_np; ++b) {
+      const int sg = d->nlh_ids[b];
+      if (sg < s0 || sg >= s1) continue;
+      CK(cudaMemcpyAsync((char *)d->nl_base + d->nlh_doff[b] * dsz, (char *)Dv + hboff[sg] * dsz,
+                         (size_t)hnn[sg] * hnn[sg] * dsz, cudaMemcpyDeviceToDevice, d->stream));
+    }
+    TcHost th;
+    th.off.assign(hboff.begin() + s0, hboff.begin() + s1);
+    th.ld.assign(hnn.begin() + s0, hnn.begin() + s1);
+    AugLimits lim{dsklo + s0, dskhi + s0, drlim + s0, dclim + s0};
+    auto slice = [&](const std::vector<int32_t> &v) { return std::vector<int32_t>(v.begin() + s0, v.begin() + s1); };
+    // one partial-Cholesky phase over the batch in the chosen factor precision
+    auto factor_phase = [&]() -> int {
+      const std::vector<int32_t> kb = slice(hkb), ke = slice(hke), na = slice(hna);
+      th.sk_lo = slice(hsklo);
+      th.sk_hi = slice(hskhi);
+      th.rlim = slice(hrlim);
+      th.clim = slice(hclim);
+      d->factor_flops += partial_chol_flops(th, kb, ke, na);
+      if (d->factor == IETI_FACTOR_FP64)
+        return potrf_partial<double>(d, D, dboff + s0, dnn + s0, kb, ke, na, dkb + s0, dke + s0, dna + s0,
+                                     dstat + s0, lim, err);
+      return potrf_partial_f32(d, d->factor, Df, dboff + s0, dnn + s0, th, kb, ke, na, dkb + s0, dke + s0,
+                               dna + s0, dstat + s0, lim, err);
+    };
+    // phase A: interior pivots -> trailing [b p b'] = Schur complement; copy S_bb
+    for (int s = s0; s < s1; ++s) {
+      hkb[s] = 0;
+      hke[s] = hni[s];
+      hna[s] = hnn[s];
+      hsklo[s] = hn[s];              // b' rows: zero in the interior columns
+      hskhi[s] = hn[s] + hnb[s];
+      hrlim[s] = INT32_MAX;          // i' rows: full updates (W_ii^{-1} and G^T come out of them)
+      hclim[s] = 0;
+    }
+    if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
+        (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
+      return fail(rc);
+    CK(cudaEventRecord(d->ev0, d->stream));
+    if ((rc = factor_phase())) return fail(rc);
+    if (maxP > 0) {
+      dim3 g(grid_for(maxP, 256), nbt);
+      if (f32)
+        k_extract_P<float, float><<<g, 256, 0, d->stream>>>(Df, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                            d->ldb + s0, d->poff + s0, (float *)d->P);
+      else if (d->mixed)
+        k_extract_P<double, float><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                             d->ldb + s0, d->poff + s0, (float *)d->P);
+      else
+        k_extract_P<double, double><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                              d->ldb + s0, d->poff + s0, (double *)d->P);
       d->launches_setup++;
     }
-    rc = e0 == cudaSuccess ? coarse_nd_factor(d, *tree, Sc, err) : IETI_ERR_CUDA;
+    // phase B: interface pivots -> trailing [p b'] = [[C_s, -Psi^T], [-Psi, -F_s]]
+    for (int s = s0; s < s1; ++s) {
+      hkb[s] = hni[s];
+      hke[s] = hni[s] + hnb[s];
+      hna[s] = hn[s] + hnb[s];       // the i' rows are done
+      hsklo[s] = hskhi[s] = 0;
+      hrlim[s] = INT32_MAX;
+      hclim[s] = 0;
+    }
+    if ((rc = put(dkb, hkb)) || (rc = put(dke, hke)) || (rc = put(dna, hna)) || (rc = put(dsklo, hsklo)) ||
+        (rc = put(dskhi, hskhi)) || (rc = put(drlim, hrlim)) || (rc = put(dclim, hclim)))
+      return fail(rc);
+    if ((rc = factor_phase())) return fail(rc);
+    CK(cudaEventRecord(d->ev1, d->stream));
+    {
+      std::vector<int32_t> hstat(nbt);
+      CK(cudaMemcpyAsync(hstat.data(), dstat + s0, nbt * 4, cudaMemcpyDeviceToHost, d->stream));
+      CK(cudaStreamSynchronize(d->stream));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, d->ev0, d->ev1));
+      d->t_factor_ms += ms;
+      for (int s = s0; s < s1; ++s)
+        if (hstat[s - s0]) {
+          err = "local block of patch " + std::to_string(s) + " is not positive definite (pivot " +
+                std::to_string(hstat[s - s0] - 1) + ")";
+          return fail(IETI_ERR_NOT_SPD);
+        }
+    }
+    if (maxH > 0) {
+      dim3 g((unsigned)std::min<int64_t>(grid_for(maxH, 256), 4096), nbt);
+      if (f32)
+        k_extract_ops<float, float><<<g, 256, 0, d->stream>>>(Df, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                              d->npp + s0, d->ldb + s0, d->ldp + s0, d->hoff + s0,
+                                                              d->qoff + s0, (float *)d->H, (float *)d->Q);
+      else if (d->mixed)
+        k_extract_ops<double, float><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                               d->npp + s0, d->ldb + s0, d->ldp + s0, d->hoff + s0,
+                                                               d->qoff + s0, (float *)d->H, (float *)d->Q);
+      else
+        k_extract_ops<double, double><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                                d->npp + s0, d->ldb + s0, d->ldp + s0, d->hoff + s0,
+                                                                d->qoff + s0, (double *)d->H, (double *)d->Q);
+      d->launches_setup++;
+    }
+    if (maxIG > 0) {
+      dim3 g((unsigned)std::min<int64_t>(grid_for(maxIG, 256), 4096), nbt);
+      if (f32)
+        k_extract_IG<float, float><<<g, 256, 0, d->stream>>>(Df, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                             d->npp + s0, d->ldi + s0, d->ldg + s0, d->igoff + s0,
+                                                             d->gtoff + s0, (float *)d->IG, (float *)d->GT);
+      else if (d->mixed)
+        k_extract_IG<double, float><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                              d->npp + s0, d->ldi + s0, d->ldg + s0, d->igoff + s0,
+                                                              d->gtoff + s0, (float *)d->IG, (float *)d->GT);
+      else
+        k_extract_IG<double, double><<<g, 256, 0, d->stream>>>(D, dboff + s0, dnn + s0, d->ni + s0, d->nb + s0,
+                                                               d->npp + s0, d->ldi + s0, d->ldg + s0, d->igoff + s0,
+                                                               d->gtoff + s0, (double *)d->IG, (double *)d->GT);
+      d->launches_setup++;
+    }
+    // coarse contributions C_s of the batch (one launch per patch, in patch order)
+    for (int s = s0; s < s1 && nc > 0; ++s) {
+      if (hnp[s] == 0) continue;
+      const int64_t cnt = (int64_t)hnp[s] * hnp[s];
+      for (int lin = 0; lin < (d->nl_np > 0 && !is_nl[s] ? 2 : 1); ++lin) {
+        double *dst = lin ? d->sc_lin : Sc;
+        const int64_t ldd = lin ? nc : ldS;
+        if (f32)
+          k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hboff[s], hnn[s], hni[s], hnb[s],
+                                                                         hnp[s], d->pc + hpofs[s], dst, ldd);
+        else
+          k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hboff[s], hnn[s], hni[s], hnb[s],
+                                                                          hnp[s], d->pc + hpofs[s], dst, ldd);
+        d->launches_setup++;
+      }
+    }
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(d->stream));
+  cudaFree(Dv);
+  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), Dv));
+  d->bytes -= arena_elems * (int64_t)dsz;
+  // ---------------- coarse: S_c = sum_s A_s^T C_s A_s, factored along the nested
+  // dissection, or inverted through [[S_c, I], [I, 0]]
+  if (nc > 0 && d->coarse_nd) {
+    auto tc0 = std::chrono::steady_clock::now();
+    rc = coarse_nd_factor(d, *tree, Sc, err);
     if (rc == IETI_OK && d->mixed) {
       // the mixed path streams the blocks as (hi, lo) FP32 pairs (in place: same 8 bytes)
       const int64_t n = d->nd_z_elems + d->nd_lt_elems;
       k_split_pairs<<<grid_for(n, 256), 256, 0, d->stream>>>(n, d->nd_Z, (float2 *)d->nd_Z);
       d->launches_setup++;
     }
-    if (e0 != cudaSuccess) err = std::string("coarse assembly failed: ") + cudaGetErrorString(e0);
     cudaStreamSynchronize(d->stream);
     cudaFree(Sc);
+    d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
+    d->bytes -= (int64_t)(ldS * ldS) * 8;
     if (rc) return fail(rc);
     d->t_coarse_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
-  } else if (d->NC > 0) {
-    int64_t nc = d->NC, ldc = 2 * nc;
-    double *Sc = nullptr;
-    if ((rc = dalloc(d, &Sc, (size_t)(ldc * ldc), err))) return fail(rc);
-    CK(cudaMemsetAsync(Sc, 0, (size_t)(ldc * ldc) * sizeof(double), d->stream));
-    for (int s = 0; s < np_; ++s) {
-      if (hnp[s] == 0) continue;
-      int64_t cnt = (int64_t)hnp[s] * hnp[s];
-      if (f32)
-        k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s], hnp[s],
-                                                                       d->pc + hpofs[s], Sc, ldc);
-      else
-        k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
-                                                                        hnp[s], d->pc + hpofs[s], Sc, ldc);
-      d->launches_setup++;
-    }
-    k_coarse_identity<<<grid_for(nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldc);
-    if (d->nl_np > 0) {
-      // the linear patches' part of S_c, kept for the refactorizations
-      if ((rc = dalloc(d, &d->sc_lin, (size_t)(nc * nc), err))) return fail(rc);
-      CK(cudaMemsetAsync(d->sc_lin, 0, (size_t)(nc * nc) * sizeof(double), d->stream));
-      std::vector<uint8_t> is_nl(np_, 0);
-      for (int sg : hs.nl.patches) is_nl[sg] = 1;
-      for (int s = 0; s < np_; ++s) {
-        if (hnp[s] == 0 || is_nl[s]) continue;
-        int64_t cnt = (int64_t)hnp[s] * hnp[s];
-        if (f32)
-          k_coarse_add<float><<<grid_for(cnt, 256), 256, 0, d->stream>>>(Df, hdoff[s], hnn[s], hni[s], hnb[s],
-                                                                         hnp[s], d->pc + hpofs[s], d->sc_lin, nc);
-        else
-          k_coarse_add<double><<<grid_for(cnt, 256), 256, 0, d->stream>>>(D, hdoff[s], hnn[s], hni[s], hnb[s],
-                                                                          hnp[s], d->pc + hpofs[s], d->sc_lin, nc);
-      }
-    }
+  } else if (nc > 0) {
+    k_coarse_identity<<<grid_for(nc, 256), 256, 0, d->stream>>>((int)nc, Sc, ldS);
     if ((rc = coarse_factor(d, Sc, err))) return fail(rc);
     CK(cudaStreamSynchronize(d->stream));
     if (d->nl_np > 0) {
@@ -3633,19 +3676,11 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     } else {
       cudaFree(Sc);
       d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
-      d->bytes -= (int64_t)(ldc * ldc) * 8;
+      d->bytes -= (int64_t)(ldS * ldS) * 8;
     }
   }
   CK(cudaStreamSynchronize(d->stream));
   CK(cudaGetLastError());
-  {
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, d->ev0, d->ev1));
-    d->t_factor_ms = ms;
-  }
-  cudaFree(Dv);
-  d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), Dv));
-  d->bytes -= hdoff[np_] * (int64_t)dsz;
   // algorithmic bytes of one PCG iteration: H and Psi once each (F apply), P once
   // (preconditioner), S_c^{-1} once, plus the lambda / B-space vectors
   d->bytes_iter = (int64_t)esz * (hh[np_] + hq[np_] + hp[np_]) +
@@ -3900,6 +3935,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->coarse_levels = d->coarse_nd ? d->nd_H + std::max(d->nd_D - 1, 0) : (d->NC > 0 ? 1 : 0);
   info->coarse_bytes = d->coarse_nd ? d->nd_bytes : 8.0 * (double)d->NC * d->NC;
   info->t_coarse_ms = d->t_coarse_ms;
+  info->factor_batches = d->factor_batches;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
@@ -3907,6 +3943,15 @@ void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
   for (int c = 0; c < IETI_K_NCLASS; ++c) out[c] = d->kstat[c];
   if (reset)
     for (int c = 0; c < IETI_K_NCLASS; ++c) d->kstat[c] = ieti_kernel_stat{};
+}
+
+void device_coarse_level_times(DeviceState *d, double *us, int n, bool reset) {
+  const int nl = std::min(TRACE_ND, d->coarse_nd ? d->nd_H + std::max(d->nd_D - 1, 0) : 0);
+  for (int k = 0; k < n; ++k) us[k] = (k < nl && d->trace_nd_n) ? d->trace_nd[k] / d->trace_nd_n : 0.0;
+  if (reset) {
+    for (double &v : d->trace_nd) v = 0;
+    d->trace_nd_n = 0;
+  }
 }
 
 void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, double *sub_us, bool reset) {

@@ -20,6 +20,7 @@ int device_set_state(DeviceState *d, const double *a, int64_t len, int mem, std:
 void device_info(const DeviceState *d, ieti_info *info);
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset);
 void device_pcg_trace(DeviceState *d, double *work_us, double *wait_us, double *sub_us, bool reset);
+void device_coarse_level_times(DeviceState *d, double *us, int n, bool reset);
 void device_destroy(DeviceState *d);
 int device_potrf_batched(int batch, double *base, const int64_t *off, const int32_t *n, const int32_t *npiv,
                          int32_t *status, cudaStream_t st, std::string &err);

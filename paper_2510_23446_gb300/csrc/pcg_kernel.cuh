@@ -103,7 +103,9 @@ constexpr int TRACE_IT = 16;
 // barrier wait (ph = 0..5), [14] start of the iteration, and for the streaming phases
 // (P1, P3, P4, P5 = sub 0..3) [16 + 3 sub + k]: k = 0 first segment staged, k = 1
 // first operator chunk arrived, k = 2 last row done
-constexpr int TRACE_SLOTS = 32;
+// [32 + lv]: end of nested-dissection level lv of the coarse solve (after its barrier)
+constexpr int TRACE_SLOTS = 64;
+constexpr int TRACE_ND = 32;
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -320,36 +322,45 @@ __device__ __noinline__ void chunk_rows_g(const T *A, int ld, int cn, const T *x
 }
 
 // y[r] = A_r . x for a chunk of fewer than 16 long rows (more than 32 16-byte units
-// each): every thread of the CTA takes a stride of the units of up to 4 rows at a time
-// (a warp reads 512 contiguous bytes of a row: no bank conflicts), partial sums are
-// reduced over the warp and then over the warps through part[] (32 entries).
+// each): a warp per row (rows w, w + 8 for cn >= 8), or, for cn < 8, wpr = 8 / cn
+// (rounded down to a power of two) warps per row, each on a slice of its units, with
+// one exchange of the partial sums through part[] (8 entries) and one CTA barrier.
+// Lanes read consecutive 16-byte units: no bank conflicts.
 template <class T>
 __device__ __noinline__ void chunk_rows_wide(const T *A, int ld, int cn, const T *xs, T *y, T *part) {
   using V = typename V16<T>::t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nv = ld / V16<T>::n;
   const V *x = reinterpret_cast<const V *>(xs);
-  for (int r0 = 0; r0 < cn; r0 += 4) {
-    const int nr = min(4, cn - r0);
-    T acc[4] = {0, 0, 0, 0};
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      const V xv = x[k];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < nr) acc[i] = fma16(reinterpret_cast<const V *>(A + (int64_t)(r0 + i) * ld)[k], xv, acc[i]);
+  int wpr = 1;
+  while (wpr * 2 * cn <= nw) wpr *= 2;
+  const int rows_per_pass = nw / wpr;
+  for (int rb = 0; rb < cn; rb += rows_per_pass) {
+    const int r = rb + warp / wpr, j = warp % wpr;
+    T s0 = 0, s1 = 0;
+    if (r < cn) {
+      const V *row = reinterpret_cast<const V *>(A + (int64_t)r * ld);
+      const int step = 32 * wpr;
+      int k = j * 32 + lane;
+      for (; k + step < nv; k += 2 * step) {
+        s0 = fma16(row[k], x[k], s0);
+        s1 = fma16(row[k + step], x[k + step], s1);
+      }
+      if (k < nv) s0 = fma16(row[k], x[k], s0);
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const T v = warp_red_t(acc[i]);
-      if (lane == 0) part[warp * 4 + i] = v;
+    const T v = warp_red_t(s0 + s1);
+    if (wpr == 1) {
+      if (lane == 0 && r < cn) y[r] = v;
+    } else {
+      if (lane == 0) part[warp] = v;
+      __syncthreads();
+      if ((int)threadIdx.x < rows_per_pass && rb + (int)threadIdx.x < cn) {
+        T t = 0;
+        for (int q = 0; q < wpr; ++q) t += part[threadIdx.x * wpr + q];
+        y[rb + threadIdx.x] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if ((int)threadIdx.x < nr) {
-      T t = 0;
-      for (int w = 0; w < nw; ++w) t += part[w * 4 + threadIdx.x];
-      y[r0 + threadIdx.x] = t;
-    }
-    __syncthreads();
   }
 }
 
@@ -398,33 +409,44 @@ __device__ __noinline__ void chunk_rows_df(const float2 *A, int ld, int cn, cons
   }
 }
 
-// the same for chunks of fewer than 16 long rows: the whole CTA on up to 4 rows at a time
+// the same for chunks of fewer than 16 long rows of (hi, lo) pairs: warps per row as in
+// chunk_rows_wide, FP64 partial sums
 __device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn, const float2 *xs, double *y,
                                                 double *part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nv = ld / 2;
   const float4 *x = reinterpret_cast<const float4 *>(xs);
-  for (int r0 = 0; r0 < cn; r0 += 4) {
-    const int nr = min(4, cn - r0);
-    float S[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      const float4 xv = x[k];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < nr) df_acc(S[i], c[i], reinterpret_cast<const float4 *>(A + (int64_t)(r0 + i) * ld)[k], xv);
+  int wpr = 1;
+  while (wpr * 2 * cn <= nw) wpr *= 2;
+  const int rows_per_pass = nw / wpr;
+  for (int rb = 0; rb < cn; rb += rows_per_pass) {
+    const int r = rb + warp / wpr, j = warp % wpr;
+    double v = 0.0;
+    if (r < cn) {
+      const float4 *row = reinterpret_cast<const float4 *>(A + (int64_t)r * ld);
+      float S0 = 0.f, c0 = 0.f, S1 = 0.f, c1 = 0.f;
+      const int step = 32 * wpr;
+      int k = j * 32 + lane;
+      for (; k + step < nv; k += 2 * step) {
+        df_acc(S0, c0, row[k], x[k]);
+        df_acc(S1, c1, row[k + step], x[k + step]);
+      }
+      if (k < nv) df_acc(S0, c0, row[k], x[k]);
+      v = ((double)S0 + (double)c0) + ((double)S1 + (double)c1);
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const double v = warp_red((double)S[i] + (double)c[i]);
-      if (lane == 0) part[warp * 4 + i] = v;
+    v = warp_red(v);
+    if (wpr == 1) {
+      if (lane == 0 && r < cn) y[r] = v;
+    } else {
+      if (lane == 0) part[warp] = v;
+      __syncthreads();
+      if ((int)threadIdx.x < rows_per_pass && rb + (int)threadIdx.x < cn) {
+        double t = 0;
+        for (int q = 0; q < wpr; ++q) t += part[threadIdx.x * wpr + q];
+        y[rb + threadIdx.x] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if ((int)threadIdx.x < nr) {
-      double t = 0;
-      for (int w = 0; w < nw; ++w) t += part[w * 4 + threadIdx.x];
-      y[r0 + threadIdx.x] = t;
-    }
-    __syncthreads();
   }
 }
 
@@ -865,6 +887,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
         cur = prefetch(ring, nd_op(lv + 1));
         if (!sync(nullptr)) return false;
       }
+      if (tsub && threadIdx.x == 0 && lv < TRACE_ND) tsub[16 + lv] = gtimer();  // tsub = trace row + 16
     }
     return true;
   };

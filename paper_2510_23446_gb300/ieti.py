@@ -44,7 +44,7 @@ class ieti_options(C.Structure):
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
                 ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
                 ("graph", C.c_int32), ("wait_limit", C.c_int32), ("coarse", C.c_int32),
-                ("coarse_leaf", C.c_int32)]
+                ("coarse_leaf", C.c_int32), ("factor_arena_mb", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -80,7 +80,7 @@ class ieti_info(C.Structure):
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
                 ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32), ("coarse_mode", C.c_int32),
                 ("coarse_nodes", C.c_int32), ("coarse_levels", C.c_int32), ("coarse_bytes", C.c_double),
-                ("t_coarse_ms", C.c_double)]
+                ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32)]
 
 
 _ctx = C.c_void_p
@@ -102,6 +102,7 @@ lib.ieti_set_state.argtypes = [_ctx, C.c_void_p, C.c_int64, C.c_int32]
 lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
 lib.ieti_coarse_tree.argtypes = [_ctx, C.POINTER(C.c_int32), C.POINTER(C.c_int64)] + [C.c_void_p] * 6
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+lib.ieti_coarse_level_times.argtypes = [_ctx, C.c_void_p, C.c_int32, C.c_int32]
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
 lib.ieti_potrf_batched_noalloc.argtypes = lib.ieti_potrf_batched.argtypes
@@ -116,7 +117,7 @@ EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", 
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
             "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32",
-            "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree"]
+            "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree", "ieti_coarse_level_times"]
 
 
 class IetiError(RuntimeError):
@@ -142,7 +143,7 @@ class Solver:
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
-                 graph=1, wait_limit=0, coarse="auto", coarse_leaf=0):
+                 graph=1, wait_limit=0, coarse="auto", coarse_leaf=0, factor_arena_mb=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -189,6 +190,7 @@ class Solver:
         op.wait_limit = int(wait_limit)
         op.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
         op.coarse_leaf = int(coarse_leaf)
+        op.factor_arena_mb = int(factor_arena_mb)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
         self.options = op
@@ -281,6 +283,11 @@ class Solver:
         self._check(lib.ieti_pcg_phase_times(self.ctx, work.ctypes.data, wait.ctypes.data, sub.ctypes.data,
                                              int(reset)))
         return {"work_us": work.tolist(), "wait_us": wait.tolist(), "sub_us": sub.reshape(4, 3).tolist()}
+
+    def coarse_level_times(self, reset=False, n=32):
+        us = np.zeros(n)
+        self._check(lib.ieti_coarse_level_times(self.ctx, us.ctypes.data, n, int(reset)))
+        return us[:self.info()["coarse_levels"]].tolist()
 
     def step(self, j, raise_on_error=True):
         p, mem = _ptr(j)

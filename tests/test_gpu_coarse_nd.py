@@ -72,3 +72,22 @@ def test_nd_option_validation(ieti):
     with pytest.raises(ieti.IetiError) as e:
         ieti.Solver.from_problem(prob, device=0, coarse="nd", pcg_mode=1, **OPTS["fp64"])
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["ragged_p23", "c4_family"])
+def test_batched_factorization_equals_one_batch(ieti, name, mode):
+    """The patch blocks factored in batches that reuse one arena (a 1 MiB budget: a few
+    patches per batch) give the operators of the one-batch factorization: same states
+    (same arithmetic per patch, coarse contributions added in the same patch order)."""
+    prob, op, ref = oracle_run(name, 2)
+    S = ieti.Solver.from_problem(prob, device=0, precond="dirichlet_stiff", factor_arena_mb=1, **OPTS[mode])
+    nb = S.info()["factor_batches"]
+    S.close()
+    assert nb > 1
+    kw = dict(precond="dirichlet_stiff", **OPTS[mode])
+    a1, _ = gpu_run(ieti, prob, 2, **kw)
+    ab, _ = gpu_run(ieti, prob, 2, factor_arena_mb=1, **kw)
+    for x, y, r in zip(a1, ab, ref):
+        assert np.array_equal(x, y)
+        assert np.linalg.norm(y - r) <= TOL[mode] * np.linalg.norm(r)
