@@ -983,7 +983,7 @@ struct DeviceState {
   // update buffer, the gather lists, and the rows of every level per CTA
   int coarse_nd = 0, nd_cw = 1, nd_H = 0, nd_D = 0, nd_nodes = 0, nd_zmax = 0;
   int32_t *nd_k0 = nullptr, *nd_nk = nullptr, *nd_ns = nullptr, *nd_zld = nullptr, *nd_ltld = nullptr,
-          *nd_sidx = nullptr, *nd_src = nullptr;
+          *nd_sidx = nullptr, *nd_src = nullptr, *nd_nch = nullptr;
   int64_t *nd_zoff = nullptr, *nd_ltoff = nullptr, *nd_soff = nullptr, *nd_uoff = nullptr, *nd_srcoff = nullptr;
   double *nd_Z = nullptr, *nd_Lt = nullptr, *nd_u = nullptr;
   int32_t *ndf_ptr = nullptr, *ndf_s = nullptr, *ndf_r0 = nullptr, *ndf_r1 = nullptr;
@@ -1489,13 +1489,15 @@ static int coarse_nd_tables(DeviceState *d, const CoarseTree &t, std::string &er
     d->ndh_fwd[t.height[p]].push_back(p);
     if (t.depth[p] > 0 && t.ns[p] > 0 && t.nk[p] > 0) d->ndh_bwd[t.depth[p] - 1].push_back(p);
   }
-  std::vector<int32_t> sidx(t.s_idx);
+  std::vector<int32_t> sidx(t.s_idx), nch(NN);
   if (sidx.empty()) sidx.push_back(0);
+  for (int p = 0; p < NN; ++p) nch[p] = t.child_ptr[p + 1] - t.child_ptr[p];
   int rc;
   if ((rc = upload(d, &d->nd_k0, t.k0, err)) || (rc = upload(d, &d->nd_nk, d->ndh_nk, err)) ||
       (rc = upload(d, &d->nd_ns, d->ndh_ns, err)) || (rc = upload(d, &d->nd_zld, d->ndh_zld, err)) ||
       (rc = upload(d, &d->nd_ltld, d->ndh_ltld, err)) || (rc = upload(d, &d->nd_sidx, sidx, err)) ||
-      (rc = upload(d, &d->nd_src, src, err)) || (rc = upload(d, &d->nd_zoff, zoff, err)) ||
+      (rc = upload(d, &d->nd_src, src, err)) || (rc = upload(d, &d->nd_nch, nch, err)) ||
+      (rc = upload(d, &d->nd_zoff, zoff, err)) ||
       (rc = upload(d, &d->nd_ltoff, ltoff, err)) || (rc = upload(d, &d->nd_soff, soff, err)) ||
       (rc = upload(d, &d->nd_uoff, uoff, err)) || (rc = upload(d, &d->nd_srcoff, srcoff_w, err)) ||
       (rc = dalloc(d, &d->nd_u, (size_t)std::max<int64_t>(u, 1), err)))
@@ -2198,7 +2200,7 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.coarse_nd = d->coarse_nd;
   a.nd_cw = d->nd_cw; a.nd_H = d->nd_H; a.nd_D = d->nd_D;
   a.nd_k0 = d->nd_k0; a.nd_nk = d->nd_nk; a.nd_ns = d->nd_ns; a.nd_zld = d->nd_zld; a.nd_ltld = d->nd_ltld;
-  a.nd_sidx = d->nd_sidx; a.nd_src = d->nd_src;
+  a.nd_sidx = d->nd_sidx; a.nd_src = d->nd_src; a.nd_nch = d->nd_nch;
   a.nd_zoff = d->nd_zoff; a.nd_ltoff = d->nd_ltoff; a.nd_soff = d->nd_soff; a.nd_uoff = d->nd_uoff;
   a.nd_srcoff = d->nd_srcoff;
   a.nd_Z = d->nd_Z; a.nd_Lt = d->nd_Lt; a.nd_u = d->nd_u;

@@ -90,7 +90,7 @@ struct PcgArgs {
   // (u_p in ubuf at uoff, the child updates gathered through src: cw entries per front
   // position, -1 = none).  Backward, by depth: q_K -= Lt_p q_S.
   int coarse_nd, nd_cw, nd_H, nd_D;
-  const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_src;
+  const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_src, *nd_nch;
   const int64_t *nd_zoff, *nd_ltoff, *nd_soff, *nd_uoff, *nd_srcoff;
   const double *nd_Z, *nd_Lt;
   double *nd_u;
@@ -829,8 +829,9 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   };
   // the child updates gathered into front position i of node p
   auto nd_gather = [&](int p, int i) {
-    const int32_t *src = a.nd_src + a.nd_srcoff[p] + (int64_t)i * a.nd_cw;
     double v = 0.0;
+    if (a.nd_nch[p] == 0) return v;  // a leaf: no child updates
+    const int32_t *src = a.nd_src + a.nd_srcoff[p] + (int64_t)i * a.nd_cw;
     for (int w = 0; w < a.nd_cw; ++w) {
       const int32_t u = src[w];
       if (u >= 0) v += ldcg(a.nd_u + u);
