@@ -215,6 +215,11 @@ int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTre
       CoarseTree c;
       int rc = build_coarse_tree(hs, leaf, top, c, err);
       if (rc) return rc;
+      // blocks wider than 2048 unknowns leave a ring stage of the solve a single row:
+      // only the candidate without merged top levels may have them
+      int widest = 0;
+      for (int p = 0; p < c.n_nodes; ++p) widest = std::max({widest, c.nk[p], c.ns[p]});
+      if (top > 0 && widest > 2048) continue;
       const double model = coarse_tree_bytes(c) / bw + coarse_tree_levels(c) * latency;
       if (!any || model < best * (1.0 - 1e-9)) {
         best = model;

@@ -2912,7 +2912,7 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
   const int iters = 16;
   std::vector<PcgSched> cand;
   for (int cps = 1; cps <= PCG_MAX_CPS; ++cps)
-    for (int ns = 2; ns <= NS_MAX; ++ns)
+    for (int ns : {2, 3, 4, 6})
       for (size_t kb : {16, 24, 32, 48, 64, 96}) cand.push_back({cps, ns, kb * 1024});
   cand.push_back(rule);
   double best_us = 1e300, rule_us = 1e300;

@@ -456,7 +456,7 @@ __device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn,
 // shared memory in chunks of whole rows through an ns-stage mbarrier ring, and the
 // first chunks of the NEXT phase are issued before the grid barrier that ends the
 // current one (they arrive while the CTA waits).
-constexpr int NS_MAX = 3;
+constexpr int NS_MAX = 6;
 struct Ring {
   unsigned char *stage;   // ns * bytes
   uint64_t *bar;          // ns mbarriers
