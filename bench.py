@@ -34,17 +34,18 @@ WORKLOADS = {
     "c4": dict(desc="c4: unit cube, 7x7x7 curved patches (+-5% interior control points), per-slab elements "
                     "uniform in {4..12} and per-slab degrees in {2,3} (local sizes ~400..9000), conductor or air "
                     "per patch with probability 1/2 (sigma=1e3), nu=1, coil J0=1, dt=1e-3",
-               gen=("c4", {}), horizon=100, outer=OUTER_TOL),
+               gen=("c4", {}), horizon=100, outer=OUTER_TOL, mixed_cg_tol=1e-7),
     "c3": dict(desc="c3: unit cube, 8x8x8 curved patches, p=2, 6^3 elements per patch, sigma log-uniform in "
                     "[1,1e4] per patch within radius 0.35, nu uniform in [0.5,2] per patch, coil J0=1, dt=1e-3",
-               gen=("c3", {}), horizon=100, outer=1e-12),
+               gen=("c3", {}), horizon=100, outer=1e-12, mixed_cg_tol=1e-7),
     "c2": dict(desc="c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
                     "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3",
-               gen=("c2", {}), horizon=50, outer=OUTER_TOL),
+               gen=("c2", {}), horizon=50, outer=OUTER_TOL, mixed_cg_tol=1e-6),
 }
 HEADLINE = "c4"
 # each path with its fastest inner PCG tolerance for the common outer stop (measured on
-# these workloads); both start every step from the time-extrapolated iterate
+# these workloads: the mixed path's per workload, mixed_cg_tol above); both start every
+# step from the time-extrapolated iterate
 OPTS = {
     "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=30,
                   factor="tf32x3", predictor=2, autotune=1, l2_persist=2),
@@ -73,7 +74,8 @@ def parse():
     ap.add_argument("--no-ablation", action="store_true", help="skip the factor-arithmetic ablation")
     ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS), help="the headline workload")
     ap.add_argument("--configs", default="c3,c2", help="comma-separated extra full-size workloads (c2, c3, c4, "
-                                                       "c5_4, c5_6; '' for none), each mixed vs FP64 over a few steps")
+                                                       "c5_4, c5_6, c5_8, c5_10; '' for none), each mixed vs FP64 over "
+                                                       "a few steps")
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps per extra workload and path")
     ap.add_argument("--profile-step", action="store_true",
                     help="small run for ncu: mixed path only, warm-up steps + 2 steps, no JSON line")
@@ -279,14 +281,21 @@ def _steps(S, torch, jd, zero, K, flush_buf, horizon, ev=None):
     return its, launches, sweeps, st
 
 
-def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer):
+def path_opts(mode, outer, mixed_cg_tol):
+    opts = dict(OPTS[mode], outer_tol=outer)
+    if mode == "mixed":
+        opts["cg_tol"] = mixed_cg_tol
+    return opts
+
+
+def time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer, mixed_cg_tol):
     """The timed run (the library as a user runs it: each step's sweep loop as one CUDA
     graph), then the same K steps on a second context with per-launch CUDA events for
     the kernel-class times and the phase trace (those need the host loop).  Both
     contexts share the autotuner's choice through a cache file."""
     tmpdir = tempfile.mkdtemp(prefix="ieti_bench_")
     cache = os.path.join(tmpdir, "schedule.txt")
-    opts = dict(OPTS[mode], outer_tol=outer)
+    opts = path_opts(mode, outer, mixed_cg_tol)
     t0 = time.perf_counter()
     S = ieti.Solver.from_problem(prob, device=dev, stream=stream, tune_cache=cache, **opts)
     t_setup = S.info()
@@ -486,11 +495,10 @@ def factor_ablation_leg(ieti, torch, prob, dev, stream, n_steps=10):
 # workload's sigma contrast (1 .. 1e4) needs the outer stop at 1e-12 for the two paths
 # to agree to 1e-8
 EXTRA = {
-    **{k: (v["desc"], v["gen"][0], v["gen"][1], v["outer"]) for k, v in WORKLOADS.items()},
-    "c5_4": ("c5 linear, 4x4x4 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
-             "dt=5e-4", "c5", dict(patches_per_dir=4, nonlinear=False), OUTER_TOL),
-    "c5_6": ("c5 linear, 6x6x6 curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 sigma=1e2, "
-             "dt=5e-4", "c5", dict(patches_per_dir=6, nonlinear=False), OUTER_TOL),
+    **{k: (v["desc"], v["gen"][0], v["gen"][1], v["outer"], v["mixed_cg_tol"]) for k, v in WORKLOADS.items()},
+    **{f"c5_{k}": (f"c5 linear, {k}x{k}x{k} curved patches, p=3, 8^3 elements per patch, conductor [0.25,0.75]^3 "
+                   f"sigma=1e2, dt=5e-4", "c5", dict(patches_per_dir=k, nonlinear=False), OUTER_TOL, 1e-6)
+       for k in (4, 6, 8, 10)},
 }
 
 
@@ -499,12 +507,12 @@ def config_leg(ieti, torch, key, dev, stream, flush_buf, K, W=2):
     and K timed steps from a^0 = 0 (L2 flushed between timed steps), states compared."""
     import numpy as np
     from workloads import make_problem
-    desc, name, kw, outer = EXTRA[key]
+    desc, name, kw, outer, mtol = EXTRA[key]
     prob = make_problem(name, **kw)
     out, states = {}, {}
     for mode in ("mixed", "fp64"):
         t0 = time.perf_counter()
-        S = ieti.Solver.from_problem(prob, device=dev, stream=stream, **dict(OPTS[mode], outer_tol=outer, max_sweeps=30))
+        S = ieti.Solver.from_problem(prob, device=dev, stream=stream, **dict(path_opts(mode, outer, mtol), max_sweeps=30))
         t_setup = time.perf_counter() - t0
         inf = S.info()
         jd = torch.from_numpy(S.load_vector(prob.coil)).to(f"cuda:{dev}")
@@ -531,7 +539,8 @@ def config_leg(ieti, torch, key, dev, stream, flush_buf, K, W=2):
         S.close()
         torch.cuda.empty_cache()
     a, b = states["mixed"], states["fp64"]
-    return {"workload": desc, "outer_tol": outer, "n_patches": prob.n_patches, "n_dofs": info["n_dofs"],
+    return {"workload": desc, "outer_tol": outer, "mixed_cg_tol": mtol, "n_patches": prob.n_patches,
+            "n_dofs": info["n_dofs"],
             "n_lambda": info["n_lambda"],
             "n_coarse": info["n_coarse"], "steps": K, "warmup": W, **out,
             "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
@@ -624,7 +633,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         clocks = Clocks(dev) if mode == "mixed" else None
-        S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer)
+        S, r = time_path(ieti, torch, prob, mode, K, W, dev, stream, flush_buf, clocks, horizon, outer,
+                         WL["mixed_cg_tol"])
         results[mode] = (S, r)
     # end-to-end through the public API with host buffers (pinned), mixed path: the same
     # steps as the timed device run (same resets, same L2 flush between steps, both
@@ -697,7 +707,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WL["desc"], "n_dofs": info["n_dofs"], "n_free": info["n_free"],
                    "n_lambda": info["n_lambda"], "n_coarse": info["n_coarse"],
-                   "precond": "dirichlet_stiff", "inner_cg_tol": OPTS["mixed"]["cg_tol"],
+                   "precond": "dirichlet_stiff", "inner_cg_tol": WL["mixed_cg_tol"],
                    "mixed_factor": OPTS["mixed"]["factor"],
                    "fp64_inner_cg_tol": OPTS["fp64"]["cg_tol"], "predictor": "3 a^l - 3 a^(l-1) + a^(l-2) (both paths)",
                    "outer_tol": outer, "l2": "flushed between timed steps (256 MiB write)",

@@ -325,6 +325,27 @@ int ieti_set_state(ieti_ctx *ctx, const double *a, int64_t len, int32_t a_mem);
 int ieti_coarse_tree(const ieti_ctx *ctx, int32_t *n_nodes, int64_t *n_s, int32_t *elim_pos, int32_t *k0,
                      int32_t *nk, int32_t *parent, int64_t *s_off, int32_t *s_idx);
 
+/* Patch-sharded layout of the dual-primal solve for n_ranks ranks (host query, 1 <=
+ * n_ranks <= min(31, patches)).  The patches are independent units (Sec. 3); the
+ * interface problem couples them through the multiplier jumps, the coarse right-hand
+ * side and the PCG dot products.  rank_of_patch[n_patches]: recursive coordinate
+ * bisection of the patch grid balanced by the local sizes.  lam_owner[n_lambda]: the rank
+ * holding the multiplier's lower patch; lam_peer[n_lambda]: the rank of its upper patch
+ * when that is another rank (the multiplier is cut: its partial jump crosses once per
+ * PCG iteration), else -1.  coarse_owner[n_coarse]: the lowest rank holding a copy of
+ * the primal unknown.  Any array may be NULL.  Errors: INVALID_ARG. */
+int ieti_shard_plan(const ieti_ctx *ctx, int32_t n_ranks, int32_t *rank_of_patch, int32_t *lam_owner,
+                    int32_t *lam_peer, int32_t *coarse_owner);
+
+/* Multipliers and patch blocks (host queries): multiplier l joins the interface copy
+ * pos_s[l] of patch s[l] to the copy pos_t[l] of patch t[l] (s < t, lambda = copy in s -
+ * copy in t; positions index the patch's interface block); per patch the block sizes
+ * ni, nb, np (interior, interface, primal copies) and, patch after patch, the coarse
+ * unknown of every primal copy (coarse ids ascending with the primal edges).  Arrays of
+ * n_lambda, n_patches and sum np entries; any may be NULL.  Errors: INVALID_ARG. */
+int ieti_multipliers(const ieti_ctx *ctx, int32_t *s, int32_t *pos_s, int32_t *t, int32_t *pos_t);
+int ieti_patch_blocks(const ieti_ctx *ctx, int32_t *ni, int32_t *nb, int32_t *np, int32_t *coarse_of_copy);
+
 /* Per-class kernel statistics accumulated since the last reset (options.profile = 1);
  * out has IETI_K_NCLASS entries.  reset != 0 clears the counters after reading. */
 int ieti_kernel_stats(ieti_ctx *ctx, ieti_kernel_stat *out, int32_t reset);

@@ -8,6 +8,7 @@
 
 #include "device.h"
 #include "host_setup.h"
+#include "shard.h"
 
 struct ieti_ctx {
   ieti::HostSetup hs;
@@ -295,6 +296,54 @@ int ieti_coarse_tree(const ieti_ctx *ctx, int32_t *n_nodes, int64_t *n_s, int32_
   if (s_off)
     for (int p = 0; p <= t.n_nodes; ++p) s_off[p] = t.n_nodes ? t.s_off[p] : 0;
   if (s_idx) std::copy(t.s_idx.begin(), t.s_idx.end(), s_idx);
+  return IETI_OK;
+}
+
+int ieti_shard_plan(const ieti_ctx *ctx, int32_t n_ranks, int32_t *rank_of_patch, int32_t *lam_owner,
+                    int32_t *lam_peer, int32_t *coarse_owner) {
+  if (!ctx) return IETI_ERR_INVALID_ARG;
+  try {
+    ieti::ShardPlan plan;
+    std::string e;
+    int rc = ieti::build_shard_plan(ctx->hs, n_ranks, plan, e);
+    if (rc) {
+      const_cast<ieti_ctx *>(ctx)->err = e;
+      return rc;
+    }
+    if (rank_of_patch) std::copy(plan.rank_of_patch.begin(), plan.rank_of_patch.end(), rank_of_patch);
+    if (lam_owner) std::copy(plan.lam_owner.begin(), plan.lam_owner.end(), lam_owner);
+    if (lam_peer) std::copy(plan.lam_peer.begin(), plan.lam_peer.end(), lam_peer);
+    if (coarse_owner) std::copy(plan.coarse_owner.begin(), plan.coarse_owner.end(), coarse_owner);
+  } catch (...) {
+    const_cast<ieti_ctx *>(ctx)->err = "ieti_shard_plan: host allocation failed";
+    return IETI_ERR_OOM;
+  }
+  return IETI_OK;
+}
+
+int ieti_multipliers(const ieti_ctx *ctx, int32_t *s, int32_t *pos_s, int32_t *t, int32_t *pos_t) {
+  if (!ctx) return IETI_ERR_INVALID_ARG;
+  const auto &L = ctx->hs.lam;
+  for (size_t l = 0; l < L.size(); ++l) {
+    if (s) s[l] = L[l].s;
+    if (pos_s) pos_s[l] = L[l].pos_s;
+    if (t) t[l] = L[l].t;
+    if (pos_t) pos_t[l] = L[l].pos_t;
+  }
+  return IETI_OK;
+}
+
+int ieti_patch_blocks(const ieti_ctx *ctx, int32_t *ni, int32_t *nb, int32_t *np, int32_t *coarse_of_copy) {
+  if (!ctx) return IETI_ERR_INVALID_ARG;
+  int64_t k = 0;
+  for (size_t p = 0; p < ctx->hs.patches.size(); ++p) {
+    const ieti::Patch &pt = ctx->hs.patches[p];
+    if (ni) ni[p] = pt.ni;
+    if (nb) nb[p] = pt.nb;
+    if (np) np[p] = pt.np;
+    for (int q = pt.ni + pt.nb; q < pt.ni + pt.nb + pt.np; ++q, ++k)
+      if (coarse_of_copy) coarse_of_copy[k] = (int32_t)ctx->hs.coarse_of_edge[pt.kept_glob[q]];
+  }
   return IETI_OK;
 }
 

@@ -103,6 +103,9 @@ lib.ieti_kernel_stats.argtypes = [_ctx, C.c_void_p, C.c_int32]
 lib.ieti_coarse_tree.argtypes = [_ctx, C.POINTER(C.c_int32), C.POINTER(C.c_int64)] + [C.c_void_p] * 6
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_coarse_level_times.argtypes = [_ctx, C.c_void_p, C.c_int32, C.c_int32]
+lib.ieti_shard_plan.argtypes = [_ctx, C.c_int32] + [C.c_void_p] * 4
+lib.ieti_multipliers.argtypes = [_ctx] + [C.c_void_p] * 4
+lib.ieti_patch_blocks.argtypes = [_ctx] + [C.c_void_p] * 4
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]
 lib.ieti_potrf_batched_noalloc.argtypes = lib.ieti_potrf_batched.argtypes
@@ -117,7 +120,8 @@ EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", 
             "ieti_dof_classes", "ieti_patch_csr", "ieti_step", "ieti_solution", "ieti_set_state",
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
             "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32",
-            "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree", "ieti_coarse_level_times"]
+            "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree", "ieti_coarse_level_times",
+            "ieti_shard_plan", "ieti_multipliers", "ieti_patch_blocks"]
 
 
 class IetiError(RuntimeError):
@@ -200,6 +204,7 @@ class Solver:
         if rc != 0:
             raise IetiError(rc, lib.ieti_setup_error().decode())
         self.n = int(lib.ieti_num_dofs(self.ctx))
+        self._P = tuple(int(x) for x in P)
 
     @classmethod
     def from_problem(cls, prob, **kw):
@@ -283,6 +288,33 @@ class Solver:
         self._check(lib.ieti_pcg_phase_times(self.ctx, work.ctypes.data, wait.ctypes.data, sub.ctypes.data,
                                              int(reset)))
         return {"work_us": work.tolist(), "wait_us": wait.tolist(), "sub_us": sub.reshape(4, 3).tolist()}
+
+    def shard_plan(self, n_ranks):
+        """ieti_shard_plan: rank of every patch, owner and peer rank of every multiplier,
+        owner of every coarse unknown."""
+        inf = self.info()
+        npat = int(np.prod(self._P))
+        rop = np.zeros(npat, dtype=np.int32)
+        own = np.zeros(inf["n_lambda"], dtype=np.int32)
+        peer = np.zeros(inf["n_lambda"], dtype=np.int32)
+        cown = np.zeros(max(inf["n_coarse"], 1), dtype=np.int32)
+        self._check(lib.ieti_shard_plan(self.ctx, int(n_ranks), rop.ctypes.data, own.ctypes.data, peer.ctypes.data,
+                                        cown.ctypes.data))
+        return dict(rank_of_patch=rop, lam_owner=own, lam_peer=peer, coarse_owner=cown[:inf["n_coarse"]])
+
+    def multipliers(self):
+        m = self.info()["n_lambda"]
+        out = [np.zeros(m, dtype=np.int32) for _ in range(4)]
+        self._check(lib.ieti_multipliers(self.ctx, *[a.ctypes.data for a in out]))
+        return dict(zip(("s", "pos_s", "t", "pos_t"), out))
+
+    def patch_blocks(self):
+        npat = int(np.prod(self._P))
+        ni, nb, np_ = (np.zeros(npat, dtype=np.int32) for _ in range(3))
+        self._check(lib.ieti_patch_blocks(self.ctx, ni.ctypes.data, nb.ctypes.data, np_.ctypes.data, None))
+        cc = np.zeros(max(int(np_.sum()), 1), dtype=np.int32)
+        self._check(lib.ieti_patch_blocks(self.ctx, None, None, None, cc.ctypes.data))
+        return dict(ni=ni, nb=nb, np=np_, coarse_of_copy=cc[:int(np_.sum())])
 
     def coarse_level_times(self, reset=False, n=32):
         us = np.zeros(n)

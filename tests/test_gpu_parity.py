@@ -280,3 +280,32 @@ def test_predictor_history_reset_by_set_state(ieti):
     R.step(j)
     assert np.linalg.norm(R.solution() - end) <= TOL["fp64"] * np.linalg.norm(end)
     R.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_c2_bench_options_match_oracle_monolithic(ieti, c2_oracle, mode):
+    """The 64-patch workload with the bench's exact options (stiffness-scaled Dirichlet,
+    quadratic time predictor, autotuned schedule, L2 hints, sweep loop as a CUDA graph,
+    TF32x3 tensor-core factors in the mixed path), element by element against the
+    oracle's monolithic sparse direct solve of Eq. (11) over three steps from a^0 = 0."""
+    prob, op = c2_oracle
+    steps = 3
+    ref = op.run_monolithic(steps)
+    opts = {"fp64": dict(precision="fp64", cg_tol=1e-11),
+            "mixed": dict(precision="mixed", cg_tol=1e-6, factor="tf32x3")}[mode]
+    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", outer_tol=1e-11, max_sweeps=30, predictor=2,
+                         autotune=1, l2_persist=2, graph=1, **opts)
+    for l, (a, b) in enumerate(zip(ref, got)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(a)
+        assert err <= TOL[mode], (mode, l, err, stats[l])
+
+
+@pytest.mark.parametrize("name", ["c3_family", "c4_family"])
+def test_autotuned_schedule_matches_oracle(ieti, name):
+    """The autotuned schedule of the persistent kernel (CTAs, ring stages and stage
+    bytes timed at setup) against the oracle, not only against the rule's schedule."""
+    prob, op, ref = oracle_run(name, 3)
+    for mode in ("fp64", "mixed"):
+        got, stats = gpu_run(ieti, prob, 3, precond="dirichlet_stiff", autotune=1, **OPTS[mode])
+        for l, (a, b) in enumerate(zip(ref, got)):
+            assert np.linalg.norm(a - b) <= TOL[mode] * np.linalg.norm(a), (name, mode, l, stats[l])
