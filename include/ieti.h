@@ -237,6 +237,8 @@ typedef struct {
   double coarse_bytes;       /* algorithmic bytes of one coarse solve */
   double t_coarse_ms;        /* host time of the coarse assembly and factorization at setup */
   int32_t factor_batches;    /* patch batches of the setup factorization */
+  int32_t pcg_seg_weight;    /* per-segment weight of the persistent kernel's row partitions (elements; the
+                                autotuner tries a few, 0 by the rule) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */
@@ -362,10 +364,12 @@ int ieti_pcg_phase_times(ieti_ctx *ctx, double *work_us, double *wait_us, double
 
 /* Per-level timing of the nested-dissection coarse solve (options.profile = 1, coarse
  * mode ND): mean over the traced PCG iterations of CTA 0's time in each level of one
- * coarse solve (forward levels by height, then backward levels by depth), from the end
- * of the previous level's grid barrier to the end of this level's, in microseconds
- * (%globaltimer).  us receives n entries (0 beyond the tree's levels).  reset != 0 clears
- * the accumulators.  Errors: INVALID_ARG, NO_DEVICE. */
+ * coarse solve (forward levels by height, then backward levels by depth), in
+ * microseconds (%globaltimer): entries 4 lv .. 4 lv + 3 of level lv hold the staging of
+ * its first vector segment (from the end of the previous level's barrier), the wait for
+ * its first operator chunk, the rows, and the wait at its grid barrier.  us receives n
+ * entries (0 beyond the tree's levels).  reset != 0 clears the accumulators.  Errors:
+ * INVALID_ARG, NO_DEVICE. */
 int ieti_coarse_level_times(ieti_ctx *ctx, double *us, int32_t n, int32_t reset);
 
 /* Batched dense partial Cholesky, the kernel family behind both Schur complements

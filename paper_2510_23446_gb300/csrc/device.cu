@@ -881,6 +881,7 @@ struct DeviceState {
   int32_t *bseg_ptr = nullptr, *bseg_s = nullptr, *bseg_r0 = nullptr, *bseg_r1 = nullptr;
   int32_t *qseg_ptr = nullptr, *qseg_s = nullptr, *qseg_r0 = nullptr, *qseg_r1 = nullptr;
   int psi_overhead = 0;  // > 0: the Psi rows have their own partition (per-row overhead in elements)
+  int seg_overhead = 0;  // per-segment weight of the row partitions (elements)
   int32_t *iseg_ptr = nullptr, *iseg_s = nullptr, *iseg_r0 = nullptr, *iseg_r1 = nullptr;
   int32_t *tseg_ptr = nullptr, *tseg_s = nullptr, *tseg_r0 = nullptr, *tseg_r1 = nullptr;
   double *kg = nullptr, *ub1 = nullptr, *uz = nullptr;
@@ -907,7 +908,7 @@ struct DeviceState {
   double trace_acc[8] = {};   // summed per-phase time (us) over traced iterations: work P1..P6, waits
   double trace_wait[8] = {};
   double trace_sub[4][3] = {};  // P1, P3, P4, P5: staging, first chunk, rows (us)
-  double trace_nd[TRACE_ND] = {};  // nested-dissection levels of the coarse solve (us, incl. barrier)
+  double trace_nd[TRACE_ND][4] = {};  // nested-dissection levels: staging, first chunk, rows, barrier (us)
   int64_t trace_nd_n = 0;
   int64_t trace_sub_n[4] = {};
   int64_t trace_n = 0;
@@ -2277,12 +2278,20 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
         d->trace_wait[ph] += (t[2 * ph + 1] - t[2 * ph]) * 1e-3;
         prev = t[2 * ph + 1];
       }
-      if (d->coarse_nd && t[32]) {
+      if (d->coarse_nd && t[35]) {
         unsigned long long prev_nd = t[3];  // the coarse phase starts after the P2 barrier
         const int nl = std::min(TRACE_ND, d->nd_H + std::max(d->nd_D - 1, 0));
-        for (int lv = 0; lv < nl && t[32 + lv]; ++lv) {
-          d->trace_nd[lv] += (t[32 + lv] - prev_nd) * 1e-3;
-          prev_nd = t[32 + lv];
+        for (int lv = 0; lv < nl && t[32 + 4 * lv + 3]; ++lv) {
+          const unsigned long long *u = t + 32 + 4 * lv;
+          if (u[0] && u[1] && u[2]) {  // a CTA without rows in a level leaves the first three empty
+            d->trace_nd[lv][0] += (u[0] - prev_nd) * 1e-3;
+            d->trace_nd[lv][1] += (u[1] - u[0]) * 1e-3;
+            d->trace_nd[lv][2] += (u[2] - u[1]) * 1e-3;
+            d->trace_nd[lv][3] += (u[3] - u[2]) * 1e-3;
+          } else {
+            d->trace_nd[lv][3] += (u[3] - prev_nd) * 1e-3;
+          }
+          prev_nd = u[3];
         }
         d->trace_nd_n++;
       }
@@ -2311,13 +2320,19 @@ static int pcg_persistent(DeviceState *d, const double *rhs, int *its, double *r
 }
 
 // contiguous byte-balanced row ranges per CTA, split into per-patch segments
-// (a row weighs its leading dimension plus `overhead` elements: the per-row epilogue)
+// (a row weighs its leading dimension plus `overhead` elements: the per-row epilogue;
+// every segment a CTA starts weighs `seg` elements more: its vector staging)
 static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std::vector<int32_t> &ld, int G,
                            std::vector<int32_t> &sptr, std::vector<int32_t> &ss, std::vector<int32_t> &r0,
-                           std::vector<int32_t> &r1, int overhead = 16) {
+                           std::vector<int32_t> &r1, int overhead = 16, int seg = 0) {
   int np_ = (int)rows_per_patch.size();
   double W = 0;
-  for (int s = 0; s < np_; ++s) W += (double)rows_per_patch[s] * (ld[s] + overhead);
+  int nonempty = 0;
+  for (int s = 0; s < np_; ++s) {
+    W += (double)rows_per_patch[s] * (ld[s] + overhead);
+    nonempty += rows_per_patch[s] > 0;
+  }
+  W += (double)seg * (nonempty + G);  // about one segment per patch plus one split per CTA
   sptr.assign(1, 0);
   ss.clear(); r0.clear(); r1.clear();
   int s = 0, r = 0;
@@ -2329,6 +2344,7 @@ static void partition_rows(const std::vector<int32_t> &rows_per_patch, const std
       // take rows of patch s until the target is reached
       int take = rows_per_patch[s] - r;
       double per = ld[s] + overhead;
+      acc += seg;
       if (c < G - 1) {
         int need = (int)std::ceil((target - acc) / per);
         take = std::max(1, std::min(take, need));
@@ -2659,6 +2675,7 @@ struct PcgSched {
   int cps = 1, ns = 3;
   size_t stage = 0;
   int psi = 0;  // 0: the Psi rows share the S_bb partition; > 0: own partition, per-row overhead
+  int seg = 0;  // per-segment weight of the row partitions (elements)
 };
 
 // widest FP64 coarse row / staged coarse vector: the dense S_c^{-1} row, or the widest
@@ -2739,7 +2756,7 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
                           {&d->tseg_ptr, &d->tseg_s, &d->tseg_r0, &d->tseg_r1}};
   std::vector<int32_t> sp, ss, r0v, r1v;
   for (int k = 0; k < 4; ++k) {
-    partition_rows(d->plan_rows[k], d->plan_ld[k], d->G, sp, ss, r0v, r1v);
+    partition_rows(d->plan_rows[k], d->plan_ld[k], d->G, sp, ss, r0v, r1v, 16, sc.seg);
     int rc;
     if ((rc = upload_cap(d, ptrs[k][0], cap_ptr, sp, err)) || (rc = upload_cap(d, ptrs[k][1], cap_seg, ss, err)) ||
         (rc = upload_cap(d, ptrs[k][2], cap_seg, r0v, err)) || (rc = upload_cap(d, ptrs[k][3], cap_seg, r1v, err)))
@@ -2757,7 +2774,7 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
           rows.push_back(dir == 0 ? d->ndh_nk[nd] + d->ndh_ns[nd] : d->ndh_nk[nd]);
           ld.push_back(dir == 0 ? d->ndh_zld[nd] : d->ndh_ltld[nd]);
         }
-        partition_rows(rows, ld, d->G, sp, ss, r0v, r1v);
+        partition_rows(rows, ld, d->G, sp, ss, r0v, r1v, 16, sc.seg);
         const int32_t base = (int32_t)S.size();
         for (int32_t v : sp) P.push_back(base + v);
         for (int32_t v : ss) S.push_back(L[v]);
@@ -2776,8 +2793,9 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
     }
   }
   d->psi_overhead = sc.psi;
+  d->seg_overhead = sc.seg;
   if (sc.psi > 0) {
-    partition_rows(d->plan_rows[4], d->plan_ld[4], d->G, sp, ss, r0v, r1v, sc.psi);
+    partition_rows(d->plan_rows[4], d->plan_ld[4], d->G, sp, ss, r0v, r1v, sc.psi, sc.seg);
     int rc;
     if ((rc = upload_cap(d, &d->qseg_ptr, cap_ptr, sp, err)) || (rc = upload_cap(d, &d->qseg_s, cap_seg, ss, err)) ||
         (rc = upload_cap(d, &d->qseg_r0, cap_seg, r0v, err)) || (rc = upload_cap(d, &d->qseg_r1, cap_seg, r1v, err)))
@@ -2851,15 +2869,19 @@ static bool tune_cache_lookup(const std::string &path, const std::string &key, P
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string tag, k;
-    long cps = 0, ns = 0, stage = 0, psi = -1;
-    if (!(ls >> tag >> k >> cps >> ns >> stage >> psi) || tag != "ieti_tune2" || k != key) continue;
+    long cps = 0, ns = 0, stage = 0, psi = -1, seg = 0;
+    // ieti_tune3 lines carry the segment weight; ieti_tune2 lines (without it) read as 0
+    if (!(ls >> tag >> k >> cps >> ns >> stage >> psi) || (tag != "ieti_tune2" && tag != "ieti_tune3") || k != key)
+      continue;
+    if (tag == "ieti_tune3" && !(ls >> seg)) continue;
     if (cps < 1 || cps > PCG_MAX_CPS || ns < 2 || ns > NS_MAX || stage < 128 || stage > 227 * 1024 || psi < 0 ||
-        psi > 4096)
+        psi > 4096 || seg < 0 || seg > (1 << 20))
       continue;
     out->cps = (int)cps;
     out->ns = (int)ns;
     out->stage = (size_t)stage;
     out->psi = (int)psi;
+    out->seg = (int)seg;
     found = true;  // the last valid entry of the key wins
   }
   return found;
@@ -2873,7 +2895,7 @@ static bool tune_cache_store(const std::string &path, const std::string &key, co
     while (f && std::getline(f, line)) {
       std::istringstream ls(line);
       std::string tag, k;
-      if ((ls >> tag >> k) && tag == "ieti_tune2" && k == key) continue;
+      if ((ls >> tag >> k) && (tag == "ieti_tune2" || tag == "ieti_tune3") && k == key) continue;
       if (!line.empty()) keep.push_back(line);
     }
   }
@@ -2882,7 +2904,8 @@ static bool tune_cache_store(const std::string &path, const std::string &key, co
     std::ofstream f(tmp, std::ios::trunc);
     if (!f) return false;
     for (auto &l : keep) f << l << "\n";
-    f << "ieti_tune2 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << " " << sc.psi << "\n";
+    f << "ieti_tune3 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << " " << sc.psi << " " << sc.seg
+      << "\n";
     if (!f.good()) return false;
   }
   return std::rename(tmp.c_str(), path.c_str()) == 0;
@@ -2947,6 +2970,27 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
     if (rc) break;
     PcgSched c = best;
     c.psi = psi;
+    std::string e2;
+    const int prc = pcg_plan(d, c, e2);
+    if (prc) {
+      err = e2;
+      rc = prc;
+      break;
+    }
+    double us = 0;
+    if ((rc = pcg_time<T>(d, rhs, iters, &us, err))) break;
+    d->tune_candidates++;
+    if (us < 0.99 * best_us) {
+      best_us = us;
+      best = c;
+    }
+  }
+  // then per-segment weights of the partitions (fewer, larger segments per CTA: each
+  // segment stages its vector before its rows)
+  for (int seg : {2048, 8192, 32768}) {
+    if (rc) break;
+    PcgSched c = best;
+    c.seg = seg;
     std::string e2;
     const int prc = pcg_plan(d, c, e2);
     if (prc) {
@@ -3938,6 +3982,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->coarse_bytes = d->coarse_nd ? d->nd_bytes : 8.0 * (double)d->NC * d->NC;
   info->t_coarse_ms = d->t_coarse_ms;
   info->factor_batches = d->factor_batches;
+  info->pcg_seg_weight = d->seg_overhead;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
@@ -3949,9 +3994,13 @@ void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {
 
 void device_coarse_level_times(DeviceState *d, double *us, int n, bool reset) {
   const int nl = std::min(TRACE_ND, d->coarse_nd ? d->nd_H + std::max(d->nd_D - 1, 0) : 0);
-  for (int k = 0; k < n; ++k) us[k] = (k < nl && d->trace_nd_n) ? d->trace_nd[k] / d->trace_nd_n : 0.0;
+  for (int k = 0; k < n; ++k) {
+    const int lv = k / 4, part = k % 4;
+    us[k] = (lv < nl && d->trace_nd_n) ? d->trace_nd[lv][part] / d->trace_nd_n : 0.0;
+  }
   if (reset) {
-    for (double &v : d->trace_nd) v = 0;
+    for (auto &row : d->trace_nd)
+      for (double &v : row) v = 0;
     d->trace_nd_n = 0;
   }
 }

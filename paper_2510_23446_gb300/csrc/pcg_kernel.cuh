@@ -103,9 +103,10 @@ constexpr int TRACE_IT = 16;
 // barrier wait (ph = 0..5), [14] start of the iteration, and for the streaming phases
 // (P1, P3, P4, P5 = sub 0..3) [16 + 3 sub + k]: k = 0 first segment staged, k = 1
 // first operator chunk arrived, k = 2 last row done
-// [32 + lv]: end of nested-dissection level lv of the coarse solve (after its barrier)
-constexpr int TRACE_SLOTS = 64;
-constexpr int TRACE_ND = 32;
+// nested-dissection level lv of the coarse solve: [32 + 4 lv + k], k = 0 first segment
+// staged, 1 first chunk arrived, 2 last row done, 3 end of the level's barrier
+constexpr int TRACE_SLOTS = 128;
+constexpr int TRACE_ND = 24;
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
               else a.nd_u[a.nd_uoff[p] + (r - nk)] = pv.x - v;
             },
             [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); },
-            lv == 0 ? tsp(1) : nullptr);
+            (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr);
       } else {
         ok = stream_phase<4, double, NDF>(
             ring, op, cur, xd, yd, errflag,
@@ -881,14 +882,15 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
               for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < ns ? ldcg(a.q + si[k]) : 0.0);
             },
             [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; },
-            [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); });
+            [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); },
+            (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr);
       }
       if (!ok) return false;
       if (lv + 1 < nd_levels) {
         cur = prefetch(ring, nd_op(lv + 1));
         if (!sync(nullptr)) return false;
       }
-      if (tsub && threadIdx.x == 0 && lv < TRACE_ND) tsub[16 + lv] = gtimer();  // tsub = trace row + 16
+      if (tsub && threadIdx.x == 0 && lv < TRACE_ND) tsub[16 + 4 * lv + 3] = gtimer();  // tsub = trace row + 16
     }
     return true;
   };

@@ -80,7 +80,7 @@ class ieti_info(C.Structure):
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
                 ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32), ("coarse_mode", C.c_int32),
                 ("coarse_nodes", C.c_int32), ("coarse_levels", C.c_int32), ("coarse_bytes", C.c_double),
-                ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32)]
+                ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32), ("pcg_seg_weight", C.c_int32)]
 
 
 _ctx = C.c_void_p
@@ -316,10 +316,13 @@ class Solver:
         self._check(lib.ieti_patch_blocks(self.ctx, None, None, None, cc.ctypes.data))
         return dict(ni=ni, nb=nb, np=np_, coarse_of_copy=cc[:int(np_.sum())])
 
-    def coarse_level_times(self, reset=False, n=32):
+    def coarse_level_times(self, reset=False):
+        """Per level of the nested-dissection coarse solve: [staging, first chunk, rows,
+        barrier wait] in microseconds (CTA 0, mean over the traced iterations)."""
+        n = 4 * 24
         us = np.zeros(n)
         self._check(lib.ieti_coarse_level_times(self.ctx, us.ctypes.data, n, int(reset)))
-        return us[:self.info()["coarse_levels"]].tolist()
+        return us.reshape(24, 4)[:min(24, self.info()["coarse_levels"])].tolist()
 
     def step(self, j, raise_on_error=True):
         p, mem = _ptr(j)

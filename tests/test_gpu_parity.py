@@ -286,14 +286,16 @@ def test_predictor_history_reset_by_set_state(ieti):
 def test_c2_bench_options_match_oracle_monolithic(ieti, c2_oracle, mode):
     """The 64-patch workload with the bench's exact options (stiffness-scaled Dirichlet,
     quadratic time predictor, autotuned schedule, L2 hints, sweep loop as a CUDA graph,
-    TF32x3 tensor-core factors in the mixed path), element by element against the
-    oracle's monolithic sparse direct solve of Eq. (11) over three steps from a^0 = 0."""
+    TF32x3 tensor-core factors in the mixed path, assembled residual to 1e-12), element
+    by element against the oracle's monolithic sparse direct solve of Eq. (11) over three
+    steps from a^0 = 0.  (With the residual stopped at 1e-11 the mixed state was 3.7e-8
+    from the oracle's: the step system amplifies the residual about 4000-fold.)"""
     prob, op = c2_oracle
     steps = 3
     ref = op.run_monolithic(steps)
     opts = {"fp64": dict(precision="fp64", cg_tol=1e-11),
             "mixed": dict(precision="mixed", cg_tol=1e-6, factor="tf32x3")}[mode]
-    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", outer_tol=1e-11, max_sweeps=30, predictor=2,
+    got, stats = gpu_run(ieti, prob, steps, precond="dirichlet_stiff", outer_tol=1e-12, max_sweeps=30, predictor=2,
                          autotune=1, l2_persist=2, graph=1, **opts)
     for l, (a, b) in enumerate(zip(ref, got)):
         err = np.linalg.norm(a - b) / np.linalg.norm(a)
