@@ -40,7 +40,7 @@ WORKLOADS = {
                gen=("c3", {}), horizon=100, outer=1e-12, mixed_cg_tol=1e-7),
     "c2": dict(desc="c2: unit cube, 4x4x4 curved patches (+-5% interior control points), p=2, 8^3 elements "
                     "per patch, conductor [0.25,0.75]^3 sigma=1e2, nu=1, coil J0=1e2, dt=1e-3",
-               gen=("c2", {}), horizon=50, outer=OUTER_TOL, mixed_cg_tol=1e-6),
+               gen=("c2", {}), horizon=50, outer=OUTER_TOL, mixed_cg_tol=1e-7),
 }
 HEADLINE = "c4"
 # each path with its fastest inner PCG tolerance for the common outer stop (measured on
@@ -49,7 +49,7 @@ HEADLINE = "c4"
 OPTS = {
     "mixed": dict(precision="mixed", precond="dirichlet_stiff", cg_tol=1e-6, outer_tol=OUTER_TOL, max_sweeps=30,
                   factor="tf32x3", predictor=2, autotune=1, l2_persist=2),
-    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-11, outer_tol=OUTER_TOL, max_sweeps=30,
+    "fp64": dict(precision="fp64", precond="dirichlet_stiff", cg_tol=1e-12, outer_tol=OUTER_TOL, max_sweeps=30,
                  predictor=2, autotune=1, l2_persist=2),
 }
 

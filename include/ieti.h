@@ -239,6 +239,8 @@ typedef struct {
   int32_t factor_batches;    /* patch batches of the setup factorization */
   int32_t pcg_seg_weight;    /* per-segment weight of the persistent kernel's row partitions (elements; the
                                 autotuner tries a few, 0 by the rule) */
+  int32_t coarse_flow;       /* 1: the nested-dissection levels wait on per-node completion counters instead of
+                                grid barriers (the autotuner's choice; 0 by the rule) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -989,6 +989,9 @@ struct DeviceState {
   double *nd_Z = nullptr, *nd_Lt = nullptr, *nd_u = nullptr;
   int32_t *ndf_ptr = nullptr, *ndf_s = nullptr, *ndf_r0 = nullptr, *ndf_r1 = nullptr;
   int32_t *ndb_ptr = nullptr, *ndb_s = nullptr, *ndb_r0 = nullptr, *ndb_r1 = nullptr;
+  int nd_flow = 0;                                      // levels wait on per-node counters, not grid barriers
+  int32_t *nd_cptr = nullptr, *nd_cidx = nullptr, *nd_parent = nullptr, *nd_nsegf = nullptr, *nd_nsegb = nullptr;
+  unsigned *nd_done = nullptr;
   std::vector<std::vector<int32_t>> ndh_fwd, ndh_bwd;   // node ids per forward / backward level
   std::vector<int32_t> ndh_nk, ndh_ns, ndh_zld, ndh_ltld;
   int64_t nd_z_elems = 0, nd_lt_elems = 0;              // padded sizes of the two operator blocks
@@ -1502,6 +1505,12 @@ static int coarse_nd_tables(DeviceState *d, const CoarseTree &t, std::string &er
       (rc = upload(d, &d->nd_ltoff, ltoff, err)) || (rc = upload(d, &d->nd_soff, soff, err)) ||
       (rc = upload(d, &d->nd_uoff, uoff, err)) || (rc = upload(d, &d->nd_srcoff, srcoff_w, err)) ||
       (rc = dalloc(d, &d->nd_u, (size_t)std::max<int64_t>(u, 1), err)))
+    return rc;
+  std::vector<int32_t> cidx(t.child_idx);
+  if (cidx.empty()) cidx.push_back(0);
+  if ((rc = upload(d, &d->nd_cptr, t.child_ptr, err)) || (rc = upload(d, &d->nd_cidx, cidx, err)) ||
+      (rc = upload(d, &d->nd_parent, t.parent, err)) || (rc = dalloc(d, &d->nd_nsegf, (size_t)NN, err)) ||
+      (rc = dalloc(d, &d->nd_nsegb, (size_t)NN, err)) || (rc = dalloc(d, &d->nd_done, (size_t)2 * NN, err)))
     return rc;
   return IETI_OK;
 }
@@ -2207,6 +2216,10 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.nd_Z = d->nd_Z; a.nd_Lt = d->nd_Lt; a.nd_u = d->nd_u;
   a.ndf_ptr = d->ndf_ptr; a.ndf_s = d->ndf_s; a.ndf_r0 = d->ndf_r0; a.ndf_r1 = d->ndf_r1;
   a.ndb_ptr = d->ndb_ptr; a.ndb_s = d->ndb_s; a.ndb_r0 = d->ndb_r0; a.ndb_r1 = d->ndb_r1;
+  a.nd_nodes = d->nd_nodes; a.nd_flow = d->nd_flow;
+  a.nd_cptr = d->nd_cptr; a.nd_cidx = d->nd_cidx; a.nd_parent = d->nd_parent;
+  a.nd_nsegf = d->nd_nsegf; a.nd_nsegb = d->nd_nsegb; a.nd_done = d->nd_done;
+  if (d->nd_flow) CK(cudaMemsetAsync(d->nd_done, 0, 2 * (size_t)d->nd_nodes * sizeof(unsigned), st));
   if (a.trace) CK(cudaMemsetAsync(d->trace, 0, TRACE_IT * TRACE_SLOTS * sizeof(unsigned long long), st));
   void *args[] = {&a};
   {
@@ -2676,6 +2689,7 @@ struct PcgSched {
   size_t stage = 0;
   int psi = 0;  // 0: the Psi rows share the S_bb partition; > 0: own partition, per-row overhead
   int seg = 0;  // per-segment weight of the row partitions (elements)
+  int flow = 0;  // nested-dissection levels wait on per-node counters instead of grid barriers
 };
 
 // widest FP64 coarse row / staged coarse vector: the dense S_c^{-1} row, or the widest
@@ -2783,6 +2797,10 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
       }
       const size_t nl = std::max<size_t>(levels.size(), 1);
       const size_t cp = nl * ((size_t)PCG_MAX_CPS * d->n_sm + 1), cs = nl * (size_t)PCG_MAX_CPS * d->n_sm + d->nd_nodes + 1;
+      std::vector<int32_t> nseg(d->nd_nodes, 0);  // segments of every node over all CTAs
+      for (int32_t v : S) nseg[v]++;
+      CK(cudaMemcpyAsync(dir == 0 ? d->nd_nsegf : d->nd_nsegb, nseg.data(), nseg.size() * 4, cudaMemcpyHostToDevice,
+                         d->stream));
       if (P.empty()) P.push_back(0);
       int rc;
       if (dir == 0 ? ((rc = upload_cap(d, &d->ndf_ptr, cp, P, err)) || (rc = upload_cap(d, &d->ndf_s, cs, S, err)) ||
@@ -2794,6 +2812,7 @@ static int pcg_plan(DeviceState *d, const PcgSched &sc, std::string &err) {
   }
   d->psi_overhead = sc.psi;
   d->seg_overhead = sc.seg;
+  d->nd_flow = d->coarse_nd ? sc.flow : 0;
   if (sc.psi > 0) {
     partition_rows(d->plan_rows[4], d->plan_ld[4], d->G, sp, ss, r0v, r1v, sc.psi, sc.seg);
     int rc;
@@ -2873,7 +2892,9 @@ static bool tune_cache_lookup(const std::string &path, const std::string &key, P
     // ieti_tune3 lines carry the segment weight; ieti_tune2 lines (without it) read as 0
     if (!(ls >> tag >> k >> cps >> ns >> stage >> psi) || (tag != "ieti_tune2" && tag != "ieti_tune3") || k != key)
       continue;
-    if (tag == "ieti_tune3" && !(ls >> seg)) continue;
+    long flow = 0;
+    if (tag == "ieti_tune3" && !(ls >> seg >> flow)) continue;
+    if (flow != 0 && flow != 1) continue;
     if (cps < 1 || cps > PCG_MAX_CPS || ns < 2 || ns > NS_MAX || stage < 128 || stage > 227 * 1024 || psi < 0 ||
         psi > 4096 || seg < 0 || seg > (1 << 20))
       continue;
@@ -2882,6 +2903,7 @@ static bool tune_cache_lookup(const std::string &path, const std::string &key, P
     out->stage = (size_t)stage;
     out->psi = (int)psi;
     out->seg = (int)seg;
+    out->flow = (int)flow;
     found = true;  // the last valid entry of the key wins
   }
   return found;
@@ -2905,7 +2927,7 @@ static bool tune_cache_store(const std::string &path, const std::string &key, co
     if (!f) return false;
     for (auto &l : keep) f << l << "\n";
     f << "ieti_tune3 " << key << " " << sc.cps << " " << sc.ns << " " << sc.stage << " " << sc.psi << " " << sc.seg
-      << "\n";
+      << " " << sc.flow << "\n";
     if (!f.good()) return false;
   }
   return std::rename(tmp.c_str(), path.c_str()) == 0;
@@ -2986,11 +3008,16 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
     }
   }
   // then per-segment weights of the partitions (fewer, larger segments per CTA: each
-  // segment stages its vector before its rows)
-  for (int seg : {2048, 8192, 32768}) {
+  // segment stages its vector before its rows), and for the nested-dissection coarse
+  // solve the per-node counters instead of grid barriers between its levels
+  std::vector<std::pair<int, int>> extra;
+  for (int seg : {2048, 8192, 32768}) extra.push_back({seg, -1});
+  if (d->coarse_nd) extra.push_back({-1, 1});
+  for (auto [seg, flow] : extra) {
     if (rc) break;
     PcgSched c = best;
-    c.seg = seg;
+    if (seg >= 0) c.seg = seg;
+    if (flow >= 0) c.flow = flow;
     std::string e2;
     const int prc = pcg_plan(d, c, e2);
     if (prc) {
@@ -3983,6 +4010,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->t_coarse_ms = d->t_coarse_ms;
   info->factor_batches = d->factor_batches;
   info->pcg_seg_weight = d->seg_overhead;
+  info->coarse_flow = d->nd_flow;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

@@ -89,13 +89,19 @@ struct PcgArgs {
   // f_K = c_K + child updates, q_K = D^{-1} f_K, u_p = f_S + child updates - Lbar f_K
   // (u_p in ubuf at uoff, the child updates gathered through src: cw entries per front
   // position, -1 = none).  Backward, by depth: q_K -= Lt_p q_S.
-  int coarse_nd, nd_cw, nd_H, nd_D;
+  int coarse_nd, nd_cw, nd_H, nd_D, nd_nodes;
   const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_src, *nd_nch;
   const int64_t *nd_zoff, *nd_ltoff, *nd_soff, *nd_uoff, *nd_srcoff;
   const double *nd_Z, *nd_Lt;
   double *nd_u;
   const int32_t *ndf_ptr, *ndf_s, *ndf_r0, *ndf_r1;   // forward rows per level: ptr [H][G + 1]
   const int32_t *ndb_ptr, *ndb_s, *ndb_r0, *ndb_r1;   // backward rows per level (depth 1 ..): ptr [D][G + 1]
+  // nd_flow = 1: the levels wait on per-node completion counters instead of grid barriers
+  // (forward: a node's children done; backward: its parent final), nd_done [2][nodes]
+  // counting finished segments (targets: solves so far x segments of the node)
+  int nd_flow;
+  const int32_t *nd_cptr, *nd_cidx, *nd_parent, *nd_nsegf, *nd_nsegb;
+  unsigned *nd_done;
 };
 
 constexpr int TRACE_IT = 16;
@@ -263,6 +269,11 @@ __device__ __forceinline__ double row_dot_df(const float2 *row, const float2 *xs
 struct NoPre {
   __device__ double2 operator()(int) const { return make_double2(0.0, 0.0); }
   __device__ double2 operator()(int, int) const { return make_double2(0.0, 0.0); }
+};
+
+// segment-completion hook of stream_phase (none by default)
+struct NoDone {
+  __device__ void operator()(int) const {}
 };
 
 // rows [r0, r1) of an operator against xs, RW rows per warp; lane i of the warp
@@ -553,17 +564,26 @@ __device__ __forceinline__ Cursor prefetch(Ring &ring, const OpRows<E> &op) {
 // Returns false (after setting the error flag and draining) when a wait timed out.
 // DF: the rows hold (hi, lo) FP32 pairs (E = double only sizes them), xs holds staged
 // pairs, y receives FP64 results (double-FP32 row kernels)
-template <int RW, class E, bool DF = false, class Stage, class Out, class Pre = NoPre>
+// done(s) runs with every thread of the CTA once all rows of the CTA's segment of s
+// are written (after a CTA barrier)
+template <int RW, class E, bool DF = false, class Stage, class Out, class Pre = NoPre, class Done = NoDone>
 __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const E *xs, E *y, unsigned *errflag,
-                             Stage stage, Out out, Pre pre = Pre(), unsigned long long *ts = nullptr) {
+                             Stage stage, Out out, Pre pre = Pre(), unsigned long long *ts = nullptr,
+                             Done done = Done()) {
+  constexpr bool kDone = !std::is_same<Done, NoDone>::value;
   while (cur.issued - 0 < ring.ns && issue_next(ring, op, cur)) {
   }
   int nseg = op.nseg();
+  int prev_s = -1;
   for (int k = 0; k < nseg; ++k) {
     int s, r0, r1, ld;
     const E *A;
     op.seg(k, s, r0, r1, ld, A);
     __syncthreads();
+    if constexpr (kDone) {
+      if (prev_s >= 0) done(prev_s);
+      prev_s = s;
+    }
     stage(s, r0, r1);
     __syncthreads();
     if (ts && k == 0 && threadIdx.x == 0) ts[0] = gtimer();
@@ -644,6 +664,12 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
     }
   }
   if (ts && threadIdx.x == 0) ts[2] = gtimer();
+  if constexpr (kDone) {
+    if (prev_s >= 0) {
+      __syncthreads();
+      done(prev_s);
+    }
+  }
   return true;
 }
 
@@ -843,7 +869,40 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
   // levels; the next level's rows are issued before the barrier
   // the mixed path's blocks are (hi, lo) FP32 pairs (double-FP32 rows), the FP64 path's FP64
   constexpr bool NDF = sizeof(T) == 4;
+  unsigned nd_epoch = 0;  // coarse solves of this launch so far (the same in every CTA)
+  // bounded wait of thread 0 until *ctr reaches target, then a CTA barrier
+  auto nd_wait = [&](const unsigned *ctr, unsigned target) {
+    if (threadIdx.x == 0) {
+      long long spins = 0;
+      while (ld_acquire(ctr) < target) {
+        if (++spins > 64) __nanosleep(32);
+        if (spins > a.spin_max) {
+          atomicExch(errflag, 1u);
+          break;
+        }
+        if ((spins & 1023) == 0 && *(volatile unsigned *)errflag) break;
+      }
+    }
+    __syncthreads();
+  };
+  auto nd_signal = [&](unsigned *ctr) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(ctr, 1u);
+    }
+  };
+  // counter of node p that marks q_K final: its backward rows if it has any, else its forward rows
+  auto nd_final = [&](int p, const unsigned *&ctr, unsigned &target) {
+    if (a.nd_nsegb[p] > 0) {
+      ctr = a.nd_done + a.nd_nodes + p;
+      target = nd_epoch * (unsigned)a.nd_nsegb[p];
+    } else {
+      ctr = a.nd_done + p;
+      target = nd_epoch * (unsigned)a.nd_nsegf[p];
+    }
+  };
   auto coarse_solve_nd = [&]() -> bool {
+    ++nd_epoch;
     double *xd = reinterpret_cast<double *>(smem_raw);
     float2 *xp = reinterpret_cast<float2 *>(smem_raw);
     double *yd = reinterpret_cast<double *>(ybuf_raw);
@@ -859,36 +918,52 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       const OpRows<double> op = nd_op(lv);
       bool ok;
       if (lv < a.nd_H) {
-        ok = stream_phase<4, double, NDF>(
-            ring, op, cur, xd, yd, errflag,
-            [&](int p, int, int) {
-              const int nk = a.nd_nk[p], ld = a.nd_zld[p], k0 = a.nd_k0[p];
-              for (int k = threadIdx.x; k < ld; k += nthr)
-                put(k, k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0);
-            },
-            [&](int p, int r, double v, double2 pv) {
-              const int nk = a.nd_nk[p];
-              if (r < nk) a.q[a.nd_k0[p] + r] = v;
-              else a.nd_u[a.nd_uoff[p] + (r - nk)] = pv.x - v;
-            },
-            [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); },
-            (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr);
+        auto stage_f = [&](int p, int, int) {
+          if (a.nd_flow)
+            for (int k = a.nd_cptr[p]; k < a.nd_cptr[p + 1]; ++k) {
+              const int ch = a.nd_cidx[k];
+              nd_wait(a.nd_done + ch, nd_epoch * (unsigned)a.nd_nsegf[ch]);
+            }
+          const int nk = a.nd_nk[p], ld = a.nd_zld[p], k0 = a.nd_k0[p];
+          for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0);
+        };
+        auto out_f = [&](int p, int r, double v, double2 pv) {
+          const int nk = a.nd_nk[p];
+          if (r < nk) a.q[a.nd_k0[p] + r] = v;
+          else a.nd_u[a.nd_uoff[p] + (r - nk)] = pv.x - v;
+        };
+        auto pre_f = [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); };
+        unsigned long long *tl = (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr;
+        if (a.nd_flow)
+          ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_f, out_f, pre_f, tl,
+                                            [&](int p) { nd_signal(a.nd_done + p); });
+        else
+          ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_f, out_f, pre_f, tl);
       } else {
-        ok = stream_phase<4, double, NDF>(
-            ring, op, cur, xd, yd, errflag,
-            [&](int p, int, int) {
-              const int ns = a.nd_ns[p], ld = a.nd_ltld[p];
-              const int32_t *si = a.nd_sidx + a.nd_soff[p];
-              for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < ns ? ldcg(a.q + si[k]) : 0.0);
-            },
-            [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; },
-            [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); },
-            (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr);
+        auto stage_b = [&](int p, int, int) {
+          if (a.nd_flow) {
+            const unsigned *ctr;
+            unsigned target;
+            nd_final(a.nd_parent[p], ctr, target);
+            nd_wait(ctr, target);
+          }
+          const int ns = a.nd_ns[p], ld = a.nd_ltld[p];
+          const int32_t *si = a.nd_sidx + a.nd_soff[p];
+          for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < ns ? ldcg(a.q + si[k]) : 0.0);
+        };
+        auto out_b = [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; };
+        auto pre_b = [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); };
+        unsigned long long *tl = (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr;
+        if (a.nd_flow)
+          ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_b, out_b, pre_b, tl,
+                                            [&](int p) { nd_signal(a.nd_done + a.nd_nodes + p); });
+        else
+          ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_b, out_b, pre_b, tl);
       }
       if (!ok) return false;
       if (lv + 1 < nd_levels) {
         cur = prefetch(ring, nd_op(lv + 1));
-        if (!sync(nullptr)) return false;
+        if (!a.nd_flow && !sync(nullptr)) return false;
       }
       if (tsub && threadIdx.x == 0 && lv < TRACE_ND) tsub[16 + 4 * lv + 3] = gtimer();  // tsub = trace row + 16
     }

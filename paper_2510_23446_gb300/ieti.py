@@ -80,7 +80,8 @@ class ieti_info(C.Structure):
                 ("pcg_sched_source", C.c_int32), ("tune_candidates", C.c_int32), ("tune_ms", C.c_double),
                 ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32), ("coarse_mode", C.c_int32),
                 ("coarse_nodes", C.c_int32), ("coarse_levels", C.c_int32), ("coarse_bytes", C.c_double),
-                ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32), ("pcg_seg_weight", C.c_int32)]
+                ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32), ("pcg_seg_weight", C.c_int32),
+                ("coarse_flow", C.c_int32)]
 
 
 _ctx = C.c_void_p

@@ -91,3 +91,35 @@ def test_batched_factorization_equals_one_batch(ieti, name, mode):
     for x, y, r in zip(a1, ab, ref):
         assert np.array_equal(x, y)
         assert np.linalg.norm(y - r) <= TOL[mode] * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["c4_family", "ragged_p23", "c3_family"])
+def test_nd_levels_on_node_counters(ieti, name, mode, tmp_path):
+    """The coarse levels waiting on per-node completion counters (a node's children
+    done; its parent final) instead of grid barriers, forced through the schedule cache:
+    the same states as with the barriers (same arithmetic and order), within the parity
+    tolerance of the oracle, in the host loop and in the step graph."""
+    prob, op, ref = oracle_run(name, 3)
+    cache = tmp_path / "tune.txt"
+    kw = dict(precond="dirichlet_stiff", coarse="nd", coarse_leaf=1, **OPTS[mode])
+    S = ieti.Solver.from_problem(prob, device=0, autotune=1, tune_cache=str(cache), **kw)
+    S.close()
+    line = [l for l in cache.read_text().splitlines() if l.startswith("ieti_tune3 ")][0].split()
+    for graph in (0, 1):
+        states = {}
+        for flow in (0, 1):
+            cache.write_text(" ".join(line[:8] + [str(flow)]) + "\n")
+            S = ieti.Solver.from_problem(prob, device=0, autotune=1, tune_cache=str(cache), graph=graph, **kw)
+            inf = S.info()
+            assert inf["pcg_sched_source"] == 3 and inf["coarse_flow"] == flow
+            j = S.load_vector(prob.coil)
+            out = []
+            for _ in range(3):
+                S.step(j)
+                out.append(S.solution().copy())
+            S.close()
+            states[flow] = out
+        for a, b, r in zip(states[0], states[1], ref):
+            assert np.array_equal(a, b)
+            assert np.linalg.norm(b - r) <= TOL[mode] * np.linalg.norm(r)
