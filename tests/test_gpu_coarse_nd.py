@@ -109,7 +109,7 @@ def test_nd_levels_on_node_counters(ieti, name, mode, tmp_path):
     for graph in (0, 1):
         states = {}
         for flow in (0, 1):
-            cache.write_text(" ".join(line[:8] + [str(flow)]) + "\n")
+            cache.write_text(" ".join(line[:7] + [str(flow)]) + "\n")
             S = ieti.Solver.from_problem(prob, device=0, autotune=1, tune_cache=str(cache), graph=graph, **kw)
             inf = S.info()
             assert inf["pcg_sched_source"] == 3 and inf["coarse_flow"] == flow
