@@ -990,6 +990,7 @@ struct DeviceState {
   int32_t *ndf_ptr = nullptr, *ndf_s = nullptr, *ndf_r0 = nullptr, *ndf_r1 = nullptr;
   int32_t *ndb_ptr = nullptr, *ndb_s = nullptr, *ndb_r0 = nullptr, *ndb_r1 = nullptr;
   int nd_flow = 0;                                      // levels wait on per-node counters, not grid barriers
+  const CoarseTree *nd_tree = nullptr;                  // kept by the context; Newton refactorizations reuse it
   int32_t *nd_cptr = nullptr, *nd_cidx = nullptr, *nd_parent = nullptr, *nd_nsegf = nullptr, *nd_nsegb = nullptr;
   unsigned *nd_done = nullptr;
   std::vector<std::vector<int32_t>> ndh_fwd, ndh_bwd;   // node ids per forward / backward level
@@ -1957,9 +1958,25 @@ static int nl_refactor(DeviceState *d, std::string &err) {
                                              d->nlb_ldg, d->nlb_igoff, d->nlb_gtoff, (TO *)d->IG, (TO *)d->GT);
   }
   if (ev[2]) cudaEventRecord(ev[2], st);
-  // coarse: by the block formula when the split exists, else linear part + the
-  // refactored patches and a full FP64 factorization
-  if (d->NC > 0 && d->cN > 0) {
+  // coarse: along the nested dissection (linear part + the refactored patches, the
+  // multifrontal FP64 factorization), by the block formula when the split exists, else
+  // linear part + the refactored patches and a full factorization of the augmented block
+  if (d->NC > 0 && d->coarse_nd) {
+    const int64_t nc = d->NC;
+    CK(cudaMemcpyAsync(d->sc_aug, d->sc_lin, (size_t)(nc * nc) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int b = 0; b < nb; ++b) {
+      if (d->nlh_np[b] == 0) continue;
+      int64_t cnt = (int64_t)d->nlh_np[b] * d->nlh_np[b];
+      k_coarse_add<TD><<<grid_for(cnt, 256), 256, 0, st>>>(W, d->nlh_doff[b], d->nlh_nn[b], d->nlh_ni[b],
+                                                           d->nlh_nb[b], d->nlh_np[b], d->pc + d->nlh_pofs[b],
+                                                           d->sc_aug, nc);
+    }
+    if ((rc = coarse_nd_factor(d, *d->nd_tree, d->sc_aug, err))) return rc;
+    if (d->mixed) {
+      const int64_t n = d->nd_z_elems + d->nd_lt_elems;
+      k_split_pairs<<<grid_for(n, 256), 256, 0, st>>>(n, d->nd_Z, (float2 *)d->nd_Z);
+    }
+  } else if (d->NC > 0 && d->cN > 0) {
     if ((rc = coarse_block_refactor<TD>(d, W, err))) return rc;
   } else if (d->NC > 0 && d->mixed && d->factor != IETI_FACTOR_FP64) {
     // the Newton iterate's coarse block in the factor arithmetic of the patches (a
@@ -3076,12 +3093,13 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     const double nc0 = (double)hs.n_coarse;
     bool nd = opt.coarse == IETI_COARSE_ND;
     if (opt.coarse == IETI_COARSE_AUTO)
-      nd = tree && tree->n_nodes > 0 && !hs.nonlinear && opt.pcg_mode == 0 && 8.0 * nc0 * nc0 > 64e6;
-    if (nd && (hs.nonlinear || opt.pcg_mode != 0 || !tree)) {
-      err = "the nested-dissection coarse solve needs a linear problem and pcg_mode 0";
+      nd = tree && tree->n_nodes > 0 && opt.pcg_mode == 0 && 8.0 * nc0 * nc0 > 64e6;
+    if (nd && (opt.pcg_mode != 0 || !tree)) {
+      err = "the nested-dissection coarse solve needs pcg_mode 0";
       return fail(IETI_ERR_INVALID_ARG);
     }
     d->coarse_nd = nd && hs.n_coarse > 0 && tree->n_nodes > 0;
+    d->nd_tree = d->coarse_nd ? tree : nullptr;
   }
   CK(cudaEventCreate(&d->ev0));
   CK(cudaEventCreate(&d->ev1));
@@ -3734,9 +3752,13 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
       d->launches_setup++;
     }
     cudaStreamSynchronize(d->stream);
-    cudaFree(Sc);
-    d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
-    d->bytes -= (int64_t)(ldS * ldS) * 8;
+    if (d->nl_np > 0) {
+      d->sc_aug = Sc;  // the assembled S_c of every Newton refactorization
+    } else {
+      cudaFree(Sc);
+      d->allocs.erase(std::find(d->allocs.begin(), d->allocs.end(), (void *)Sc));
+      d->bytes -= (int64_t)(ldS * ldS) * 8;
+    }
     if (rc) return fail(rc);
     d->t_coarse_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
   } else if (nc > 0) {

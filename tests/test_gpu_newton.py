@@ -147,3 +147,19 @@ def test_linear_law_equals_linear_solver(ieti):
     for a, b in zip(ref, got):
         assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
     assert all(s["sweeps"] <= 2 for s in stats)
+
+
+@pytest.mark.parametrize("name", ["c1_law", "uneven_law", "buried_law"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_newton_with_nested_dissection_coarse_solve(ieti, name, mode):
+    """Newton with the coarse problem refactored along the nested dissection at every
+    tangent (the assembled S_c of the linear patches plus the refactored ones, the
+    multifrontal factorization): the oracle's states within the path's tolerance."""
+    steps = 2
+    prob, npb, ref, its = oracle(name, steps)
+    got, stats, info = gpu_run(ieti, prob, steps, coarse="nd", coarse_leaf=1, **OPTS[mode])
+    assert info["coarse_mode"] == 2 and info["nl_coarse_block"] == 0
+    for l, (a, b) in enumerate(zip(ref, got)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(a)
+        assert err <= TOL[mode], (name, mode, l, err, stats[l])
+        assert stats[l]["refactors"] == stats[l]["sweeps"]
