@@ -984,9 +984,9 @@ struct DeviceState {
   // update buffer, the gather lists, and the rows of every level per CTA
   int coarse_nd = 0, nd_cw = 1, nd_H = 0, nd_D = 0, nd_nodes = 0, nd_zmax = 0;
   int32_t *nd_k0 = nullptr, *nd_nk = nullptr, *nd_ns = nullptr, *nd_zld = nullptr, *nd_ltld = nullptr,
-          *nd_sidx = nullptr, *nd_src = nullptr, *nd_nch = nullptr;
+          *nd_sidx = nullptr, *nd_dst = nullptr, *nd_nch = nullptr;
   int64_t *nd_zoff = nullptr, *nd_ltoff = nullptr, *nd_soff = nullptr, *nd_uoff = nullptr, *nd_srcoff = nullptr;
-  double *nd_Z = nullptr, *nd_Lt = nullptr, *nd_u = nullptr;
+  double *nd_Z = nullptr, *nd_Lt = nullptr, *nd_slot = nullptr;
   int32_t *ndf_ptr = nullptr, *ndf_s = nullptr, *ndf_r0 = nullptr, *ndf_r1 = nullptr;
   int32_t *ndb_ptr = nullptr, *ndb_s = nullptr, *ndb_r0 = nullptr, *ndb_r1 = nullptr;
   int nd_flow = 0;                                      // levels wait on per-node counters, not grid barriers
@@ -1483,9 +1483,17 @@ static int coarse_nd_tables(DeviceState *d, const CoarseTree &t, std::string &er
     return IETI_ERR_TOO_LARGE;
   }
   d->nd_cw = cw;
-  std::vector<int32_t> src((size_t)sr * cw, -1);
+  if ((int64_t)sr * cw >= (int64_t)INT32_MAX) {
+    err = "coarse problem too large for the nested-dissection solver";
+    return IETI_ERR_TOO_LARGE;
+  }
+  // slot w of front position i of node p receives the update of the w-th child that
+  // contributes there (child order): every update row of every node has one slot in
+  // its parent's front (dst), so that a parent reads its positions' updates
+  // contiguously; slots that no child fills stay zero
+  std::vector<int32_t> dst(std::max<int64_t>(u, 1), 0);
   for (int64_t i = 0; i < sr; ++i)
-    for (size_t w = 0; w < lists[i].size(); ++w) src[(size_t)i * cw + w] = lists[i][w];
+    for (size_t w = 0; w < lists[i].size(); ++w) dst[lists[i][w]] = (int32_t)(i * cw + (int64_t)w);
   std::vector<int64_t> srcoff_w(NN), soff(t.s_off.begin(), t.s_off.end() - 1);
   for (int p = 0; p < NN; ++p) srcoff_w[p] = srcoff[p] * cw;
   d->ndh_fwd.assign(d->nd_H, {});
@@ -1501,12 +1509,13 @@ static int coarse_nd_tables(DeviceState *d, const CoarseTree &t, std::string &er
   if ((rc = upload(d, &d->nd_k0, t.k0, err)) || (rc = upload(d, &d->nd_nk, d->ndh_nk, err)) ||
       (rc = upload(d, &d->nd_ns, d->ndh_ns, err)) || (rc = upload(d, &d->nd_zld, d->ndh_zld, err)) ||
       (rc = upload(d, &d->nd_ltld, d->ndh_ltld, err)) || (rc = upload(d, &d->nd_sidx, sidx, err)) ||
-      (rc = upload(d, &d->nd_src, src, err)) || (rc = upload(d, &d->nd_nch, nch, err)) ||
+      (rc = upload(d, &d->nd_dst, dst, err)) || (rc = upload(d, &d->nd_nch, nch, err)) ||
       (rc = upload(d, &d->nd_zoff, zoff, err)) ||
       (rc = upload(d, &d->nd_ltoff, ltoff, err)) || (rc = upload(d, &d->nd_soff, soff, err)) ||
       (rc = upload(d, &d->nd_uoff, uoff, err)) || (rc = upload(d, &d->nd_srcoff, srcoff_w, err)) ||
-      (rc = dalloc(d, &d->nd_u, (size_t)std::max<int64_t>(u, 1), err)))
+      (rc = dalloc(d, &d->nd_slot, (size_t)std::max<int64_t>(sr * cw, 2), err)))
     return rc;
+  CK(cudaMemsetAsync(d->nd_slot, 0, (size_t)std::max<int64_t>(sr * cw, 2) * sizeof(double), d->stream));
   std::vector<int32_t> cidx(t.child_idx);
   if (cidx.empty()) cidx.push_back(0);
   if ((rc = upload(d, &d->nd_cptr, t.child_ptr, err)) || (rc = upload(d, &d->nd_cidx, cidx, err)) ||
@@ -2227,10 +2236,10 @@ static int pcg_launch(DeviceState *d, const double *rhs, cudaStream_t st, std::s
   a.coarse_nd = d->coarse_nd;
   a.nd_cw = d->nd_cw; a.nd_H = d->nd_H; a.nd_D = d->nd_D;
   a.nd_k0 = d->nd_k0; a.nd_nk = d->nd_nk; a.nd_ns = d->nd_ns; a.nd_zld = d->nd_zld; a.nd_ltld = d->nd_ltld;
-  a.nd_sidx = d->nd_sidx; a.nd_src = d->nd_src; a.nd_nch = d->nd_nch;
+  a.nd_sidx = d->nd_sidx; a.nd_dst = d->nd_dst; a.nd_nch = d->nd_nch;
   a.nd_zoff = d->nd_zoff; a.nd_ltoff = d->nd_ltoff; a.nd_soff = d->nd_soff; a.nd_uoff = d->nd_uoff;
   a.nd_srcoff = d->nd_srcoff;
-  a.nd_Z = d->nd_Z; a.nd_Lt = d->nd_Lt; a.nd_u = d->nd_u;
+  a.nd_Z = d->nd_Z; a.nd_Lt = d->nd_Lt; a.nd_slot = d->nd_slot;
   a.ndf_ptr = d->ndf_ptr; a.ndf_s = d->ndf_s; a.ndf_r0 = d->ndf_r0; a.ndf_r1 = d->ndf_r1;
   a.ndb_ptr = d->ndb_ptr; a.ndb_s = d->ndb_s; a.ndb_r0 = d->ndb_r0; a.ndb_r1 = d->ndb_r1;
   a.nd_nodes = d->nd_nodes; a.nd_flow = d->nd_flow;

@@ -86,14 +86,16 @@ struct PcgArgs {
   // unknowns sidx[soff .. soff + ns).  Z_p = [D_p^{-1}; Lbar_p] ((nk + ns) x nk, leading
   // dimension zld) with D_p the node's pivot block after the updates of its subtree and
   // Lbar_p = F_SK D_p^{-1}; Lt_p = Lbar_p^T (nk x ns, ltld).  Forward, by height:
-  // f_K = c_K + child updates, q_K = D^{-1} f_K, u_p = f_S + child updates - Lbar f_K
-  // (u_p in ubuf at uoff, the child updates gathered through src: cw entries per front
-  // position, -1 = none).  Backward, by depth: q_K -= Lt_p q_S.
+  // f_K = c_K + child updates, q_K = D^{-1} f_K, u_p = f_S + child updates - Lbar f_K.
+  // Child updates live in slots: cw per front position of every node (node p's from
+  // srcoff[p]), slot w of a position filled by the w-th child contributing there (zero
+  // if none); row j of u_p goes to slot dst[uoff[p] + j] of its parent's front.
+  // Backward, by depth: q_K -= Lt_p q_S.
   int coarse_nd, nd_cw, nd_H, nd_D, nd_nodes;
-  const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_src, *nd_nch;
+  const int32_t *nd_k0, *nd_nk, *nd_ns, *nd_zld, *nd_ltld, *nd_sidx, *nd_dst, *nd_nch;
   const int64_t *nd_zoff, *nd_ltoff, *nd_soff, *nd_uoff, *nd_srcoff;
   const double *nd_Z, *nd_Lt;
-  double *nd_u;
+  double *nd_slot;
   const int32_t *ndf_ptr, *ndf_s, *ndf_r0, *ndf_r1;   // forward rows per level: ptr [H][G + 1]
   const int32_t *ndb_ptr, *ndb_s, *ndb_r0, *ndb_r1;   // backward rows per level (depth 1 ..): ptr [D][G + 1]
   // nd_flow = 1: the levels wait on per-node completion counters instead of grid barriers
@@ -854,15 +856,27 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
       a.cc[k] = c;
     }
   };
-  // the child updates gathered into front position i of node p
-  auto nd_gather = [&](int p, int i) {
-    double v = 0.0;
-    if (a.nd_nch[p] == 0) return v;  // a leaf: no child updates
-    const int32_t *src = a.nd_src + a.nd_srcoff[p] + (int64_t)i * a.nd_cw;
-    for (int w = 0; w < a.nd_cw; ++w) {
-      const int32_t u = src[w];
-      if (u >= 0) v += ldcg(a.nd_u + u);
+  // the node of the coarse-level segment being processed (set by the stage functors,
+  // read by the row epilogues of the segment)
+  int nd_snk = 0, nd_sk0 = 0, nd_snch = 0;
+  int64_t nd_sbase = 0, nd_suoff = 0;
+  auto nd_seg = [&](int p) {
+    nd_snk = a.nd_nk[p];
+    nd_sk0 = a.nd_k0[p];
+    nd_snch = a.nd_nch[p];
+    nd_sbase = a.nd_srcoff[p];
+    nd_suoff = a.nd_uoff[p];
+  };
+  // the child updates of front position i of the current node (the sum of its slots)
+  auto nd_slots = [&](int i) -> double {
+    if (nd_snch == 0) return 0.0;  // a leaf: no child updates
+    const double *sl = a.nd_slot + nd_sbase + (int64_t)i * a.nd_cw;
+    if (a.nd_cw == 2) {
+      const double2 v = __ldcg(reinterpret_cast<const double2 *>(sl));
+      return v.x + v.y;
     }
+    double v = 0.0;
+    for (int w = 0; w < a.nd_cw; ++w) v += ldcg(sl + w);
     return v;
   };
   // nested-dissection solve q = S_c^{-1} c: one phase per level, a grid barrier between
@@ -924,15 +938,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
               const int ch = a.nd_cidx[k];
               nd_wait(a.nd_done + ch, nd_epoch * (unsigned)a.nd_nsegf[ch]);
             }
-          const int nk = a.nd_nk[p], ld = a.nd_zld[p], k0 = a.nd_k0[p];
-          for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < nk ? ldcg(a.cc + k0 + k) + nd_gather(p, k) : 0.0);
+          nd_seg(p);
+          const int nk = nd_snk, ld = a.nd_zld[p];
+          // f_K: four positions per thread and round, their loads issued together
+          for (int kb = threadIdx.x; kb < ld; kb += 4 * nthr) {
+            double f[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = kb + u * nthr;
+              f[u] = k < nk ? ldcg(a.cc + nd_sk0 + k) + nd_slots(k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (kb + u * nthr < ld) put(kb + u * nthr, f[u]);
+          }
         };
-        auto out_f = [&](int p, int r, double v, double2 pv) {
-          const int nk = a.nd_nk[p];
-          if (r < nk) a.q[a.nd_k0[p] + r] = v;
-          else a.nd_u[a.nd_uoff[p] + (r - nk)] = pv.x - v;
+        auto out_f = [&](int, int r, double v, double2 pv) {
+          if (r < nd_snk) a.q[nd_sk0 + r] = v;
+          else a.nd_slot[(int64_t)pv.y] = pv.x - v;
         };
-        auto pre_f = [&](int p, int r) { return make_double2(r >= a.nd_nk[p] ? nd_gather(p, r) : 0.0, 0.0); };
+        // S rows: the child updates of the position and the slot of the row in the parent
+        auto pre_f = [&](int, int r) {
+          return r >= nd_snk ? make_double2(nd_slots(r), (double)a.nd_dst[nd_suoff + (r - nd_snk)])
+                             : make_double2(0.0, 0.0);
+        };
         unsigned long long *tl = (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr;
         if (a.nd_flow)
           ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_f, out_f, pre_f, tl,
@@ -947,12 +976,24 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
             nd_final(a.nd_parent[p], ctr, target);
             nd_wait(ctr, target);
           }
+          nd_seg(p);
           const int ns = a.nd_ns[p], ld = a.nd_ltld[p];
           const int32_t *si = a.nd_sidx + a.nd_soff[p];
-          for (int k = threadIdx.x; k < ld; k += nthr) put(k, k < ns ? ldcg(a.q + si[k]) : 0.0);
+          // q_S: four positions per thread and round (the index loads, then the values)
+          for (int kb = threadIdx.x; kb < ld; kb += 4 * nthr) {
+            int idx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) idx[u] = kb + u * nthr < ns ? si[kb + u * nthr] : -1;
+            double f[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) f[u] = idx[u] >= 0 ? ldcg(a.q + idx[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (kb + u * nthr < ld) put(kb + u * nthr, f[u]);
+          }
         };
-        auto out_b = [&](int p, int r, double v, double2 pv) { a.q[a.nd_k0[p] + r] = pv.x - v; };
-        auto pre_b = [&](int p, int r) { return make_double2(ldcg(a.q + a.nd_k0[p] + r), 0.0); };
+        auto out_b = [&](int, int r, double v, double2 pv) { a.q[nd_sk0 + r] = pv.x - v; };
+        auto pre_b = [&](int, int r) { return make_double2(ldcg(a.q + nd_sk0 + r), 0.0); };
         unsigned long long *tl = (tsub && lv < TRACE_ND) ? tsub + 16 + 4 * lv : nullptr;
         if (a.nd_flow)
           ok = stream_phase<4, double, NDF>(ring, op, cur, xd, yd, errflag, stage_b, out_b, pre_b, tl,
