@@ -395,38 +395,53 @@ __device__ __forceinline__ void df_acc(float &S, float &c, float4 a, float4 x) {
   S = s;
 }
 
+// (S, c) += (S2, c2) for double-FP32 partial sums: TwoSum of the leading parts, the
+// compensations and the rounding error of that sum into c (FP32 only)
+__device__ __forceinline__ void df_add(float &S, float &c, float S2, float c2) {
+  const float s = S + S2, bb = s - S;
+  c = (c + c2) + ((S - (s - bb)) + (S2 - bb));
+  S = s;
+}
+
 // y[r] = A_r . x (FP64 results) for the rows of a chunk of (hi, lo) pairs, G lanes per
-// row, two accumulators per lane; ld in pairs (even)
-template <int G>
-__device__ __noinline__ void chunk_rows_df(const float2 *A, int ld, int cn, const float2 *xs, double *y) {
+// row, NACC accumulator pairs per lane; ld in pairs (even).  The lane partials are
+// combined in double-FP32 (df_add, shuffles of FP32 pairs): one FP64 conversion per
+// row, so the FP64 pipe (a small fraction of the FP32 rate on this part) stays idle.
+template <int G, int NACC>
+__device__ __forceinline__ void chunk_rows_df(const float2 *A, int ld, int cn, const float2 *xs, double *y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int sub = lane / G, j = lane % G;
   const int nv = ld / 2;
   const float4 *x = reinterpret_cast<const float4 *>(xs);
   for (int r0 = warp * (32 / G); r0 < cn; r0 += nw * (32 / G)) {
     const int r = r0 + sub;
-    double v = 0.0;
+    float S[NACC], c[NACC];
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) S[i] = c[i] = 0.f;
     if (r < cn) {
       const float4 *row = reinterpret_cast<const float4 *>(A + (int64_t)r * ld);
-      float S0 = 0.f, c0 = 0.f, S1 = 0.f, c1 = 0.f;
       int k = j;
-      for (; k + G < nv; k += 2 * G) {
-        df_acc(S0, c0, row[k], x[k]);
-        df_acc(S1, c1, row[k + G], x[k + G]);
+      for (; k + (NACC - 1) * G < nv; k += NACC * G) {
+#pragma unroll
+        for (int i = 0; i < NACC; ++i) df_acc(S[i], c[i], row[k + i * G], x[k + i * G]);
       }
-      if (k < nv) df_acc(S0, c0, row[k], x[k]);
-      v = ((double)S0 + (double)c0) + ((double)S1 + (double)c1);
+      for (; k < nv; k += G) df_acc(S[0], c[0], row[k], x[k]);
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (j == 0 && r < cn) y[r] = v;
+    for (int i = 1; i < NACC; ++i) df_add(S[0], c[0], S[i], c[i]);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const float S2 = __shfl_xor_sync(0xffffffffu, S[0], o), c2 = __shfl_xor_sync(0xffffffffu, c[0], o);
+      df_add(S[0], c[0], S2, c2);
+    }
+    if (j == 0 && r < cn) y[r] = (double)S[0] + (double)c[0];
   }
 }
 
-// the same for chunks of fewer than 16 long rows of (hi, lo) pairs: warps per row as in
-// chunk_rows_wide, FP64 partial sums
-__device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn, const float2 *xs, double *y,
-                                                double *part) {
+// the same for chunks of fewer than 8 long rows of (hi, lo) pairs: warps per row as in
+// chunk_rows_wide, the warps' double-FP32 partials exchanged through part (FP32 pairs)
+__device__ __forceinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn, const float2 *xs, double *y,
+                                                float2 *part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nv = ld / 2;
   const float4 *x = reinterpret_cast<const float4 *>(xs);
@@ -435,10 +450,9 @@ __device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn,
   const int rows_per_pass = nw / wpr;
   for (int rb = 0; rb < cn; rb += rows_per_pass) {
     const int r = rb + warp / wpr, j = warp % wpr;
-    double v = 0.0;
+    float S0 = 0.f, c0 = 0.f, S1 = 0.f, c1 = 0.f;
     if (r < cn) {
       const float4 *row = reinterpret_cast<const float4 *>(A + (int64_t)r * ld);
-      float S0 = 0.f, c0 = 0.f, S1 = 0.f, c1 = 0.f;
       const int step = 32 * wpr;
       int k = j * 32 + lane;
       for (; k + step < nv; k += 2 * step) {
@@ -446,18 +460,25 @@ __device__ __noinline__ void chunk_rows_df_wide(const float2 *A, int ld, int cn,
         df_acc(S1, c1, row[k + step], x[k + step]);
       }
       if (k < nv) df_acc(S0, c0, row[k], x[k]);
-      v = ((double)S0 + (double)c0) + ((double)S1 + (double)c1);
     }
-    v = warp_red(v);
+    df_add(S0, c0, S1, c1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float S2 = __shfl_xor_sync(0xffffffffu, S0, o), c2 = __shfl_xor_sync(0xffffffffu, c0, o);
+      df_add(S0, c0, S2, c2);
+    }
     if (wpr == 1) {
-      if (lane == 0 && r < cn) y[r] = v;
+      if (lane == 0 && r < cn) y[r] = (double)S0 + (double)c0;
     } else {
-      if (lane == 0) part[warp] = v;
+      if (lane == 0) part[warp] = make_float2(S0, c0);
       __syncthreads();
       if ((int)threadIdx.x < rows_per_pass && rb + (int)threadIdx.x < cn) {
-        double t = 0;
-        for (int q = 0; q < wpr; ++q) t += part[threadIdx.x * wpr + q];
-        y[rb + threadIdx.x] = t;
+        float S = 0.f, c = 0.f;
+        for (int q = 0; q < wpr; ++q) {
+          const float2 t = part[threadIdx.x * wpr + q];
+          df_add(S, c, t.x, t.y);
+        }
+        y[rb + threadIdx.x] = (double)S + (double)c;
       }
       __syncthreads();
     }
@@ -631,9 +652,15 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
         double *yc = reinterpret_cast<double *>(y) + (ring.consumed & 1ull) * RPC_MAX;
         const float2 *ap = reinterpret_cast<const float2 *>(buf);
         const float2 *xp = reinterpret_cast<const float2 *>(xs);
-        if (split == 1) chunk_rows_df<1>(ap, ld, cn, xp, yc);
-        else if (split == 2) chunk_rows_df_wide(ap, ld, cn, xp, yc, yc + RPC_MAX / 2);
-        else chunk_rows_df<8>(ap, ld, cn, xp, yc);
+        // lanes per row by row length (about 10 to 20 16-byte units per lane; measured
+        // on shared-memory chunks of 13 to 81 rows); fewer than 8 long rows: warps per row
+        if (nv <= 32) chunk_rows_df<1, 2>(ap, ld, cn, xp, yc);
+        else if (cn < 8 && nv > 160)
+          chunk_rows_df_wide(ap, ld, cn, xp, yc, reinterpret_cast<float2 *>(yc + RPC_MAX / 2));
+        else if (nv <= 80) chunk_rows_df<4, 2>(ap, ld, cn, xp, yc);
+        else if (nv <= 160) chunk_rows_df<8, 4>(ap, ld, cn, xp, yc);
+        else if (nv <= 320) chunk_rows_df<16, 2>(ap, ld, cn, xp, yc);
+        else chunk_rows_df<32, 2>(ap, ld, cn, xp, yc);
         __syncthreads();
         issue_next(ring, op, cur);
 #pragma unroll
