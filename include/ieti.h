@@ -170,6 +170,9 @@ typedef struct {
   int32_t factor_arena_mb; /* budget of the setup factorization's arena of dense patch blocks, MiB: the
                               patches are factored in batches that fit it (0: 64 GB or 40% of the free
                               device memory, whichever is smaller) */
+  int32_t coarse_top;    /* nested dissection: k >= 2 merges the separators of the top k levels of the
+                            bisection into one dense root block, 1 merges none; 0: none when coarse_leaf
+                            is given, else chosen with the leaf size by the same model */
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */

@@ -40,6 +40,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->wait_limit < 0) { err = "wait_limit must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse < IETI_COARSE_AUTO || o->coarse > IETI_COARSE_ND) { err = "bad coarse"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse_leaf < 0) { err = "coarse_leaf must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->coarse_top < 0) { err = "coarse_top must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->factor_arena_mb < 0) { err = "factor_arena_mb must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
@@ -61,12 +62,14 @@ int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ct
     ctx = new ieti_ctx();
     ctx->opt = *options;
     rc = ctx->hs.build(problem, options->host_threads, g_setup_err);
-    // nested-dissection tree of the coarse problem: the given leaf size, or the shape of
-    // least modelled solve time (~4 TB/s streaming, ~12 us per grid-synchronised level)
-    if (rc == IETI_OK)
-      rc = options->coarse_leaf > 0
-               ? ieti::build_coarse_tree(ctx->hs, options->coarse_leaf, 0, ctx->tree, g_setup_err)
-               : ieti::choose_coarse_tree(ctx->hs, 4e12, 12e-6, ctx->tree, g_setup_err);
+    // nested-dissection tree of the coarse problem: the given leaf size and top merge, or
+    // the shape of least modelled solve time over the free ones (~4 TB/s streaming,
+    // ~12 us per synchronised level)
+    if (rc == IETI_OK) {
+      const int leaf = options->coarse_leaf;
+      const int top = options->coarse_top > 0 ? options->coarse_top : (leaf > 0 ? 1 : 0);
+      rc = ieti::choose_coarse_tree(ctx->hs, 4e12, 12e-6, leaf, top, ctx->tree, g_setup_err);
+    }
     if (rc == IETI_OK && options->device >= 0)
       rc = ieti::device_setup(ctx->hs, &ctx->tree, ctx->opt, &ctx->dev, g_setup_err);
   } catch (const std::bad_alloc &) {

@@ -205,9 +205,11 @@ double coarse_tree_bytes(const CoarseTree &t) {
 
 int coarse_tree_levels(const CoarseTree &t) { return t.n_nodes ? t.n_height + std::max(t.n_depth - 1, 0) : 0; }
 
-int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTree &t, std::string &err) {
-  const int leaves[] = {1, 8, 16, 27, 64, 125};
-  const int tops[] = {0, 2, 3};
+int choose_coarse_tree(const HostSetup &hs, double bw, double latency, int leaf_fixed, int top_fixed,
+                       CoarseTree &t, std::string &err) {
+  std::vector<int> leaves = {1, 8, 16, 27, 64, 125}, tops = {0, 2, 3};
+  if (leaf_fixed > 0) leaves = {leaf_fixed};
+  if (top_fixed > 0) tops = {top_fixed > 1 ? top_fixed : 0};
   double best = 1e300;
   bool any = false;
   for (int leaf : leaves)
@@ -216,10 +218,10 @@ int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTre
       int rc = build_coarse_tree(hs, leaf, top, c, err);
       if (rc) return rc;
       // blocks wider than 2048 unknowns leave a ring stage of the solve a single row:
-      // only the candidate without merged top levels may have them
+      // only the candidate without merged top levels may have them (unless fixed)
       int widest = 0;
       for (int p = 0; p < c.n_nodes; ++p) widest = std::max({widest, c.nk[p], c.ns[p]});
-      if (top > 0 && widest > 2048) continue;
+      if (top > 0 && widest > 2048 && top_fixed == 0) continue;
       const double model = coarse_tree_bytes(c) / bw + coarse_tree_levels(c) * latency;
       if (!any || model < best * (1.0 - 1e-9)) {
         best = model;

@@ -50,7 +50,9 @@ double coarse_tree_bytes(const CoarseTree &t);
 int coarse_tree_levels(const CoarseTree &t);
 
 // Tree shape of least modelled solve time over a fixed candidate list of leaf sizes
-// and top merges: bytes / bw + phases * latency.
-int choose_coarse_tree(const HostSetup &hs, double bw, double latency, CoarseTree &t, std::string &err);
+// and top merges: bytes / bw + phases * latency.  leaf > 0 / top > 0 fix that
+// parameter (top 1: no merge).
+int choose_coarse_tree(const HostSetup &hs, double bw, double latency, int leaf, int top, CoarseTree &t,
+                       std::string &err);
 
 }  // namespace ieti

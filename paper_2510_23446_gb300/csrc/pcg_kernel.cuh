@@ -247,27 +247,6 @@ __device__ __forceinline__ void rows_dot(const T *A, int64_t ld, int r, int nval
   for (int i = 0; i < R; ++i) out[i] = warp_red_t(out[i]);
 }
 
-// dot products of one row of double-FP32 pairs (hi, lo) with staged pairs, by one
-// warp: exact products (TwoProd by FMA) accumulated with TwoSum in FP32, so the
-// result carries ~2^-46 relative accuracy without the FP64 pipe; the final
-// cross-lane sum is done in FP64 (one row per warp, cheap)
-__device__ __forceinline__ double row_dot_df(const float2 *row, const float2 *xs, int n) {
-  int lane = threadIdx.x & 31;
-  float sh = 0.f, sl = 0.f;
-  for (int k = lane; k < n; k += 32) {
-    float2 av = row[k], xv = xs[k];
-    float p = av.x * xv.x;
-    float e = fmaf(av.x, xv.x, -p);
-    float t = fmaf(av.x, xv.y, fmaf(av.y, xv.x, e));
-    float sum = sh + p;
-    float bb = sum - sh;
-    float err = (sh - (sum - bb)) + (p - bb);
-    sh = sum;
-    sl += err + t;
-  }
-  return warp_red((double)sh + (double)sl);
-}
-
 struct NoPre {
   __device__ double2 operator()(int) const { return make_double2(0.0, 0.0); }
   __device__ double2 operator()(int, int) const { return make_double2(0.0, 0.0); }
@@ -702,51 +681,14 @@ __device__ bool stream_phase(Ring &ring, const OpRows<E> &op, Cursor &cur, const
   return true;
 }
 
-// stream the rows of a single-segment OpRows<double> and hand each chunk to consume
-// (buffer, ld, first row, rows); stage() runs once before the first chunk
-template <class Stage, class Consume>
-__device__ bool stream_phase_raw(Ring &ring, const OpRows<double> &op, Cursor &cur, unsigned *errflag, Stage stage,
-                                 Consume consume, unsigned long long *ts = nullptr) {
-  while (cur.issued < ring.ns && issue_next(ring, op, cur)) {
-  }
-  if (op.nseg() == 0) return true;
-  int s, r0, r1, ld;
-  const double *A;
-  op.seg(0, s, r0, r1, ld, A);
-  __syncthreads();
-  stage();
-  __syncthreads();
-  if (ts && threadIdx.x == 0) ts[0] = gtimer();
-  int rpc = rows_per_chunk<double>(ring, ld);
-  for (int c0 = 0; r0 + c0 < r1; c0 += rpc) {
-    int st = (int)(ring.consumed % ring.ns);
-    unsigned parity = (unsigned)((ring.consumed / ring.ns) & 1ull);
-    bool ok = mbar_wait(ring.bar + st, parity);
-    if (__syncthreads_or(!ok)) {
-      atomicExch(errflag, 1u);
-      for (unsigned long long g = ring.consumed + 1; g < ring.issued; ++g)
-        mbar_wait(ring.bar + (g % ring.ns), (unsigned)((g / ring.ns) & 1ull));
-      ring.consumed = ring.issued;
-      return false;
-    }
-    if (ts && c0 == 0 && threadIdx.x == 0) ts[1] = gtimer();
-    ring.consumed++;
-    consume(reinterpret_cast<const double *>(ring.stage + (size_t)st * ring.bytes), ld, r0 + c0,
-            min(rpc, r1 - r0 - c0));
-    __syncthreads();
-    issue_next(ring, op, cur);
-  }
-  if (ts && threadIdx.x == 0) ts[2] = gtimer();
-  return true;
-}
-
 // ND: the coarse solve by nested dissection (a separate instantiation, so that the
 // dense-coarse kernel carries none of its code or registers)
 template <class T, bool ND>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constant__ PcgArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sh[32];
-  using YB = typename std::conditional<ND, double, T>::type;  // the FP64 coarse rows stage their results too
+  // the coarse rows (FP64, or double-FP32 pairs in the mixed path) stage FP64 results too
+  using YB = typename std::conditional<ND || sizeof(T) == 4, double, T>::type;
   __shared__ __align__(16) YB ybuf_raw[2 * RPC_MAX];  // row results of the last two chunks
   T *ybuf = reinterpret_cast<T *>(ybuf_raw);
   __shared__ __align__(8) uint64_t ring_bar[NS_MAX];
@@ -1048,26 +990,19 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_ddsolve(const __grid_constan
                              },
                              [&](int, int r, double v, double2) { a.q[r] = v; }, NoPre(), tsp(1));
     } else {
-      // rows of (hi, lo) pairs, streamed as doubles (8 bytes per entry), computed in
-      // double-FP32 arithmetic by warp-per-row dots
+      // rows of (hi, lo) pairs, streamed as 8-byte entries, through the double-FP32 row
+      // kernels of the ring loop
       float2 *xp = reinterpret_cast<float2 *>(smem_raw);
-      int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      return stream_phase_raw(ring, opS, cur, errflag,
-                              [&]() {
-                                for (int k = threadIdx.x; k < a.ldc; k += nthr) {
-                                  double c = k < a.nc ? ldcg(a.cc + k) : 0.0;
-                                  float hi = (float)c;
-                                  xp[k] = make_float2(hi, (float)(c - (double)hi));
-                                }
-                              },
-                              [&](const double *buf, int ld, int row0, int nrows) {
-                                const float2 *rows = reinterpret_cast<const float2 *>(buf);
-                                for (int r = warp; r < nrows; r += nw) {
-                                  double v = row_dot_df(rows + (int64_t)r * ld, xp, a.nc);
-                                  if (lane == 0) a.q[row0 + r] = v;
-                                }
-                              },
-                              tsp(1));
+      return stream_phase<4, double, true>(ring, opS, cur, reinterpret_cast<const double *>(smem_raw),
+                                           reinterpret_cast<double *>(ybuf_raw), errflag,
+                                           [&](int, int, int) {
+                                             for (int k = threadIdx.x; k < a.ldc; k += nthr) {
+                                               const double c = k < a.nc ? ldcg(a.cc + k) : 0.0;
+                                               const float hi = (float)c;
+                                               xp[k] = make_float2(hi, (float)(c - (double)hi));
+                                             }
+                                           },
+                                           [&](int, int r, double v, double2) { a.q[r] = v; }, NoPre(), tsp(1));
     }
   };
   // zf = zb - Psi q on the interface rows; out(global B index, zf, ub)

@@ -45,13 +45,13 @@ def ieti():
     return mod
 
 
-def _setup(ieti, name, leaf):
+def _setup(ieti, name, leaf, top=0):
     if name not in _ORACLE:
         prob = CASES[name]()
         I = OracleProblem(prob).ietidp()
         _ORACLE[name] = (prob, I.Sc, np.nonzero(I.dec.gauge.cls == 1)[0])
     prob, Sc, prim = _ORACLE[name]
-    S = ieti.Solver.from_problem(prob, device=-1, coarse_leaf=leaf)
+    S = ieti.Solver.from_problem(prob, device=-1, coarse_leaf=leaf, coarse_top=top)
     t = S.coarse_tree()
     S.close()
     # oracle coarse index i (primal edges ascending) -> elimination position
@@ -72,10 +72,14 @@ def _nodes(t):
     return nn, S, kids
 
 
-@pytest.mark.parametrize("leaf", [1, 8])
+# (leaf size, top merge): coarse_top k >= 2 merges the separators of the top k levels
+SHAPES = [(1, 0), (8, 0), (1, 2), (1, 3)]
+
+
+@pytest.mark.parametrize("leaf,top", SHAPES)
 @pytest.mark.parametrize("name", list(CASES))
-def test_tree_is_an_elimination_structure(ieti, name, leaf):
-    t, Sp = _setup(ieti, name, leaf)
+def test_tree_is_an_elimination_structure(ieti, name, leaf, top):
+    t, Sp = _setup(ieti, name, leaf, top)
     nn, S, kids = _nodes(t)
     nc = Sp.shape[0]
     assert nn > 0 and t["k0"][0] == 0 and t["k0"][-1] + t["nk"][-1] == nc
@@ -96,10 +100,10 @@ def test_tree_is_an_elimination_structure(ieti, name, leaf):
         assert all(node[x] in anc[p] for x in S[p])
 
 
-@pytest.mark.parametrize("leaf", [1, 8])
+@pytest.mark.parametrize("leaf,top", SHAPES)
 @pytest.mark.parametrize("name", list(CASES))
-def test_fronts_hold_the_fill(ieti, name, leaf):
-    t, Sp = _setup(ieti, name, leaf)
+def test_fronts_hold_the_fill(ieti, name, leaf, top):
+    t, Sp = _setup(ieti, name, leaf, top)
     nn, S, _ = _nodes(t)
     L = np.linalg.cholesky(Sp)
     tiny = 1e-12 * np.abs(L).max()
@@ -153,11 +157,21 @@ def _multifrontal_solve(t, Sp, c):
     return q
 
 
-@pytest.mark.parametrize("leaf", [1, 2, 8])
+@pytest.mark.parametrize("leaf,top", SHAPES + [(2, 0)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_multifrontal_sweeps_solve_the_coarse_problem(ieti, name, leaf):
-    t, Sp = _setup(ieti, name, leaf)
+def test_multifrontal_sweeps_solve_the_coarse_problem(ieti, name, leaf, top):
+    t, Sp = _setup(ieti, name, leaf, top)
     c = np.random.default_rng(7).standard_normal(Sp.shape[0])
     q = _multifrontal_solve(t, Sp, c)
     ref = np.linalg.solve(Sp, c)
     assert np.linalg.norm(q - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", ["c4_family", "ragged_p23"])
+def test_top_merge_forms_one_root_block(ieti, name):
+    """coarse_top = 2 moves the first bisection level's separators into the root: fewer
+    nodes, a larger last block, the same unknowns."""
+    t1, _ = _setup(ieti, name, 1, 1)
+    t2, _ = _setup(ieti, name, 1, 2)
+    assert len(t2["nk"]) < len(t1["nk"])
+    assert t2["nk"][-1] > t1["nk"][-1] and t2["nk"].sum() == t1["nk"].sum()

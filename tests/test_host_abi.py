@@ -108,6 +108,8 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     dict(precision="fp64", graph=2),
     dict(precision="fp64", l2_persist=3),
     dict(precision="fp64", wait_limit=-1),
+    dict(precision="fp64", coarse_leaf=-1),
+    dict(precision="fp64", coarse_top=-1),
 ])
 def test_invalid_options_return_codes(ieti, kw):
     prob = make_problem("c1")
