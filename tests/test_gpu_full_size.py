@@ -6,7 +6,10 @@ quadratic time predictor, FP64 outer stop 1e-12, the coarse solve the library pi
   edge DOFs);
 * the 343-patch workload of uneven patches (per-slab elements in {4..12} and degrees in
   {2, 3}, conductor or air per patch with sigma = 1e3; 720,617 edge DOFs, 32,994 coarse
-  unknowns, the nested-dissection coarse solve).
+  unknowns, the nested-dissection coarse solve);
+* the 8x8x8 member of the p = 3 patch-count sweep (curved patches of 8^3 elements,
+  sigma = 1e2 in the patches centred in [0.25, 0.75]^3, linear; 1,574,640 edge DOFs,
+  10,354 coarse unknowns, nested dissection, the setup factorization in batches).
 
 The whole oracle is too slow at these sizes, so outputs are checked where the oracle
 computes them one patch at a time: in a conducting patch away from the outer
@@ -48,14 +51,20 @@ def ieti():
     return mod
 
 
-@pytest.fixture(scope="module", params=["c3", "c4"])
+def _problem(name):
+    if name == "c5_8":
+        return make_problem("c5", patches_per_dir=8, nonlinear=False)
+    return make_problem(name)
+
+
+@pytest.fixture(scope="module", params=["c3", "c4", "c5_8"])
 def runs(ieti, request):
     import torch
-    prob = make_problem(request.param)
+    prob = _problem(request.param)
     out = {}
     for mode in ("mixed", "fp64"):
         S = ieti.Solver.from_problem(prob, device=0, **OPTS[mode])
-        if request.param == "c4":
+        if request.param in ("c4", "c5_8"):
             assert S.info()["coarse_mode"] == 2      # the nested-dissection coarse solve
         jd = torch.from_numpy(S.load_vector(prob.coil)).cuda()
         states, stats = [], []
