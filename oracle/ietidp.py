@@ -87,6 +87,17 @@ class Decomposition:
         # load split weights (1/k for a DOF shared by k patches)
         self.load_w = [1.0 / L.n_share[asm.l2g[s]] for s in range(self.n_patches)]
 
+    def pair_space(self):
+        """U (m x k, sparse): one column per pair of patches (s < t) joined by at least one
+        multiplier, the indicator of that pair's multipliers.  U^T lambda are the
+        patch-pair sums of lambda, the deflation space of the balanced preconditioner
+        (Sec. 5 recommends deflation in the Dirichlet preconditioner; this is that
+        recommendation's reading, see IETIDP)."""
+        pairs = sorted({(s1, s2) for (_, s1, _, s2, _) in self.lam})
+        col = {p: j for j, p in enumerate(pairs)}
+        cols = [col[(s1, s2)] for (_, s1, _, s2, _) in self.lam]
+        return sp.csr_matrix((np.ones(self.m), (np.arange(self.m), cols)), shape=(self.m, len(pairs)))
+
     def scaled_B(self, W_diag, mode):
         """B_D,s: entry of the copy in s for the multiplier (s,t) times delta_t^dagger."""
         if mode in (PRECOND_NONE, PRECOND_DIRICHLET):
@@ -113,9 +124,16 @@ class Decomposition:
 
 
 class IETIDP:
-    """FETI-DP operators for W_s = M_s + dt K_s (dense local blocks, LAPACK)."""
+    """FETI-DP operators for W_s = M_s + dt K_s (dense local blocks, LAPACK).
 
-    def __init__(self, dec: Decomposition, precond=PRECOND_DIRICHLET):
+    deflation=True (or an explicit U) wraps the preconditioner M in the balancing form
+        M_bal = (I - P) M (I - P)^T + U E^{-1} U^T,  P = U E^{-1} U^T F,  E = U^T F U,
+    with U the patch-pair space of ``Decomposition.pair_space``: Sec. 5 recommends
+    "deflation in the Dirichlet preconditioner" without fixing its form; this is the
+    balancing (projector) form of a deflation space for dual-primal methods, which
+    keeps M_bal symmetric so plain PCG applies and leaves the solution unchanged."""
+
+    def __init__(self, dec: Decomposition, precond=PRECOND_DIRICHLET, deflation=False, U=None):
         self.dec = dec
         asm = dec.asm
         dt = dec.prob.dt
@@ -155,6 +173,12 @@ class IETIDP:
         self.Sc = Sc
         self.Sc_f = sla.cho_factor(Sc, lower=True) if n_c else None
         self.BD = dec.scaled_B(W_diag, precond)
+        self.U = None
+        if deflation or U is not None:
+            self.U = dec.pair_space() if U is None else sp.csr_matrix(U)
+            Ud = self.U.toarray()
+            self.FU = np.column_stack([self.apply_F(Ud[:, j]) for j in range(Ud.shape[1])])
+            self.E_f = sla.cho_factor(self.U.T @ self.FU, lower=True)
 
     # B_s^T acting from lambda-space to the r-space (zeros on interior DOFs)
     def _BT(self, s, v):
@@ -183,13 +207,21 @@ class IETIDP:
             out += self._B(s, y)
         return out
 
-    def apply_precond(self, r):
+    def _dirichlet(self, r):
         if self.precond == PRECOND_NONE:
             return r.copy()
         out = np.zeros(self.dec.m)
         for s in range(self.dec.n_patches):
             out += self.BD[s] @ (self.Wbb_S[s] @ (self.BD[s].T @ r))
         return out
+
+    def apply_precond(self, r):
+        if self.U is None:
+            return self._dirichlet(r)
+        # M_bal r = (I - P) M (I - P)^T r + U E^{-1} U^T r, with (I - P)^T = I - F U E^{-1} U^T
+        ur = self.U.T @ r
+        w = self._dirichlet(r - self.FU @ sla.cho_solve(self.E_f, ur))
+        return w + self.U @ sla.cho_solve(self.E_f, ur - self.FU.T @ w)
 
     def rhs(self, f_loc):
         """d and g_c for local right-hand sides f_s (patch-local numbering)."""

@@ -32,10 +32,11 @@ class OracleProblem:
             self._dec = Decomposition(self.prob, self.asm, self.gauge)
         return self._dec
 
-    def ietidp(self, precond=PRECOND_DIRICHLET):
-        if precond not in self._ieti:
-            self._ieti[precond] = IETIDP(self.dec, precond)
-        return self._ieti[precond]
+    def ietidp(self, precond=PRECOND_DIRICHLET, deflation=False):
+        key = (precond, bool(deflation))
+        if key not in self._ieti:
+            self._ieti[key] = IETIDP(self.dec, precond, deflation=deflation)
+        return self._ieti[key]
 
     def run_monolithic(self, n_steps, j_of_step=None, a0=None):
         a = np.zeros(self.asm.lat.n_edges) if a0 is None else a0.copy()
@@ -46,8 +47,8 @@ class OracleProblem:
             out.append(a)
         return out
 
-    def run_ietidp(self, n_steps, tol, precond=PRECOND_DIRICHLET, j_of_step=None, a0=None):
-        I = self.ietidp(precond)
+    def run_ietidp(self, n_steps, tol, precond=PRECOND_DIRICHLET, j_of_step=None, a0=None, deflation=False):
+        I = self.ietidp(precond, deflation)
         a = np.zeros(self.asm.lat.n_edges) if a0 is None else a0.copy()
         out, its = [], []
         for l in range(n_steps):
