@@ -594,17 +594,23 @@ def precond_contrast_leg(ieti, torch, dev, stream, n_steps=4):
     for n in (2, 4, 6):
         prob = make_problem("c3", patches_per_dir=4, n_el=n)
         row = {}
-        for pc in ("none", "dirichlet", "dirichlet_mult", "dirichlet_stiff"):
+        for key, pc, defl in (("none", "none", 0), ("dirichlet", "dirichlet", 0),
+                              ("dirichlet_mult", "dirichlet_mult", 0), ("dirichlet_stiff", "dirichlet_stiff", 0),
+                              ("balanced_dirichlet", "dirichlet", 1), ("balanced_stiff", "dirichlet_stiff", 1)):
             S = ieti.Solver.from_problem(prob, device=dev, stream=stream, precision="fp64", precond=pc,
-                                         cg_tol=1e-8, max_sweeps=1, cg_max_it=20000)
+                                         cg_tol=1e-8, max_sweeps=1, cg_max_it=20000, deflation=defl)
             jd = torch.from_numpy(S.load_vector(prob.coil)).to(f"cuda:{dev}")
             its = [S.step(jd, raise_on_error=False)["cg_its"] for _ in range(n_steps)]
-            row[pc] = float(sum(its) / n_steps)
-            n_dofs, n_coarse = S.n, S.info()["n_coarse"]
+            row[key] = float(sum(its) / n_steps)
+            n_dofs, n_coarse, k = S.n, S.info()["n_coarse"], S.info()["deflation_dim"]
+            if defl:
+                pairs = k
             S.close()
-        out[f"H/h={n}"] = {"elements_per_patch": f"{n}^3", "n_dofs": n_dofs, "n_coarse": n_coarse, "mean_cg_its": row}
+        out[f"H/h={n}"] = {"elements_per_patch": f"{n}^3", "n_dofs": n_dofs, "n_coarse": n_coarse,
+                           "patch_pairs": pairs, "mean_cg_its": row}
     return {"workload": "4x4x4 curved p=2 patches, sigma log-uniform in [1,1e4] per patch within radius 0.35, "
-                        f"nu in [0.5,2], coil J0=1, dt=1e-3; FP64 path, PCG tol 1e-8, one sweep, {n_steps} steps",
+                        f"nu in [0.5,2], coil J0=1, dt=1e-3; FP64 path, PCG tol 1e-8, one sweep, {n_steps} steps; "
+                        "balanced_*: the preconditioner in balancing form over the patch-pair space",
             "by_h": out}
 
 

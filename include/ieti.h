@@ -173,6 +173,16 @@ typedef struct {
   int32_t coarse_top;    /* nested dissection: k >= 2 merges the separators of the top k levels of the
                             bisection into one dense root block, 1 merges none; 0: none when coarse_leaf
                             is given, else chosen with the leaf size by the same model */
+  /* 1: the preconditioner (any precond, also NONE) in balancing form, the reading of
+   * the deflation that Sec. 5 recommends for the Dirichlet preconditioner:
+   *   M_bal = (I - P) M (I - P)^T + U E^{-1} U^T,  P = U E^{-1} U^T F,  E = U^T F U,
+   * with U one column per pair of patches joined by multipliers (the indicator of that
+   * pair's multipliers).  M_bal is symmetric and the solution is unchanged.  Setup
+   * applies F to the k columns of U (k = ieti_info.deflation_dim) and keeps F U (k x m
+   * FP64) on the device; every PCG iteration streams it twice.  The dual problem then
+   * runs in the host-loop PCG (pcg_mode 1, no graph).  IETI_ERR_TOO_LARGE when
+   * 8 k m > 8 GB or k > 8192.  0: off. */
+  int32_t deflation;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */
@@ -244,6 +254,7 @@ typedef struct {
                                 autotuner tries a few, 0 by the rule) */
   int32_t coarse_flow;       /* 1: the nested-dissection levels wait on per-node completion counters instead of
                                 grid barriers (the autotuner's choice; 0 by the rule) */
+  int32_t deflation_dim;     /* columns of the balanced preconditioner's pair space (0: off) */
 } ieti_info;
 
 /* Kernel classes timed when options.profile = 1 (CUDA events on the step stream). */

@@ -41,6 +41,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->coarse < IETI_COARSE_AUTO || o->coarse > IETI_COARSE_ND) { err = "bad coarse"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse_leaf < 0) { err = "coarse_leaf must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse_top < 0) { err = "coarse_top must be >= 0"; return IETI_ERR_INVALID_ARG; }
+  if (o->deflation != 0 && o->deflation != 1) { err = "deflation must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
   if (o->factor_arena_mb < 0) { err = "factor_arena_mb must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";

@@ -885,6 +885,12 @@ struct DeviceState {
   int32_t *iseg_ptr = nullptr, *iseg_s = nullptr, *iseg_r0 = nullptr, *iseg_r1 = nullptr;
   int32_t *tseg_ptr = nullptr, *tseg_s = nullptr, *tseg_r0 = nullptr, *tseg_r1 = nullptr;
   double *kg = nullptr, *ub1 = nullptr, *uz = nullptr;
+  // balanced (deflated) preconditioner: k patch pairs, the pair of every multiplier,
+  // the multipliers of every pair (CSR), F U (k rows of length m), E^{-1} (k x k, FP64)
+  int defl_k = 0;
+  int32_t *defl_pair = nullptr, *defl_ptr = nullptr, *defl_lam = nullptr;
+  double *defl_FUt = nullptr, *defl_Einv = nullptr, *defl_ur = nullptr, *defl_c = nullptr, *defl_fw = nullptr;
+  double *defl_rh = nullptr, *defl_w = nullptr;
   double *Sdf = nullptr;  // mixed path: S_c^{-1} as (hi, lo) FP32 pairs, viewed as doubles
   // per-iteration operators (H, Q, P, coarse) share one arena, the L2 access-policy window
   unsigned char *iter_arena = nullptr;
@@ -2104,8 +2110,112 @@ static void apply_F(DeviceState *d, const double *v, double *out, const double *
   d->nlaunch++;
 }
 
+// ---- balanced (deflated) preconditioner  M_bal = (I - P) M (I - P)^T + U E^{-1} U^T,
+// P = U E^{-1} U^T F, E = U^T F U, U the patch-pair indicator space of the multipliers
+
+// ur[j] = sum of v over the multipliers of pair j (one block per pair)
+__global__ void k_pair_sums(int k, const int32_t *ptr, const int32_t *lam, const double *v, double *ur) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  if (j >= k) return;
+  double acc = 0.0;
+  for (int t = ptr[j] + threadIdx.x; t < ptr[j + 1]; t += blockDim.x) acc += v[lam[t]];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    ur[j] = t;
+  }
+}
+
+// c = Einv (a - b)   (b may be null; k x k row-major, thread per row)
+__global__ void k_small_gemv(int k, const double *Einv, const double *a, const double *b, double *c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double acc = 0.0;
+  for (int j = 0; j < k; ++j) acc += Einv[(int64_t)i * k + j] * (b ? a[j] - b[j] : a[j]);
+  c[i] = acc;
+}
+
+// out[l] = v[l] - sum_j FUt[j][l] c[j]   (thread per multiplier, the k rows read coalesced)
+__global__ void k_defl_sub(int64_t m, int k, const double *FUt, const double *c, const double *v, double *out) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= m) return;
+  double acc = v[l];
+  for (int j = 0; j < k; ++j) acc -= FUt[(int64_t)j * m + l] * c[j];
+  out[l] = acc;
+}
+
+// fw[j] = FUt[j] . w   (one block per row)
+__global__ void k_defl_dots(int64_t m, int k, const double *FUt, const double *w, double *fw) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  if (j >= k) return;
+  const double *row = FUt + (int64_t)j * m;
+  double acc = 0.0;
+  for (int64_t l = threadIdx.x; l < m; l += blockDim.x) acc += row[l] * w[l];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    fw[j] = t;
+  }
+}
+
+// out[l] = w[l] + c[pair[l]]; partial sums of out . dotv (PCG's (r, z))
+__global__ void k_defl_finish(int64_t m, const int32_t *pair, const double *w, const double *c, double *out,
+                              const double *dotv, double *part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[l] + c[pair[l]];
+    out[l] = v;
+    if (dotv) acc += v * dotv[l];
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// v[l] = (pair[l] == j)
+__global__ void k_pair_indicator(int64_t m, const int32_t *pair, int j, double *v) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l < m) v[l] = pair[l] == j ? 1.0 : 0.0;
+}
+
+template <class T>
+static void apply_dirichlet(DeviceState *d, const double *rv, double *out, const double *dotv, double *part);
+
 template <class T>
 static void apply_precond(DeviceState *d, const double *rv, double *out, const double *dotv, double *part) {
+  if (d->defl_k == 0) {
+    apply_dirichlet<T>(d, rv, out, dotv, part);
+    return;
+  }
+  cudaStream_t st = d->stream;
+  const int64_t m = d->M;
+  const int k = d->defl_k;
+  k_pair_sums<<<k, 128, 0, st>>>(k, d->defl_ptr, d->defl_lam, rv, d->defl_ur);          // U^T r
+  k_small_gemv<<<grid_for(k, 128), 128, 0, st>>>(k, d->defl_Einv, d->defl_ur, nullptr, d->defl_c);
+  k_defl_sub<<<grid_for(m, 256), 256, 0, st>>>(m, k, d->defl_FUt, d->defl_c, rv, d->defl_rh);  // (I - P)^T r
+  apply_dirichlet<T>(d, d->defl_rh, d->defl_w, rv, part);                                 // w = M (...)
+  k_defl_dots<<<k, 256, 0, st>>>(m, k, d->defl_FUt, d->defl_w, d->defl_fw);              // (F U)^T w
+  k_small_gemv<<<grid_for(k, 128), 128, 0, st>>>(k, d->defl_Einv, d->defl_ur, d->defl_fw, d->defl_c);
+  k_defl_finish<<<RED_BLOCKS, 256, 0, st>>>(m, d->defl_pair, d->defl_w, d->defl_c, out, dotv, part);
+  d->nlaunch += 6;
+}
+
+template <class T>
+static void apply_dirichlet(DeviceState *d, const double *rv, double *out, const double *dotv, double *part) {
   cudaStream_t st = d->stream;
   int pcnd = d->opt.precond;
   if (pcnd == IETI_PRECOND_NONE) {
@@ -3078,9 +3188,101 @@ static int pcg_autotune(DeviceState *d, std::string &err) {
   return IETI_OK;
 }
 
-int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options &opt, DeviceState **out,
+// The balanced preconditioner's deflation space: one column per pair of patches
+// (s < t) joined by multipliers, the indicator of that pair's multipliers.  F U by k
+// applications of the dual operator (the setup's operators, the path's precision),
+// E = U^T F U summed on the host in FP64, E^{-1} by a host Cholesky (k is the number of
+// patch pairs: hundreds to a few thousand).
+template <class T>
+static int deflation_setup(DeviceState *d, const HostSetup &hs, std::string &err) {
+  const int64_t m = d->M;
+  if (m == 0) return IETI_OK;
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  pairs.reserve(hs.lam.size());
+  for (const Multiplier &L : hs.lam) pairs.emplace_back(L.s, L.t);
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  const int k = (int)pairs.size();
+  if ((double)k * (double)m * 8.0 > 8e9 || k > 8192) {
+    err = "balanced preconditioner: the patch-pair space is too large (" + std::to_string(k) + " pairs x " +
+          std::to_string(m) + " multipliers)";
+    return IETI_ERR_TOO_LARGE;
+  }
+  std::vector<int32_t> pair_of(m), ptr(k + 1, 0), lam_of(m);
+  for (int64_t l = 0; l < m; ++l) {
+    const auto it = std::lower_bound(pairs.begin(), pairs.end(), std::make_pair(hs.lam[l].s, hs.lam[l].t));
+    pair_of[l] = (int32_t)(it - pairs.begin());
+    ptr[pair_of[l] + 1]++;
+  }
+  for (int j = 0; j < k; ++j) ptr[j + 1] += ptr[j];
+  {
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t l = 0; l < m; ++l) lam_of[fill[pair_of[l]]++] = (int32_t)l;
+  }
+  int rc;
+  if ((rc = upload(d, &d->defl_pair, pair_of, err)) || (rc = upload(d, &d->defl_ptr, ptr, err)) ||
+      (rc = upload(d, &d->defl_lam, lam_of, err)) || (rc = dalloc(d, &d->defl_FUt, (size_t)k * m, err)) ||
+      (rc = dalloc(d, &d->defl_Einv, (size_t)k * k, err)) || (rc = dalloc(d, &d->defl_ur, (size_t)k, err)) ||
+      (rc = dalloc(d, &d->defl_c, (size_t)k, err)) || (rc = dalloc(d, &d->defl_fw, (size_t)k, err)) ||
+      (rc = dalloc(d, &d->defl_rh, (size_t)m, err)) || (rc = dalloc(d, &d->defl_w, (size_t)m, err)))
+    return rc;
+  cudaStream_t st = d->stream;
+  for (int j = 0; j < k; ++j) {
+    k_pair_indicator<<<grid_for(m, 256), 256, 0, st>>>(m, d->defl_pair, j, d->defl_w);
+    apply_F<T>(d, d->defl_w, d->defl_FUt + (int64_t)j * m, d->defl_w, d->part);
+  }
+  d->launches_setup += 3 * (int64_t)k;
+  CK(cudaGetLastError());
+  std::vector<double> FUt((size_t)k * m), E((size_t)k * k, 0.0);
+  CK(cudaMemcpyAsync(FUt.data(), d->defl_FUt, FUt.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j = 0; j < k; ++j)
+    for (int64_t l = 0; l < m; ++l) E[(size_t)pair_of[l] * k + j] += FUt[(size_t)j * m + l];
+  for (int i = 0; i < k; ++i)       // F is symmetric: average the two rounding orders
+    for (int j = 0; j < i; ++j) E[(size_t)i * k + j] = E[(size_t)j * k + i] = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
+  // Cholesky E = L L^T (lower, in place), then E^{-1} = L^{-T} L^{-1} column by column
+  for (int j = 0; j < k; ++j) {
+    double dj = E[(size_t)j * k + j];
+    for (int q = 0; q < j; ++q) dj -= E[(size_t)j * k + q] * E[(size_t)j * k + q];
+    if (!(dj > 0.0)) {
+      err = "balanced preconditioner: U^T F U is not positive definite (pair " + std::to_string(j) + ")";
+      return IETI_ERR_NOT_SPD;
+    }
+    const double ljj = std::sqrt(dj);
+    E[(size_t)j * k + j] = ljj;
+    for (int i = j + 1; i < k; ++i) {
+      double v = E[(size_t)i * k + j];
+      for (int q = 0; q < j; ++q) v -= E[(size_t)i * k + q] * E[(size_t)j * k + q];
+      E[(size_t)i * k + j] = v / ljj;
+    }
+  }
+  std::vector<double> Einv((size_t)k * k), col(k);
+  for (int c = 0; c < k; ++c) {
+    for (int i = 0; i < k; ++i) {   // L y = e_c
+      double v = i == c ? 1.0 : 0.0;
+      for (int q = 0; q < i; ++q) v -= E[(size_t)i * k + q] * col[q];
+      col[i] = v / E[(size_t)i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {  // L^T x = y
+      double v = col[i];
+      for (int q = i + 1; q < k; ++q) v -= E[(size_t)q * k + i] * col[q];
+      col[i] = v / E[(size_t)i * k + i];
+    }
+    for (int i = 0; i < k; ++i) Einv[(size_t)i * k + c] = col[i];
+  }
+  CK(cudaMemcpyAsync(d->defl_Einv, Einv.data(), Einv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  d->defl_k = k;
+  return IETI_OK;
+}
+
+int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options &opt_in, DeviceState **out,
                  std::string &err) {
   auto t0 = std::chrono::steady_clock::now();
+  // the balanced preconditioner runs in the host-loop PCG (its projections are extra
+  // passes between the library's kernels)
+  ieti_options opt = opt_in;
+  if (opt.deflation) opt.pcg_mode = 1;
   DeviceState *d = new DeviceState();
   *out = nullptr;
   d->opt = opt;
@@ -3935,6 +4137,8 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     CK(cudaStreamSynchronize(d->stream));
     d->refactors = 0;
   }
+  if (opt.deflation && (rc = d->mixed ? deflation_setup<float>(d, hs, err) : deflation_setup<double>(d, hs, err)))
+    return fail(rc);
   if (opt.autotune && opt.pcg_mode == 0) {
     rc = d->mixed ? pcg_autotune<float>(d, err) : pcg_autotune<double>(d, err);
     if (rc) return fail(rc);
@@ -4042,6 +4246,7 @@ void device_info(const DeviceState *d, ieti_info *info) {
   info->factor_batches = d->factor_batches;
   info->pcg_seg_weight = d->seg_overhead;
   info->coarse_flow = d->nd_flow;
+  info->deflation_dim = d->defl_k;
 }
 
 void device_kernel_stats(DeviceState *d, ieti_kernel_stat *out, bool reset) {

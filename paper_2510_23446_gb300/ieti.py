@@ -44,7 +44,8 @@ class ieti_options(C.Structure):
                 ("factor", C.c_int32), ("refactor", C.c_int32), ("newton_tol", C.c_double),
                 ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
                 ("graph", C.c_int32), ("wait_limit", C.c_int32), ("coarse", C.c_int32),
-                ("coarse_leaf", C.c_int32), ("factor_arena_mb", C.c_int32), ("coarse_top", C.c_int32)]
+                ("coarse_leaf", C.c_int32), ("factor_arena_mb", C.c_int32), ("coarse_top", C.c_int32),
+                ("deflation", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -81,7 +82,7 @@ class ieti_info(C.Structure):
                 ("tune_us_per_it", C.c_double * 2), ("step_graph", C.c_int32), ("coarse_mode", C.c_int32),
                 ("coarse_nodes", C.c_int32), ("coarse_levels", C.c_int32), ("coarse_bytes", C.c_double),
                 ("t_coarse_ms", C.c_double), ("factor_batches", C.c_int32), ("pcg_seg_weight", C.c_int32),
-                ("coarse_flow", C.c_int32)]
+                ("coarse_flow", C.c_int32), ("deflation_dim", C.c_int32)]
 
 
 _ctx = C.c_void_p
@@ -148,7 +149,8 @@ class Solver:
                  precision="fp64", precond="dirichlet_stiff", cg_tol=1e-10, cg_max_it=5000,
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
-                 graph=1, wait_limit=0, coarse="auto", coarse_leaf=0, factor_arena_mb=0, coarse_top=0):
+                 graph=1, wait_limit=0, coarse="auto", coarse_leaf=0, factor_arena_mb=0, coarse_top=0,
+                 deflation=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -196,6 +198,7 @@ class Solver:
         op.coarse = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
         op.coarse_leaf = int(coarse_leaf)
         op.coarse_top = int(coarse_top)
+        op.deflation = int(deflation)
         op.factor_arena_mb = int(factor_arena_mb)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive
