@@ -360,7 +360,7 @@ __device__ __noinline__ void chunk_rows_wide(const T *A, int ld, int cn, const T
 // Double-FP32 rows: entries stored as (hi, lo) FP32 pairs of FP64 values, dotted with
 // staged (hi, lo) pairs by exact FP32 products (TwoProd by FMA) accumulated with TwoSum;
 // the cross terms hi*lo + lo*hi go into the compensation, lo*lo (2^-48) is dropped.
-// About 2^-46 relative per dot, on the FP32 pipe (GB300's FP64 pipe is ~1/64 of it).
+// About 2^-45 of sum |a x| per dot, on the FP32 pipe (GB300's FP64 pipe is ~1/64 of it).
 // One 16-byte unit = two pairs.
 __device__ __forceinline__ void df_acc(float &S, float &c, float4 a, float4 x) {
   const float p0 = a.x * x.x, e0 = fmaf(a.x, x.x, -p0), t0 = fmaf(a.x, x.y, a.y * x.x);
