@@ -3203,7 +3203,7 @@ static int deflation_setup(DeviceState *d, const HostSetup &hs, std::string &err
   std::sort(pairs.begin(), pairs.end());
   pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
   const int k = (int)pairs.size();
-  if ((double)k * (double)m * 8.0 > 8e9 || k > 8192) {
+  if ((double)k * (double)m * 8.0 > 8e9 || k > 4096) {  // F U on the device, E^{-1} by a host Cholesky
     err = "balanced preconditioner: the patch-pair space is too large (" + std::to_string(k) + " pairs x " +
           std::to_string(m) + " multipliers)";
     return IETI_ERR_TOO_LARGE;
