@@ -108,3 +108,28 @@ def test_residuals_stay_orthogonal_to_the_pair_space():
         rz_new = r @ z
         p = z + rz_new / rz * p
         rz = rz_new
+
+
+@pytest.mark.parametrize("prob", _cases(), ids=lambda p: p.name)
+def test_library_pair_space_matches_oracle(prob):
+    """The library builds the balanced preconditioner's pair space from its own
+    multiplier list (host setup, the same data the device path uses): the pairs of
+    patches joined by multipliers and the number of multipliers per pair are the
+    oracle's."""
+    try:
+        from paper_2510_23446_gb300 import ieti
+    except Exception as e:   # noqa: BLE001
+        pytest.skip(f"library not built: {e}")
+    S = ieti.Solver.from_problem(prob, device=-1)
+    lam = S.multipliers()
+    S.close()
+    lib = {}
+    for s, t in zip(lam["s"], lam["t"]):
+        assert s < t
+        lib[(int(s), int(t))] = lib.get((int(s), int(t)), 0) + 1
+    dec = OracleProblem(prob).dec
+    ora = {}
+    for (_, s, _, t, _) in dec.lam:
+        ora[(s, t)] = ora.get((s, t), 0) + 1
+    assert lib == ora
+    assert dec.pair_space().shape[1] == len(lib)
