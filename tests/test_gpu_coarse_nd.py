@@ -59,6 +59,26 @@ def test_nd_equals_dense_coarse(ieti, name, graph):
         assert abs(s["cg_its"] - t["cg_its"]) <= 1
 
 
+@pytest.mark.parametrize("name", ["c4_family", "ragged_p23"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_nd_top_merged_tree_matches_oracle(ieti, name, mode):
+    """coarse_top = 2: the first bisection level's separators merged into one dense
+    root block (fewer levels, a wider root): the same states within the path's
+    tolerance."""
+    prob, op, ref = oracle_run(name, 2)
+    kw = dict(precond="dirichlet_stiff", coarse="nd", coarse_leaf=1, **OPTS[mode])
+    S = ieti.Solver.from_problem(prob, device=0, coarse_top=2, **kw)
+    merged = S.info()["coarse_nodes"]
+    S.close()
+    S = ieti.Solver.from_problem(prob, device=0, **kw)
+    plain = S.info()["coarse_nodes"]
+    S.close()
+    assert merged < plain
+    got, stats = gpu_run(ieti, prob, 2, coarse_top=2, **kw)
+    for l, (a, b) in enumerate(zip(ref, got)):
+        assert np.linalg.norm(a - b) <= TOL[mode] * np.linalg.norm(a), (name, mode, l, stats[l])
+
+
 def test_nd_with_autotuned_schedule(ieti):
     """The autotuner re-cuts the level partitions for every schedule it times."""
     prob, op, ref = oracle_run("c4_family", 2)
