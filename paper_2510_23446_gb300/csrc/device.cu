@@ -3238,8 +3238,11 @@ static int deflation_setup(DeviceState *d, const HostSetup &hs, std::string &err
   CK(cudaStreamSynchronize(st));
   for (int j = 0; j < k; ++j)
     for (int64_t l = 0; l < m; ++l) E[(size_t)pair_of[l] * k + j] += FUt[(size_t)j * m + l];
-  for (int i = 0; i < k; ++i)       // F is symmetric: average the two rounding orders
-    for (int j = 0; j < i; ++j) E[(size_t)i * k + j] = E[(size_t)j * k + i] = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
+  for (int i = 0; i < k; ++i)  // F is symmetric: average the two rounding orders
+    for (int j = 0; j < i; ++j) {
+      const double v = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
+      E[(size_t)i * k + j] = E[(size_t)j * k + i] = v;
+    }
   // Cholesky E = L L^T (lower, in place), then E^{-1} = L^{-T} L^{-1} column by column
   for (int j = 0; j < k; ++j) {
     double dj = E[(size_t)j * k + j];
