@@ -3309,7 +3309,9 @@ int device_setup(const HostSetup &hs, const CoarseTree *tree, const ieti_options
     if (opt.coarse == IETI_COARSE_AUTO)
       nd = tree && tree->n_nodes > 0 && opt.pcg_mode == 0 && 8.0 * nc0 * nc0 > 64e6;
     if (nd && (opt.pcg_mode != 0 || !tree)) {
-      err = "the nested-dissection coarse solve needs pcg_mode 0";
+      err = opt.deflation ? "the nested-dissection coarse solve needs the persistent PCG (deflation runs the "
+                            "host-loop PCG)"
+                          : "the nested-dissection coarse solve needs pcg_mode 0";
       return fail(IETI_ERR_INVALID_ARG);
     }
     d->coarse_nd = nd && hs.n_coarse > 0 && tree->n_nodes > 0;
