@@ -180,8 +180,9 @@ typedef struct {
    * pair's multipliers).  M_bal is symmetric and the solution is unchanged.  Setup
    * applies F to the k columns of U (k = ieti_info.deflation_dim) and keeps F U (k x m
    * FP64) on the device; every PCG iteration streams it twice.  The dual problem then
-   * runs in the host-loop PCG (pcg_mode 1, no graph).  IETI_ERR_TOO_LARGE when
-   * 8 k m > 8 GB or k > 4096.  0: off. */
+   * runs in the host-loop PCG (pcg_mode 1, no graph), so the coarse problem uses the
+   * dense inverse (coarse = ND is refused).  IETI_ERR_TOO_LARGE when 8 k m > 8 GB or
+   * k > 4096.  0: off. */
   int32_t deflation;
 } ieti_options;
 
