@@ -356,6 +356,15 @@ int ieti_coarse_tree(const ieti_ctx *ctx, int32_t *n_nodes, int64_t *n_s, int32_
 int ieti_shard_plan(const ieti_ctx *ctx, int32_t n_ranks, int32_t *rank_of_patch, int32_t *lam_owner,
                     int32_t *lam_peer, int32_t *coarse_owner);
 
+/* The coarse solve (Sec. 3: the primal Schur complement S_c) on the ranks of
+ * ieti_shard_plan (host query).  node_rank[n_nodes of ieti_coarse_tree]: the rank that
+ * computes node p of the nested-dissection tree when every patch of the node's box is on
+ * that rank (its whole subtree then is too), else -1: a shared node of the top, computed
+ * by every rank after one sum over the ranks of the owned subtrees' updates into the
+ * shared fronts.  Each rank then holds the coarse values its patches need without a
+ * further exchange.  Errors: INVALID_ARG (n_ranks out of range, NULL). */
+int ieti_shard_coarse(const ieti_ctx *ctx, int32_t n_ranks, int32_t *node_rank);
+
 /* Multipliers and patch blocks (host queries): multiplier l joins the interface copy
  * pos_s[l] of patch s[l] to the copy pos_t[l] of patch t[l] (s < t, lambda = copy in s -
  * copy in t; positions index the patch's interface block); per patch the block sizes

@@ -325,6 +325,26 @@ int ieti_shard_plan(const ieti_ctx *ctx, int32_t n_ranks, int32_t *rank_of_patch
   return IETI_OK;
 }
 
+int ieti_shard_coarse(const ieti_ctx *ctx, int32_t n_ranks, int32_t *node_rank) {
+  if (!ctx || !node_rank) return IETI_ERR_INVALID_ARG;
+  try {
+    ieti::ShardPlan plan;
+    std::vector<int32_t> nr;
+    std::string e;
+    int rc = ieti::build_shard_plan(ctx->hs, n_ranks, plan, e);
+    if (!rc) rc = ieti::shard_coarse_nodes(ctx->hs, ctx->tree, plan, nr, e);
+    if (rc) {
+      const_cast<ieti_ctx *>(ctx)->err = e;
+      return rc;
+    }
+    std::copy(nr.begin(), nr.end(), node_rank);
+  } catch (...) {
+    const_cast<ieti_ctx *>(ctx)->err = "ieti_shard_coarse: host allocation failed";
+    return IETI_ERR_OOM;
+  }
+  return IETI_OK;
+}
+
 int ieti_multipliers(const ieti_ctx *ctx, int32_t *s, int32_t *pos_s, int32_t *t, int32_t *pos_t) {
   if (!ctx) return IETI_ERR_INVALID_ARG;
   const auto &L = ctx->hs.lam;

@@ -1,6 +1,8 @@
 // Patch-sharded layout for several ranks (see shard.h).
 #include "shard.h"
 
+#include "coarse_nd.h"
+
 #include <algorithm>
 #include <cmath>
 #include <functional>
@@ -104,6 +106,34 @@ int build_shard_plan(const HostSetup &hs, int n_ranks, ShardPlan &plan, std::str
       plan.coarse_ranks[c] |= 1 << r;
     }
   }
+  return IETI_OK;
+}
+
+int shard_coarse_nodes(const HostSetup &hs, const CoarseTree &t, const ShardPlan &plan,
+                       std::vector<int32_t> &node_rank, std::string &err) {
+  node_rank.assign(t.n_nodes, -1);
+  auto pid = [&](int a, int b, int c) { return a + hs.P[0] * (b + hs.P[1] * c); };
+  for (int p = 0; p < t.n_nodes; ++p) {
+    const int *bx = t.box.data() + 6 * (size_t)p;
+    int r = -2;  // -2: no patch seen yet
+    for (int c = bx[4]; c < bx[5] && r != -1; ++c)
+      for (int b = bx[2]; b < bx[3] && r != -1; ++b)
+        for (int a = bx[0]; a < bx[1]; ++a) {
+          const int q = plan.rank_of_patch[pid(a, b, c)];
+          if (r == -2) r = q;
+          else if (q != r) {
+            r = -1;
+            break;
+          }
+        }
+    node_rank[p] = r < 0 ? -1 : r;
+  }
+  // the subtree property the exchange relies on
+  for (int p = 0; p < t.n_nodes; ++p)
+    if (t.parent[p] >= 0 && node_rank[t.parent[p]] >= 0 && node_rank[t.parent[p]] != node_rank[p]) {
+      err = "shard_coarse_nodes: a node's parent is owned by another rank";
+      return IETI_ERR_INVALID_ARG;
+    }
   return IETI_OK;
 }
 

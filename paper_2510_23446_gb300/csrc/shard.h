@@ -29,4 +29,14 @@ struct ShardPlan {
 
 int build_shard_plan(const HostSetup &hs, int n_ranks, ShardPlan &plan, std::string &err);
 
+// The coarse solve on the same ranks: node p of the nested-dissection tree belongs to
+// rank r when every patch of its box is on r (its rows and the subtree below it are
+// computed there), else -1: a shared node of the top, computed by every rank once the
+// owned subtrees' updates into it are summed over the ranks (one allreduce per solve;
+// a descendant of an owned node is owned by the same rank, an ancestor of a shared
+// node is shared).
+struct CoarseTree;
+int shard_coarse_nodes(const HostSetup &hs, const CoarseTree &t, const ShardPlan &plan,
+                       std::vector<int32_t> &node_rank, std::string &err);
+
 }  // namespace ieti

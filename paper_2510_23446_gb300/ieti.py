@@ -106,6 +106,7 @@ lib.ieti_coarse_tree.argtypes = [_ctx, C.POINTER(C.c_int32), C.POINTER(C.c_int64
 lib.ieti_pcg_phase_times.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
 lib.ieti_coarse_level_times.argtypes = [_ctx, C.c_void_p, C.c_int32, C.c_int32]
 lib.ieti_shard_plan.argtypes = [_ctx, C.c_int32] + [C.c_void_p] * 4
+lib.ieti_shard_coarse.argtypes = [_ctx, C.c_int32, C.c_void_p]
 lib.ieti_multipliers.argtypes = [_ctx] + [C.c_void_p] * 4
 lib.ieti_patch_blocks.argtypes = [_ctx] + [C.c_void_p] * 4
 lib.ieti_potrf_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -123,7 +124,7 @@ EXPORTED = ["ieti_setup", "ieti_setup_error", "ieti_num_dofs", "ieti_get_info", 
             "ieti_last_error", "ieti_destroy", "ieti_kernel_stats", "ieti_pcg_phase_times",
             "ieti_potrf_batched", "ieti_potrf_batched_noalloc", "ieti_potrf_batched_f32",
             "ieti_quad_points", "ieti_load_vector_points", "ieti_coarse_tree", "ieti_coarse_level_times",
-            "ieti_shard_plan", "ieti_multipliers", "ieti_patch_blocks"]
+            "ieti_shard_plan", "ieti_shard_coarse", "ieti_multipliers", "ieti_patch_blocks"]
 
 
 class IetiError(RuntimeError):
@@ -306,6 +307,13 @@ class Solver:
         self._check(lib.ieti_shard_plan(self.ctx, int(n_ranks), rop.ctypes.data, own.ctypes.data, peer.ctypes.data,
                                         cown.ctypes.data))
         return dict(rank_of_patch=rop, lam_owner=own, lam_peer=peer, coarse_owner=cown[:inf["n_coarse"]])
+
+    def shard_coarse(self, n_ranks):
+        """ieti_shard_coarse: the rank computing every node of the coarse tree (-1: shared)."""
+        n = len(self.coarse_tree()["k0"])
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        self._check(lib.ieti_shard_coarse(self.ctx, int(n_ranks), out.ctypes.data))
+        return out[:n]
 
     def multipliers(self):
         m = self.info()["n_lambda"]
