@@ -184,6 +184,11 @@ typedef struct {
    * dense inverse (coarse = ND is refused).  IETI_ERR_TOO_LARGE when 8 k m > 8 GB or
    * k > 4096.  0: off. */
   int32_t deflation;
+  /* n >= 2: the nested-dissection tree is cut where ieti_shard_plan cuts the patch grid
+   * for n ranks (then the rest by midpoints), so that every rank's patches form whole
+   * subtrees and the shared top of ieti_shard_coarse is only the ranks' separators;
+   * 0 or 1: midpoint cuts.  At most 31 and at most the number of patches. */
+  int32_t coarse_ranks;
 } ieti_options;
 
 #define IETI_REFACTOR_EVERY 0  /* at every Newton iterate (Newton's method) */

@@ -42,6 +42,7 @@ static int check_options(const ieti_options *o, std::string &err) {
   if (o->coarse_leaf < 0) { err = "coarse_leaf must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->coarse_top < 0) { err = "coarse_top must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->deflation != 0 && o->deflation != 1) { err = "deflation must be 0 or 1"; return IETI_ERR_INVALID_ARG; }
+  if (o->coarse_ranks < 0 || o->coarse_ranks > 31) { err = "coarse_ranks must be in [0, 31]"; return IETI_ERR_INVALID_ARG; }
   if (o->factor_arena_mb < 0) { err = "factor_arena_mb must be >= 0"; return IETI_ERR_INVALID_ARG; }
   if (o->precision == IETI_PREC_FP64 && o->factor != IETI_FACTOR_FP64) {
     err = "the FP64 precision mode factors in FP64 (factor must be IETI_FACTOR_FP64)";
@@ -69,7 +70,12 @@ int ieti_setup(const ieti_problem *problem, const ieti_options *options, ieti_ct
     if (rc == IETI_OK) {
       const int leaf = options->coarse_leaf;
       const int top = options->coarse_top > 0 ? options->coarse_top : (leaf > 0 ? 1 : 0);
-      rc = ieti::choose_coarse_tree(ctx->hs, 4e12, 12e-6, leaf, top, ctx->tree, g_setup_err);
+      ieti::ShardPlan plan;
+      const bool aligned = options->coarse_ranks > 1;
+      if (aligned) rc = ieti::build_shard_plan(ctx->hs, options->coarse_ranks, plan, g_setup_err);
+      if (rc == IETI_OK)
+        rc = ieti::choose_coarse_tree(ctx->hs, 4e12, 12e-6, leaf, top, ctx->tree, g_setup_err,
+                                      aligned ? &plan.cuts : nullptr);
     }
     if (rc == IETI_OK && options->device >= 0)
       rc = ieti::device_setup(ctx->hs, &ctx->tree, ctx->opt, &ctx->dev, g_setup_err);

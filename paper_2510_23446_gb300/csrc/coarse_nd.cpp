@@ -25,7 +25,8 @@ int CoarseTree::front_index(int p, int32_t x) const {
   return nk[p] + (int)(it - b);
 }
 
-int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err) {
+int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err,
+                      const std::vector<BoxCut> *cuts) {
   t = CoarseTree();
   t.nc = hs.n_coarse;
   t.leaf_max = std::max(1, leaf_max);
@@ -70,7 +71,14 @@ int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t,
     int d = 0;
     for (int e = 1; e < 3; ++e)
       if (ext[e] > ext[d]) d = e;
-    const int m = box[2 * d] + ext[d] / 2;
+    int m = box[2 * d] + ext[d] / 2;
+    if (cuts)
+      for (const BoxCut &bc : *cuts)
+        if (std::equal(box, box + 6, bc.box)) {
+          d = bc.d;
+          m = bc.m;
+          break;
+        }
     std::vector<int32_t> mine, left, right;
     for (int32_t c : alive) {
       if (lo[3 * c + d] < m && hi[3 * c + d] >= m) mine.push_back(c);
@@ -206,7 +214,7 @@ double coarse_tree_bytes(const CoarseTree &t) {
 int coarse_tree_levels(const CoarseTree &t) { return t.n_nodes ? t.n_height + std::max(t.n_depth - 1, 0) : 0; }
 
 int choose_coarse_tree(const HostSetup &hs, double bw, double latency, int leaf_fixed, int top_fixed,
-                       CoarseTree &t, std::string &err) {
+                       CoarseTree &t, std::string &err, const std::vector<BoxCut> *cuts) {
   std::vector<int> leaves = {1, 8, 16, 27, 64, 125}, tops = {0, 2, 3};
   if (leaf_fixed > 0) leaves = {leaf_fixed};
   if (top_fixed > 0) tops = {top_fixed > 1 ? top_fixed : 0};
@@ -215,7 +223,7 @@ int choose_coarse_tree(const HostSetup &hs, double bw, double latency, int leaf_
   for (int leaf : leaves)
     for (int top : tops) {
       CoarseTree c;
-      int rc = build_coarse_tree(hs, leaf, top, c, err);
+      int rc = build_coarse_tree(hs, leaf, top, c, err, cuts);
       if (rc) return rc;
       // blocks wider than 2048 unknowns leave a ring stage of the solve a single row:
       // only the candidate without merged top levels may have them (unless fixed)

@@ -42,7 +42,16 @@ struct CoarseTree {
 // Build the tree for the coarse unknowns of `hs` (boxes of leaf_max patches or fewer
 // are not cut further; with top > 1 the separators of the top `top` levels form one
 // root block; empty nodes are removed and their children re-attached).
-int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err);
+// cuts (optional): boxes {x0, x1, y0, y1, z0, z1} with a prescribed cut {d, m}: a box
+// equal to one of them is cut at plane m of direction d instead of the midpoint of its
+// longest side (the cuts of a patch-sharded plan, so that every rank's patches form
+// whole subtrees)
+struct BoxCut {
+  int box[6];
+  int d, m;
+};
+int build_coarse_tree(const HostSetup &hs, int leaf_max, int top, CoarseTree &t, std::string &err,
+                      const std::vector<BoxCut> *cuts = nullptr);
 
 // Algorithmic bytes of one coarse solve on the tree (Z rows forward, Lt rows backward)
 // and its grid-synchronised phases (levels by height, then by depth below the roots).
@@ -53,6 +62,6 @@ int coarse_tree_levels(const CoarseTree &t);
 // and top merges: bytes / bw + phases * latency.  leaf > 0 / top > 0 fix that
 // parameter (top 1: no merge).
 int choose_coarse_tree(const HostSetup &hs, double bw, double latency, int leaf, int top, CoarseTree &t,
-                       std::string &err);
+                       std::string &err, const std::vector<BoxCut> *cuts = nullptr);
 
 }  // namespace ieti

@@ -1,8 +1,6 @@
 // Patch-sharded layout for several ranks (see shard.h).
 #include "shard.h"
 
-#include "coarse_nd.h"
-
 #include <algorithm>
 #include <cmath>
 #include <functional>
@@ -72,6 +70,11 @@ int build_shard_plan(const HostSetup &hs, int n_ranks, ShardPlan &plan, std::str
     std::copy(box, box + 6, br);
     bl[2 * d + 1] = box[2 * d] + best;
     br[2 * d] = box[2 * d] + best;
+    BoxCut bc;
+    std::copy(box, box + 6, bc.box);
+    bc.d = d;
+    bc.m = box[2 * d] + best;
+    plan.cuts.push_back(bc);
     split(bl, r0, r0 + nl);
     split(br, r0 + nl, r1);
   };

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "coarse_nd.h"
 #include "host_setup.h"
 
 namespace ieti {
@@ -25,6 +26,7 @@ struct ShardPlan {
   std::vector<int32_t> coarse_owner;    // [n_coarse] lowest rank holding a copy
   std::vector<int32_t> coarse_ranks;    // [n_coarse] bit mask of the ranks holding copies (n_ranks <= 31)
   std::vector<double> rank_weight;      // [n_ranks] summed local sizes
+  std::vector<BoxCut> cuts;             // the bisection's cuts (box, direction, plane)
 };
 
 int build_shard_plan(const HostSetup &hs, int n_ranks, ShardPlan &plan, std::string &err);
@@ -35,7 +37,6 @@ int build_shard_plan(const HostSetup &hs, int n_ranks, ShardPlan &plan, std::str
 // owned subtrees' updates into it are summed over the ranks (one allreduce per solve;
 // a descendant of an owned node is owned by the same rank, an ancestor of a shared
 // node is shared).
-struct CoarseTree;
 int shard_coarse_nodes(const HostSetup &hs, const CoarseTree &t, const ShardPlan &plan,
                        std::vector<int32_t> &node_rank, std::string &err);
 

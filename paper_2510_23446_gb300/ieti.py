@@ -45,7 +45,7 @@ class ieti_options(C.Structure):
                 ("predictor", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
                 ("graph", C.c_int32), ("wait_limit", C.c_int32), ("coarse", C.c_int32),
                 ("coarse_leaf", C.c_int32), ("factor_arena_mb", C.c_int32), ("coarse_top", C.c_int32),
-                ("deflation", C.c_int32)]
+                ("deflation", C.c_int32), ("coarse_ranks", C.c_int32)]
 
 
 class ieti_coil(C.Structure):
@@ -151,7 +151,7 @@ class Solver:
                  outer_tol=1e-12, max_sweeps=None, pcg_mode=0, host_threads=0, stream=None, profile=0, l2_persist=2,
                  factor="fp64", refactor="every", newton_tol=0.0, predictor=0, autotune=0, tune_cache=None,
                  graph=1, wait_limit=0, coarse="auto", coarse_leaf=0, factor_arena_mb=0, coarse_top=0,
-                 deflation=0):
+                 deflation=0, coarse_ranks=0):
         self._keep = []
 
         def arr(x, dt_):
@@ -200,6 +200,7 @@ class Solver:
         op.coarse_leaf = int(coarse_leaf)
         op.coarse_top = int(coarse_top)
         op.deflation = int(deflation)
+        op.coarse_ranks = int(coarse_ranks)
         op.factor_arena_mb = int(factor_arena_mb)
         if tune_cache is not None:
             op.tune_cache = os.fsencode(tune_cache)      # the structure keeps the bytes alive

@@ -111,6 +111,8 @@ def test_invalid_inputs_return_codes(ieti, mutate, code):
     dict(precision="fp64", coarse_leaf=-1),
     dict(precision="fp64", coarse_top=-1),
     dict(precision="fp64", deflation=2),
+    dict(precision="fp64", coarse_ranks=32),
+    dict(precision="fp64", coarse_ranks=-1),
 ])
 def test_invalid_options_return_codes(ieti, kw):
     prob = make_problem("c1")

@@ -29,13 +29,13 @@ def _free_port():
     return p
 
 
-def _problem(name, world):
+def _problem(name, world, aligned=False):
     from paper_2510_23446_gb300 import ieti
     from oracle.stepping import OracleProblem
     prob = CASES[name]()
     I = OracleProblem(prob).ietidp()
     prim = np.nonzero(I.dec.gauge.cls == 1)[0]
-    S = ieti.Solver.from_problem(prob, device=-1, coarse_leaf=1)
+    S = ieti.Solver.from_problem(prob, device=-1, coarse_leaf=1, coarse_ranks=world if aligned else 0)
     t = S.coarse_tree()
     nr = S.shard_coarse(world)
     S.close()
@@ -45,14 +45,14 @@ def _problem(name, world):
     return t, nr, Sp
 
 
-def _rank_main(rank, world, port, name, out_q):
+def _rank_main(rank, world, port, name, aligned, out_q):
     import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        t, nr, Sp = _problem(name, world)
+        t, nr, Sp = _problem(name, world, aligned)
         nn, S, kids = _nodes(t)
         k0, nk = t["k0"], t["nk"]
         front = [np.concatenate([np.arange(k0[p], k0[p] + nk[p]), S[p]]) for p in range(nn)]
@@ -140,16 +140,18 @@ def _rank_main(rank, world, port, name, out_q):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("aligned", [False, True])
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("name", NAMES)
-def test_sharded_coarse_solve_equals_dense(name, world):
+def test_sharded_coarse_solve_equals_dense(name, world, aligned):
+    """aligned: the tree cut where the plan cuts the patch grid (option coarse_ranks)."""
     pytest.importorskip("torch")
     try:
         from paper_2510_23446_gb300 import ieti  # noqa: F401
     except Exception as e:   # noqa: BLE001
         pytest.skip(f"library not built: {e}")
     import torch.multiprocessing as mp
-    t, nr, Sp = _problem(name, world)
+    t, nr, Sp = _problem(name, world, aligned)
     nn = len(t["k0"])
     par = t["parent"]
     # ownership: whole subtrees per rank, a shared top, every rank owning something
@@ -160,7 +162,7 @@ def test_sharded_coarse_solve_equals_dense(name, world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, aligned, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=240) for _ in range(world)]
@@ -175,3 +177,27 @@ def test_sharded_coarse_solve_equals_dense(name, world):
         owned += mine
     assert np.all(covered >= 1)
     assert sorted(owned) == sorted(int(p) for p in np.nonzero(nr >= 0)[0])   # each owned node on one rank
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_aligned_tree_shrinks_the_shared_top(name):
+    """Cutting the tree where the ranks are cut leaves no more shared bytes than the
+    midpoint tree, the same unknowns, and a shared top of only rank-spanning boxes."""
+    try:
+        from paper_2510_23446_gb300 import ieti
+    except Exception as e:   # noqa: BLE001
+        pytest.skip(f"library not built: {e}")
+    prob = CASES[name]()
+
+    def shared_bytes(world, aligned):
+        S = ieti.Solver.from_problem(prob, device=-1, coarse_leaf=1, coarse_ranks=world if aligned else 0)
+        t = S.coarse_tree()
+        nr = S.shard_coarse(world)
+        S.close()
+        nk, ns = t["nk"], np.diff(t["s_off"])
+        byt = 8.0 * ((nk + ns) * nk + nk * ns)
+        return byt[nr < 0].sum(), int(nk.sum())
+
+    for world in (2, 3, 4):
+        (b0, n0), (b1, n1) = shared_bytes(world, False), shared_bytes(world, True)
+        assert n0 == n1 and b1 <= b0 * (1 + 1e-12), (world, b0, b1)
