@@ -398,10 +398,19 @@ struct ElemBasis {
   std::vector<int> lid;          // local DOF ids of the active functions
 };
 
+// Reference quantities of one point (REF visits): DF, DF^{-1}, and the reference values
+// w_hat and curls c_hat of the active functions (3 per function)
+struct PointRef {
+  const double (*J)[3];
+  const double (*inv)[3];
+  const double *wh, *ch;
+};
+
 // Visit every quadrature point of every element of a patch with the geometry
 // (x = F(xi), DF, det DF, weight) and the physical quantities of all active
 // functions: U_a = DF c_hat_a (= det * curl w_a) and V_a = DF^{-T} w_hat_a (= w_a).
-template <class Fn>
+// REF: the callback also gets the point's PointRef.
+template <bool REF = false, class Fn>
 static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const DirData dd[3], Fn &&fn) {
   const double *net = hs.ctrl.data() + hs.ctrl_off[s];
   int n0 = pt.n[0], n1 = pt.n[1];
@@ -484,23 +493,32 @@ static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const Di
                         wv[0] = 0; wv[1] = 0; wv[2] = Nx * Ny * Dz;
                         cv[0] = Nx * dNy * Dz; cv[1] = -dNx * Ny * Dz; cv[2] = 0;
                       }
-                      for (int r = 0; r < 3; ++r) {
-                        U[3 * t + r] = J[r][0] * cv[0] + J[r][1] * cv[1] + J[r][2] * cv[2];
-                        // (DF^{-T} w)_r = sum_j inv[j][r] w_j
-                        V[3 * t + r] = inv[0][r] * wv[0] + inv[1][r] * wv[1] + inv[2][r] * wv[2];
-                      }
+                      if constexpr (!REF)
+                        for (int r = 0; r < 3; ++r) {
+                          U[3 * t + r] = J[r][0] * cv[0] + J[r][1] * cv[1] + J[r][2] * cv[2];
+                          // (DF^{-T} w)_r = sum_j inv[j][r] w_j
+                          V[3 * t + r] = inv[0][r] * wv[0] + inv[1][r] * wv[1] + inv[2][r] * wv[2];
+                        }
                     }
               }
-              fn(el, nloc, lid.data(), F, det, w, U.data(), V.data());
+              if constexpr (REF) {
+                const PointRef pr{J, inv, wh.data(), ch.data()};
+                fn(el, nloc, lid.data(), F, det, w, pr);
+              } else {
+                fn(el, nloc, lid.data(), F, det, w, U.data(), V.data());
+              }
             }
       }
 }
 
-// out[a][b] = sum_k Ws[a][k] Ut[k][b] (n x n, row-major): the upper triangle by blocks
-// of eight rows and 32 terms (the row block and the terms' slice of Ut stay in the
-// first-level cache), the inner loop an axpy over b that vectorises without
-// reordering any sum; then mirrored
-static void gram_upper(const double *Ws, const double *Ut, int n, int K, double *out) {
+// out[a][b] = sum_k Ws[a][k] Ut[k][b] (n x n, row-major) for rows k of Ut that vanish
+// outside the column ranges [lo[k % 3][i], hi[k % 3][i]), i < 2 (reference curls lack
+// their own component, reference values have only it): the products with those zeros
+// are not formed.  The upper triangle by blocks of eight rows and 32 terms (the row
+// block and the terms' slice of Ut stay in the first-level cache), the inner loop an
+// axpy over b that vectorises without reordering any sum; then mirrored
+static void gram_upper_sparse(const double *Ws, const double *Ut, int n, int K, const int lo[3][2],
+                              const int hi[3][2], double *out) {
   constexpr int AB = 8, KC = 32;
   for (int k0 = 0; k0 < K; k0 += KC) {
     const int k1 = std::min(K, k0 + KC);
@@ -513,7 +531,9 @@ static void gram_upper(const double *Ws, const double *Ut, int n, int K, double 
           const double w = ws[k];
           if (w == 0.0) continue;
           const double *ut = Ut + (size_t)k * n;
-          for (int b = a0; b < n; ++b) o[b] += w * ut[b];
+          const int r = k % 3;
+          for (int i = 0; i < 2; ++i)
+            for (int b = std::max(a0, lo[r][i]); b < hi[r][i]; ++b) o[b] += w * ut[b];
         }
       }
     }
@@ -533,10 +553,22 @@ void HostSetup::assemble_patch(Patch &pt) const {
   pt.M = pt.K;
   const double *sig = sigma_el.data() + el_off[s];
   const double *nu = nu_el.data() + el_off[s];
-  // K_e = sum over the element's points of (nu w / det) (DF c_hat_a) . (DF c_hat_b) and
-  // M_e = sum of (sigma w det) w_a . w_b, formed per element as K_e = Ws Ut with the
-  // weighted values Ws (n x 3Q) and the plain values transposed Ut (3Q x n)
+  // K_e = sum over the element's points of (nu w / det) (DF c_hat_a) . (DF c_hat_b)
+  //     = sum of c_hat_a^T G c_hat_b,  G = (nu w / det) DF^T DF, and
+  // M_e = sum of (sigma w det) w_a . w_b = sum of w_hat_a^T H w_hat_b,
+  //       H = (sigma w det) DF^{-1} DF^{-T},
+  // formed per element as K_e = Ws Ut with Ws = (G c_hat_a) per point (n x 3Q) and the
+  // reference curls transposed Ut (3Q x n), which lack their own component; M_e the same
+  // with H w_hat_a and the reference values, which have only their own component
   const int K3 = 3 * dd[0].q * dd[1].q * dd[2].q;
+  const int nl0 = pt.p[0] * (pt.p[1] + 1) * (pt.p[2] + 1), nl1 = (pt.p[0] + 1) * pt.p[1] * (pt.p[2] + 1);
+  const int nl2 = (pt.p[0] + 1) * (pt.p[1] + 1) * pt.p[2], nel = nl0 + nl1 + nl2;
+  const int bs[4] = {0, nl0, nl0 + nl1, nel};  // element-local function blocks by component
+  // row r of a point: curls are zero on block r, values are zero off block r
+  const int klo[3][2] = {{bs[1], 0}, {bs[0], bs[2]}, {bs[0], 0}};
+  const int khi[3][2] = {{bs[3], 0}, {bs[1], bs[3]}, {bs[2], 0}};
+  const int mlo[3][2] = {{bs[0], 0}, {bs[1], 0}, {bs[2], 0}};
+  const int mhi[3][2] = {{bs[1], 0}, {bs[2], 0}, {bs[3], 0}};
   // element-local function index of the first function of every (component, c, b)
   // group and the group's length (the a-run), in the order the element lists them
   std::vector<std::pair<int, int>> groups;
@@ -560,10 +592,10 @@ void HostSetup::assemble_patch(Patch &pt) const {
     if (cur_el < 0) return;
     const int n = cur_n;
     Ke.assign((size_t)n * n, 0.0);
-    gram_upper(Ws.data(), Ut.data(), n, K3, Ke.data());
+    gram_upper_sparse(Ws.data(), Ut.data(), n, K3, klo, khi, Ke.data());
     if (any_m) {
       Me.assign((size_t)n * n, 0.0);
-      gram_upper(Vs.data(), Vt.data(), n, K3, Me.data());
+      gram_upper_sparse(Vs.data(), Vt.data(), n, K3, mlo, mhi, Me.data());
     }
     // the element's columns of one (component, c, b) group are consecutive DOF ids
     // whose CSR entries are consecutive in every row (a row's columns of one
@@ -581,8 +613,8 @@ void HostSetup::assemble_patch(Patch &pt) const {
         }
       }
   };
-  for_each_point(*this, pt, s, dd, [&](int el, int nloc, const int *lid, const double *, double det, double w,
-                                       const double *U, const double *V) {
+  for_each_point<true>(*this, pt, s, dd, [&](int el, int nloc, const int *lid, const double *, double det,
+                                             double w, const PointRef &pr) {
     if (el != cur_el) {
       flush();
       cur_el = el;
@@ -599,14 +631,22 @@ void HostSetup::assemble_patch(Patch &pt) const {
     const double ck = nl_element(s, el) ? 0.0 : nu[el] * w / det;
     const double cm = sig[el] * w * det;
     if (cm != 0.0) any_m = true;
-    for (int a = 0; a < nloc; ++a)
+    double G[3][3], H[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        G[r][c] = ck * (pr.J[0][r] * pr.J[0][c] + pr.J[1][r] * pr.J[1][c] + pr.J[2][r] * pr.J[2][c]);
+        H[r][c] = cm * (pr.inv[r][0] * pr.inv[c][0] + pr.inv[r][1] * pr.inv[c][1] + pr.inv[r][2] * pr.inv[c][2]);
+      }
+    for (int a = 0; a < nloc; ++a) {
+      const double *cv = pr.ch + 3 * a, *wv = pr.wh + 3 * a;
       for (int r = 0; r < 3; ++r) {
         const int k = 3 * qi + r;
-        Ws[(size_t)a * K3 + k] = ck * U[3 * a + r];
-        Ut[(size_t)k * nloc + a] = U[3 * a + r];
-        Vs[(size_t)a * K3 + k] = cm * V[3 * a + r];
-        Vt[(size_t)k * nloc + a] = V[3 * a + r];
+        Ws[(size_t)a * K3 + k] = G[r][0] * cv[0] + G[r][1] * cv[1] + G[r][2] * cv[2];
+        Ut[(size_t)k * nloc + a] = cv[r];
+        Vs[(size_t)a * K3 + k] = H[r][0] * wv[0] + H[r][1] * wv[1] + H[r][2] * wv[2];
+        Vt[(size_t)k * nloc + a] = wv[r];
       }
+    }
     ++qi;
   });
   flush();
