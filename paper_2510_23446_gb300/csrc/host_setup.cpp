@@ -398,19 +398,18 @@ struct ElemBasis {
   std::vector<int> lid;          // local DOF ids of the active functions
 };
 
-// Reference quantities of one point (REF visits): DF, DF^{-1}, and the reference values
-// w_hat and curls c_hat of the active functions (3 per function)
+// Geometry of one point (GEOM visits): DF and DF^{-1}
 struct PointRef {
   const double (*J)[3];
   const double (*inv)[3];
-  const double *wh, *ch;
 };
 
 // Visit every quadrature point of every element of a patch with the geometry
 // (x = F(xi), DF, det DF, weight) and the physical quantities of all active
 // functions: U_a = DF c_hat_a (= det * curl w_a) and V_a = DF^{-T} w_hat_a (= w_a).
-// REF: the callback also gets the point's PointRef.
-template <bool REF = false, class Fn>
+// GEOM: the callback gets the point's PointRef instead of the functions' values (none
+// are formed).
+template <bool GEOM = false, class Fn>
 static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const DirData dd[3], Fn &&fn) {
   const double *net = hs.ctrl.data() + hs.ctrl_off[s];
   int n0 = pt.n[0], n1 = pt.n[1];
@@ -471,7 +470,7 @@ static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const Di
               inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
               // reference values and curls of the active functions
               t = 0;
-              for (int comp = 0; comp < 3; ++comp) {
+              for (int comp = 0; comp < 3 && !GEOM; ++comp) {
                 int na = (comp == 0) ? p0 : p0 + 1, nb = (comp == 1) ? p1 : p1 + 1, nc = (comp == 2) ? p2 : p2 + 1;
                 for (int c = 0; c < nc; ++c)
                   for (int b = 0; b < nb; ++b)
@@ -493,16 +492,15 @@ static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const Di
                         wv[0] = 0; wv[1] = 0; wv[2] = Nx * Ny * Dz;
                         cv[0] = Nx * dNy * Dz; cv[1] = -dNx * Ny * Dz; cv[2] = 0;
                       }
-                      if constexpr (!REF)
-                        for (int r = 0; r < 3; ++r) {
-                          U[3 * t + r] = J[r][0] * cv[0] + J[r][1] * cv[1] + J[r][2] * cv[2];
-                          // (DF^{-T} w)_r = sum_j inv[j][r] w_j
-                          V[3 * t + r] = inv[0][r] * wv[0] + inv[1][r] * wv[1] + inv[2][r] * wv[2];
-                        }
+                      for (int r = 0; r < 3; ++r) {
+                        U[3 * t + r] = J[r][0] * cv[0] + J[r][1] * cv[1] + J[r][2] * cv[2];
+                        // (DF^{-T} w)_r = sum_j inv[j][r] w_j
+                        V[3 * t + r] = inv[0][r] * wv[0] + inv[1][r] * wv[1] + inv[2][r] * wv[2];
+                      }
                     }
               }
-              if constexpr (REF) {
-                const PointRef pr{J, inv, wh.data(), ch.data()};
+              if constexpr (GEOM) {
+                const PointRef pr{J, inv};
                 fn(el, nloc, lid.data(), F, det, w, pr);
               } else {
                 fn(el, nloc, lid.data(), F, det, w, U.data(), V.data());
@@ -511,35 +509,63 @@ static void for_each_point(const HostSetup &hs, const Patch &pt, int s, const Di
       }
 }
 
-// out[a][b] = sum_k Ws[a][k] Ut[k][b] (n x n, row-major) for rows k of Ut that vanish
-// outside the column ranges [lo[k % 3][i], hi[k % 3][i]), i < 2 (reference curls lack
-// their own component, reference values have only it): the products with those zeros
-// are not formed.  The upper triangle by blocks of eight rows and 32 terms (the row
-// block and the terms' slice of Ut stay in the first-level cache), the inner loop an
-// axpy over b that vectorises without reordering any sum; then mirrored
-static void gram_upper_sparse(const double *Ws, const double *Ut, int n, int K, const int lo[3][2],
-                              const int hi[3][2], double *out) {
-  constexpr int AB = 8, KC = 32;
-  for (int k0 = 0; k0 < K; k0 += KC) {
-    const int k1 = std::min(K, k0 + KC);
-    for (int a0 = 0; a0 < n; a0 += AB) {
-      const int a1 = std::min(n, a0 + AB);
-      for (int a = a0; a < a1; ++a) {
-        double *o = out + (size_t)a * n;
-        const double *ws = Ws + (size_t)a * K;
-        for (int k = k0; k < k1; ++k) {
-          const double w = ws[k];
-          if (w == 0.0) continue;
-          const double *ut = Ut + (size_t)k * n;
-          const int r = k % 3;
-          for (int i = 0; i < 2; ++i)
-            for (int b = std::max(a0, lo[r][i]); b < hi[r][i]; ++b) o[b] += w * ut[b];
+// Element matrices by sum factorisation.  Every reference curl component and every
+// reference value of an edge function is a product of 1-D factors (N, N' or D per
+// direction), so a block sum over the element's points
+//   E[a][b] += sign * sum_q X_a(qx) Y_a(qy) Z_a(qz) W(q) X_b(qx) Y_b(qy) Z_b(qz)
+// is formed by contracting z, then y, then x (tensor-product quadrature).
+struct Factor1D {
+  const double *t[3];  // per direction: [function][point] values
+  int n[3];            // functions per direction
+};
+
+static void sf_block(const Factor1D &A, const Factor1D &B, const int q[3], const double *W, double sign, int n,
+                     int ra, int rb, double *E, std::vector<double> &t1, std::vector<double> &t2) {
+  const int qx = q[0], qy = q[1], qz = q[2];
+  const int az = A.n[2], bz = B.n[2], ay = A.n[1], by = B.n[1], ax = A.n[0], bx = B.n[0];
+  // t1[(kx * qy + ky) * az * bz + cz * bz + cz'] = sum_kz Za[cz](kz) Zb[cz'](kz) W(kx, ky, kz)
+  t1.assign((size_t)qx * qy * az * bz, 0.0);
+  for (int kz = 0; kz < qz; ++kz)
+    for (int ky = 0; ky < qy; ++ky)
+      for (int kx = 0; kx < qx; ++kx) {
+        const double w = W[kx + qx * (ky + qy * kz)];
+        double *o = &t1[(size_t)(kx * qy + ky) * az * bz];
+        for (int cz = 0; cz < az; ++cz) {
+          const double zw = A.t[2][cz * qz + kz] * w;
+          for (int dz = 0; dz < bz; ++dz) o[cz * bz + dz] += zw * B.t[2][dz * qz + kz];
+        }
+      }
+  // t2[((kx * ay + cy) * by + dy) * az * bz + zz] = sum_ky Ya[cy](ky) Yb[dy](ky) t1[kx][ky][zz]
+  const int zz = az * bz;
+  t2.assign((size_t)qx * ay * by * zz, 0.0);
+  for (int kx = 0; kx < qx; ++kx)
+    for (int ky = 0; ky < qy; ++ky) {
+      const double *src = &t1[(size_t)(kx * qy + ky) * zz];
+      for (int cy = 0; cy < ay; ++cy) {
+        const double ya = A.t[1][cy * qy + ky];
+        for (int dy = 0; dy < by; ++dy) {
+          const double yy = ya * B.t[1][dy * qy + ky];
+          double *o = &t2[((size_t)(kx * ay + cy) * by + dy) * zz];
+          for (int u = 0; u < zz; ++u) o[u] += yy * src[u];
         }
       }
     }
-  }
-  for (int a = 1; a < n; ++a)
-    for (int b = 0; b < a; ++b) out[(size_t)a * n + b] = out[(size_t)b * n + a];
+  // E[ra + (cx + ax (cy + ay cz))][rb + (dx + bx (dy + by dz))] += sign sum_kx Xa Xb t2
+  for (int kx = 0; kx < qx; ++kx)
+    for (int cx = 0; cx < ax; ++cx) {
+      const double xa = sign * A.t[0][cx * qx + kx];
+      for (int dx = 0; dx < bx; ++dx) {
+        const double xx = xa * B.t[0][dx * qx + kx];
+        for (int cy = 0; cy < ay; ++cy)
+          for (int dy = 0; dy < by; ++dy) {
+            const double *src = &t2[((size_t)(kx * ay + cy) * by + dy) * zz];
+            for (int cz = 0; cz < az; ++cz) {
+              double *row = E + (size_t)(ra + cx + ax * (cy + ay * cz)) * n + rb + dx;
+              for (int dz = 0; dz < bz; ++dz) row[(size_t)bx * (dy + by * dz)] += xx * src[cz * bz + dz];
+            }
+          }
+      }
+    }
 }
 
 void HostSetup::assemble_patch(Patch &pt) const {
@@ -556,27 +582,21 @@ void HostSetup::assemble_patch(Patch &pt) const {
   // K_e = sum over the element's points of (nu w / det) (DF c_hat_a) . (DF c_hat_b)
   //     = sum of c_hat_a^T G c_hat_b,  G = (nu w / det) DF^T DF, and
   // M_e = sum of (sigma w det) w_a . w_b = sum of w_hat_a^T H w_hat_b,
-  //       H = (sigma w det) DF^{-1} DF^{-T},
-  // formed per element as K_e = Ws Ut with Ws = (G c_hat_a) per point (n x 3Q) and the
-  // reference curls transposed Ut (3Q x n), which lack their own component; M_e the same
-  // with H w_hat_a and the reference values, which have only their own component
-  const int K3 = 3 * dd[0].q * dd[1].q * dd[2].q;
-  const int nl0 = pt.p[0] * (pt.p[1] + 1) * (pt.p[2] + 1), nl1 = (pt.p[0] + 1) * pt.p[1] * (pt.p[2] + 1);
-  const int nl2 = (pt.p[0] + 1) * (pt.p[1] + 1) * pt.p[2], nel = nl0 + nl1 + nl2;
-  const int bs[4] = {0, nl0, nl0 + nl1, nel};  // element-local function blocks by component
-  // row r of a point: curls are zero on block r, values are zero off block r
-  const int klo[3][2] = {{bs[1], 0}, {bs[0], bs[2]}, {bs[0], 0}};
-  const int khi[3][2] = {{bs[3], 0}, {bs[1], bs[3]}, {bs[2], 0}};
-  const int mlo[3][2] = {{bs[0], 0}, {bs[1], 0}, {bs[2], 0}};
-  const int mhi[3][2] = {{bs[1], 0}, {bs[2], 0}, {bs[3], 0}};
+  //       H = (sigma w det) DF^{-1} DF^{-T}:
+  // by sum factorisation over the 1-D factors of the reference curls and values
+  const int q[3] = {dd[0].q, dd[1].q, dd[2].q};
+  const int Q = q[0] * q[1] * q[2];
+  const int p0 = pt.p[0], p1 = pt.p[1], p2 = pt.p[2];
+  const int nl0 = p0 * (p1 + 1) * (p2 + 1), nl1 = (p0 + 1) * p1 * (p2 + 1), nl2 = (p0 + 1) * (p1 + 1) * p2;
+  const int n = nl0 + nl1 + nl2;
+  const int bs[3] = {0, nl0, nl0 + nl1};  // element-local function blocks by component
   // element-local function index of the first function of every (component, c, b)
   // group and the group's length (the a-run), in the order the element lists them
   std::vector<std::pair<int, int>> groups;
   {
     int t = 0;
     for (int comp = 0; comp < 3; ++comp) {
-      const int na = (comp == 0) ? pt.p[0] : pt.p[0] + 1, nb = (comp == 1) ? pt.p[1] : pt.p[1] + 1,
-                nc = (comp == 2) ? pt.p[2] : pt.p[2] + 1;
+      const int na = (comp == 0) ? p0 : p0 + 1, nb = (comp == 1) ? p1 : p1 + 1, nc = (comp == 2) ? p2 : p2 + 1;
       for (int c = 0; c < nc; ++c)
         for (int b = 0; b < nb; ++b) {
           groups.push_back({t, na});
@@ -584,18 +604,69 @@ void HostSetup::assemble_patch(Patch &pt) const {
         }
     }
   }
-  int cur_el = -1, cur_n = 0, qi = 0;
-  bool any_m = false;
-  std::vector<double> Ws, Ut, Vs, Vt, Ke, Me;
+  // 1-D tables of the current element, [function][point]: N, N' (p + 1 functions) and D
+  // (p functions) per direction
+  std::vector<double> tN[3], tdN[3], tD[3];
+  for (int d = 0; d < 3; ++d) {
+    tN[d].resize((size_t)(pt.p[d] + 1) * q[d]);
+    tdN[d].resize((size_t)(pt.p[d] + 1) * q[d]);
+    tD[d].resize((size_t)pt.p[d] * q[d]);
+  }
+  // factors of the reference curl component r of component c's functions, with signs:
+  // c = 0: (D, N, N') r = 1, -(D, N', N) r = 2; c = 1: -(N, D, N') r = 0, (N', D, N) r = 2;
+  // c = 2: (N, N', D) r = 0, -(N', N, D) r = 1.  Values of component c: D along c, N else.
+  enum { TN = 0, TDN = 1, TD = 2 };
+  static const int curl_tab[3][2][4] = {{{1, TD, TN, TDN}, {2, TD, TDN, TN}},
+                                        {{0, TN, TD, TDN}, {2, TDN, TD, TN}},
+                                        {{0, TN, TDN, TD}, {1, TDN, TN, TD}}};
+  static const double curl_sign[3][2] = {{1.0, -1.0}, {-1.0, 1.0}, {1.0, -1.0}};
+  auto table = [&](int d, int type) -> const double * {
+    return type == TN ? tN[d].data() : (type == TDN ? tdN[d].data() : tD[d].data());
+  };
+  auto count = [&](int d, int type) { return type == TD ? pt.p[d] : pt.p[d] + 1; };
+  auto factor = [&](int tx, int ty, int tz) {
+    Factor1D f;
+    const int ty3[3] = {tx, ty, tz};
+    for (int d = 0; d < 3; ++d) {
+      f.t[d] = table(d, ty3[d]);
+      f.n[d] = count(d, ty3[d]);
+    }
+    return f;
+  };
+  std::vector<double> Gq((size_t)9 * Q), Hq((size_t)9 * Q), Ke, Me, t1, t2;
   std::vector<int> cur_lid;
+  int cur_el = -1, qi = 0;
+  bool any_m = false;
   auto flush = [&]() {
     if (cur_el < 0) return;
-    const int n = cur_n;
+    const int e3[3] = {cur_el % pt.ne[0], (cur_el / pt.ne[0]) % pt.ne[1], cur_el / (pt.ne[0] * pt.ne[1])};
+    for (int d = 0; d < 3; ++d)
+      for (int k = 0; k < q[d]; ++k) {
+        for (int a = 0; a <= pt.p[d]; ++a) {
+          tN[d][(size_t)a * q[d] + k] = dd[d].Nv(e3[d], k, a);
+          tdN[d][(size_t)a * q[d] + k] = dd[d].dNv(e3[d], k, a);
+        }
+        for (int a = 0; a < pt.p[d]; ++a) tD[d][(size_t)a * q[d] + k] = dd[d].Dv(e3[d], k, a);
+      }
     Ke.assign((size_t)n * n, 0.0);
-    gram_upper_sparse(Ws.data(), Ut.data(), n, K3, klo, khi, Ke.data());
+    for (int ca = 0; ca < 3; ++ca)
+      for (int i = 0; i < 2; ++i) {
+        const int *fa = curl_tab[ca][i];
+        const Factor1D A = factor(fa[1], fa[2], fa[3]);
+        for (int cb = 0; cb < 3; ++cb)
+          for (int j = 0; j < 2; ++j) {
+            const int *fb = curl_tab[cb][j];
+            sf_block(A, factor(fb[1], fb[2], fb[3]), q, &Gq[(size_t)(fa[0] * 3 + fb[0]) * Q],
+                     curl_sign[ca][i] * curl_sign[cb][j], n, bs[ca], bs[cb], Ke.data(), t1, t2);
+          }
+      }
     if (any_m) {
       Me.assign((size_t)n * n, 0.0);
-      gram_upper_sparse(Vs.data(), Vt.data(), n, K3, mlo, mhi, Me.data());
+      for (int ca = 0; ca < 3; ++ca)
+        for (int cb = 0; cb < 3; ++cb)
+          sf_block(factor(ca == 0 ? TD : TN, ca == 1 ? TD : TN, ca == 2 ? TD : TN),
+                   factor(cb == 0 ? TD : TN, cb == 1 ? TD : TN, cb == 2 ? TD : TN), q,
+                   &Hq[(size_t)(ca * 3 + cb) * Q], 1.0, n, bs[ca], bs[cb], Me.data(), t1, t2);
     }
     // the element's columns of one (component, c, b) group are consecutive DOF ids
     // whose CSR entries are consecutive in every row (a row's columns of one
@@ -618,35 +689,21 @@ void HostSetup::assemble_patch(Patch &pt) const {
     if (el != cur_el) {
       flush();
       cur_el = el;
-      cur_n = nloc;
       cur_lid.assign(lid, lid + nloc);
       qi = 0;
       any_m = false;
-      Ws.assign((size_t)nloc * K3, 0.0);
-      Ut.assign((size_t)K3 * nloc, 0.0);
-      Vs.assign((size_t)nloc * K3, 0.0);
-      Vt.assign((size_t)K3 * nloc, 0.0);
     }
     // the nonlinear law's stiffness is assembled on the device at every Newton iterate
     const double ck = nl_element(s, el) ? 0.0 : nu[el] * w / det;
     const double cm = sig[el] * w * det;
     if (cm != 0.0) any_m = true;
-    double G[3][3], H[3][3];
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c) {
-        G[r][c] = ck * (pr.J[0][r] * pr.J[0][c] + pr.J[1][r] * pr.J[1][c] + pr.J[2][r] * pr.J[2][c]);
-        H[r][c] = cm * (pr.inv[r][0] * pr.inv[c][0] + pr.inv[r][1] * pr.inv[c][1] + pr.inv[r][2] * pr.inv[c][2]);
+        Gq[(size_t)(r * 3 + c) * Q + qi] =
+            ck * (pr.J[0][r] * pr.J[0][c] + pr.J[1][r] * pr.J[1][c] + pr.J[2][r] * pr.J[2][c]);
+        Hq[(size_t)(r * 3 + c) * Q + qi] =
+            cm * (pr.inv[r][0] * pr.inv[c][0] + pr.inv[r][1] * pr.inv[c][1] + pr.inv[r][2] * pr.inv[c][2]);
       }
-    for (int a = 0; a < nloc; ++a) {
-      const double *cv = pr.ch + 3 * a, *wv = pr.wh + 3 * a;
-      for (int r = 0; r < 3; ++r) {
-        const int k = 3 * qi + r;
-        Ws[(size_t)a * K3 + k] = G[r][0] * cv[0] + G[r][1] * cv[1] + G[r][2] * cv[2];
-        Ut[(size_t)k * nloc + a] = cv[r];
-        Vs[(size_t)a * K3 + k] = H[r][0] * wv[0] + H[r][1] * wv[1] + H[r][2] * wv[2];
-        Vt[(size_t)k * nloc + a] = wv[r];
-      }
-    }
     ++qi;
   });
   flush();
